@@ -1,0 +1,208 @@
+"""Pins of the oracle ratio kernels: exact identities (Eqs. 7-8), special cases,
+window closed form (Eq. 9), App. A envelope and tail bounds, truncation."""
+import itertools
+import math
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import workload
+from oracle import bounds, data, mf, ratio, reconstruct
+from workload import Template
+
+
+def _setup(n=1 << 14, k=4):
+    cfg = workload.config(1, n_override=n, k_override=k)
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    ref, nb = cfg.groups[0]
+    z_ref, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    return cfg, ip, x, ref, nb, z_ref
+
+
+def _full_mf(cfg, ip, x, t):
+    z, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, t.m1, t.m2, cfg.pn_order, t.tc, t.phic)
+    return z
+
+
+def test_window_closed_form():
+    f_low, f_high, dl, dh = 40.0, 459.0, 3.0, 53.0
+    f = np.array([f_low - dl, f_low - dl / 2, f_low, 100.0, f_high, f_high + dh / 2, f_high + dh, 0.0, 600.0])
+    w = ratio.window(f, f_low, f_high, dl, dh)
+    assert np.allclose(w, [0.0, 0.5, 1.0, 1.0, 1.0, 0.5, 0.0, 0.0, 0.0], atol=1e-15)
+    # continuity and monotonic tapers
+    g = np.linspace(f_low - dl, f_low, 101)
+    assert np.all(np.diff(ratio.window(g, f_low, f_high, dl, dh)) >= -1e-15)
+    g = np.linspace(f_high, f_high + dh, 101)
+    assert np.all(np.diff(ratio.window(g, f_low, f_high, dl, dh)) <= 1e-15)
+
+
+def test_untruncated_identity_reproduces_full_matched_filter():
+    """Eqs. (7)-(8): with the whole circular kernel, reconstruction equals direct MF."""
+    cfg, ip, x, ref, nb, z_ref = _setup()
+    for t in nb[:3]:
+        K, _ = ratio.kernel_spectrum(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
+        rho = ratio.kernel_full(K, cfg.n)
+        zf = _full_mf(cfg, ip, x, t)
+        # circular convolution by FFT of the full kernel (exact identity check)
+        zh = np.fft.ifft(np.fft.fft(z_ref) * np.fft.fft(rho))
+        assert np.abs(zh - zf).max() / np.abs(zf).max() < 1e-12
+
+
+def test_untruncated_identity_direct_sum_small():
+    cfg, ip, x, ref, nb, z_ref = _setup(n=1 << 11, k=2)
+    t = nb[1]
+    K, _ = ratio.kernel_spectrum(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
+    rho = ratio.kernel_full(K, cfg.n)
+    zh = reconstruct.reconstruct_direct(z_ref, 0, rho)
+    zf = _full_mf(cfg, ip, x, t)
+    assert np.abs(zh - zf).max() / np.abs(zf).max() < 1e-12
+
+
+def test_special_cases_identity_shift_phase():
+    cfg, ip, x, ref, nb, z_ref = _setup()
+    n = cfg.n
+    # same template: z unchanged
+    for tgt, expect in [
+        (ref, z_ref),
+        (replace(ref, tc=37 / cfg.fs), np.roll(z_ref, -37)),        # z^[i] = z_ref[i + 37]
+        (replace(ref, tc=-5 / cfg.fs), np.roll(z_ref, 5)),
+        (replace(ref, phic=0.9), z_ref * np.exp(-0.9j)),
+    ]:
+        K, _ = ratio.kernel_spectrum(ref, tgt, n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, df_low=4.0)
+        rho = ratio.kernel_full(K, n)
+        zh = np.fft.ifft(np.fft.fft(z_ref) * np.fft.fft(rho))
+        assert np.abs(zh - expect).max() / np.abs(z_ref).max() < 1e-12
+
+
+def test_kernel_parseval():
+    cfg, ip, x, ref, nb, z_ref = _setup()
+    K, _ = ratio.kernel_spectrum(ref, nb[0], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
+    rho = ratio.kernel_full(K, cfg.n)
+    assert abs(np.sum(np.abs(rho) ** 2) / (np.sum(np.abs(K) ** 2) / cfg.n) - 1) < 1e-12
+
+
+def _long_pair():
+    """A pair with a long kernel (f_low = 20 Hz, 3.5PN), as in the paper's figures."""
+    n, fs = 1 << 17, 1024.0
+    ref = Template(1.6, 1.5)
+    tgt = Template(1.64, 1.48)
+    return n, fs, 20.0, fs / 2 - 53.0, ref, tgt
+
+
+def test_kernel_envelope_follows_stationary_phase():
+    """Eq. (A11): inside the support |rho[m]| ~ dt / sqrt(|dt'(f*)|) with dt(f*) = -m dt."""
+    n, fs, fl, fh, ref, tgt = _long_pair()
+    ip = np.ones(n // 2 + 1)
+    K, dfl = ratio.kernel_spectrum(ref, tgt, n, fs, fl, fh, 7, ip)
+    rho = ratio.kernel_full(K, n)
+    d_lo = bounds.delta_t(np.array([fl]), ref, tgt, 7)[0]
+    d_hi = bounds.delta_t(np.array([fh]), ref, tgt, 7)[0]
+    lo, hi = sorted([-d_lo, -d_hi])                     # lag-time support [lo, hi]
+    assert hi - lo > 1.0                                  # a long kernel
+    m = np.arange(int(math.ceil((lo + 0.2 * (hi - lo)) * fs)), int((hi - 0.2 * (hi - lo)) * fs))
+    env = bounds.stationary_envelope(m / fs, ref, tgt, 7, fl, fh, 1 / fs)
+    got = np.abs(rho[m % n])
+    ok = np.isfinite(env)
+    # local RMS over 64 lags removes the SPA interference ripple
+    k = 64
+    ratio_ = np.sqrt(np.convolve(got[ok] ** 2, np.ones(k) / k, "valid")) / np.convolve(env[ok], np.ones(k) / k, "valid")
+    assert np.median(ratio_) == pytest.approx(1.0, abs=0.1)
+    # and most energy lies in the stationary support
+    sup = np.arange(int(lo * fs) - 64, int(hi * fs) + 64)
+    assert np.sum(np.abs(rho[sup % n]) ** 2) / np.sum(np.abs(rho) ** 2) > 0.99
+
+
+def test_kernel_tails_below_appendix_bounds_and_window_shortens_them():
+    """Eqs. (A9)-(A10): tails beyond the support decay below the bounds (x2 slack
+    for the one-sided vs 2 Re form); without the window (df = 0) they are longer (Fig. 2)."""
+    n, fs, fl, fh, ref, tgt = _long_pair()
+    ip = np.ones(n // 2 + 1)
+    K, dfl = ratio.kernel_spectrum(ref, tgt, n, fs, fl, fh, 7, ip)
+    rho = ratio.kernel_full(K, n)
+    d_lo = bounds.delta_t(np.array([fl]), ref, tgt, 7)[0]
+    d_hi = bounds.delta_t(np.array([fh]), ref, tgt, 7)[0]
+    # low-frequency end of the support is at lag time -d_lo; go 2..10 / df_low beyond it
+    sgn = np.sign(-d_lo - (-d_hi))
+    t_lo = -d_lo + sgn * np.linspace(2.0 / dfl, 10.0 / dfl, 200)
+    b_lo = bounds.low_tail_bound(t_lo, ref, tgt, 7, fl, dfl, 1 / fs)
+    got_lo = np.abs(rho[np.round(t_lo * fs).astype(int) % n])
+    assert np.all(got_lo <= 2.0 * b_lo + 1e-12)
+    t_hi = -d_hi - sgn * np.linspace(2.0 / 53.0, 10.0 / 53.0, 50)
+    b_hi = bounds.high_tail_bound(t_hi, ref, tgt, 7, fh, 53.0, 1 / fs)
+    got_hi = np.abs(rho[np.round(t_hi * fs).astype(int) % n])
+    assert np.all(got_hi <= 2.0 * b_hi + 1e-12)
+    # the unwindowed kernel has a longer tail at the same lags
+    K0, _ = ratio.kernel_spectrum(ref, tgt, n, fs, fl, fh, 7, ip, df_low=0.0, df_high=0.0)
+    rho0 = ratio.kernel_full(K0, n)
+    got0 = np.abs(rho0[np.round(t_lo * fs).astype(int) % n])
+    assert np.median(got0) > 5 * np.median(got_lo)
+    _, L_win, _ = ratio.truncate(rho, 1e-3)
+    _, L_raw, _ = ratio.truncate(rho0, 1e-3)
+    assert L_raw > L_win
+
+
+def _brute_arc(mask):
+    n = mask.size
+    best = None
+    for L in range(0, n + 1):
+        for m0 in range(n):
+            cover = np.zeros(n, bool)
+            cover[(m0 + np.arange(L)) % n] = True
+            if np.all(cover[mask]):
+                sl = ratio.signed_lag(m0, n)
+                if best is None or L < best[1] or (L == best[1] and sl < ratio.signed_lag(best[0], n)):
+                    best = (m0, L)
+        if best is not None:
+            return best
+    return best
+
+
+def test_minimal_arc_brute_force():
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 3, 5, 8, 9, 16):
+        for _ in range(60):
+            mask = rng.random(n) < rng.uniform(0.05, 0.6)
+            if not mask.any():
+                mask[rng.integers(0, n)] = True
+            assert ratio.minimal_arc(mask) == _brute_arc(mask), (n, mask)
+    # explicit ties: two kept lags diametrically opposite
+    mask = np.zeros(8, bool)
+    mask[[1, 5]] = True
+    assert ratio.minimal_arc(mask) == _brute_arc(mask) == (5, 5)   # start -3 beats start 1
+    mask = np.zeros(8, bool)
+    mask[[0, 4]] = True
+    assert ratio.minimal_arc(mask) == _brute_arc(mask) == (0, 5)   # start 0 beats start +4 (n/2 maps to +n/2)
+
+
+def test_truncation_keeps_threshold_region_and_is_monotone():
+    cfg, ip, x, ref, nb, z_ref = _setup(n=1 << 15, k=2)
+    t = nb[0]
+    K, _ = ratio.kernel_spectrum(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
+    rho = ratio.kernel_full(K, cfg.n)
+    zf = _full_mf(cfg, ip, x, t)
+    errs, Ls = [], []
+    for thr in (1e-2, 1e-3, 1e-4, 1e-5):
+        m0, L, c = ratio.truncate(rho, thr)
+        kept = (m0 + np.arange(L)) % cfg.n
+        outside = np.setdiff1d(np.arange(cfg.n), kept)
+        assert np.all(np.abs(rho[outside]) < thr * np.abs(rho).max())
+        assert np.array_equal(c, rho[kept])
+        zh = reconstruct.reconstruct_direct(z_ref, m0, c)
+        errs.append(np.abs(zh - zf).max() / np.abs(zf).max())
+        Ls.append(L)
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    assert all(a < b for a, b in zip(Ls, Ls[1:]))
+    # Sec. II.D / abstract: O(1e-4)-level agreement once truncated at 1e-3
+    assert errs[1] < 5e-3
+
+
+def test_truncation_degenerate_inputs():
+    assert ratio.truncate(np.zeros(16, complex), 1e-3)[:2] == (0, 0)
+    d = np.zeros(16, complex)
+    d[15] = 2.0
+    m0, L, c = ratio.truncate(d, 1e-3)
+    assert (m0, L) == (-1, 1) and c[0] == 2.0
+    m0, L, c = ratio.truncate(np.ones(16, complex), 1e-3)
+    assert L == 16
