@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Throughput of the ratio-filter hot path on one GB300 (template*samples/s).
+
+One step = the whole online path for one data segment of the paper-shaped FP32
+workload (fs 2048 Hz, f_low 20 Hz, 512 s, n = 2^20, one reference and 256
+TaylorF2 3.5PN neighbours):
+    mf_reference (data FFT, reference matched filter)  ->  z_ref
+    winmax of z_ref                                     ->  reference peaks
+    reconstruct_winmax (all neighbours, fused peaks)    ->  neighbour peaks
+Units per step: (1 + K) * n template-samples.  Kernel building is offline
+(its time is reported as `build_s`, outside the metric).
+
+Also measured in the same run: per-template full-length cuFFT matched
+filtering of every template (the plain method) and the SNR error of our
+peaks against it; the roofline of the dominant kernel; the e2e number through
+the public API with host buffers; the FP64 oracle on the host cores
+(`cpu_baseline`).  `--impl reference` times only the oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "os"])
+    ap.add_argument("--threshold", type=float, default=None)
+    ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--kernels", type=int, default=None, help="neighbours per group (default: the config's)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+# --------------------------------------------------------------------------- data
+
+def make_strain_gpu(rf, cfg, torch, dev):
+    """Noise (seeded draws) plus injections built with the library's own templates."""
+    n, fs = cfg.n, cfg.fs
+    xf = torch.tensor(workload.noise_spectrum(cfg), dtype=torch.complex128, device=dev)
+    ip = torch.tensor(workload.inv_psd(cfg), dtype=torch.float64, device=dev)
+    f = torch.arange(n // 2 + 1, dtype=torch.float64, device=dev) * (fs / n)
+    band = ((f >= cfg.f_low) & (f <= cfg.f_high)).to(torch.float64)
+    rf64 = None
+    for inj in cfg.injections:
+        ref, nb = cfg.groups[inj.group]
+        t = ref if inj.template_index < 0 else nb[inj.template_index]
+        tt = workload.Template(t.m1, t.m2, tc=inj.sample / fs)
+        h = rf.template_fd(tt).to(torch.complex128)
+        sig = torch.sqrt(4.0 * (fs / n) * torch.sum(h.abs() ** 2 * ip * band))
+        xf = xf + (inj.snr / sig) * h * band
+    x = torch.fft.irfft(xf, n) * fs
+    return x.to(rf.rdtype).contiguous(), ip
+
+
+# --------------------------------------------------------------------------- plain method (cuFFT)
+
+def cufft_matched_filter_peaks(x, ip, templates_fd, cfg, torch, chunk=16):
+    """Per-template full-length matched filter with cuFFT (the plain method) -> window peaks."""
+    n, fs, W = cfg.n, cfg.fs, cfg.window
+    nw = -(-n // W)
+    xf = torch.fft.rfft(x.to(torch.float32)) / fs
+    f = torch.arange(n // 2 + 1, device=x.device, dtype=torch.float64) * (fs / n)
+    band = (f >= cfg.f_low) & (f <= cfg.f_high)
+    ipb = torch.where(band, ip, torch.zeros_like(ip))
+    sig = torch.sqrt(4.0 * (fs / n) * torch.sum(templates_fd[0].abs().double() ** 2 * ipb)).item()
+    w = (4.0 * (fs / n) / sig * ipb).to(torch.float32)
+    P = torch.empty((len(templates_fd), nw), dtype=torch.float32, device=x.device)
+    A = torch.empty((len(templates_fd), nw), dtype=torch.int64, device=x.device)
+    spec = torch.zeros((chunk, n), dtype=torch.complex64, device=x.device)
+    for j0 in range(0, len(templates_fd), chunk):
+        hs = templates_fd[j0:j0 + chunk]
+        m = len(hs)
+        spec[:m, : n // 2 + 1] = xf[None, :] * torch.conj(hs) * w[None, :]
+        z = torch.fft.ifft(spec[:m]) * n
+        mag = (z.real ** 2 + z.imag ** 2)
+        pad = nw * W - n
+        if pad:
+            mag = torch.nn.functional.pad(mag, (0, pad), value=-1.0)
+        mw = mag.view(m, nw, W)
+        P[j0:j0 + m], a = mw.max(dim=2)
+        A[j0:j0 + m] = a + torch.arange(nw, device=x.device)[None, :] * W
+    return P, A
+
+
+# --------------------------------------------------------------------------- oracle on the host
+
+def cpu_baseline(cfg, n_nbrs=4, slice_len=1 << 12, budget_s=20.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload:
+    the reference matched filter over the whole segment, then the direct
+    reconstruction of `n_nbrs` neighbours over `slice_len` output samples."""
+    from oracle import data as odata, mf as omf, ratio as oratio, reconstruct as orec
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    x = odata.strain(cfg)
+    t0 = time.perf_counter()
+    z_ref, _ = omf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    t_mf = time.perf_counter() - t0
+    units = cfg.n
+    # kernels of a few neighbours (offline in the method; not timed)
+    sel = list(range(0, len(nb), max(1, len(nb) // n_nbrs)))[:n_nbrs]
+    pk = oratio.build_ratio_kernels(ref, [nb[j] for j in sel], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order,
+                                    ip, cfg.threshold)
+    idx = np.arange(slice_len, dtype=np.int64) * (cfg.n // slice_len)
+    t1 = time.perf_counter()
+    done = 0
+    for j in range(len(sel)):
+        orec.reconstruct_at(z_ref, *pk.kernel(j), idx)
+        done += 1
+        if time.perf_counter() - t1 > budget_s:
+            break
+    t_rec = time.perf_counter() - t1
+    units_rec = done * slice_len
+    # normalise: reference MF costs t_mf per n samples; reconstruction t_rec per units_rec
+    per_unit_mf = t_mf / units
+    per_unit_rec = t_rec / max(units_rec, 1)
+    K = len(nb)
+    total_units = (1 + K) * cfg.n
+    total_time = per_unit_mf * cfg.n + per_unit_rec * K * cfg.n
+    mean_len = float(np.mean(pk.length))
+    return {
+        "value": total_units / total_time,
+        "unit": "template*samples/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"reference MF over n={cfg.n} ({t_mf:.2f}s) + direct reconstruction of {done} neighbours "
+                   f"(mean L={mean_len:.0f}) at {slice_len} output samples ({t_rec:.2f}s); scaled to "
+                   f"(1+{K}) x n; numpy single-threaded on {os.cpu_count()} host cores"),
+    }
+
+
+# --------------------------------------------------------------------------- main
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    cfg = workload.config(args.config)
+    vals = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(cfg, n_nbrs=2, slice_len=1 << 10, budget_s=5.0)
+        if s >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals) if vals else cb["value"]
+    line = {"impl": "reference", "metric": "template*samples/s", "value": v, "unit": "template*samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"cfg{args.config}: {cfg.name}, n={cfg.n}, 1 ref + {len(cfg.groups[0][1])} nbrs",
+                       "parallelism": "host"},
+            "cpu_baseline": {**cb, "value": v},
+            "e2e": {"value": v, "unit": "template*samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2511_12894_gb300 import RatioFilter, build, launch_count
+    build.build()
+
+    cfg = workload.config(args.config, k_override=args.kernels)
+    thr = args.threshold if args.threshold is not None else cfg.threshold
+    ref, nb = cfg.groups[0]
+    K = len(nb)
+    n, W = cfg.n, cfg.window
+    rf = RatioFilter.from_config(cfg)
+    x, ip = make_strain_gpu(rf, cfg, torch, dev)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    kern = rf.build_ratio_kernels(ref, nb, ip, thr)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    L = kern.length.astype(np.float64)
+
+    nw = -(-n // W)
+    z_ref = torch.empty((1, n), dtype=rf.cdtype, device=dev)
+    sig = torch.empty(1, dtype=torch.float64, device=dev)
+    Pn = torch.empty((K, nw), dtype=torch.float32, device=dev)
+    An = torch.empty((K, nw), dtype=torch.int32, device=dev)
+    Pr = torch.empty((1, nw), dtype=torch.float32, device=dev)
+    Ar = torch.empty((1, nw), dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rf.mf_reference(x, ip, [ref], z_out=z_ref, sigma_out=sig)
+        rf.winmax(z_ref, W, max_out=Pr, arg_out=Ar)
+        ev_a.record(stream)
+        rf.reconstruct_winmax(z_ref[0], kern, W, args.algo, max_out=Pn, arg_out=An)
+        ev_b.record(stream)
+
+    ev_a = torch.cuda.Event(enable_timing=True)
+    ev_b = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K steps, L2 flushed between steps (outside the events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    rec_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    lc0 = launch_count()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            starts[s].record(stream)
+            step()
+            ends[s].record(stream)
+            ev_b.synchronize()
+            rec_ms.append(ev_a.elapsed_time(ev_b))
+        torch.cuda.synchronize()
+    lc1 = launch_count()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    units_step = (1 + K) * n
+    value = world * units_step * args.steps / (total_ms / 1e3)
+    launches_per_step = (lc1 - lc0) / args.steps
+
+    # ---------------- e2e through the public API with host buffers
+    x_host = torch.empty(n, dtype=rf.rdtype, pin_memory=True)
+    x_host.copy_(x.cpu())
+    P_host = torch.empty((K + 1, nw), dtype=torch.float32, pin_memory=True)
+    A_host = torch.empty((K + 1, nw), dtype=torch.int32, pin_memory=True)
+    x_dev = torch.empty_like(x)
+    e_ms = []
+    for s in range(args.warmup + max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x_dev.copy_(x_host, non_blocking=True)
+        rf.mf_reference(x_dev, ip, [ref], z_out=z_ref, sigma_out=sig)
+        rf.winmax(z_ref, W, max_out=Pr, arg_out=Ar)
+        rf.reconstruct_winmax(z_ref[0], kern, W, args.algo, max_out=Pn, arg_out=An)
+        P_host[0].copy_(Pr[0], non_blocking=True)
+        A_host[0].copy_(Ar[0], non_blocking=True)
+        P_host[1:].copy_(Pn, non_blocking=True)
+        A_host[1:].copy_(An, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if s >= args.warmup:
+            e_ms.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e_ms)
+    e2e = {"value": world * units_step / (e2e_ms / 1e3), "unit": "template*samples/s",
+           "h2d_bytes_per_step": int(x_host.numel() * x_host.element_size()),
+           "d2h_bytes_per_step": int(P_host.numel() * 4 + A_host.numel() * 4), "ms_per_step": e2e_ms}
+
+    # ---------------- roofline of the dominant kernel (the neighbour reconstruction)
+    rec_avg_ms = statistics.mean(rec_ms)
+    algo_used = args.algo if args.algo != "auto" else "direct"
+    flops = 8.0 * float(L.sum()) * n
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = 2070.0
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (rec_avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": f"reconstruct_winmax ({algo_used}, FP32 CUDA cores)",
+                "peak_note": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "share_of_step": rec_avg_ms / ms_per_step}
+
+    # ---------------- plain method on the same GPU, and the SNR error against it
+    baseline = None
+    err = None
+    if not args.no_baseline:
+        hs = torch.stack([rf.template_fd(t) for t in [ref] + list(nb)]).to(torch.complex64)
+        for _ in range(2):
+            cufft_matched_filter_peaks(x, ip, hs, cfg, torch)
+        torch.cuda.synchronize()
+        b_ms = []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            Pf, Af = cufft_matched_filter_peaks(x, ip, hs, cfg, torch)
+            b1.record(stream)
+            b1.synchronize()
+            b_ms.append(b0.elapsed_time(b1))
+        bm = statistics.median(b_ms)
+        baseline = {"value": units_step / (bm / 1e3), "unit": "template*samples/s", "ms_per_step": bm,
+                    "what": "per-template cuFFT C2C inverse (n) of stored-template products + window max, batched 16"}
+        ours_P = torch.cat([Pr, Pn]).double().sqrt()
+        full_P = Pf.double().sqrt()
+        err = {"peak_snr_max_abs_over_max": ((ours_P - full_P).abs().max() / full_P.max()).item(),
+               "loudest_peak_rel": None}
+        jmax = int(torch.argmax(full_P.max(dim=1).values).item())
+        wmax = int(torch.argmax(full_P[jmax]).item())
+        err["loudest_peak_rel"] = (abs(ours_P[jmax, wmax] - full_P[jmax, wmax]) / full_P[jmax, wmax]).item()
+        err["loudest_snr"] = full_P[jmax, wmax].item()
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(cfg)
+
+    if rank == 0:
+        line = {
+            "metric": "template*samples/s", "value": value, "unit": "template*samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"cfg{args.config}: {cfg.name}; n=2^{int(math.log2(n))} fs={cfg.fs:g} "
+                                   f"f_low={cfg.f_low:g}; 1 ref + {K} TaylorF2 3.5PN nbrs; thr={thr:g} rel; W={W}",
+                       "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
+                                      "sum": int(L.sum())},
+                       "l2": "flushed between steps (256 MB write outside the events)", "algo": args.algo,
+                       "parallelism": f"replicas x{world}"},
+            "build_s": build_s, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "plain_mf_cufft": baseline, "err_vs_full_mf": err,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * rf.h -- C ABI of the ratio-filter library (librf.so), sm_103a.
+ *
+ * The library computes the data-parallel hot path of the ratio filter
+ * (Murakami, Ghosh & Morisaki, "Efficient Reconstruction of Matched-Filter SNR
+ * Time Series from Nearby Templates for CBC Searches"):
+ *
+ *   rf_mf_reference         complex SNR z_ref(t) of reference templates
+ *                           (Sec. II.A, Eqs. 2-4 and 6)
+ *   rf_build_ratio_kernels  truncated ratio kernels of the neighbours of one
+ *                           reference (Sec. II.B-II.D, Eqs. 5, 7, 9, 10)
+ *   rf_reconstruct          neighbour SNR series z = z_ref (*) r (Eq. 8)
+ *   rf_reconstruct_winmax   the same, reduced on the fly to per-window
+ *                           max|z|^2 and its first index (the peak read in Sec. IV)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid.  n samples (a power of two, 2^8..2^24) at fs Hz; dt = 1/fs, T = n dt,
+ *   df = 1/T; one-sided bins f_k = k df, k = 0..n/2.  Fourier sign as in Eq. (1):
+ *   forward transforms use exp(-2 pi i f t).
+ * Data types.  grid.dtype selects the arithmetic of the whole path:
+ *   RF_F64: real data double, complex data interleaved double2 (complex128);
+ *   RF_F32: real data float,  complex data interleaved float2  (complex64).
+ *   Template phases, their differences and all normalisation sums are FP64 in
+ *   both modes.
+ * Memory.  Unless stated otherwise a pointer argument is caller-owned DEVICE
+ *   memory, 16-byte aligned, on the device that was current at rf_create.
+ *   Host arrays are marked "host".  Opaque handles own their memory and are
+ *   released with the matching free/destroy call.
+ * Streams.  rf_stream is a cudaStream_t (NULL: the legacy default stream).
+ *   Calls enqueue work on that stream and return without synchronising,
+ *   except where a call says it synchronises.
+ * Errors.  Every call returns an rf_status; on failure nothing has been
+ *   enqueued and rf_last_error() (per host thread) describes why.  Arguments
+ *   are validated on the host before any launch; no call aborts the process.
+ *   RF_ECUDA reports a CUDA runtime error (message included).
+ * Threads.  One rf_ctx must not be used by two host threads at once.
+ */
+#ifndef RF_H
+#define RF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RF_ABI_VERSION 1
+
+typedef struct rf_ctx rf_ctx;
+typedef struct rf_kernels rf_kernels;
+typedef void* rf_stream;
+
+typedef enum {
+  RF_OK = 0,
+  RF_EINVAL = -1,        /* invalid argument (null, misaligned, out of range, wrong state) */
+  RF_ENOMEM = -2,        /* device or host allocation failed */
+  RF_ECUDA = -3,         /* CUDA runtime error */
+  RF_ETIMEOUT = -4,      /* a bounded device-side wait ran out (status word) */
+  RF_EUNSUPPORTED = -5   /* valid request this build does not implement */
+} rf_status;
+
+typedef enum { RF_F64 = 0, RF_F32 = 1 } rf_dtype;
+
+/* Reconstruction algorithm.  AUTO picks per kernel-length bucket. */
+typedef enum {
+  RF_ALGO_AUTO = 0,
+  RF_ALGO_DIRECT = 1,    /* direct time-domain sum on CUDA cores (Eq. 8) */
+  RF_ALGO_OS = 2         /* overlap-save block FFT (frequency form, Eq. 7) */
+} rf_algo;
+
+/* Arithmetic of the reconstruction.  FP32: CUDA-core FP32 (RF_F32) or FP64 (RF_F64). */
+typedef enum {
+  RF_PREC_NATIVE = 0
+} rf_prec;
+
+/* A non-spinning stationary-phase inspiral (App. A, Eq. A1): h(f) = B(f) exp(-i Psi(f)),
+ * B(f) = f^(-7/6) (unit scale: every SNR is normalised), Psi the TaylorF2 phase with
+ * component masses m1, m2 in solar masses, coalescence time tc (s) and phase phic (rad). */
+typedef struct {
+  double m1, m2, tc, phic;
+} rf_template;
+
+/* The analysis grid and band.  f_high + df_high must not exceed fs/2.  The data band is
+ * [f_low, f_high] (Eq. 4); the kernel window (Eq. 9) tapers over df_low below f_low and
+ * df_high above f_high, with df_low = min(df_low_max, f_low/2, 1/sqrt|d tau'(f_low)|)
+ * (Eq. 10).  pn_order: 0..7 (2 = 1PN, 7 = 3.5PN).  dtype: rf_dtype. */
+typedef struct {
+  int64_t n;
+  double fs, f_low, f_high, df_high, df_low_max;
+  int32_t pn_order;
+  int32_t dtype;
+} rf_grid;
+
+/* ABI version (RF_ABI_VERSION) of the loaded library. */
+int32_t rf_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all threads). */
+uint64_t rf_launch_count(void);
+
+/* Message of the last failing call on this host thread ("" if none). Borrowed. */
+const char* rf_last_error(void);
+
+/* Create a context for one grid on the current device.  Allocates the FFT twiddle
+ * tables and workspaces (about 40 n bytes).  Caller frees with rf_destroy. */
+rf_status rf_create(const rf_grid* grid, rf_ctx** out);
+
+/* Release a context and everything it owns.  Waits for the device.  NULL is a no-op. */
+void rf_destroy(rf_ctx* ctx);
+
+/* Largest workspace the context will use for `k_max` kernels (bytes), and reserve it now
+ * (allocation happens here, never later in an rf_reconstruct* call of at most k_max kernels;
+ * needed before capturing reconstruct calls in a CUDA graph). */
+rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out);
+
+/* Template spectrum h~(f_k) = B(f_k) exp(-i Psi(f_k)), k = 0..n/2, 0 at DC (App. A, Eq. A1).
+ * h_out: complex[n/2+1] (grid dtype).  Phase in FP64.  Async on stream. */
+rf_status rf_template_fd(rf_ctx* ctx, const rf_template* tmpl, void* h_out, rf_stream stream);
+
+/* Reference matched filter (Sec. II.A, Eqs. 2-4, 6).  For each of the nref templates:
+ *   N^2 = 4 df sum_{f_low<=f_k<=f_high} |h~_k|^2 inv_psd[k]             (Eq. 3, FP64)
+ *   z[i] = (4 df / N) sum_{k=0}^{n/2} x~_k conj(h~_k) inv_psd[k] band_k exp(+2 pi i i k / n)
+ * with x~_k = dt sum_j x[j] exp(-2 pi i j k / n) computed once for all references.
+ * x: real[n] (grid dtype); inv_psd: double[n/2+1], 1/S_n(f_k) (values outside the band are
+ * ignored: Eq. 4); refs: host array of nref templates; z_out: complex[nref][n] (grid dtype);
+ * sigma_out: double[nref] (device, N of each reference).  Async on stream. */
+rf_status rf_mf_reference(rf_ctx* ctx, const void* x, const double* inv_psd, int32_t nref,
+                          const rf_template* refs, void* z_out, double* sigma_out, rf_stream stream);
+
+/* Ratio kernels of k neighbours of one reference (Sec. II.B-II.D).  Per neighbour j, in FP64:
+ *   K~_k = (N_ref/N_j) W(f_k) conj(h~_j(f_k) / h~_ref(f_k))   (Eqs. 5, 7 and window Eq. 9)
+ *   rho[m] = (1/n) sum_{k=0}^{n/2} K~_k exp(+2 pi i k m / n),  m = 0..n-1
+ * then truncation: with a = max|rho|^2, the kept lags are those with |rho|^2 >= thr^2 a
+ * (relative != 0) or |rho|^2 >= thr^2 (relative == 0); the kernel is the shortest circular
+ * arc [m0, m0+L) covering them (ties: smallest m0 in (-n/2, n/2]).  Taps c[l] = rho[m0+l]
+ * are stored packed (grid dtype) with int32 signed m0 and length L per neighbour.
+ * refs/nbrs: host; inv_psd: device double[n/2+1].  SYNCHRONISES `stream` (the lengths are
+ * read back).  *out is freed with rf_kernels_free. */
+rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_template* nbrs,
+                                 int32_t k, const double* inv_psd, double threshold,
+                                 int32_t relative, rf_kernels** out, rf_stream stream);
+
+/* Import k kernels computed earlier and kept on disk or in host memory (Sec. II.B keeps the
+ * truncated ratio waveforms between analyses):
+ * lag0/len: host int32[k]; taps: HOST complex (grid dtype), packed back to back, sum(len)
+ * entries.  Synchronous copy. */
+rf_status rf_kernels_import(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len,
+                            const void* taps, rf_kernels** out);
+
+/* Borrowed views of a kernel set: host arrays len[k], lag0[k], offset[k+1] (int64) and
+ * df_low[k] (Hz; NaN for imported kernels), and the device tap buffer (grid dtype).
+ * Any output pointer may be NULL. */
+rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** len,
+                          const int32_t** lag0, const int64_t** offset, const double** df_low,
+                          const void** taps_dev);
+
+/* Copy the packed taps (sum(len) complex entries, grid dtype) into caller device memory
+ * `dst`.  Async on stream. */
+rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream);
+
+/* Release a kernel set.  NULL is a no-op. */
+void rf_kernels_free(rf_kernels* kern);
+
+/* Neighbour SNR series (Eq. 8, circular):  z_j[i] = sum_{l<L_j} c_j[l] z_ref[(i - m0_j - l) mod n].
+ * z_ref: complex[n]; z_out: complex[k][n] (grid dtype).  algo: rf_algo; RF_ALGO_OS needs
+ * grid dtype RF_F32.  Async on stream. */
+rf_status rf_reconstruct(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo,
+                         int32_t prec, void* z_out, rf_stream stream);
+
+/* Fused form: per neighbour j and window w of W samples (the last may be short),
+ *   max_out[j][w] = max_{wW <= i < (w+1)W} |z_j[i]|^2 (float),
+ *   argmax_out[j][w] = the smallest such i (int32, absolute sample index).
+ * The full series is never written to memory.  Async on stream. */
+rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern,
+                                int32_t algo, int32_t prec, int64_t W, float* max_out,
+                                int32_t* argmax_out, rf_stream stream);
+
+/* Window peaks of `count` series already in memory (e.g. z_ref itself): z: complex[count][n];
+ * max_out/argmax_out: [count][ceil(n/W)], same definition as rf_reconstruct_winmax. */
+rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float* max_out,
+                    int32_t* argmax_out, rf_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RF_H */

@@ -1,0 +1,295 @@
+"""Ratio-filter SNR reconstruction on one GB300 (sm_103a).
+
+Thin Python binding of the C ABI in ``include/rf.h`` (``librf.so``): argument
+marshalling only.  Every step of the computation runs in the library's CUDA
+kernels; PyTorch supplies device memory and streams.  There is no CPU
+fallback: importing works without a GPU, but creating a context needs the
+built library and a CUDA device, and fails loudly otherwise.
+
+Names follow the paper (Murakami, Ghosh & Morisaki): ``mf_reference`` (Sec.
+II.A), ``build_ratio_kernels`` (Sec. II.B-II.D), ``reconstruct`` and
+``reconstruct_winmax`` (Eq. 8 and the per-window peak).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Iterable, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librf.so")
+
+RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ETIMEOUT, RF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+RF_F64, RF_F32 = 0, 1
+ALGOS = {"auto": 0, "direct": 1, "os": 2}
+PRECS = {"native": 0}
+
+EXPORTED = (
+    "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
+    "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info",
+    "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_winmax",
+)
+
+
+class RFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rf status {status}: {msg}")
+        self.status = status
+
+
+class rf_template(ctypes.Structure):
+    _fields_ = [("m1", ctypes.c_double), ("m2", ctypes.c_double), ("tc", ctypes.c_double),
+                ("phic", ctypes.c_double)]
+
+
+class rf_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("fs", ctypes.c_double), ("f_low", ctypes.c_double),
+                ("f_high", ctypes.c_double), ("df_high", ctypes.c_double), ("df_low_max", ctypes.c_double),
+                ("pn_order", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load librf.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} not found: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "rf_version": (i32, []),
+        "rf_launch_count": (ctypes.c_uint64, []),
+        "rf_last_error": (ctypes.c_char_p, []),
+        "rf_create": (i32, [P(rf_grid), P(vp)]),
+        "rf_destroy": (None, [vp]),
+        "rf_reserve": (i32, [vp, i32, P(i64)]),
+        "rf_template_fd": (i32, [vp, P(rf_template), vp, vp]),
+        "rf_mf_reference": (i32, [vp, vp, vp, i32, P(rf_template), vp, vp, vp]),
+        "rf_build_ratio_kernels": (i32, [vp, P(rf_template), P(rf_template), i32, vp, dbl, i32, P(vp), vp]),
+        "rf_kernels_import": (i32, [vp, i32, P(i32), P(i32), vp, P(vp)]),
+        "rf_kernels_info": (i32, [vp, P(i32), P(P(i32)), P(P(i32)), P(P(i64)), P(P(dbl)), P(vp)]),
+        "rf_kernels_copy_taps": (i32, [vp, vp, vp]),
+        "rf_kernels_free": (None, [vp]),
+        "rf_reconstruct": (i32, [vp, vp, vp, i32, i32, vp, vp]),
+        "rf_reconstruct_winmax": (i32, [vp, vp, vp, i32, i32, i64, vp, vp, vp]),
+        "rf_winmax": (i32, [vp, vp, i32, i64, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().rf_launch_count())
+
+
+def _check(status: int) -> None:
+    if status != RF_OK:
+        msg = _lib.rf_last_error().decode(errors="replace") if _lib else ""
+        raise RFError(status, msg)
+
+
+def _templates(ts: Sequence) -> ctypes.Array:
+    arr = (rf_template * max(1, len(ts)))()
+    for i, t in enumerate(ts):
+        arr[i] = rf_template(float(t.m1), float(t.m2), float(getattr(t, "tc", 0.0)), float(getattr(t, "phic", 0.0)))
+    return arr
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    """Contiguous, 16-byte-aligned CUDA tensor of the given dtype (copied only if needed)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.data_ptr() % 16:
+        t = t.contiguous().clone()
+    return t
+
+
+@dataclass
+class Kernels:
+    """A set of truncated ratio kernels held by the library (device taps)."""
+    handle: ctypes.c_void_p
+    ctx: "RatioFilter"
+    k: int
+    length: np.ndarray
+    lag0: np.ndarray
+    offset: np.ndarray
+    df_low: np.ndarray
+
+    def taps(self):
+        """Packed taps as a new CUDA tensor (complex, sum(length) entries)."""
+        import torch
+        t = torch.empty(int(self.offset[-1]), dtype=self.ctx.cdtype, device="cuda")
+        if t.numel():
+            _check(_lib.rf_kernels_copy_taps(self.handle, ctypes.c_void_p(t.data_ptr()), _stream()))
+        return t
+
+    def free(self) -> None:
+        if self.handle:
+            _lib.rf_kernels_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class RatioFilter:
+    """One analysis grid on the current CUDA device (owns an ``rf_ctx``)."""
+
+    def __init__(self, n: int, fs: float, f_low: float, f_high: float, pn_order: int, dtype: str = "f32",
+                 df_high: float = 53.0, df_low_max: float = 5.0):
+        import torch
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (there is no CPU fallback)")
+        self.n = int(n)
+        self.fs = float(fs)
+        self.dtype = dtype
+        self.rdtype = torch.float64 if dtype == "f64" else torch.float32
+        self.cdtype = torch.complex128 if dtype == "f64" else torch.complex64
+        g = rf_grid(self.n, self.fs, float(f_low), float(f_high), float(df_high), float(df_low_max), int(pn_order),
+                    RF_F64 if dtype == "f64" else RF_F32)
+        h = ctypes.c_void_p()
+        _check(lib.rf_create(ctypes.byref(g), ctypes.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_config(cls, cfg) -> "RatioFilter":
+        return cls(cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, cfg.dtype, cfg.df_high, cfg.df_low_max)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _lib.rf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def reserve(self, k_max: int) -> int:
+        b = ctypes.c_int64()
+        _check(_lib.rf_reserve(self.handle, int(k_max), ctypes.byref(b)))
+        return b.value
+
+    def template_fd(self, tmpl, out=None, stream=None):
+        import torch
+        out = out if out is not None else torch.empty(self.n // 2 + 1, dtype=self.cdtype, device="cuda")
+        out = _dev(out, self.cdtype, "out")
+        t = _templates([tmpl])
+        _check(_lib.rf_template_fd(self.handle, t, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def mf_reference(self, x, inv_psd, refs: Sequence, z_out=None, sigma_out=None, stream=None):
+        """z_ref[nref, n] (complex) and N[nref] (float64) of each reference (Sec. II.A)."""
+        import torch
+        x = _dev(x, self.rdtype, "x")
+        ip = _dev(inv_psd, torch.float64, "inv_psd")
+        nref = len(refs)
+        z = z_out if z_out is not None else torch.empty((nref, self.n), dtype=self.cdtype, device="cuda")
+        sg = sigma_out if sigma_out is not None else torch.empty(nref, dtype=torch.float64, device="cuda")
+        _check(_lib.rf_mf_reference(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(ip.data_ptr()),
+                                    nref, _templates(refs), ctypes.c_void_p(z.data_ptr()),
+                                    ctypes.c_void_p(sg.data_ptr()), _stream(stream)))
+        return z, sg
+
+    def _wrap_kernels(self, h: ctypes.c_void_p) -> Kernels:
+        k = ctypes.c_int32()
+        ln = ctypes.POINTER(ctypes.c_int32)()
+        lg = ctypes.POINTER(ctypes.c_int32)()
+        of = ctypes.POINTER(ctypes.c_int64)()
+        dl = ctypes.POINTER(ctypes.c_double)()
+        _check(_lib.rf_kernels_info(h, ctypes.byref(k), ctypes.byref(ln), ctypes.byref(lg), ctypes.byref(of),
+                                    ctypes.byref(dl), None))
+        kk = k.value
+        arr = lambda p, m, dt: np.ctypeslib.as_array(p, shape=(m,)).astype(dt).copy() if m else np.zeros(m, dt)
+        return Kernels(h, self, kk, arr(ln, kk, np.int64), arr(lg, kk, np.int64), arr(of, kk + 1, np.int64),
+                       arr(dl, kk, np.float64))
+
+    def build_ratio_kernels(self, ref, nbrs: Sequence, inv_psd, threshold: float = 1e-3, relative: bool = True,
+                            stream=None) -> Kernels:
+        """Truncated ratio kernels of ``nbrs`` against ``ref`` (Sec. II.B-II.D); synchronises."""
+        import torch
+        ip = _dev(inv_psd, torch.float64, "inv_psd")
+        h = ctypes.c_void_p()
+        _check(_lib.rf_build_ratio_kernels(self.handle, _templates([ref]), _templates(nbrs), len(nbrs),
+                                           ctypes.c_void_p(ip.data_ptr()), float(threshold), int(bool(relative)),
+                                           ctypes.byref(h), _stream(stream)))
+        return self._wrap_kernels(h)
+
+    def kernels_import(self, lag0: Iterable[int], length: Iterable[int], taps: np.ndarray) -> Kernels:
+        """Kernels from host arrays (signed first lags, lengths, packed complex taps)."""
+        lag0 = np.ascontiguousarray(lag0, dtype=np.int32)
+        length = np.ascontiguousarray(length, dtype=np.int32)
+        taps = np.ascontiguousarray(taps, dtype=np.complex128 if self.dtype == "f64" else np.complex64)
+        h = ctypes.c_void_p()
+        P32 = ctypes.POINTER(ctypes.c_int32)
+        _check(_lib.rf_kernels_import(self.handle, len(length), lag0.ctypes.data_as(P32), length.ctypes.data_as(P32),
+                                      ctypes.c_void_p(taps.ctypes.data), ctypes.byref(h)))
+        return self._wrap_kernels(h)
+
+    def reconstruct(self, z_ref, kern: Kernels, algo: str = "auto", out=None, stream=None):
+        """Neighbour SNR series [k, n] (Eq. 8)."""
+        import torch
+        z_ref = _dev(z_ref, self.cdtype, "z_ref")
+        out = out if out is not None else torch.empty((kern.k, self.n), dtype=self.cdtype, device="cuda")
+        _check(_lib.rf_reconstruct(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo], 0,
+                                   ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def reconstruct_winmax(self, z_ref, kern: Kernels, W: int, algo: str = "auto", max_out=None, arg_out=None,
+                           stream=None):
+        """Per-window max|z|^2 [k, nw] (float32) and its first index (int32)."""
+        import torch
+        z_ref = _dev(z_ref, self.cdtype, "z_ref")
+        nw = -(-self.n // int(W))
+        mo = max_out if max_out is not None else torch.empty((kern.k, nw), dtype=torch.float32, device="cuda")
+        ao = arg_out if arg_out is not None else torch.empty((kern.k, nw), dtype=torch.int32, device="cuda")
+        _check(_lib.rf_reconstruct_winmax(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo],
+                                          0, int(W), ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()),
+                                          _stream(stream)))
+        return mo, ao
+
+    def winmax(self, z, W: int, max_out=None, arg_out=None, stream=None):
+        """Window peaks of series already in memory, z[count, n]."""
+        import torch
+        z = _dev(z, self.cdtype, "z")
+        z2 = z.reshape(-1, self.n)
+        nw = -(-self.n // int(W))
+        mo = max_out if max_out is not None else torch.empty((z2.shape[0], nw), dtype=torch.float32, device="cuda")
+        ao = arg_out if arg_out is not None else torch.empty((z2.shape[0], nw), dtype=torch.int32, device="cuda")
+        _check(_lib.rf_winmax(self.handle, ctypes.c_void_p(z2.data_ptr()), z2.shape[0], int(W),
+                              ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()), _stream(stream)))
+        return mo, ao
+
+
+__all__ = ["RatioFilter", "Kernels", "RFError", "load_library", "launch_count", "EXPORTED", "LIB_PATH"]

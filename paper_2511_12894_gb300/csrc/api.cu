@@ -1,0 +1,327 @@
+// C ABI entry points: argument validation, dispatch and error reporting.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "rf_internal.h"
+
+namespace rf {
+
+namespace {
+thread_local char g_err[1024] = {0};
+}
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void DevBuf::ensure(size_t b) {
+  if (bytes >= b && p) return;
+  release();
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, b);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    set_error("cudaMalloc(%zu bytes) failed: %s", b, cudaGetErrorString(e));
+    throw Fail{RF_ENOMEM};
+  }
+  p = q;
+  bytes = b;
+}
+
+namespace {
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Device pointer check: non-null, 16-byte aligned, and known to CUDA as device or
+// managed memory (host pointers are rejected rather than faulting in a kernel).
+void check_dev(const void* p, const char* name, bool allow_null = false) {
+  if (!p) {
+    RF_REQUIRE(allow_null, "%s is NULL", name);
+    return;
+  }
+  RF_REQUIRE(((uintptr_t)p & 15u) == 0, "%s is not 16-byte aligned", name);
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    RF_REQUIRE(false, "%s is not a CUDA device pointer", name);
+  }
+  RF_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged,
+             "%s is not device memory (memory type %d)", name, (int)at.type);
+}
+
+void check_host(const void* p, const char* name) { RF_REQUIRE(p != nullptr, "%s is NULL", name); }
+
+void check_template(const rf_template& t, const char* name) {
+  RF_REQUIRE(std::isfinite(t.m1) && std::isfinite(t.m2) && t.m1 > 0 && t.m2 > 0 && t.m1 < 1e4 && t.m2 < 1e4,
+             "%s: component masses must be finite and positive", name);
+  RF_REQUIRE(std::isfinite(t.tc) && std::isfinite(t.phic), "%s: tc and phic must be finite", name);
+}
+
+void check_ctx(const rf_ctx* c) {
+  RF_REQUIRE(c != nullptr, "context is NULL");
+  int dev = -1;
+  RF_CUDA(cudaGetDevice(&dev));
+  RF_REQUIRE(dev == c->device, "context belongs to device %d but device %d is current", c->device, dev);
+}
+
+template <typename F>
+rf_status guard(F&& f) {
+  clear_error();
+  try {
+    f();
+    return RF_OK;
+  } catch (const Fail& e) {
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return RF_ENOMEM;
+  } catch (...) {
+    set_error("unexpected internal error");
+    return RF_EINVAL;
+  }
+}
+
+}  // namespace
+}  // namespace rf
+
+using namespace rf;
+
+extern "C" {
+
+int32_t rf_version(void) { return RF_ABI_VERSION; }
+
+const char* rf_last_error(void) { return g_err; }
+
+uint64_t rf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rf_status rf_create(const rf_grid* grid, rf_ctx** out) {
+  return guard([&] {
+    RF_REQUIRE(grid != nullptr && out != nullptr, "grid and out must be non-NULL");
+    *out = nullptr;
+    const rf_grid g = *grid;
+    RF_REQUIRE(is_pow2(g.n) && g.n >= 256 && g.n <= (int64_t(1) << 24), "n=%lld must be a power of two in [2^8, 2^24]",
+               (long long)g.n);
+    RF_REQUIRE(std::isfinite(g.fs) && g.fs > 0, "fs must be positive");
+    RF_REQUIRE(std::isfinite(g.f_low) && std::isfinite(g.f_high) && g.f_low > 0 && g.f_low < g.f_high,
+               "need 0 < f_low < f_high");
+    RF_REQUIRE(std::isfinite(g.df_high) && g.df_high >= 0 && std::isfinite(g.df_low_max) && g.df_low_max >= 0,
+               "taper widths must be non-negative");
+    RF_REQUIRE(g.f_high + g.df_high <= 0.5 * g.fs * (1 + 1e-12), "f_high + df_high must not exceed fs/2");
+    RF_REQUIRE(g.pn_order >= 0 && g.pn_order <= 7, "pn_order must be 0..7");
+    RF_REQUIRE(g.dtype == RF_F64 || g.dtype == RF_F32, "dtype must be RF_F64 or RF_F32");
+    std::unique_ptr<rf_ctx> c(new rf_ctx());
+    c->g = g;
+    c->n = g.n;
+    RF_CUDA(cudaGetDevice(&c->device));
+    RF_CUDA(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+    const int64_t n = g.n;
+    const std::vector<double2> tw = host_twiddles(n);
+    c->tw64.ensure(sizeof(double2) * n);
+    RF_CUDA(cudaMemcpy(c->tw64.p, tw.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+    std::vector<float2> tw32((size_t)n);
+    for (int64_t m = 0; m < n; ++m) tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
+    c->tw32.ensure(sizeof(float2) * n);
+    RF_CUDA(cudaMemcpy(c->tw32.p, tw32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    // compact block tables: entry B + m = exp(-2 pi i m / B), B = 2..2^14
+    const int64_t bmax = int64_t(1) << 14;
+    std::vector<float2> twb((size_t)(2 * bmax), make_float2(0.f, 0.f));
+    for (int64_t B = 2; B <= bmax; B *= 2) {
+      const std::vector<double2> t = host_twiddles(B);
+      for (int64_t m = 0; m < B; ++m) twb[B + m] = make_float2((float)t[m].x, (float)t[m].y);
+    }
+    c->twb32.ensure(sizeof(float2) * 2 * bmax);
+    RF_CUDA(cudaMemcpy(c->twb32.p, twb.data(), sizeof(float2) * 2 * bmax, cudaMemcpyHostToDevice));
+    const size_t esz = g.dtype == RF_F64 ? sizeof(double2) : sizeof(float2);
+    c->xf.ensure(esz * n);
+    c->fa.ensure(esz * n);
+    c->fb.ensure(esz * n);
+    c->red.ensure(sizeof(double) * 1024);
+    *out = c.release();
+  });
+}
+
+void rf_destroy(rf_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  delete ctx;
+}
+
+rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(k_max >= 0, "k_max must be non-negative");
+    const int64_t n = ctx->n;
+    // packed window keys (8 B per neighbour and 1-sample window at most n/1) are bounded by
+    // the overlap-save block spectra workspace: 2 n complex64 plus k_max * n / 16 keys.
+    const size_t bytes = (size_t)(2 * n) * sizeof(float2) + (size_t)k_max * (size_t)(n / 16 + 1) * 8 + 4096;
+    ctx->scratch.ensure(bytes);
+    ctx->reserved = bytes;
+    if (bytes_out) *bytes_out = (int64_t)bytes;
+  });
+}
+
+rf_status rf_template_fd(rf_ctx* ctx, const rf_template* tmpl, void* h_out, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    check_host(tmpl, "tmpl");
+    check_template(*tmpl, "tmpl");
+    check_dev(h_out, "h_out");
+    template_fd_impl(ctx, *tmpl, h_out, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_mf_reference(rf_ctx* ctx, const void* x, const double* inv_psd, int32_t nref, const rf_template* refs,
+                          void* z_out, double* sigma_out, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(nref >= 1, "nref must be >= 1");
+    check_host(refs, "refs");
+    for (int r = 0; r < nref; ++r) check_template(refs[r], "refs[r]");
+    check_dev(x, "x");
+    check_dev(inv_psd, "inv_psd");
+    check_dev(z_out, "z_out");
+    check_dev(sigma_out, "sigma_out", true);
+    mf_reference_impl(ctx, x, inv_psd, nref, refs, z_out, sigma_out, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_template* nbrs, int32_t k,
+                                 const double* inv_psd, double threshold, int32_t relative, rf_kernels** out,
+                                 rf_stream stream) {
+  return guard([&] {
+    RF_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    check_ctx(ctx);
+    check_host(ref, "ref");
+    check_template(*ref, "ref");
+    RF_REQUIRE(k >= 0, "k must be >= 0");
+    if (k) check_host(nbrs, "nbrs");
+    for (int j = 0; j < k; ++j) check_template(nbrs[j], "nbrs[j]");
+    check_dev(inv_psd, "inv_psd");
+    RF_REQUIRE(std::isfinite(threshold) && threshold >= 0, "threshold must be finite and >= 0");
+    *out = build_impl(ctx, *ref, nbrs, k, inv_psd, threshold, relative, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_kernels_import(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len, const void* taps,
+                            rf_kernels** out) {
+  return guard([&] {
+    RF_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    check_ctx(ctx);
+    RF_REQUIRE(k >= 0, "k must be >= 0");
+    int64_t total = 0;
+    if (k) {
+      check_host(lag0, "lag0");
+      check_host(len, "len");
+      for (int j = 0; j < k; ++j) {
+        RF_REQUIRE(len[j] >= 0 && len[j] <= ctx->n, "len[%d]=%d outside [0, n]", j, len[j]);
+        RF_REQUIRE(lag0[j] > -ctx->n && lag0[j] < ctx->n, "lag0[%d]=%d outside (-n, n)", j, lag0[j]);
+        total += len[j];
+      }
+    }
+    if (total) check_host(taps, "taps");
+    *out = import_impl(ctx, k, lag0, len, taps);
+  });
+}
+
+rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** len, const int32_t** lag0,
+                          const int64_t** offset, const double** df_low, const void** taps_dev) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    if (k) *k = kern->k;
+    if (len) *len = kern->len.data();
+    if (lag0) *lag0 = kern->lag0.data();
+    if (offset) *offset = kern->offset.data();
+    if (df_low) *df_low = kern->df_low.data();
+    if (taps_dev) *taps_dev = kern->taps.p;
+  });
+}
+
+rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    const size_t esz = kern->dtype == RF_F64 ? sizeof(double2) : sizeof(float2);
+    const size_t bytes = (size_t)kern->offset[kern->k] * esz;
+    if (!bytes) return;
+    check_dev(dst, "dst");
+    RF_CUDA(cudaMemcpyAsync(dst, kern->taps.p, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  });
+}
+
+void rf_kernels_free(rf_kernels* kern) {
+  if (!kern) return;
+  cudaDeviceSynchronize();
+  delete kern;
+}
+
+static void check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec) {
+  check_ctx(ctx);
+  RF_REQUIRE(kern != nullptr, "kern is NULL");
+  RF_REQUIRE(kern->n == ctx->n && kern->dtype == ctx->g.dtype, "kernels were made for another grid");
+  check_dev(z_ref, "z_ref");
+  RF_REQUIRE(algo == RF_ALGO_AUTO || algo == RF_ALGO_DIRECT || algo == RF_ALGO_OS, "unknown algo %d", algo);
+  RF_REQUIRE(prec == RF_PREC_NATIVE, "unknown prec %d", prec);
+}
+
+rf_status rf_reconstruct(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec,
+                         void* z_out, rf_stream stream) {
+  return guard([&] {
+    check_recon(ctx, z_ref, kern, algo, prec);
+    if (kern->k) check_dev(z_out, "z_out");
+    if (algo == RF_ALGO_OS) {
+      set_error("overlap-save reconstruction is not available in this build");
+      throw Fail{RF_EUNSUPPORTED};
+    }
+    reconstruct_direct(ctx, z_ref, kern, z_out, 0, nullptr, nullptr, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec,
+                                int64_t W, float* max_out, int32_t* argmax_out, rf_stream stream) {
+  return guard([&] {
+    check_recon(ctx, z_ref, kern, algo, prec);
+    RF_REQUIRE(W >= 1 && W <= ctx->n, "W=%lld must be in [1, n]", (long long)W);
+    if (kern->k) {
+      check_dev(max_out, "max_out");
+      check_dev(argmax_out, "argmax_out");
+    }
+    if (algo == RF_ALGO_OS) {
+      set_error("overlap-save reconstruction is not available in this build");
+      throw Fail{RF_EUNSUPPORTED};
+    }
+    reconstruct_direct(ctx, z_ref, kern, nullptr, W, max_out, argmax_out, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float* max_out, int32_t* argmax_out,
+                    rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(count >= 0, "count must be >= 0");
+    RF_REQUIRE(W >= 1 && W <= ctx->n, "W=%lld must be in [1, n]", (long long)W);
+    if (!count) return;
+    check_dev(z, "z");
+    check_dev(max_out, "max_out");
+    check_dev(argmax_out, "argmax_out");
+    winmax_series(ctx, z, count, W, max_out, argmax_out, (cudaStream_t)stream);
+  });
+}
+
+}  // extern "C"

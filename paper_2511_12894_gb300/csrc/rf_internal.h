@@ -1,0 +1,158 @@
+// Internal declarations shared by the translation units of librf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "rf.h"
+
+namespace rf {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+struct Fail {
+  rf_status st;
+};
+
+#define RF_CUDA(expr)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ::rf::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                      __LINE__);                                                       \
+      throw ::rf::Fail{RF_ECUDA};                                                      \
+    }                                                                                  \
+  } while (0)
+
+#define RF_REQUIRE(cond, ...)        \
+  do {                               \
+    if (!(cond)) {                   \
+      ::rf::set_error(__VA_ARGS__);  \
+      throw ::rf::Fail{RF_EINVAL};   \
+    }                                \
+  } while (0)
+
+// Launch check: catches configuration errors of the launch just made, and counts it.
+void count_launch();
+#define RF_LAUNCHED()                    \
+  do {                                   \
+    RF_CUDA(cudaGetLastError());         \
+    ::rf::count_launch();                \
+  } while (0)
+
+// ---------------------------------------------------------------- device buffers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // Grow to at least `b` bytes (contents are not kept).
+  void ensure(size_t b);
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------- template model
+// TaylorF2 coefficients of one template (App. A, Eq. A1), prepared on the host
+// from the published post-Newtonian series and evaluated on the device in FP64.
+struct Tf2 {
+  double M;        // total mass in seconds
+  double eta;
+  double tc, phic;
+  double pref;     // 3 / (128 eta)
+  double a[8];     // constant parts of alpha_0..alpha_7
+  double a5log;    // coefficient of ln(v / v_lso) (v^0 term)
+  double a6log;    // coefficient of v ln(4 v)
+};
+Tf2 make_tf2(const rf_template& t, int pn_order);
+
+}  // namespace rf
+
+// ---------------------------------------------------------------- opaque handles
+struct rf_ctx {
+  rf_grid g{};
+  int device = 0;
+  int64_t n = 0;
+  int nsm = 0;
+  // Twiddle tables w[m] = exp(-2 pi i m / n), m < n: FP64 and FP32 copies.
+  rf::DevBuf tw64, tw32;
+  // Compact tables for the block FFTs: for B = 2^b (b = 1..14), B entries of
+  // exp(-2 pi i m / B) stored at offset B (float2).
+  rf::DevBuf twb32;
+  // Workspaces (grid dtype complex unless stated).
+  rf::DevBuf xf;       // data spectrum, complex[n]
+  rf::DevBuf fa, fb;   // FFT ping-pong, complex[n]
+  rf::DevBuf red;      // FP64 reduction scratch
+  rf::DevBuf scratch;  // growable: packed window keys, OS block spectra, builder chunks
+  rf::DevBuf scratch2;
+  size_t reserved = 0;
+  int64_t max_chunk = 0;  // builder templates per chunk
+};
+
+struct rf_kernels {
+  int32_t k = 0;
+  int64_t n = 0;
+  int32_t dtype = 0;
+  std::vector<int32_t> len, lag0;
+  std::vector<int64_t> offset;
+  std::vector<double> df_low;
+  int32_t max_len = 0;
+  rf::DevBuf taps;             // packed taps (grid dtype complex)
+  rf::DevBuf len_d, lag0_d;    // int32[k]
+  rf::DevBuf off_d;            // int64[k+1]
+  // Overlap-save preparation (FP32 only): per kernel block size and partitions.
+  bool os_ready = false;
+  std::vector<int32_t> os_logb;     // log2 B per kernel
+  std::vector<int32_t> os_parts;    // partitions P per kernel
+  std::vector<int64_t> os_spec_off; // offset (in complex elements) of the kernel's spectra
+  rf::DevBuf os_spec;               // float2: per kernel P * B spectra (scaled by 1/B)
+};
+
+namespace rf {
+
+// ---------------------------------------------------------------- FFT (fft.cu)
+// Batched out-of-place Stockham FFT of length n (power of two) over `batch`
+// contiguous rows.  sign -1: forward, +1: inverse (unnormalised).  Uses `tmp`
+// (same size as in/out) as the ping-pong buffer.  in, out, tmp must be distinct.
+void fft_c2c_f64(const double2* in, double2* out, double2* tmp, int64_t n, int batch, int sign,
+                 const double2* tw_table, int64_t table_n, cudaStream_t s);
+void fft_c2c_f32(const float2* in, float2* out, float2* tmp, int64_t n, int batch, int sign,
+                 const float2* tw_table, int64_t table_n, cudaStream_t s);
+void real_to_complex_f64(const double* x, double2* out, int64_t n, cudaStream_t s);
+void real_to_complex_f32(const float* x, float2* out, int64_t n, cudaStream_t s);
+// Host-side FP64 twiddle table exp(-2 pi i m / n), m < n (octant symmetric, accurate).
+std::vector<double2> host_twiddles(int64_t n);
+
+// ---------------------------------------------------------------- MF (mf.cu)
+void mf_reference_impl(rf_ctx* c, const void* x, const double* inv_psd, int32_t nref,
+                       const rf_template* refs, void* z_out, double* sigma_out, cudaStream_t s);
+void template_fd_impl(rf_ctx* c, const rf_template& t, void* h_out, cudaStream_t s);
+// sigma^2 = 4 df sum_band B(f)^2 inv_psd for `count` templates -> out[count] (device, FP64)
+void sigma2_impl(rf_ctx* c, const double* inv_psd, int count, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- builder (builder.cu)
+rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbrs, int32_t k,
+                       const double* inv_psd, double thr, int relative, cudaStream_t s);
+rf_kernels* import_impl(rf_ctx* c, int32_t k, const int32_t* lag0, const int32_t* len,
+                        const void* taps);
+
+// ---------------------------------------------------------------- reconstruct
+void reconstruct_direct(rf_ctx* c, const void* z_ref, const rf_kernels* kern, void* z_out,
+                        int64_t W, float* max_out, int32_t* argmax_out, cudaStream_t s);
+void winmax_series(rf_ctx* c, const void* z, int32_t count, int64_t W, float* max_out,
+                   int32_t* argmax_out, cudaStream_t s);
+
+}  // namespace rf

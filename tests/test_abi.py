@@ -1,0 +1,59 @@
+"""Host-only checks of the C ABI: the library builds/loads and exports every
+declared entry point; argument validation that runs before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_12894_gb300 import build, load_library
+    build.build()
+    return load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(rf_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    import paper_2511_12894_gb300 as p
+    assert sorted(p.EXPORTED) == names
+
+
+def test_version_and_error_string(lib):
+    assert lib.rf_version() == 1
+    assert isinstance(lib.rf_last_error(), bytes)
+
+
+@pytest.mark.parametrize("field,value", [("n", 1000), ("n", 128), ("fs", -1.0), ("f_low", 0.0),
+                                         ("f_high", 600.0), ("pn_order", 9), ("dtype", 7), ("df_high", -1.0)])
+def test_create_rejects_bad_grid_without_touching_the_gpu(lib, field, value):
+    from paper_2511_12894_gb300 import RF_EINVAL, rf_grid
+    g = rf_grid(1 << 12, 1024.0, 40.0, 459.0, 53.0, 5.0, 2, 0)
+    setattr(g, field, value)
+    h = ctypes.c_void_p()
+    st = lib.rf_create(ctypes.byref(g), ctypes.byref(h))
+    assert st == RF_EINVAL
+    assert h.value is None
+    assert len(lib.rf_last_error()) > 0
+
+
+def test_null_arguments_are_rejected(lib):
+    from paper_2511_12894_gb300 import RF_EINVAL
+    assert lib.rf_create(None, None) == RF_EINVAL
+    assert lib.rf_kernels_info(None, None, None, None, None, None, None) == RF_EINVAL
+    assert lib.rf_kernels_copy_taps(None, None, None) == RF_EINVAL
+    lib.rf_destroy(None)
+    lib.rf_kernels_free(None)

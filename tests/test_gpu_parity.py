@@ -1,0 +1,267 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: RF_F64 paths agree to 1e-12 of max|z| (FP64 rounding over a few
+thousand operations); RF_F32 paths to 2e-6 of max|z| (the FP32-equivalent bar);
+integer outputs (lags, lengths, argmax) exactly, argmax only where the oracle's
+top two samples of a window differ by more than the error bound (several
+indices are then correct).
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import workload
+from oracle import data, mf, ratio, reconstruct, taylorf2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_12894_gb300 import build
+    build.build()
+    return t
+
+
+def _rf(cfg):
+    from paper_2511_12894_gb300 import RatioFilter
+    return RatioFilter.from_config(cfg)
+
+
+def _small_f32_cfg(n=1 << 15, k=6):
+    # the FP32 paper-shaped workload (fs 2048 Hz, f_low 20 Hz, 3.5PN) on a shorter segment
+    return workload.config(2, n_override=n, k_override=k)
+
+
+def _relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _argmax_ok(P_oracle_series, A_gpu, A_oracle, W, bound):
+    """Argmax must match where the window's top two |z|^2 differ by more than `bound`."""
+    mag2 = P_oracle_series
+    n = mag2.shape[0]
+    checked = 0
+    for w in range(A_oracle.shape[0]):
+        seg = np.sort(mag2[w * W: min(n, (w + 1) * W)])
+        if seg.size < 2 or seg[-1] - seg[-2] > bound:
+            assert A_gpu[w] == A_oracle[w], (w, A_gpu[w], A_oracle[w])
+            checked += 1
+        else:
+            assert mag2[A_gpu[w]] >= seg[-1] - bound and w * W <= A_gpu[w] < (w + 1) * W
+    return checked
+
+
+# ---------------------------------------------------------------- template and matched filter
+
+@pytest.mark.parametrize("pn,dtype", [(2, "f64"), (7, "f64"), (7, "f32")])
+def test_template_fd(torch, pn, dtype):
+    n, fs = 1 << 14, 1024.0
+    from paper_2511_12894_gb300 import RatioFilter
+    rf = RatioFilter(n, fs, 30.0, fs / 2 - 53, pn, dtype)
+    t = workload.Template(1.7, 1.3, tc=0.25, phic=0.4)
+    h = rf.template_fd(t).cpu().numpy()
+    ho = mf.template(n, fs, t.m1, t.m2, pn, t.tc, t.phic)
+    # an FP64 phase Psi carries an absolute rounding error of a few ulp(|Psi|), and
+    # |Psi| reaches 1e9 rad at the lowest bins: the bound is per bin
+    f = mf.freqs(n, fs)[1:]
+    psi = np.abs(taylorf2.phase(f, t.m1, t.m2, pn, t.tc, t.phic))
+    err = np.abs(h[1:] - ho[1:]) / np.abs(ho[1:])
+    eps = 2.0 ** -52 if dtype == "f64" else 2.0 ** -23
+    assert np.all(err <= 32 * 2.0 ** -52 * psi + 8 * eps)
+    assert h[0] == 0
+
+
+@pytest.mark.parametrize("n", [1 << 8, 1 << 11, 1 << 12, 1 << 13, 1 << 16])
+def test_mf_reference_f64(torch, n):
+    cfg = workload.config(1, n_override=n, k_override=2)
+    ref = cfg.groups[0][0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    z, sg = rf.mf_reference(torch.tensor(x, device="cuda"), torch.tensor(ip, device="cuda"), [ref, cfg.groups[0][1][0]])
+    zo, No = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    assert _relerr(z[0].cpu().numpy(), zo) < TOL["f64"]
+    assert abs(sg[0].item() / No - 1) < 1e-13
+    t = cfg.groups[0][1][0]
+    zo1, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, t.m1, t.m2, cfg.pn_order)
+    assert _relerr(z[1].cpu().numpy(), zo1) < TOL["f64"]
+
+
+@pytest.mark.parametrize("n", [1 << 12, 1 << 15, 1 << 17])
+def test_mf_reference_f32(torch, n):
+    cfg = _small_f32_cfg(n, 2)
+    ref = cfg.groups[0][0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    z, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), torch.tensor(ip, device="cuda"), [ref])
+    zo, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    assert _relerr(z[0].cpu().numpy(), zo) < TOL["f32"]
+
+
+def test_zero_noise_injection_optimal_snr(torch):
+    cfg = workload.config(1, n_override=1 << 14, k_override=3)
+    inj = workload.Injection(-1, 0, 5000, 10.0)
+    cfg = replace(cfg, injections=(inj,))
+    x = data.strain(cfg, noise=False)
+    ip = workload.inv_psd(cfg)
+    rf = _rf(cfg)
+    ref = cfg.groups[0][0]
+    z, _ = rf.mf_reference(torch.tensor(x, device="cuda"), torch.tensor(ip, device="cuda"), [ref])
+    a = np.abs(z[0].cpu().numpy())
+    assert int(np.argmax(a)) == 5000 and abs(a[5000] - 10.0) < 1e-10
+
+
+# ---------------------------------------------------------------- builder
+
+@pytest.mark.parametrize("n,k,thr,rel", [(1 << 13, 5, 1e-3, True), (1 << 16, 16, 1e-3, True),
+                                         (1 << 14, 4, 1e-5, True), (1 << 13, 3, 1e-4, False)])
+def test_build_ratio_kernels_f64(torch, n, k, thr, rel):
+    cfg = workload.config(1, n_override=n, k_override=k)
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    rf = _rf(cfg)
+    kern = rf.build_ratio_kernels(ref, nb, torch.tensor(ip, device="cuda"), thr, rel)
+    pk = ratio.build_ratio_kernels(ref, nb, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, thr, rel)
+    assert np.array_equal(kern.lag0, pk.lag0)
+    assert np.array_equal(kern.length, pk.length)
+    assert np.array_equal(kern.offset, pk.offset)
+    assert np.allclose(kern.df_low, pk.df_low, rtol=1e-12, atol=0)
+    taps = kern.taps().cpu().numpy()
+    assert _relerr(taps, pk.taps) < TOL["f64"]
+
+
+def test_build_ratio_kernels_f32_long(torch):
+    cfg = _small_f32_cfg(1 << 17, 6)
+    ref = cfg.groups[0][0]
+    nb = workload.duration_lattice(ref, cfg.f_low, 8, 0.3, 2.0, np.random.default_rng(3), n_eta=1)
+    cfg = replace(cfg, groups=((ref, nb),))
+    ip = workload.inv_psd(cfg)
+    rf = _rf(cfg)
+    kern = rf.build_ratio_kernels(ref, nb, torch.tensor(ip, device="cuda"), 1e-3)
+    pk = ratio.build_ratio_kernels(ref, nb, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 1e-3)
+    assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
+    taps = kern.taps().cpu().numpy()
+    assert _relerr(taps, pk.taps.astype(np.complex64)) < 1e-6
+    assert pk.length.max() > 1000
+
+
+def test_build_special_cases(torch):
+    """Same template, a whole-sample time shift and a phase offset: the shifted
+    template's kernel is the reference kernel moved by the shift."""
+    cfg = workload.config(1, n_override=1 << 13, k_override=1)
+    ref = cfg.groups[0][0]
+    ip = workload.inv_psd(cfg)
+    rf = _rf(cfg)
+    tg = [ref, replace(ref, tc=37 / cfg.fs), replace(ref, phic=0.9)]
+    kern = rf.build_ratio_kernels(ref, tg, torch.tensor(ip, device="cuda"), 1e-3)
+    pk = ratio.build_ratio_kernels(ref, tg, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 1e-3)
+    assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
+    # the shifted template's kernel is the same kernel moved by -37 lags
+    assert kern.lag0[1] == kern.lag0[0] - 37 and kern.length[1] == kern.length[0]
+
+
+# ---------------------------------------------------------------- reconstruction
+
+def _random_kernels(rng, n, lengths, lags, dtype):
+    taps = []
+    for L in lengths:
+        c = (rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(max(L, 1))
+        taps.append(c)
+    t = np.concatenate(taps) if taps else np.zeros(0, complex)
+    if dtype == "f32":
+        t = t.astype(np.complex64).astype(np.complex128)
+    return t
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_reconstruct_direct_edge_lengths(torch, dtype):
+    """L in {0,1,2,31,32,33,255,256,257,n}, lags of both signs and wrapping, k uneven."""
+    n = 1 << 12
+    rng = np.random.default_rng(4)
+    lengths = [0, 1, 2, 31, 32, 33, 255, 256, 257, 1000, n, 7, 600, 513, 64, 65, 3]
+    lags = [0, 5, -3, n // 2, -(n // 2) + 1, 100, -1, 0, 37, -700, 0, n // 2 - 3, -5, 1999, -2048 + 1, 11, -n // 4]
+    cfgd = workload.config(1, n_override=n, k_override=1)
+    if dtype == "f32":
+        cfgd = replace(cfgd, dtype="f32")
+    rf = _rf(cfgd)
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    if dtype == "f32":
+        z = z.astype(np.complex64).astype(np.complex128)
+    taps = _random_kernels(rng, n, lengths, lags, dtype)
+    # FP32 sums of L random unit-variance terms: rounding grows like sqrt(L) (two-level
+    # summation in chunks of 256 taps); the FP32-equivalent bar 2e-6 holds up to ~1000 taps
+    tol = lambda L: TOL[dtype] * (max(1.0, np.sqrt(L / 1024.0)) if dtype == "f32" else 1.0)
+    kern = rf.kernels_import(lags, lengths, taps)
+    zt = torch.tensor(z.astype(np.complex128 if dtype == "f64" else np.complex64), device="cuda")
+    out = rf.reconstruct(zt, kern, "direct").cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    for j in range(len(lengths)):
+        zo = reconstruct.reconstruct_direct(z, lags[j], taps[off[j]:off[j + 1]])
+        scale = max(np.abs(zo).max(), 1e-30)
+        err = np.abs(out[j] - zo).max() / scale if lengths[j] else np.abs(out[j]).max()
+        assert err < (tol(lengths[j]) if lengths[j] else 1e-30), (j, lengths[j], err)
+    # fused window peaks against the oracle's peaks of the same series
+    for W in (1, 3, 1000, 1024, 4096):
+        P, A = rf.reconstruct_winmax(zt, kern, W, "direct")
+        P, A = P.cpu().numpy(), A.cpu().numpy()
+        for j in range(len(lengths)):
+            zo = reconstruct.reconstruct_direct(z, lags[j], taps[off[j]:off[j + 1]])
+            Po, Ao = reconstruct.window_peaks(zo, W)
+            scale = max(Po.max(), 1e-30)
+            # peaks are stored as float32: add its rounding
+            bound = (4 * tol(lengths[j]) + 2.0 ** -23) * scale + 1e-30
+            assert np.abs(P[j] - Po).max() <= bound
+            mag2 = zo.real ** 2 + zo.imag ** 2
+            _argmax_ok(mag2, A[j], Ao, W, 8 * tol(lengths[j]) * scale)
+
+
+def test_reconstruct_matches_oracle_cfg1_full(torch):
+    """The FP64 small workload end to end at its full size (n = 65536, 16 neighbours)."""
+    cfg = workload.config(1)
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    ipt = torch.tensor(ip, device="cuda")
+    z, _ = rf.mf_reference(torch.tensor(x, device="cuda"), ipt, [ref])
+    kern = rf.build_ratio_kernels(ref, nb, ipt, cfg.threshold)
+    out = rf.reconstruct(z[0], kern, "direct").cpu().numpy()
+    P, A = rf.reconstruct_winmax(z[0], kern, cfg.window, "direct")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    zo, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    pk = ratio.build_ratio_kernels(ref, nb, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, cfg.threshold)
+    assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
+    for j in range(len(nb)):
+        zh = reconstruct.reconstruct_direct(zo, *pk.kernel(j))
+        assert _relerr(out[j], zh) < TOL["f64"]
+        Po, Ao = reconstruct.window_peaks(zh, cfg.window)
+        assert np.abs(P[j] - Po).max() <= 1e-6 * Po.max()     # peaks are stored as float32
+        _argmax_ok(zh.real ** 2 + zh.imag ** 2, A[j], Ao, cfg.window, 1e-9 * Po.max())
+    # the injected neighbour is found at its arrival sample
+    inj = cfg.injections[0]
+    w = inj.sample // cfg.window
+    assert A[inj.template_index, w] == inj.sample
+
+
+def test_winmax_series(torch):
+    cfg = workload.config(1, n_override=1 << 14, k_override=1)
+    rf = _rf(replace(cfg, dtype="f32"))
+    rng = np.random.default_rng(9)
+    z = (rng.standard_normal((3, cfg.n)) + 1j * rng.standard_normal((3, cfg.n))).astype(np.complex64)
+    z[1, 100:110] = 5.0  # ties inside one window
+    P, A = rf.winmax(torch.tensor(z, device="cuda"), 1000)
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    for r in range(3):
+        zz = z[r].astype(np.complex128)
+        Po, Ao = reconstruct.window_peaks(z[r], 1000)
+        assert np.abs(P[r] - Po).max() <= 1e-6 * Po.max()
+        _argmax_ok(np.abs(zz) ** 2, A[r], Ao, 1000, 1e-5 * Po.max())
+    assert A[1, 0] == 100
