@@ -180,6 +180,36 @@ rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels
 rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float* max_out,
                     int32_t* argmax_out, rf_stream stream);
 
+/* Reference matched filter without any device allocation.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot call
+ * cudaMalloc: for example a plug-in whose host application owns all device memory
+ * through its own pool, or a low-latency loop that must not pay for (or synchronise
+ * the device on) an allocation.  Such a caller cannot create an rf_ctx, because
+ * rf_create allocates the FFT tables and workspaces.
+ *
+ * It computes what rf_mf_reference computes for one reference template (same
+ * arguments, nref = 1, grid passed by value instead of a context) and allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.  Its
+ * workspace is a static device array of about 4 MiB compiled into librf.so, which
+ * every GPU that loads the library keeps until the process exits.  That bounds the
+ * segment: grid->n must be a power of two in [2^8, 2^16]; larger n returns RF_EINVAL
+ * with a message and launches nothing.
+ *
+ * The first call made with a given device current looks up the workspace's device
+ * address (cudaGetSymbolAddress) and remembers it; make that first call before any
+ * stream capture on that device.  All calls share the one workspace and it keeps the
+ * last call's contents; every call rewrites each part it reads, so results never
+ * depend on an earlier call.  Calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race on the workspace and corrupt each other:
+ * serialise them, e.g. on one stream.
+ *
+ * x, inv_psd, z_out (complex[n]) and sigma_out (double[1], may be NULL) are caller
+ * device memory, 16-byte aligned; ref is host memory.  Async on stream. */
+rf_status rf_mf_reference_noalloc(const rf_grid* grid, const void* x, const double* inv_psd,
+                                  const rf_template* ref, void* z_out, double* sigma_out,
+                                  rf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

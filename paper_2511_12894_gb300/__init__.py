@@ -31,6 +31,7 @@ EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_winmax",
+    "rf_mf_reference_noalloc",
 )
 
 
@@ -82,6 +83,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_reconstruct": (i32, [vp, vp, vp, i32, i32, vp, vp]),
         "rf_reconstruct_winmax": (i32, [vp, vp, vp, i32, i32, i64, vp, vp, vp]),
         "rf_winmax": (i32, [vp, vp, i32, i64, vp, vp, vp]),
+        "rf_mf_reference_noalloc": (i32, [P(rf_grid), vp, vp, P(rf_template), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -292,4 +294,25 @@ class RatioFilter:
         return mo, ao
 
 
-__all__ = ["RatioFilter", "Kernels", "RFError", "load_library", "launch_count", "EXPORTED", "LIB_PATH"]
+def mf_reference_noalloc(grid: rf_grid, x, inv_psd, ref, z_out, sigma_out=None, stream=None) -> None:
+    """The reference matched filter for callers that cannot allocate device memory.
+
+    Wraps ``rf_mf_reference_noalloc``: the library allocates nothing and uses a static
+    device workspace (n <= 2^16).  All buffers are the caller's CUDA tensors; calls that
+    overlap on the GPU race on the shared workspace.
+    """
+    import torch
+    lib = load_library()
+    cd = torch.complex128 if grid.dtype == RF_F64 else torch.complex64
+    rd = torch.float64 if grid.dtype == RF_F64 else torch.float32
+    x = _dev(x, rd, "x")
+    ip = _dev(inv_psd, torch.float64, "inv_psd")
+    if z_out.dtype != cd or not z_out.is_cuda or not z_out.is_contiguous():
+        raise TypeError("z_out must be a contiguous CUDA tensor of the grid's complex dtype")
+    sp = ctypes.c_void_p(sigma_out.data_ptr()) if sigma_out is not None else None
+    _check(lib.rf_mf_reference_noalloc(ctypes.byref(grid), ctypes.c_void_p(x.data_ptr()),
+                                       ctypes.c_void_p(ip.data_ptr()), _templates([ref]),
+                                       ctypes.c_void_p(z_out.data_ptr()), sp, _stream(stream)))
+
+
+__all__ = ["mf_reference_noalloc", "rf_grid", "RatioFilter", "Kernels", "RFError", "load_library", "launch_count", "EXPORTED", "LIB_PATH"]

@@ -1,5 +1,6 @@
 // Reference matched filter (Sec. II.A, Eqs. 2-4 and 6) and template spectra.
 #include <cmath>
+#include <mutex>
 
 #include "cplx.cuh"
 #include "rf_internal.h"
@@ -200,4 +201,157 @@ void template_fd_impl(rf_ctx* c, const rf_template& t, void* h_out, cudaStream_t
   RF_LAUNCHED();
 }
 
+// ---------------------------------------------------------------- allocation-free variant
+// rf_mf_reference_noalloc: the reference matched filter for callers that may not
+// allocate device memory.  Its workspace is the file-scope array below (about
+// 4 MiB, reserved in every GPU that loads the library, until the process exits).
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 16;
+constexpr size_t kNoAllocSlot = (size_t)kNoAllocMaxN * sizeof(double2);  // one complex128 row of kNoAllocMaxN
+constexpr size_t kNoAllocRed = 8192;                                      // FP64 partial sums + sigma^2
+constexpr size_t kNoAllocBytes = 4 * kNoAllocSlot + kNoAllocRed;
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// exp(-2 pi i m / n), m < n, into the workspace (rebuilt on every call).
+template <typename V>
+__global__ void __launch_bounds__(256) k_noalloc_twiddles(V* __restrict__ tw, int64_t n) {
+  using R = typename real_of<V>::type;
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double s, c;
+  sincospi(2.0 * (double)m / (double)n, &s, &c);
+  tw[m] = cmake<V>((R)c, (R)(-s));
+}
+
+}  // namespace
+
 }  // namespace rf
+
+// The workspace.  Host code must not use this name as an address: it is a host-side
+// stand-in.  The device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char rf_noalloc_scratch[rf::kNoAllocBytes];
+
+namespace rf {
+namespace {
+
+// Device address of rf_noalloc_scratch on the current device, looked up on the first
+// call made with that device current and remembered.
+unsigned char* noalloc_scratch_address() {
+  int dev = -1;
+  RF_CUDA(cudaGetDevice(&dev));
+  RF_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, "device ordinal %d is beyond %d", dev, kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, rf_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();
+      set_error("cudaGetSymbolAddress of the static workspace failed on device %d: %s", dev,
+                cudaGetErrorString(e));
+      throw Fail{RF_ECUDA};
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  return static_cast<unsigned char*>(g_noalloc_addr[dev]);
+}
+
+void noalloc_check_dev(const void* p, const char* name, bool allow_null) {
+  if (!p) {
+    RF_REQUIRE(allow_null, "%s is NULL", name);
+    return;
+  }
+  RF_REQUIRE(((uintptr_t)p & 15u) == 0, "%s is not 16-byte aligned", name);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    RF_REQUIRE(false, "%s is not a CUDA device pointer", name);
+  }
+  RF_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged, "%s is not device memory", name);
+}
+
+void mf_reference_noalloc_impl(const rf_grid& g, const void* x, const double* inv_psd, const rf_template& ref,
+                               void* z_out, double* sigma_out, cudaStream_t s) {
+  RF_REQUIRE(g.n >= 256 && (g.n & (g.n - 1)) == 0, "n=%lld must be a power of two >= 256", (long long)g.n);
+  RF_REQUIRE(g.n <= kNoAllocMaxN, "n=%lld exceeds the static workspace limit n <= %lld of rf_mf_reference_noalloc",
+             (long long)g.n, (long long)kNoAllocMaxN);
+  RF_REQUIRE(std::isfinite(g.fs) && g.fs > 0, "fs must be positive");
+  RF_REQUIRE(std::isfinite(g.f_low) && std::isfinite(g.f_high) && g.f_low > 0 && g.f_low < g.f_high,
+             "need 0 < f_low < f_high");
+  RF_REQUIRE(g.f_high + g.df_high <= 0.5 * g.fs * (1 + 1e-12) && g.df_high >= 0,
+             "f_high + df_high must not exceed fs/2");
+  RF_REQUIRE(g.pn_order >= 0 && g.pn_order <= 7, "pn_order must be 0..7");
+  RF_REQUIRE(g.dtype == RF_F64 || g.dtype == RF_F32, "dtype must be RF_F64 or RF_F32");
+  RF_REQUIRE(std::isfinite(ref.m1) && std::isfinite(ref.m2) && ref.m1 > 0 && ref.m2 > 0 && std::isfinite(ref.tc) &&
+                 std::isfinite(ref.phic),
+             "ref: masses must be positive and all fields finite");
+  noalloc_check_dev(x, "x", false);
+  noalloc_check_dev(inv_psd, "inv_psd", false);
+  noalloc_check_dev(z_out, "z_out", false);
+  noalloc_check_dev(sigma_out, "sigma_out", true);
+
+  unsigned char* ws = noalloc_scratch_address();
+  const int64_t n = g.n;
+  const double df = g.fs / (double)n;
+  void* tw = ws;
+  void* xf = ws + kNoAllocSlot;
+  void* fa = ws + 2 * kNoAllocSlot;
+  void* fb = ws + 3 * kNoAllocSlot;
+  double* part = reinterpret_cast<double*>(ws + 4 * kNoAllocSlot);
+  double* sig2 = part + kRedBlocks;
+  static_assert((kRedBlocks + 1) * sizeof(double) <= kNoAllocRed, "reduction slots");
+  // Every region is fully rewritten below before it is read (twiddles, spectra, partial
+  // sums), so nothing left by an earlier call leaks into this one.
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  k_sigma2_partial<<<kRedBlocks, kRedThreads, 0, s>>>(inv_psd, n / 2 + 1, df, g.f_low, g.f_high, part);
+  RF_LAUNCHED();
+  k_sum_partials<<<1, kRedThreads, 0, s>>>(part, kRedBlocks, sig2);
+  RF_LAUNCHED();
+  const Tf2 p = make_tf2(ref, g.pn_order);
+  if (g.dtype == RF_F64) {
+    k_noalloc_twiddles<double2><<<grid, 256, 0, s>>>(static_cast<double2*>(tw), n);
+    RF_LAUNCHED();
+    real_to_complex_f64(static_cast<const double*>(x), static_cast<double2*>(fa), n, s);
+    fft_c2c_f64(static_cast<double2*>(fa), static_cast<double2*>(xf), static_cast<double2*>(fb), n, 1, -1,
+                static_cast<double2*>(tw), n, s);
+    k_mf_pointwise<double2><<<grid, 256, 0, s>>>(static_cast<double2*>(xf), inv_psd, sig2, p, n, df, g.f_low,
+                                                 g.f_high, static_cast<double2*>(fa), sigma_out);
+    RF_LAUNCHED();
+    fft_c2c_f64(static_cast<double2*>(fa), static_cast<double2*>(z_out), static_cast<double2*>(fb), n, 1, +1,
+                static_cast<double2*>(tw), n, s);
+  } else {
+    k_noalloc_twiddles<float2><<<grid, 256, 0, s>>>(static_cast<float2*>(tw), n);
+    RF_LAUNCHED();
+    real_to_complex_f32(static_cast<const float*>(x), static_cast<float2*>(fa), n, s);
+    fft_c2c_f32(static_cast<float2*>(fa), static_cast<float2*>(xf), static_cast<float2*>(fb), n, 1, -1,
+                static_cast<float2*>(tw), n, s);
+    k_mf_pointwise<float2><<<grid, 256, 0, s>>>(static_cast<float2*>(xf), inv_psd, sig2, p, n, df, g.f_low,
+                                                g.f_high, static_cast<float2*>(fa), sigma_out);
+    RF_LAUNCHED();
+    fft_c2c_f32(static_cast<float2*>(fa), static_cast<float2*>(z_out), static_cast<float2*>(fb), n, 1, +1,
+                static_cast<float2*>(tw), n, s);
+  }
+}
+
+}  // namespace
+}  // namespace rf
+
+extern "C" rf_status rf_mf_reference_noalloc(const rf_grid* grid, const void* x, const double* inv_psd,
+                                             const rf_template* ref, void* z_out, double* sigma_out,
+                                             rf_stream stream) {
+  rf::clear_error();
+  try {
+    RF_REQUIRE(grid != nullptr && ref != nullptr, "grid and ref must be non-NULL");
+    rf::mf_reference_noalloc_impl(*grid, x, inv_psd, *ref, z_out, sigma_out, (cudaStream_t)stream);
+    return RF_OK;
+  } catch (const rf::Fail& e) {
+    return e.st;
+  } catch (...) {
+    rf::set_error("unexpected internal error");
+    return RF_EINVAL;
+  }
+}
