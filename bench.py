@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--algo", default="auto", choices=["auto", "direct", "os"])
     ap.add_argument("--threshold", type=float, default=None)
+    ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default 8192)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--kernels", type=int, default=None, help="neighbours per group (default: the config's)")
@@ -179,8 +180,12 @@ def cpu_baseline(cfg, n_nbrs=4, slice_len=1 << 12, budget_s=20.0):
     z_ref, _ = omf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
     t_mf = time.perf_counter() - t0
     units = cfg.n
-    # kernels of a few neighbours (offline in the method; not timed)
-    sel = list(range(0, len(nb), max(1, len(nb) // n_nbrs)))[:n_nbrs]
+    # kernels of a few neighbours (offline in the method; not timed), chosen at quantiles of
+    # the duration offset, which sets the kernel length (Sec. II.B)
+    tau_ref = workload.newtonian_duration(ref, cfg.f_low)
+    off = np.array([abs(workload.newtonian_duration(t, cfg.f_low) - tau_ref) for t in nb])
+    order = np.argsort(off)
+    sel = [int(order[min(len(nb) - 1, int((q + 0.5) * len(nb) / n_nbrs))]) for q in range(n_nbrs)]
     pk = oratio.build_ratio_kernels(ref, [nb[j] for j in sel], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order,
                                     ip, cfg.threshold)
     idx = np.arange(slice_len, dtype=np.int64) * (cfg.n // slice_len)
@@ -261,9 +266,13 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     kern = rf.build_ratio_kernels(ref, nb, ip, thr)
+    algo_used = args.algo if args.algo != "auto" else ("os" if cfg.dtype == "f32" else "direct")
+    if algo_used == "os":
+        kern.prepare(args.block)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     L = kern.length.astype(np.float64)
+    B = args.block or 8192
 
     nw = -(-n // W)
     z_ref = torch.empty((1, n), dtype=rf.cdtype, device=dev)
@@ -349,15 +358,21 @@ def main():
 
     # ---------------- roofline of the dominant kernel (the neighbour reconstruction)
     rec_avg_ms = statistics.mean(rec_ms)
-    algo_used = args.algo if args.algo != "auto" else "direct"
-    flops = 8.0 * float(L.sum()) * n
+    if algo_used == "os":
+        # per output block of H = B/2 samples: one inverse B-point FFT (5 B log2 B) and
+        # P_j complex multiply-adds per bin (8 P_j B); the segment spectra are shared
+        H = B // 2
+        P = np.maximum(1, np.ceil(L / H))
+        flops = float(np.sum((5.0 * B * math.log2(B) + 8.0 * P * B) / H)) * n
+    else:
+        flops = 8.0 * float(L.sum()) * n
     props = torch.cuda.get_device_properties(dev)
     sm_max = 2070.0
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (rec_avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": f"reconstruct_winmax ({algo_used}, FP32 CUDA cores)",
+                "kernel": f"reconstruct_winmax ({algo_used}{', B=%d' % B if algo_used == 'os' else ''}, FP32 CUDA cores)",
                 "peak_note": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "share_of_step": rec_avg_ms / ms_per_step}
 

@@ -66,7 +66,7 @@ typedef enum { RF_F64 = 0, RF_F32 = 1 } rf_dtype;
 typedef enum {
   RF_ALGO_AUTO = 0,
   RF_ALGO_DIRECT = 1,    /* direct time-domain sum on CUDA cores (Eq. 8) */
-  RF_ALGO_OS = 2         /* overlap-save block FFT (frequency form, Eq. 7) */
+  RF_ALGO_OS = 2         /* overlap-save block FFT (frequency form, Eq. 7), FP32 */
 } rf_algo;
 
 /* Arithmetic of the reconstruction.  FP32: CUDA-core FP32 (RF_F32) or FP64 (RF_F64). */
@@ -154,6 +154,13 @@ rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** le
                           const int32_t** lag0, const int64_t** offset, const double** df_low,
                           const void** taps_dev);
 
+/* Prepare a kernel set for overlap-save reconstruction (RF_F32 grids, n >= 512): block
+ * size B (a power of two in [512, 16384], <= n; 0 picks the default 8192), partitions of
+ * B/2 taps, and their spectra FFT_B(taps)/B computed in FP64 and stored as complex64 inside
+ * the kernel set.  The first overlap-save reconstruction prepares with the default block if
+ * this was not called.  Allocates; SYNCHRONISES `stream`. */
+rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, rf_stream stream);
+
 /* Copy the packed taps (sum(len) complex entries, grid dtype) into caller device memory
  * `dst`.  Async on stream. */
 rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream);
@@ -162,8 +169,12 @@ rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stre
 void rf_kernels_free(rf_kernels* kern);
 
 /* Neighbour SNR series (Eq. 8, circular):  z_j[i] = sum_{l<L_j} c_j[l] z_ref[(i - m0_j - l) mod n].
- * z_ref: complex[n]; z_out: complex[k][n] (grid dtype).  algo: rf_algo; RF_ALGO_OS needs
- * grid dtype RF_F32.  Async on stream. */
+ * z_ref: complex[n]; z_out: complex[k][n] (grid dtype).  algo: rf_algo.  RF_ALGO_OS needs an
+ * RF_F32 grid with n >= 512 (else RF_EUNSUPPORTED) and evaluates the same sum through the
+ * frequency form (Eq. 7) in overlap-save blocks; RF_ALGO_AUTO takes OS on RF_F32 grids and the
+ * direct sum on RF_F64 grids.  The context's workspace grows on first use (2 n complex64 for
+ * OS; see rf_reserve).  Async on stream, except that an OS call on a kernel set that was not
+ * prepared prepares it first (see rf_kernels_prepare). */
 rf_status rf_reconstruct(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo,
                          int32_t prec, void* z_out, rf_stream stream);
 

@@ -138,15 +138,10 @@ rf_status rf_create(const rf_grid* grid, rf_ctx** out) {
     for (int64_t m = 0; m < n; ++m) tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
     c->tw32.ensure(sizeof(float2) * n);
     RF_CUDA(cudaMemcpy(c->tw32.p, tw32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
-    // compact block tables: entry B + m = exp(-2 pi i m / B), B = 2..2^14
-    const int64_t bmax = int64_t(1) << 14;
-    std::vector<float2> twb((size_t)(2 * bmax), make_float2(0.f, 0.f));
-    for (int64_t B = 2; B <= bmax; B *= 2) {
-      const std::vector<double2> t = host_twiddles(B);
-      for (int64_t m = 0; m < B; ++m) twb[B + m] = make_float2((float)t[m].x, (float)t[m].y);
-    }
-    c->twb32.ensure(sizeof(float2) * 2 * bmax);
-    RF_CUDA(cudaMemcpy(c->twb32.p, twb.data(), sizeof(float2) * 2 * bmax, cudaMemcpyHostToDevice));
+    // stage twiddle tables of the overlap-save block FFTs
+    const std::vector<float2> twb = block_fft_tables(c->twb_off);
+    c->twb32.ensure(sizeof(float2) * twb.size());
+    RF_CUDA(cudaMemcpy(c->twb32.p, twb.data(), sizeof(float2) * twb.size(), cudaMemcpyHostToDevice));
     const size_t esz = g.dtype == RF_F64 ? sizeof(double2) : sizeof(float2);
     c->xf.ensure(esz * n);
     c->fa.ensure(esz * n);
@@ -166,10 +161,8 @@ rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out) {
   return guard([&] {
     check_ctx(ctx);
     RF_REQUIRE(k_max >= 0, "k_max must be non-negative");
-    const int64_t n = ctx->n;
-    // packed window keys (8 B per neighbour and 1-sample window at most n/1) are bounded by
-    // the overlap-save block spectra workspace: 2 n complex64 plus k_max * n / 16 keys.
-    const size_t bytes = (size_t)(2 * n) * sizeof(float2) + (size_t)k_max * (size_t)(n / 16 + 1) * 8 + 4096;
+    // overlap-save segment spectra plus packed window keys for windows of >= 16 samples
+    const size_t bytes = os_workspace_bytes(ctx, k_max, 16);
     ctx->scratch.ensure(bytes);
     ctx->reserved = bytes;
     if (bytes_out) *bytes_out = (int64_t)bytes;
@@ -254,6 +247,19 @@ rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** le
   });
 }
 
+rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    RF_REQUIRE(kern->n == ctx->n && kern->dtype == ctx->g.dtype, "kernels were made for another grid");
+    if (ctx->g.dtype != RF_F32 || ctx->n < 512) {
+      set_error("overlap-save needs an RF_F32 grid with n >= 512");
+      throw Fail{RF_EUNSUPPORTED};
+    }
+    os_prepare(ctx, kern, block ? block : os_default_block(ctx), (cudaStream_t)stream);
+  });
+}
+
 rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream) {
   return guard([&] {
     RF_REQUIRE(kern != nullptr, "kern is NULL");
@@ -271,42 +277,48 @@ void rf_kernels_free(rf_kernels* kern) {
   delete kern;
 }
 
-static void check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec) {
+static int check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec) {
   check_ctx(ctx);
   RF_REQUIRE(kern != nullptr, "kern is NULL");
   RF_REQUIRE(kern->n == ctx->n && kern->dtype == ctx->g.dtype, "kernels were made for another grid");
   check_dev(z_ref, "z_ref");
   RF_REQUIRE(algo == RF_ALGO_AUTO || algo == RF_ALGO_DIRECT || algo == RF_ALGO_OS, "unknown algo %d", algo);
   RF_REQUIRE(prec == RF_PREC_NATIVE, "unknown prec %d", prec);
+  const bool os_ok = ctx->g.dtype == RF_F32 && ctx->n >= 512;
+  if (algo == RF_ALGO_OS && !os_ok) {
+    set_error("overlap-save needs an RF_F32 grid with n >= 512");
+    throw Fail{RF_EUNSUPPORTED};
+  }
+  if (algo == RF_ALGO_AUTO) algo = os_ok ? RF_ALGO_OS : RF_ALGO_DIRECT;
+  return algo;
 }
 
 rf_status rf_reconstruct(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec,
                          void* z_out, rf_stream stream) {
   return guard([&] {
-    check_recon(ctx, z_ref, kern, algo, prec);
+    const int a = check_recon(ctx, z_ref, kern, algo, prec);
     if (kern->k) check_dev(z_out, "z_out");
-    if (algo == RF_ALGO_OS) {
-      set_error("overlap-save reconstruction is not available in this build");
-      throw Fail{RF_EUNSUPPORTED};
-    }
-    reconstruct_direct(ctx, z_ref, kern, z_out, 0, nullptr, nullptr, (cudaStream_t)stream);
+    if (a == RF_ALGO_OS)
+      reconstruct_os(ctx, z_ref, const_cast<rf_kernels*>(kern), z_out, 0, nullptr, nullptr, (cudaStream_t)stream);
+    else
+      reconstruct_direct(ctx, z_ref, kern, z_out, 0, nullptr, nullptr, (cudaStream_t)stream);
   });
 }
 
 rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec,
                                 int64_t W, float* max_out, int32_t* argmax_out, rf_stream stream) {
   return guard([&] {
-    check_recon(ctx, z_ref, kern, algo, prec);
+    const int a = check_recon(ctx, z_ref, kern, algo, prec);
     RF_REQUIRE(W >= 1 && W <= ctx->n, "W=%lld must be in [1, n]", (long long)W);
     if (kern->k) {
       check_dev(max_out, "max_out");
       check_dev(argmax_out, "argmax_out");
     }
-    if (algo == RF_ALGO_OS) {
-      set_error("overlap-save reconstruction is not available in this build");
-      throw Fail{RF_EUNSUPPORTED};
-    }
-    reconstruct_direct(ctx, z_ref, kern, nullptr, W, max_out, argmax_out, (cudaStream_t)stream);
+    if (a == RF_ALGO_OS)
+      reconstruct_os(ctx, z_ref, const_cast<rf_kernels*>(kern), nullptr, W, max_out, argmax_out,
+                     (cudaStream_t)stream);
+    else
+      reconstruct_direct(ctx, z_ref, kern, nullptr, W, max_out, argmax_out, (cudaStream_t)stream);
   });
 }
 

@@ -1,0 +1,104 @@
+// Block FFT of B complex64 points held by one thread block: B/16 threads, 16
+// points per thread, Stockham radix-16 stages through shared memory plus one
+// final radix-2/4/8 stage when log2(B) is not a multiple of 4.
+//
+// Stage with radix R and Ns = product of the earlier radices maps butterfly b
+// (k = b mod Ns) as  a[t] = in[b + t B/R] * w^(t k),  w = exp(sign 2 pi i / (Ns R)),
+// a = DFT_R(a),  out[(b - k) R + k + t Ns] = a[t]  (natural order after the last stage).
+//
+// Input: before run(), thread `tid` holds v[t] = x[tid + t B/16] for t < 16.
+// Output: after run(), thread `tid` holds, for q < 16/RL and t < RL,
+//   v[q RL + t] = X[b + t B/RL],  b = tid + q NT   (RL = radix of the last stage).
+// Shared memory: B + B/16 float2 (index p is stored at p + p/16, which makes the
+// stride-16 writes of the first stage bank-conflict free).
+//
+// Twiddles come from per-stage tables laid out in thread order: the stage with
+// radix R and Ns has a table of R*Ns entries, entry t*Ns + k = exp(-2 pi i t k / (R Ns)),
+// so the loads of a warp are contiguous.  The tables of the middle stages and of the
+// last stage follow each other; a block size B needs block_table_size<B>() entries
+// (built on the host by block_fft_tables).
+#pragma once
+
+#include "cplx.cuh"
+
+namespace rf {
+
+__device__ __forceinline__ int bf_pad(int p) { return p + (p >> 4); }
+
+template <int B>
+struct BlockFFTShape {
+  static constexpr int LOGB = (B == 256) ? 8 : (B == 512) ? 9 : (B == 1024) ? 10 : (B == 2048) ? 11
+                            : (B == 4096) ? 12 : (B == 8192) ? 13 : (B == 16384) ? 14 : -1;
+  static_assert(LOGB > 0, "block size");
+  static constexpr int NT = B / 16;
+  static constexpr int N16 = LOGB / 4;                 // radix-16 stages
+  static constexpr int REM = LOGB % 4;
+  static constexpr int RL = REM ? (1 << REM) : 16;     // radix of the last stage
+  static constexpr int SMEM = B + B / 16;              // float2 entries
+};
+
+// Radix-16 stages between the first and the last stage.
+template <int B>
+__host__ __device__ constexpr int block_mid_stages() {
+  return (BlockFFTShape<B>::REM ? BlockFFTShape<B>::N16 : BlockFFTShape<B>::N16 - 1) - 1;
+}
+
+// Entries of the stage twiddle tables of block size B: 16 Ns per middle stage, then B for
+// the last stage.
+template <int B>
+__host__ __device__ constexpr int block_table_size() {
+  int s = 0, ns = 16;
+  for (int st = 0; st < block_mid_stages<B>(); ++st) {
+    s += 16 * ns;
+    ns *= 16;
+  }
+  return s + B;
+}
+
+// tw: the stage tables of B.  SIGN: -1 forward, +1 inverse (unnormalised).
+template <int B, int SIGN>
+__device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const float2* __restrict__ tw) {
+  using S = BlockFFTShape<B>;
+  constexpr int NT = S::NT;
+  const int tid = threadIdx.x;
+  // first stage: Ns = 1, no twiddles, out[b*16 + t]
+  dft<16, SIGN>(v);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) sm[bf_pad(tid * 16 + t)] = v[t];
+  __syncthreads();
+  int Ns = 16;
+  // middle radix-16 stages (all but the last stage)
+  constexpr int MID = block_mid_stages<B>();
+#pragma unroll
+  for (int st = 0; st < MID; ++st) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = sm[bf_pad(tid + t * (B / 16))];
+    __syncthreads();
+    const int k = tid & (Ns - 1);
+#pragma unroll
+    for (int t = 1; t < 16; ++t) v[t] = tw_apply<SIGN>(v[t], __ldg(tw + t * Ns + k));
+    dft<16, SIGN>(v);
+    const int base = (tid - k) * 16 + k;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) sm[bf_pad(base + t * Ns)] = v[t];
+    __syncthreads();
+    tw += 16 * Ns;
+    Ns *= 16;
+  }
+  // last stage: radix RL, Ns = B / RL, every butterfly index b < Ns so k = b
+  constexpr int RL = S::RL;
+#pragma unroll
+  for (int q = 0; q < 16 / RL; ++q) {
+    const int b = tid + q * NT;
+    float2 a[RL];
+#pragma unroll
+    for (int t = 0; t < RL; ++t) a[t] = sm[bf_pad(b + t * (B / RL))];
+#pragma unroll
+    for (int t = 1; t < RL; ++t) a[t] = tw_apply<SIGN>(a[t], __ldg(tw + t * (B / RL) + b));
+    dft<RL, SIGN>(a);
+#pragma unroll
+    for (int t = 0; t < RL; ++t) v[q * RL + t] = a[t];
+  }
+}
+
+}  // namespace rf

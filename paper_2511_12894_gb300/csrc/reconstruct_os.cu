@@ -1,0 +1,396 @@
+// Overlap-save reconstruction (frequency form of the ratio identity, Eq. 7) with
+// uniformly partitioned kernels, FP32.
+//
+// With block size B and hop H = B/2:
+//   segment spectra (once per reference, shared by all neighbours)
+//     Zs[s] = FFT_B( z_ref[(s H - H + t) mod n], t < B ),          s < NS = n / H
+//   kernel partition spectra (once per kernel set, FP64 then rounded)
+//     C[j][p] = FFT_B( c_j[p H + u] for u < H, zero above ) / B,   p < P_j = ceil(L_j / H)
+//   output block s of neighbour j
+//     y = IFFT_B( sum_p Zs[(s - p) mod NS] C[j][p] ),  w_j[s H + t - H] = y[t] for H <= t < B,
+// which is w_j[i'] = sum_l c_j[l] z_ref[(i' - l) mod n], and z_j[i] = w_j[(i - m0_j) mod n]:
+// the first lag is applied by relabelling outputs, so every neighbour shares Zs.
+// The window peaks are reduced per warp and merged across blocks with 64-bit
+// atomicMax on (float bits of |z|^2) << 32 | (2^32 - 1 - i), which orders by value
+// and then by the smallest index.
+#include <algorithm>
+#include <cmath>
+#include <memory>
+
+#include "blockfft.cuh"
+#include "rf_internal.h"
+
+namespace rf {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long pack_key(float v, unsigned int i) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - i);
+}
+
+template <int B>
+__global__ void __launch_bounds__(B / 16) k_os_segments(const float2* __restrict__ z_ref, int64_t n,
+                                                        const float2* __restrict__ tw, float2* __restrict__ Zs) {
+  using S = BlockFFTShape<B>;
+  extern __shared__ float2 sm[];
+  constexpr int H = B / 2;
+  const int64_t s = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  float2 v[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) v[t] = z_ref[(s * H - H + tid + t * (B / 16)) & mask];
+  block_fft<B, -1>(v, sm, tw);
+  float2* out = Zs + s * B;
+#pragma unroll
+  for (int q = 0; q < 16 / S::RL; ++q)
+#pragma unroll
+    for (int t = 0; t < S::RL; ++t) out[tid + q * S::NT + t * (B / S::RL)] = v[q * S::RL + t];
+}
+
+template <int B, bool WINMAX>
+__global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restrict__ Zs, const float2* __restrict__ Cs,
+                                              const int64_t* __restrict__ spec_off, const int* __restrict__ parts,
+                                              const int* __restrict__ lag0, const float2* __restrict__ tw, int64_t n,
+                                              int NS, int SC, float2* __restrict__ z_out,
+                                              unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
+                                              int fastwin) {
+  using S = BlockFFTShape<B>;
+  constexpr int NT = S::NT;
+  constexpr int H = B / 2;
+  constexpr int RL = S::RL;
+  constexpr int CH = H / NT;  // outputs per thread in the peak reduction (8)
+  extern __shared__ float2 sm[];
+  const int j = blockIdx.y;
+  const int P = parts[j];
+  const int64_t m0 = lag0[j];
+  const float2* C = Cs + spec_off[j];
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  const int s0 = blockIdx.x * SC;
+  const int s1 = min(NS, s0 + SC);
+  for (int s = s0; s < s1; ++s) {
+    float2 v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = make_float2(0.f, 0.f);
+    // partitions outermost: each pass issues all 32 loads of the thread's bins at once
+    for (int p = 0; p < P; ++p) {
+      int sp = s - p;
+      sp += (sp < 0) ? NS : 0;
+      const float2* zp = Zs + (int64_t)sp * B + tid;
+      const float2* cp = C + (int64_t)p * B + tid;
+#pragma unroll
+      for (int h = 0; h < 16; h += 8) {
+        float2 z[8], c[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          z[t] = __ldg(zp + (h + t) * (B / 16));
+          c[t] = __ldg(cp + (h + t) * (B / 16));
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          v[h + t].x = fmaf(z[t].x, c[t].x, fmaf(-z[t].y, c[t].y, v[h + t].x));
+          v[h + t].y = fmaf(z[t].x, c[t].y, fmaf(z[t].y, c[t].x, v[h + t].y));
+        }
+      }
+    }
+    block_fft<B, +1>(v, sm, tw);
+    const int64_t base = ((int64_t)s * H + m0) & mask;  // output index of block position H
+    if (!WINMAX) {
+      float2* out = z_out + (int64_t)j * n;
+#pragma unroll
+      for (int q = 0; q < 16 / RL; ++q)
+#pragma unroll
+        for (int t = RL / 2; t < RL; ++t) {
+          const int idx = tid + q * NT + t * (B / RL);  // >= H
+          out[(base + idx - H) & mask] = v[q * RL + t];
+        }
+      __syncthreads();  // the next block's FFT overwrites the shared memory read above
+    } else {
+      __syncthreads();  // the last FFT stage has finished reading shared memory
+      float* mag = reinterpret_cast<float*>(sm);
+#pragma unroll
+      for (int q = 0; q < 16 / RL; ++q)
+#pragma unroll
+        for (int t = RL / 2; t < RL; ++t) {
+          const int idx = tid + q * NT + t * (B / RL);
+          const float2 y = v[q * RL + t];
+          mag[idx - H] = y.x * y.x + y.y * y.y;
+        }
+      __syncthreads();
+      unsigned long long* kj = keys + (int64_t)j * nw;
+      const int lane = tid & 31;
+      const int qbase = tid * CH;
+      bool slow = !fastwin;
+      unsigned long long kA = 0, kB = 0;
+      int64_t wA = 0, wB = 0;
+      if (fastwin) {
+        const int64_t i_warp = (base + (int64_t)(tid - lane) * CH) & mask;
+        wA = i_warp / W;
+        wB = (wA + 1 == nw) ? 0 : wA + 1;
+        float mv[CH];
+#pragma unroll
+        for (int e = 0; e < CH; e += 4) *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + qbase + e);
+#pragma unroll
+        for (int e = 0; e < CH; ++e) {
+          const int64_t i = (base + qbase + e) & mask;
+          const int64_t w = i / W;
+          const unsigned long long key = pack_key(mv[e], (unsigned int)i);
+          if (w == wA) kA = max(kA, key);
+          else if (w == wB) kB = max(kB, key);
+          else slow = true;
+        }
+      }
+      const bool any_slow = __any_sync(0xffffffffu, slow);
+      if (any_slow) {
+        for (int e = 0; e < CH; ++e) {
+          const int64_t i = (base + qbase + e) & mask;
+          atomicMax(kj + i / W, pack_key(mag[qbase + e], (unsigned int)i));
+        }
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
+          kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
+        }
+        if (lane == 0) {
+          if (kA) atomicMax(kj + wA, kA);
+          if (kB) atomicMax(kj + wB, kB);
+        }
+      }
+      __syncthreads();  // mag (shared memory) is reused by the next block's FFT
+    }
+  }
+}
+
+__global__ void k_unpack_keys(const unsigned long long* __restrict__ keys, int64_t count, float* __restrict__ mx,
+                              int* __restrict__ arg) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const unsigned long long k = keys[i];
+  mx[i] = __uint_as_float((unsigned int)(k >> 32));
+  arg[i] = (int)(0xffffffffu - (unsigned int)(k & 0xffffffffull));
+}
+
+// rows[g][u] = taps of partition (j, p) = g, promoted to FP64, zero above H or L_j
+__global__ void k_os_fill(const float2* __restrict__ taps, const int64_t* __restrict__ off,
+                          const int* __restrict__ len, const int* __restrict__ gj, const int* __restrict__ gp,
+                          int B, double2* __restrict__ rows) {
+  const int g = blockIdx.y;
+  const int j = gj[g], p = gp[g];
+  const int H = B / 2;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < B; u += gridDim.x * blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    const int l = p * H + u;
+    if (u < H && l < len[j]) {
+      const float2 c = taps[off[j] + l];
+      v = make_double2((double)c.x, (double)c.y);
+    }
+    rows[(int64_t)g * B + u] = v;
+  }
+}
+
+__global__ void k_os_round(const double2* __restrict__ spec, int64_t count, double scale, float2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = make_float2((float)(spec[i].x * scale), (float)(spec[i].y * scale));
+}
+
+template <int B>
+size_t os_smem() {
+  return sizeof(float2) * BlockFFTShape<B>::SMEM;
+}
+
+template <int B>
+void launch_os_segments(rf_ctx* c, const float2* z_ref, float2* Zs, cudaStream_t s) {
+  const int NS = (int)(c->n / (B / 2));
+  const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<B>::LOGB];
+  auto fn = k_os_segments<B>;
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<B>()));
+  fn<<<NS, B / 16, os_smem<B>(), s>>>(z_ref, c->n, tw, Zs);
+  RF_LAUNCHED();
+}
+
+template <int B, bool WINMAX>
+void launch_os(rf_ctx* c, const rf_kernels* kern, const float2* Zs, float2* z_out, unsigned long long* keys,
+               int64_t W, cudaStream_t s) {
+  const int NS = (int)(c->n / (B / 2));
+  const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<B>::LOGB];
+  const int64_t nw = WINMAX ? (c->n + W - 1) / W : 0;
+  // segments per block: enough blocks for every SM several times over
+  int SC = 8;
+  while (SC > 1 && (int64_t)kern->k * ((NS + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
+  const int nchunk = (NS + SC - 1) / SC;
+  const int fastwin = (WINMAX && W >= 32 * (B / 2) / (B / 16)) ? 1 : 0;  // a warp's outputs span <= 2 windows
+  auto fn = k_os<B, WINMAX>;
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<B>()));
+  int64_t done = 0;
+  while (done < kern->k) {
+    const int cnt = (int)std::min<int64_t>(65535, kern->k - done);
+    dim3 grid((unsigned)nchunk, (unsigned)cnt);
+    fn<<<grid, B / 16, os_smem<B>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>() + done,
+                                          kern->os_parts_d.as<int>() + done, kern->lag0_d.as<int>() + done, tw, c->n,
+                                          NS, SC, z_out ? z_out + done * c->n : nullptr,
+                                          keys ? keys + done * nw : nullptr, W, nw, fastwin);
+    RF_LAUNCHED();
+    done += cnt;
+  }
+}
+
+template <typename F>
+void dispatch_b(int B, F&& f) {
+  switch (B) {
+    case 512: f(std::integral_constant<int, 512>{}); break;
+    case 1024: f(std::integral_constant<int, 1024>{}); break;
+    case 2048: f(std::integral_constant<int, 2048>{}); break;
+    case 4096: f(std::integral_constant<int, 4096>{}); break;
+    case 8192: f(std::integral_constant<int, 8192>{}); break;
+    case 16384: f(std::integral_constant<int, 16384>{}); break;
+    default: RF_REQUIRE(false, "overlap-save block size %d is not supported", B);
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// Stage tables of one block size, in the order block_fft reads them.
+template <int B>
+void append_tables(std::vector<float2>& out) {
+  using S = BlockFFTShape<B>;
+  const size_t start = out.size();
+  int Ns = 16;
+  for (int st = 0; st < block_mid_stages<B>(); ++st) {
+    const std::vector<double2> w = host_twiddles(16 * (int64_t)Ns);  // exp(-2 pi i m / (16 Ns))
+    for (int t = 0; t < 16; ++t)
+      for (int k = 0; k < Ns; ++k) {
+        const double2 v = w[(size_t)t * k];
+        out.push_back(make_float2((float)v.x, (float)v.y));
+      }
+    Ns *= 16;
+  }
+  const std::vector<double2> w = host_twiddles(B);  // last stage: exp(-2 pi i t b / B)
+  for (int t = 0; t < S::RL; ++t)
+    for (int b = 0; b < B / S::RL; ++b) {
+      const double2 v = w[(size_t)t * b];
+      out.push_back(make_float2((float)v.x, (float)v.y));
+    }
+  if (out.size() - start != (size_t)block_table_size<B>()) throw Fail{RF_EINVAL};
+}
+
+}  // namespace
+
+std::vector<float2> block_fft_tables(int64_t off[16]) {
+  std::vector<float2> out;
+  for (int b = 0; b < 16; ++b) off[b] = 0;
+  off[9] = (int64_t)out.size();
+  append_tables<512>(out);
+  off[10] = (int64_t)out.size();
+  append_tables<1024>(out);
+  off[11] = (int64_t)out.size();
+  append_tables<2048>(out);
+  off[12] = (int64_t)out.size();
+  append_tables<4096>(out);
+  off[13] = (int64_t)out.size();
+  append_tables<8192>(out);
+  off[14] = (int64_t)out.size();
+  append_tables<16384>(out);
+  return out;
+}
+
+int os_default_block(const rf_ctx* c) {
+  int B = 8192;
+  while (B > 512 && B > c->n) B /= 2;
+  return B;
+}
+
+void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s) {
+  RF_REQUIRE(kern->dtype == RF_F32, "overlap-save needs the FP32 grid");
+  RF_REQUIRE(B >= 512 && B <= 16384 && (B & (B - 1)) == 0 && B <= c->n, "overlap-save block %d invalid for n=%lld", B,
+             (long long)c->n);
+  if (kern->os_ready && kern->os_B == B) return;
+  const int H = B / 2;
+  const int k = kern->k;
+  std::vector<int> parts(k);
+  std::vector<int64_t> off(k + 1, 0);
+  std::vector<int> gj, gp;
+  for (int j = 0; j < k; ++j) {
+    parts[j] = std::max(1, (kern->len[j] + H - 1) / H);
+    off[j + 1] = off[j] + (int64_t)parts[j] * B;
+    for (int p = 0; p < parts[j]; ++p) {
+      gj.push_back(j);
+      gp.push_back(p);
+    }
+  }
+  const int G = (int)gj.size();
+  kern->os_ready = false;
+  kern->os_spec.ensure(std::max<size_t>(16, sizeof(float2) * (size_t)off[k]));
+  kern->os_off_d.ensure(sizeof(int64_t) * (k + 1));
+  kern->os_parts_d.ensure(std::max<size_t>(16, sizeof(int) * k));
+  if (k) {
+    RF_CUDA(cudaMemcpyAsync(kern->os_off_d.p, off.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, s));
+    RF_CUDA(cudaMemcpyAsync(kern->os_parts_d.p, parts.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  }
+  DevBuf gjd, gpd, rows;
+  gjd.ensure(std::max<size_t>(16, sizeof(int) * G));
+  gpd.ensure(std::max<size_t>(16, sizeof(int) * G));
+  if (G) {
+    RF_CUDA(cudaMemcpyAsync(gjd.p, gj.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s));
+    RF_CUDA(cudaMemcpyAsync(gpd.p, gp.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s));
+  }
+  // FP64 transforms of the partitions, a bounded number of rows at a time
+  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)256 << 20) / (3LL * B * 16)));
+  rows.ensure((size_t)3 * chunk * B * sizeof(double2));
+  double2* in = rows.as<double2>();
+  double2* out = in + (int64_t)chunk * B;
+  double2* tmp = out + (int64_t)chunk * B;
+  for (int g0 = 0; g0 < G; g0 += chunk) {
+    const int cnt = std::min(chunk, G - g0);
+    dim3 grid((unsigned)((B + 255) / 256), (unsigned)cnt);
+    k_os_fill<<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(), kern->len_d.as<int>(),
+                                   gjd.as<int>() + g0, gpd.as<int>() + g0, B, in);
+    RF_LAUNCHED();
+    fft_c2c_f64(in, out, tmp, B, cnt, -1, c->tw64.as<double2>(), c->n, s);
+    const int64_t count = (int64_t)cnt * B;
+    k_os_round<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, count, 1.0 / (double)B,
+                                                                kern->os_spec.as<float2>() + (int64_t)g0 * B);
+    RF_LAUNCHED();
+  }
+  RF_CUDA(cudaStreamSynchronize(s));  // the row buffers are released on return
+  kern->os_parts = parts;
+  kern->os_B = B;
+  kern->os_ready = true;
+}
+
+size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W) {
+  const int64_t nw = W > 0 ? (c->n + W - 1) / W : 0;
+  return sizeof(float2) * (size_t)(2 * c->n) + sizeof(unsigned long long) * (size_t)k * (size_t)nw + 256;
+}
+
+void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,
+                    int32_t* argmax_out, cudaStream_t s) {
+  if (kern->k == 0) return;
+  const int B = kern->os_ready ? kern->os_B : os_default_block(c);
+  if (!kern->os_ready) os_prepare(c, kern, B, s);
+  const bool win = max_out != nullptr;
+  const size_t need = os_workspace_bytes(c, kern->k, win ? W : 0);
+  c->scratch.ensure(need);
+  float2* Zs = c->scratch.as<float2>();
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(Zs + 2 * c->n);
+  const int64_t nw = win ? (c->n + W - 1) / W : 0;
+  if (win) RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)kern->k * nw, s));
+  dispatch_b(B, [&](auto bc) {
+    constexpr int BB = decltype(bc)::value;
+    launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), Zs, s);
+    if (win)
+      launch_os<BB, true>(c, kern, Zs, nullptr, keys, W, s);
+    else
+      launch_os<BB, false>(c, kern, Zs, static_cast<float2*>(z_out), nullptr, 0, s);
+  });
+  if (win) {
+    const int64_t count = (int64_t)kern->k * nw;
+    k_unpack_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
+    RF_LAUNCHED();
+  }
+}
+
+}  // namespace rf

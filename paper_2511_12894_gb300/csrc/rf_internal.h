@@ -89,9 +89,10 @@ struct rf_ctx {
   int nsm = 0;
   // Twiddle tables w[m] = exp(-2 pi i m / n), m < n: FP64 and FP32 copies.
   rf::DevBuf tw64, tw32;
-  // Compact tables for the block FFTs: for B = 2^b (b = 1..14), B entries of
-  // exp(-2 pi i m / B) stored at offset B (float2).
+  // Stage twiddle tables of the block FFTs (float2), B = 2^9 .. 2^14; the tables of
+  // block size 2^b start at entry twb_off[b].
   rf::DevBuf twb32;
+  int64_t twb_off[16] = {0};
   // Workspaces (grid dtype complex unless stated).
   rf::DevBuf xf;       // data spectrum, complex[n]
   rf::DevBuf fa, fb;   // FFT ping-pong, complex[n]
@@ -113,12 +114,14 @@ struct rf_kernels {
   rf::DevBuf taps;             // packed taps (grid dtype complex)
   rf::DevBuf len_d, lag0_d;    // int32[k]
   rf::DevBuf off_d;            // int64[k+1]
-  // Overlap-save preparation (FP32 only): per kernel block size and partitions.
+  // Overlap-save preparation (FP32 only): block size B, partitions P_j = ceil(L_j / (B/2)),
+  // and the partition spectra FFT_B(taps) / B, kernel after kernel.
   bool os_ready = false;
-  std::vector<int32_t> os_logb;     // log2 B per kernel
-  std::vector<int32_t> os_parts;    // partitions P per kernel
-  std::vector<int64_t> os_spec_off; // offset (in complex elements) of the kernel's spectra
-  rf::DevBuf os_spec;               // float2: per kernel P * B spectra (scaled by 1/B)
+  int os_B = 0;
+  std::vector<int32_t> os_parts;
+  rf::DevBuf os_spec;      // float2 [sum_j P_j][B]
+  rf::DevBuf os_off_d;     // int64 [k+1]: element offset of kernel j's first partition spectrum
+  rf::DevBuf os_parts_d;   // int32 [k]
 };
 
 namespace rf {
@@ -135,6 +138,9 @@ void real_to_complex_f64(const double* x, double2* out, int64_t n, cudaStream_t 
 void real_to_complex_f32(const float* x, float2* out, int64_t n, cudaStream_t s);
 // Host-side FP64 twiddle table exp(-2 pi i m / n), m < n (octant symmetric, accurate).
 std::vector<double2> host_twiddles(int64_t n);
+// Stage twiddle tables of the block FFTs for B = 2^9 .. 2^14 (float2, concatenated), with
+// the entry offset of each block size in off[log2 B].
+std::vector<float2> block_fft_tables(int64_t off[16]);
 
 // ---------------------------------------------------------------- MF (mf.cu)
 void mf_reference_impl(rf_ctx* c, const void* x, const double* inv_psd, int32_t nref,
@@ -154,5 +160,11 @@ void reconstruct_direct(rf_ctx* c, const void* z_ref, const rf_kernels* kern, vo
                         int64_t W, float* max_out, int32_t* argmax_out, cudaStream_t s);
 void winmax_series(rf_ctx* c, const void* z, int32_t count, int64_t W, float* max_out,
                    int32_t* argmax_out, cudaStream_t s);
+// overlap-save (reconstruct_os.cu); FP32 grids, block sizes 512..16384
+int os_default_block(const rf_ctx* c);
+void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s);
+size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W);
+void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,
+                    int32_t* argmax_out, cudaStream_t s);
 
 }  // namespace rf

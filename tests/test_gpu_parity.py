@@ -265,3 +265,128 @@ def test_winmax_series(torch):
         assert np.abs(P[r] - Po).max() <= 1e-6 * Po.max()
         _argmax_ok(np.abs(zz) ** 2, A[r], Ao, 1000, 1e-5 * Po.max())
     assert A[1, 0] == 100
+
+
+# ---------------------------------------------------------------- overlap-save
+
+@pytest.mark.parametrize("B", [512, 1024, 8192, 16384])
+def test_reconstruct_os_edge_lengths(torch, B):
+    """Overlap-save against the oracle's direct sum: lengths around the partition size
+    H = B/2, lengths above n/2, lags of both signs and wrapping, windows down to 1 sample."""
+    n = 1 << 15
+    H = B // 2
+    rng = np.random.default_rng(B)
+    lengths = [1, 2, 31, 255, 256, 257, H - 1, H, H + 1, 2 * H + 7, 1000, n // 2 + 3, 0]
+    lags = [0, -5, 37, n // 2, -(n // 2) + 1, 100, -1000, 3, 7000, -2, 11, -n // 4, 5]
+    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype="f32")
+    rf = _rf(cfg)
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    taps = [((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(max(L, 1))).astype(np.complex64)
+            for L in lengths]
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    kern.prepare(B)
+    zt = torch.tensor(z, device="cuda")
+    out = rf.reconstruct(zt, kern, "os").cpu().numpy()
+    zo = [reconstruct.reconstruct_direct(z.astype(np.complex128), lags[j], taps[j].astype(np.complex128))
+          for j in range(len(lengths))]
+    for j, L in enumerate(lengths):
+        if L == 0:
+            assert np.abs(out[j]).max() == 0.0
+            continue
+        assert _relerr(out[j], zo[j]) < TOL["f32"], (B, j, L)
+    for W in (1, 3, 1000, 2048, n):
+        P, A = rf.reconstruct_winmax(zt, kern, W, "os")
+        P, A = P.cpu().numpy(), A.cpu().numpy()
+        for j, L in enumerate(lengths):
+            Po, Ao = reconstruct.window_peaks(zo[j], W)
+            if L == 0:
+                assert np.all(P[j] == 0)
+                continue
+            assert np.abs(P[j] - Po).max() <= 4 * TOL["f32"] * Po.max()
+            _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, W, 8 * TOL["f32"] * Po.max())
+
+
+def _cfg2_long(n=1 << 17, k=8, dmax=4.0):
+    cfg = workload.config(2, n_override=n, k_override=k)
+    ref = cfg.groups[0][0]
+    nb = workload.duration_lattice(ref, cfg.f_low, k, 0.3, dmax, np.random.default_rng(3), n_eta=1)
+    inj = (workload.Injection(2, 0, n // 3, 15.0),)
+    return replace(cfg, groups=((ref, nb),), injections=inj)
+
+
+def test_reconstruct_os_paper_shaped_kernels(torch):
+    """Reconstruct-only: the oracle's z_ref and kernels (rounded to complex64) through
+    overlap-save, against the oracle's FP64 direct sum of the same rounded inputs; and the
+    whole GPU path (matched filter, builder, overlap-save) against the FP64 oracle."""
+    cfg = _cfg2_long()
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    zo_ref, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    pk = ratio.build_ratio_kernels(ref, nb, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, cfg.threshold)
+    assert pk.length.max() > 4096          # several partitions at B = 8192
+    rf = _rf(cfg)
+    z32 = zo_ref.astype(np.complex64)
+    kern = rf.kernels_import(pk.lag0, pk.length, pk.taps.astype(np.complex64))
+    for B in (2048, 8192):
+        kern.prepare(B)
+        out = rf.reconstruct(torch.tensor(z32, device="cuda"), kern, "os").cpu().numpy()
+        for j in range(len(nb)):
+            m0, c = pk.kernel(j)
+            zh = reconstruct.reconstruct_direct(z32.astype(np.complex128), m0, c.astype(np.complex64))
+            assert _relerr(out[j], zh) < TOL["f32"], (B, j)
+    # whole path
+    ipt = torch.tensor(ip, device="cuda")
+    zg, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), ipt, [ref])
+    kg = rf.build_ratio_kernels(ref, nb, ipt, cfg.threshold)
+    assert np.array_equal(kg.lag0, pk.lag0) and np.array_equal(kg.length, pk.length)
+    out = rf.reconstruct(zg[0], kg, "auto").cpu().numpy()
+    P, A = rf.reconstruct_winmax(zg[0], kg, cfg.window, "auto")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    for j in range(len(nb)):
+        zh = reconstruct.reconstruct_direct(zo_ref, *pk.kernel(j))
+        assert _relerr(out[j], zh) < TOL["f32"], j
+        Po, Ao = reconstruct.window_peaks(zh, cfg.window)
+        assert np.abs(P[j] - Po).max() <= 4 * TOL["f32"] * Po.max()
+        _argmax_ok(zh.real ** 2 + zh.imag ** 2, A[j], Ao, cfg.window, 8 * TOL["f32"] * Po.max())
+    inj = cfg.injections[0]
+    assert A[inj.template_index, inj.sample // cfg.window] == inj.sample
+
+
+def test_full_size_paper_workload_sampled(torch):
+    """The benchmark's workload at full size (n = 2^20, 256 neighbours) in the launch
+    configuration the benchmark times; checked on sampled outputs computed one by one by
+    the oracle, and by properties of the window peaks that hold at any size."""
+    cfg = workload.config(2)
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    ipt = torch.tensor(ip, device="cuda")
+    zg, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), ipt, [ref])
+    kern = rf.build_ratio_kernels(ref, nb, ipt, cfg.threshold)
+    P, A = rf.reconstruct_winmax(zg[0], kern, cfg.window, "auto")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    zo_ref, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    assert _relerr(zg[0].cpu().numpy(), zo_ref) < TOL["f32"]
+    rng = np.random.default_rng(0)
+    order = np.argsort(kern.length)
+    sample = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    pk = ratio.build_ratio_kernels(ref, [nb[j] for j in sample], cfg.n, cfg.fs, cfg.f_low, cfg.f_high,
+                                   cfg.pn_order, ip, cfg.threshold)
+    for q, j in enumerate(sample):
+        assert kern.lag0[j] == pk.lag0[q] and kern.length[j] == pk.length[q]
+        m0, c = pk.kernel(q)
+        # the reported peak equals the oracle's value at the reported index ...
+        wins = rng.choice(P.shape[1], 24, replace=False)
+        vals = reconstruct.reconstruct_at(zo_ref, m0, c, A[j, wins])
+        assert np.abs(P[j, wins] - np.abs(vals) ** 2).max() <= 4 * TOL["f32"] * P[j].max()
+        # ... and no sampled sample of those windows exceeds it
+        for w in wins[:6]:
+            idx = w * cfg.window + rng.choice(cfg.window, 48, replace=False)
+            v = np.abs(reconstruct.reconstruct_at(zo_ref, m0, c, idx)) ** 2
+            assert np.all(v <= P[j, w] + 4 * TOL["f32"] * P[j].max())
+    # the injections are recovered at their arrival samples
+    for inj in cfg.injections:
+        w = inj.sample // cfg.window
+        assert abs(int(A[inj.template_index, w]) - inj.sample) <= 1
