@@ -186,6 +186,21 @@ rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels
                                 int32_t algo, int32_t prec, int64_t W, float* max_out,
                                 int32_t* argmax_out, rf_stream stream);
 
+/* Batched fused form for G references, each with its own neighbours (Sec. III.A: groups
+ * are independent): per reference g, z_refs[g] is its z_ref (device complex[n]) and ks[g]
+ * its kernel set; the rows of max_out/argmax_out ([sum_g k_g][ceil(n/W)]) follow the order
+ * of the groups and, inside a group, of its neighbours.  Runs overlap-save (RF_F32 grid,
+ * n >= 512; algo must be RF_ALGO_AUTO or RF_ALGO_OS) as one persistent launch over
+ * (neighbour, output-block chunk) work units.  z_refs and ks are host arrays.  The first
+ * call with a given set of references and kernel sets (or after any of them is re-prepared)
+ * builds and uploads the work list and allocates the per-reference segment spectra
+ * (G x 2n complex64) and window keys, synchronously; later calls with the same arguments
+ * only enqueue kernels, so a warmed-up call can be captured in a CUDA graph.  Kernel sets
+ * that are not prepared for overlap-save are prepared first.  Async on stream otherwise. */
+rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_refs, rf_kernels* const* ks,
+                                 int32_t algo, int32_t prec, int64_t W, float* max_out,
+                                 int32_t* argmax_out, rf_stream stream);
+
 /* Window peaks of `count` series already in memory (e.g. z_ref itself): z: complex[count][n];
  * max_out/argmax_out: [count][ceil(n/W)], same definition as rf_reconstruct_winmax. */
 rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float* max_out,

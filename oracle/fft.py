@@ -65,5 +65,5 @@ def dft_naive(x: np.ndarray, sign: float = -1.0) -> np.ndarray:
     j = np.arange(n)
     # reduce j*k mod n exactly in integers before forming the angle
     jk = np.outer(j, j) % n
-    mat = np.exp(sign * 2j * np.pi * jk / n)
+    mat = np.exp(sign * 2j * np.pi * np.arange(n) / n)[jk]
     return x @ mat.T

@@ -30,7 +30,7 @@ PRECS = {"native": 0}
 EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
-    "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_winmax",
+    "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc",
 )
 
@@ -84,6 +84,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_reconstruct": (i32, [vp, vp, vp, i32, i32, vp, vp]),
         "rf_reconstruct_winmax": (i32, [vp, vp, vp, i32, i32, i64, vp, vp, vp]),
         "rf_winmax": (i32, [vp, vp, i32, i64, vp, vp, vp]),
+        "rf_reconstruct_batched": (i32, [vp, i32, P(vp), P(vp), i32, i32, i64, vp, vp, vp]),
         "rf_mf_reference_noalloc": (i32, [P(rf_grid), vp, vp, P(rf_template), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -284,6 +285,27 @@ class RatioFilter:
         _check(_lib.rf_reconstruct_winmax(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo],
                                           0, int(W), ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()),
                                           _stream(stream)))
+        return mo, ao
+
+    def reconstruct_batched(self, z_refs: Sequence, kerns: Sequence[Kernels], W: int, algo: str = "auto",
+                            max_out=None, arg_out=None, stream=None):
+        """Fused window peaks of several references' neighbours in one persistent launch.
+
+        z_refs: CUDA complex tensors of length n (one per reference); kerns: their kernel
+        sets.  Returns ([sum k, nw] float32 peaks, int32 first indices), groups in order."""
+        import torch
+        G = len(z_refs)
+        zs = [_dev(z, self.cdtype, "z_refs[g]") for z in z_refs]
+        rows = sum(k.k for k in kerns)
+        nw = -(-self.n // int(W))
+        mo = max_out if max_out is not None else torch.empty((rows, nw), dtype=torch.float32, device="cuda")
+        ao = arg_out if arg_out is not None else torch.empty((rows, nw), dtype=torch.int32, device="cuda")
+        zp = (ctypes.c_void_p * G)(*[z.data_ptr() for z in zs])
+        kp = (ctypes.c_void_p * G)(*[k.handle.value if isinstance(k.handle, ctypes.c_void_p) else k.handle
+                                     for k in kerns])
+        _check(_lib.rf_reconstruct_batched(self.handle, G, zp, kp, ALGOS[algo], 0, int(W),
+                                           ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()),
+                                           _stream(stream)))
         return mo, ao
 
     def winmax(self, z, W: int, max_out=None, arg_out=None, stream=None):

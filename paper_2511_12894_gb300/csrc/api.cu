@@ -322,6 +322,27 @@ rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels
   });
 }
 
+rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_refs, rf_kernels* const* ks,
+                                 int32_t algo, int32_t prec, int64_t W, float* max_out, int32_t* argmax_out,
+                                 rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(G >= 1, "G must be >= 1");
+    RF_REQUIRE(z_refs != nullptr && ks != nullptr, "z_refs and ks must be non-NULL host arrays");
+    RF_REQUIRE(W >= 1 && W <= ctx->n, "W=%lld must be in [1, n]", (long long)W);
+    int64_t rows = 0;
+    for (int g = 0; g < G; ++g) {
+      const int a = check_recon(ctx, z_refs[g], ks[g], algo, prec);
+      RF_REQUIRE(a == RF_ALGO_OS, "the batched form runs overlap-save (RF_F32 grid, n >= 512)");
+      rows += ks[g]->k;
+    }
+    if (!rows) return;
+    check_dev(max_out, "max_out");
+    check_dev(argmax_out, "argmax_out");
+    reconstruct_batched(ctx, G, z_refs, ks, W, max_out, argmax_out, (cudaStream_t)stream);
+  });
+}
+
 rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float* max_out, int32_t* argmax_out,
                     rf_stream stream) {
   return guard([&] {

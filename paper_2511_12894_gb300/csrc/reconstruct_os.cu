@@ -48,27 +48,45 @@ __global__ void __launch_bounds__(B / 16) k_os_segments(const float2* __restrict
     for (int t = 0; t < S::RL; ++t) out[tid + q * S::NT + t * (B / S::RL)] = v[q * S::RL + t];
 }
 
+// One neighbour's output blocks [s0, s1): spectral products, inverse block FFT, then either
+// the series (zrow != nullptr) or the window peaks (keys row kj).
+// Segment spectra of several references: block (s, g) transforms segment s of z_refs[g].
+template <int B>
+__global__ void __launch_bounds__(B / 16) k_os_segments_batched(const float2* const* __restrict__ z_refs, int64_t n,
+                                                                const float2* __restrict__ tw,
+                                                                float2* __restrict__ Zs_all) {
+  using S = BlockFFTShape<B>;
+  extern __shared__ float2 sm[];
+  constexpr int H = B / 2;
+  const int64_t s = blockIdx.x;
+  const int64_t g = blockIdx.y;
+  const int64_t NS = n / H;
+  const float2* z_ref = z_refs[g];
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  float2 v[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) v[t] = z_ref[(s * H - H + tid + t * (B / 16)) & mask];
+  block_fft<B, -1>(v, sm, tw);
+  float2* out = Zs_all + (g * NS + s) * B;
+#pragma unroll
+  for (int q = 0; q < 16 / S::RL; ++q)
+#pragma unroll
+    for (int t = 0; t < S::RL; ++t) out[tid + q * S::NT + t * (B / S::RL)] = v[q * S::RL + t];
+}
+
 template <int B, bool WINMAX>
-__global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restrict__ Zs, const float2* __restrict__ Cs,
-                                              const int64_t* __restrict__ spec_off, const int* __restrict__ parts,
-                                              const int* __restrict__ lag0, const float2* __restrict__ tw, int64_t n,
-                                              int NS, int SC, float2* __restrict__ z_out,
-                                              unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
-                                              int fastwin) {
+__device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const float2* __restrict__ C, int P,
+                                          int64_t m0, const float2* __restrict__ tw, int64_t n, int NS, int s0,
+                                          int s1, float2* __restrict__ zrow, unsigned long long* __restrict__ kj,
+                                          int64_t W, int64_t nw, int fastwin, float2* sm) {
   using S = BlockFFTShape<B>;
   constexpr int NT = S::NT;
   constexpr int H = B / 2;
   constexpr int RL = S::RL;
   constexpr int CH = H / NT;  // outputs per thread in the peak reduction (8)
-  extern __shared__ float2 sm[];
-  const int j = blockIdx.y;
-  const int P = parts[j];
-  const int64_t m0 = lag0[j];
-  const float2* C = Cs + spec_off[j];
   const int tid = threadIdx.x;
   const int64_t mask = n - 1;
-  const int s0 = blockIdx.x * SC;
-  const int s1 = min(NS, s0 + SC);
   for (int s = s0; s < s1; ++s) {
     float2 v[16];
 #pragma unroll
@@ -97,13 +115,12 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restri
     block_fft<B, +1>(v, sm, tw);
     const int64_t base = ((int64_t)s * H + m0) & mask;  // output index of block position H
     if (!WINMAX) {
-      float2* out = z_out + (int64_t)j * n;
 #pragma unroll
       for (int q = 0; q < 16 / RL; ++q)
 #pragma unroll
         for (int t = RL / 2; t < RL; ++t) {
           const int idx = tid + q * NT + t * (B / RL);  // >= H
-          out[(base + idx - H) & mask] = v[q * RL + t];
+          zrow[(base + idx - H) & mask] = v[q * RL + t];
         }
       __syncthreads();  // the next block's FFT overwrites the shared memory read above
     } else {
@@ -118,19 +135,19 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restri
           mag[idx - H] = y.x * y.x + y.y * y.y;
         }
       __syncthreads();
-      unsigned long long* kj = keys + (int64_t)j * nw;
       const int lane = tid & 31;
       const int qbase = tid * CH;
       bool slow = !fastwin;
       unsigned long long kA = 0, kB = 0;
       int64_t wA = 0, wB = 0;
+      float mv[CH];
+#pragma unroll
+      for (int e = 0; e < CH; e += 4)
+        *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + qbase + e);
       if (fastwin) {
         const int64_t i_warp = (base + (int64_t)(tid - lane) * CH) & mask;
         wA = i_warp / W;
         wB = (wA + 1 == nw) ? 0 : wA + 1;
-        float mv[CH];
-#pragma unroll
-        for (int e = 0; e < CH; e += 4) *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + qbase + e);
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
           const int64_t i = (base + qbase + e) & mask;
@@ -145,7 +162,7 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restri
       if (any_slow) {
         for (int e = 0; e < CH; ++e) {
           const int64_t i = (base + qbase + e) & mask;
-          atomicMax(kj + i / W, pack_key(mag[qbase + e], (unsigned int)i));
+          atomicMax(kj + i / W, pack_key(mv[e], (unsigned int)i));
         }
       } else {
 #pragma unroll
@@ -160,6 +177,56 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restri
       }
       __syncthreads();  // mag (shared memory) is reused by the next block's FFT
     }
+  }
+}
+
+template <int B, bool WINMAX>
+__global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restrict__ Zs, const float2* __restrict__ Cs,
+                                              const int64_t* __restrict__ spec_off, const int* __restrict__ parts,
+                                              const int* __restrict__ lag0, const float2* __restrict__ tw, int64_t n,
+                                              int NS, int SC, float2* __restrict__ z_out,
+                                              unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
+                                              int fastwin) {
+  extern __shared__ float2 sm[];
+  const int j = blockIdx.y;
+  const int s0 = blockIdx.x * SC;
+  const int s1 = min(NS, s0 + SC);
+  os_blocks<B, WINMAX>(Zs, Cs + spec_off[j], parts[j], lag0[j], tw, n, NS, s0, s1,
+                       WINMAX ? nullptr : z_out + (int64_t)j * n, WINMAX ? keys + (int64_t)j * nw : nullptr, W, nw,
+                       fastwin, sm);
+}
+
+// Batched form: neighbours of several references in one persistent launch.  Each item
+// describes one neighbour (its partition spectra, partitions, first lag, the segment
+// spectra of its reference and its output row); work units are (item, chunk of SC
+// output blocks), claimed in order from an atomic counter, so the units of one
+// reference run together and its segment spectra stay in L2.
+struct OsItem {
+  const float2* C;
+  const float2* Zs;
+  int P;
+  int lag0;
+  long long row;
+};
+
+template <int B>
+__global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* __restrict__ items, int64_t units,
+                                                                 int nchunk, const float2* __restrict__ tw, int64_t n,
+                                                                 int NS, int SC, unsigned long long* __restrict__ keys,
+                                                                 int64_t W, int64_t nw, int fastwin,
+                                                                 unsigned long long* __restrict__ counter) {
+  extern __shared__ float2 sm[];
+  __shared__ long long s_unit;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long u = s_unit;
+    __syncthreads();
+    if (u >= units) break;
+    const OsItem it = items[u / nchunk];
+    const int s0 = (int)(u % nchunk) * SC;
+    const int s1 = min(NS, s0 + SC);
+    os_blocks<B, true>(it.Zs, it.C, it.P, it.lag0, tw, n, NS, s0, s1, nullptr, keys + it.row * nw, W, nw, fastwin, sm);
   }
 }
 
@@ -220,7 +287,7 @@ void launch_os(rf_ctx* c, const rf_kernels* kern, const float2* Zs, float2* z_ou
   int SC = 8;
   while (SC > 1 && (int64_t)kern->k * ((NS + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
   const int nchunk = (NS + SC - 1) / SC;
-  const int fastwin = (WINMAX && W >= 32 * (B / 2) / (B / 16)) ? 1 : 0;  // a warp's outputs span <= 2 windows
+  const int fastwin = (WINMAX && W >= 256) ? 1 : 0;  // a warp's 256 outputs span <= 2 windows
   auto fn = k_os<B, WINMAX>;
   RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<B>()));
   int64_t done = 0;
@@ -359,6 +426,8 @@ void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s) {
   kern->os_parts = parts;
   kern->os_B = B;
   kern->os_ready = true;
+  static unsigned long long version = 0;
+  kern->os_version = ++version;
 }
 
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W) {
@@ -391,6 +460,91 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
     k_unpack_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
     RF_LAUNCHED();
   }
+}
+
+void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
+                         float* max_out, int32_t* argmax_out, cudaStream_t s) {
+  // one block size for the whole batch (the first prepared kernel set decides)
+  int B = 0;
+  for (int g = 0; g < G && !B; ++g)
+    if (ks[g]->os_ready) B = ks[g]->os_B;
+  if (!B) B = os_default_block(c);
+  for (int g = 0; g < G; ++g)
+    if (!ks[g]->os_ready || ks[g]->os_B != B) os_prepare(c, ks[g], B, s);
+  const int H = B / 2;
+  const int64_t n = c->n;
+  const int NS = (int)(n / H);
+  const int64_t nw = (n + W - 1) / W;
+  // plan key: block size, window, references and kernel sets with their spectra versions
+  std::vector<unsigned long long> key;
+  key.push_back((unsigned long long)B);
+  key.push_back((unsigned long long)W);
+  for (int g = 0; g < G; ++g) {
+    key.push_back((unsigned long long)(uintptr_t)z_refs[g]);
+    key.push_back((unsigned long long)(uintptr_t)ks[g]);
+    key.push_back(ks[g]->os_version);
+  }
+  int64_t rows = 0;
+  for (int g = 0; g < G; ++g) rows += ks[g]->k;
+  if (key != c->batch_key) {
+    std::vector<OsItem> items;
+    items.reserve((size_t)rows);
+    c->batch_zs.ensure(sizeof(float2) * (size_t)G * NS * B);
+    const float2* zs_all = c->batch_zs.as<float2>();
+    int64_t row = 0;
+    for (int g = 0; g < G; ++g) {
+      const rf_kernels* k = ks[g];
+      int64_t off = 0;
+      for (int j = 0; j < k->k; ++j) {
+        items.push_back(OsItem{k->os_spec.as<float2>() + off, zs_all + (int64_t)g * NS * B, k->os_parts[j],
+                               k->lag0[j], (long long)row++});
+        off += (int64_t)k->os_parts[j] * B;
+      }
+    }
+    std::vector<const float2*> zp(G);
+    for (int g = 0; g < G; ++g) zp[g] = static_cast<const float2*>(z_refs[g]);
+    c->batch_key.clear();
+    c->batch_items.ensure(std::max<size_t>(16, sizeof(OsItem) * items.size()));
+    c->batch_zptr.ensure(sizeof(const float2*) * G);
+    c->batch_keys.ensure(sizeof(unsigned long long) * ((size_t)rows * nw + 1));
+    if (!items.empty())
+      RF_CUDA(cudaMemcpy(c->batch_items.p, items.data(), sizeof(OsItem) * items.size(), cudaMemcpyHostToDevice));
+    RF_CUDA(cudaMemcpy(c->batch_zptr.p, zp.data(), sizeof(const float2*) * G, cudaMemcpyHostToDevice));
+    c->batch_key = key;
+    c->batch_B = B;
+    c->batch_rows = rows;
+    c->batch_nw = nw;
+  }
+  if (!rows) return;
+  unsigned long long* keys = c->batch_keys.as<unsigned long long>();
+  unsigned long long* counter = keys + rows * nw;
+  RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * ((size_t)rows * nw + 1), s));
+  int SC = 8;
+  while (SC > 1 && rows * ((NS + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
+  const int nchunk = (NS + SC - 1) / SC;
+  const int64_t units = rows * nchunk;
+  const int fastwin = (W >= 256) ? 1 : 0;  // a warp's 256 outputs span <= 2 windows
+  dispatch_b(B, [&](auto bc) {
+    constexpr int BB = decltype(bc)::value;
+    const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<BB>::LOGB];
+    auto seg = k_os_segments_batched<BB>;
+    RF_CUDA(cudaFuncSetAttribute(seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
+    RF_REQUIRE(G <= 65535, "at most 65535 references per batch");
+    seg<<<dim3((unsigned)NS, (unsigned)G), BB / 16, os_smem<BB>(), s>>>(c->batch_zptr.as<const float2*>(), n, tw,
+                                                                       c->batch_zs.as<float2>());
+    RF_LAUNCHED();
+    auto fn = k_os_batched<BB>;
+    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
+    int per_sm = 0;
+    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BB / 16, os_smem<BB>()));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * c->nsm, units));
+    fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>(), units, nchunk, tw, n, NS, SC,
+                                                      keys, W, nw, fastwin, counter);
+    RF_LAUNCHED();
+  });
+  const int64_t count = rows * nw;
+  k_unpack_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
+  RF_LAUNCHED();
 }
 
 }  // namespace rf

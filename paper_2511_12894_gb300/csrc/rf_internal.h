@@ -101,6 +101,13 @@ struct rf_ctx {
   rf::DevBuf scratch2;
   size_t reserved = 0;
   int64_t max_chunk = 0;  // builder templates per chunk
+  // Batched overlap-save plan (rf_reconstruct_batched): work items, reference pointers,
+  // segment spectra of every reference and packed window keys, kept while the same
+  // references and kernel sets come back (so repeated calls allocate and copy nothing).
+  std::vector<unsigned long long> batch_key;
+  int batch_B = 0;
+  int64_t batch_rows = 0, batch_nw = 0;
+  rf::DevBuf batch_items, batch_zptr, batch_zs, batch_keys;
 };
 
 struct rf_kernels {
@@ -118,6 +125,7 @@ struct rf_kernels {
   // and the partition spectra FFT_B(taps) / B, kernel after kernel.
   bool os_ready = false;
   int os_B = 0;
+  unsigned long long os_version = 0;  // changes whenever the spectra are rebuilt
   std::vector<int32_t> os_parts;
   rf::DevBuf os_spec;      // float2 [sum_j P_j][B]
   rf::DevBuf os_off_d;     // int64 [k+1]: element offset of kernel j's first partition spectrum
@@ -166,5 +174,7 @@ void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W);
 void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,
                     int32_t* argmax_out, cudaStream_t s);
+void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
+                         float* max_out, int32_t* argmax_out, cudaStream_t s);
 
 }  // namespace rf

@@ -390,3 +390,92 @@ def test_full_size_paper_workload_sampled(torch):
     for inj in cfg.injections:
         w = inj.sample // cfg.window
         assert abs(int(A[inj.template_index, w]) - inj.sample) <= 1
+
+
+# ---------------------------------------------------------------- batched form
+
+def _batch_cfg(n=1 << 15):
+    """Three references of the batched workload with uneven neighbour counts."""
+    base = workload.config(4, n_override=n, k_override=24)
+    rng = np.random.default_rng(44)
+    groups = []
+    for g, k in enumerate((2, 5, 3)):
+        ref = base.groups[g][0]
+        nb = workload.duration_lattice(ref, base.f_low, k, 0.05, 3.0, rng, eta_range=(0.235, 0.25), n_eta=1)
+        groups.append((ref, nb))
+    return replace(base, groups=tuple(groups), injections=(workload.Injection(1, 1, n // 2, 12.0),))
+
+
+def test_reconstruct_batched_matches_per_group_and_oracle(torch):
+    cfg = _batch_cfg()
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    ipt = torch.tensor(ip, device="cuda")
+    refs = [g[0] for g in cfg.groups]
+    z, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), ipt, refs)
+    kerns = [rf.build_ratio_kernels(r, nb, ipt, cfg.threshold) for r, nb in cfg.groups]
+    W = cfg.window
+    P, A = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W)
+    P2, A2 = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W)   # cached plan
+    assert torch.equal(P, P2) and torch.equal(A, A2)
+    row = 0
+    for g, (ref, nb) in enumerate(cfg.groups):
+        Pg, Ag = rf.reconstruct_winmax(z[g], kerns[g], W, "os")
+        assert torch.equal(P[row:row + len(nb)], Pg) and torch.equal(A[row:row + len(nb)], Ag)
+        zo, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+        pk = ratio.build_ratio_kernels(ref, nb, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip,
+                                       cfg.threshold)
+        for j in range(len(nb)):
+            zh = reconstruct.reconstruct_direct(zo, *pk.kernel(j))
+            Po, Ao = reconstruct.window_peaks(zh, W)
+            Pj, Aj = P[row + j].cpu().numpy(), A[row + j].cpu().numpy()
+            assert np.abs(Pj - Po).max() <= 4 * TOL["f32"] * Po.max()
+            _argmax_ok(zh.real ** 2 + zh.imag ** 2, Aj, Ao, W, 8 * TOL["f32"] * Po.max())
+        row += len(nb)
+    # a re-prepared kernel set (other block size) invalidates the cached plan
+    for k in kerns:
+        k.prepare(2048)
+    P3, A3 = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W)
+    assert torch.allclose(P3, P, rtol=4 * TOL["f32"], atol=4 * TOL["f32"] * P.max().item())
+
+
+def test_batched_step_captures_in_a_cuda_graph(torch):
+    """After a warm-up call, the whole online step (matched filter of every reference,
+    reference peaks, batched reconstruction) replays from a CUDA graph with the same result."""
+    cfg = _batch_cfg()
+    ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
+    x = torch.tensor(data.strain(cfg), dtype=torch.float32, device="cuda")
+    rf = _rf(cfg)
+    refs = [g[0] for g in cfg.groups]
+    kerns = [rf.build_ratio_kernels(r, nb, ip, cfg.threshold) for r, nb in cfg.groups]
+    G, n, W = len(refs), cfg.n, cfg.window
+    nw = -(-n // W)
+    z = torch.empty((G, n), dtype=torch.complex64, device="cuda")
+    sg = torch.empty(G, dtype=torch.float64, device="cuda")
+    rows = sum(k.k for k in kerns)
+    P = torch.empty((rows, nw), dtype=torch.float32, device="cuda")
+    A = torch.empty((rows, nw), dtype=torch.int32, device="cuda")
+    Pr = torch.empty((G, nw), dtype=torch.float32, device="cuda")
+    Ar = torch.empty((G, nw), dtype=torch.int32, device="cuda")
+    rf.reserve(rows)
+
+    def step():
+        rf.mf_reference(x, ip, refs, z_out=z, sigma_out=sg)
+        rf.winmax(z, W, max_out=Pr, arg_out=Ar)
+        rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, max_out=P, arg_out=A)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    P0, A0, Pr0 = P.clone(), A.clone(), Pr.clone()
+    P.zero_(); A.zero_(); Pr.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(P, P0) and torch.equal(A, A0) and torch.equal(Pr, Pr0)

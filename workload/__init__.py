@@ -206,6 +206,9 @@ def duration_lattice(ref: Template, f_low: float, k: int, dtau_min: float, dtau_
             continue
         mc = ref.mchirp * (tau_ref / tau) ** 0.6
         m1, m2 = _masses_from_mchirp_eta(mc, eta)
+        if m2 < mrange[0]:
+            # too unequal for this chirp mass: fall back to the equal-mass node
+            m1, m2 = _masses_from_mchirp_eta(mc, 0.25)
         if not (mrange[0] <= m2 <= m1 <= mrange[1]):
             continue
         out.append(Template(m1, m2))
@@ -266,6 +269,8 @@ def config(i: int, n_override: Optional[int] = None, k_override: Optional[int] =
         groups = []
         for g in range(n_ref):
             m1, m2 = _masses_from_mchirp_eta(mcs[g], rb.uniform(0.235, 0.25))
+            if m2 < 1.0:  # keep both components in 1-3 M_sun
+                m1, m2 = _masses_from_mchirp_eta(mcs[g], 0.25)
             ref = Template(m1, m2)
             k = int(rb.integers(32, 513)) if k_override is None else max(2, k_override)
             nb = duration_lattice(ref, 20.0, k, 0.02, 30.0, rb, eta_range=(0.18, 0.25))
