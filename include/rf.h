@@ -66,12 +66,22 @@ typedef enum { RF_F64 = 0, RF_F32 = 1 } rf_dtype;
 typedef enum {
   RF_ALGO_AUTO = 0,
   RF_ALGO_DIRECT = 1,    /* direct time-domain sum on CUDA cores (Eq. 8) */
-  RF_ALGO_OS = 2         /* overlap-save block FFT (frequency form, Eq. 7), FP32 */
+  RF_ALGO_OS = 2,        /* overlap-save block FFT (frequency form, Eq. 7), FP32 */
+  RF_ALGO_GEMM = 3       /* direct sum as a Hankel x taps complex GEMM on the tcgen05 tensor
+                            cores (kernels of at most 512 taps, n a multiple of 128) */
 } rf_algo;
 
-/* Arithmetic of the reconstruction.  FP32: CUDA-core FP32 (RF_F32) or FP64 (RF_F64). */
+/* Arithmetic of the reconstruction.  RF_PREC_NATIVE: the grid dtype on CUDA cores (direct,
+ * overlap-save).  The tensor-core form (RF_ALGO_GEMM) splits every z_ref and tap value into
+ * BF16 terms x = x0 + x1 + x2 (x_k = bf16 of the remainder) and accumulates in FP32:
+ * RF_PREC_BF16 keeps x0 y0 (plain BF16, about 3 significant digits), RF_PREC_BF16X3 adds
+ * x0 y1 + x1 y0, RF_PREC_BF16X6 adds x0 y2 + x1 y1 + x2 y0, RF_PREC_BF16X9 all nine products. */
 typedef enum {
-  RF_PREC_NATIVE = 0
+  RF_PREC_NATIVE = 0,
+  RF_PREC_BF16 = 1,
+  RF_PREC_BF16X3 = 2,
+  RF_PREC_BF16X6 = 3,
+  RF_PREC_BF16X9 = 4
 } rf_prec;
 
 /* A non-spinning stationary-phase inspiral (App. A, Eq. A1): h(f) = B(f) exp(-i Psi(f)),
@@ -200,6 +210,11 @@ rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels
 rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_refs, rf_kernels* const* ks,
                                  int32_t algo, int32_t prec, int64_t W, float* max_out,
                                  int32_t* argmax_out, rf_stream stream);
+
+/* Device-side status of the context: waits for the device, then returns RF_OK, or
+ * RF_ETIMEOUT if a bounded device-side wait of an earlier call ran out (that call's outputs
+ * are then incomplete), and clears it. */
+rf_status rf_device_status(rf_ctx* ctx);
 
 /* Window peaks of `count` series already in memory (e.g. z_ref itself): z: complex[count][n];
  * max_out/argmax_out: [count][ceil(n/W)], same definition as rf_reconstruct_winmax. */

@@ -24,14 +24,14 @@ LIB_PATH = os.path.join(HERE, "librf.so")
 
 RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ETIMEOUT, RF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 RF_F64, RF_F32 = 0, 1
-ALGOS = {"auto": 0, "direct": 1, "os": 2}
-PRECS = {"native": 0}
+ALGOS = {"auto": 0, "direct": 1, "os": 2, "gemm": 3}
+PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
 
 EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
-    "rf_mf_reference_noalloc",
+    "rf_mf_reference_noalloc", "rf_device_status",
 )
 
 
@@ -86,6 +86,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_winmax": (i32, [vp, vp, i32, i64, vp, vp, vp]),
         "rf_reconstruct_batched": (i32, [vp, i32, P(vp), P(vp), i32, i32, i64, vp, vp, vp]),
         "rf_mf_reference_noalloc": (i32, [P(rf_grid), vp, vp, P(rf_template), vp, vp, vp]),
+        "rf_device_status": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -265,17 +266,21 @@ class RatioFilter:
                                       ctypes.c_void_p(taps.ctypes.data), ctypes.byref(h)))
         return self._wrap_kernels(h)
 
-    def reconstruct(self, z_ref, kern: Kernels, algo: str = "auto", out=None, stream=None):
+    def reconstruct(self, z_ref, kern: Kernels, algo: str = "auto", out=None, stream=None, prec: str = "native"):
         """Neighbour SNR series [k, n] (Eq. 8)."""
         import torch
         z_ref = _dev(z_ref, self.cdtype, "z_ref")
         out = out if out is not None else torch.empty((kern.k, self.n), dtype=self.cdtype, device="cuda")
-        _check(_lib.rf_reconstruct(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo], 0,
-                                   ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        _check(_lib.rf_reconstruct(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo],
+                                   PRECS[prec], ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
 
+    def device_status(self) -> None:
+        """Raise if a bounded device-side wait of an earlier call ran out (synchronises)."""
+        _check(_lib.rf_device_status(self.handle))
+
     def reconstruct_winmax(self, z_ref, kern: Kernels, W: int, algo: str = "auto", max_out=None, arg_out=None,
-                           stream=None):
+                           stream=None, prec: str = "native"):
         """Per-window max|z|^2 [k, nw] (float32) and its first index (int32)."""
         import torch
         z_ref = _dev(z_ref, self.cdtype, "z_ref")
@@ -283,8 +288,8 @@ class RatioFilter:
         mo = max_out if max_out is not None else torch.empty((kern.k, nw), dtype=torch.float32, device="cuda")
         ao = arg_out if arg_out is not None else torch.empty((kern.k, nw), dtype=torch.int32, device="cuda")
         _check(_lib.rf_reconstruct_winmax(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo],
-                                          0, int(W), ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()),
-                                          _stream(stream)))
+                                          PRECS[prec], int(W), ctypes.c_void_p(mo.data_ptr()),
+                                          ctypes.c_void_p(ao.data_ptr()), _stream(stream)))
         return mo, ao
 
     def reconstruct_batched(self, z_refs: Sequence, kerns: Sequence[Kernels], W: int, algo: str = "auto",

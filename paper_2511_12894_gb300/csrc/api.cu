@@ -147,6 +147,8 @@ rf_status rf_create(const rf_grid* grid, rf_ctx** out) {
     c->fa.ensure(esz * n);
     c->fb.ensure(esz * n);
     c->red.ensure(sizeof(double) * 1024);
+    c->status.ensure(sizeof(int) * 4);
+    RF_CUDA(cudaMemset(c->status.p, 0, sizeof(int) * 4));
     *out = c.release();
   });
 }
@@ -282,8 +284,18 @@ static int check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, i
   RF_REQUIRE(kern != nullptr, "kern is NULL");
   RF_REQUIRE(kern->n == ctx->n && kern->dtype == ctx->g.dtype, "kernels were made for another grid");
   check_dev(z_ref, "z_ref");
-  RF_REQUIRE(algo == RF_ALGO_AUTO || algo == RF_ALGO_DIRECT || algo == RF_ALGO_OS, "unknown algo %d", algo);
-  RF_REQUIRE(prec == RF_PREC_NATIVE, "unknown prec %d", prec);
+  RF_REQUIRE(algo == RF_ALGO_AUTO || algo == RF_ALGO_DIRECT || algo == RF_ALGO_OS || algo == RF_ALGO_GEMM,
+             "unknown algo %d", algo);
+  RF_REQUIRE(prec >= RF_PREC_NATIVE && prec <= RF_PREC_BF16X9, "unknown prec %d", prec);
+  if (algo == RF_ALGO_GEMM) {
+    RF_REQUIRE(prec != RF_PREC_NATIVE, "the tensor-core form needs a split precision (RF_PREC_BF16*)");
+    if (kern->max_len > gemm_max_len() || ctx->n % 128 != 0) {
+      set_error("the tensor-core form takes kernels of at most %d taps and n a multiple of 128", gemm_max_len());
+      throw Fail{RF_EUNSUPPORTED};
+    }
+    return algo;
+  }
+  RF_REQUIRE(prec == RF_PREC_NATIVE, "split precisions apply to RF_ALGO_GEMM only");
   const bool os_ok = ctx->g.dtype == RF_F32 && ctx->n >= 512;
   if (algo == RF_ALGO_OS && !os_ok) {
     set_error("overlap-save needs an RF_F32 grid with n >= 512");
@@ -300,6 +312,9 @@ rf_status rf_reconstruct(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern,
     if (kern->k) check_dev(z_out, "z_out");
     if (a == RF_ALGO_OS)
       reconstruct_os(ctx, z_ref, const_cast<rf_kernels*>(kern), z_out, 0, nullptr, nullptr, (cudaStream_t)stream);
+    else if (a == RF_ALGO_GEMM)
+      reconstruct_gemm(ctx, z_ref, const_cast<rf_kernels*>(kern), prec, z_out, 0, nullptr, nullptr,
+                       (cudaStream_t)stream);
     else
       reconstruct_direct(ctx, z_ref, kern, z_out, 0, nullptr, nullptr, (cudaStream_t)stream);
   });
@@ -317,6 +332,9 @@ rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels
     if (a == RF_ALGO_OS)
       reconstruct_os(ctx, z_ref, const_cast<rf_kernels*>(kern), nullptr, W, max_out, argmax_out,
                      (cudaStream_t)stream);
+    else if (a == RF_ALGO_GEMM)
+      reconstruct_gemm(ctx, z_ref, const_cast<rf_kernels*>(kern), prec, nullptr, W, max_out, argmax_out,
+                       (cudaStream_t)stream);
     else
       reconstruct_direct(ctx, z_ref, kern, nullptr, W, max_out, argmax_out, (cudaStream_t)stream);
   });
@@ -341,6 +359,22 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
     check_dev(argmax_out, "argmax_out");
     reconstruct_batched(ctx, G, z_refs, ks, W, max_out, argmax_out, (cudaStream_t)stream);
   });
+}
+
+rf_status rf_device_status(rf_ctx* ctx) {
+  rf_status out = RF_OK;
+  const rf_status st = guard([&] {
+    check_ctx(ctx);
+    RF_CUDA(cudaDeviceSynchronize());
+    int v = 0;
+    RF_CUDA(cudaMemcpy(&v, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) {
+      RF_CUDA(cudaMemset(ctx->status.p, 0, sizeof(int)));
+      set_error("a bounded device-side wait ran out (status %d)", v);
+      out = (rf_status)v;
+    }
+  });
+  return st != RF_OK ? st : out;
 }
 
 rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float* max_out, int32_t* argmax_out,

@@ -1,0 +1,445 @@
+// Direct reconstruction (Eq. 8) as a complex GEMM on the tcgen05 tensor cores, with
+// split-BF16 operands and FP32 accumulation in tensor memory.
+//
+// For a tile of 128 outputs i' = i0 + m and a group of NJ neighbours whose taps are padded
+// to LP (a multiple of 16), with taps read in reverse (t = LP - 1 - l):
+//   w_j[i0 + m] = sum_t z[b + m + t] c_j[LP - 1 - t],   b = i0 - LP + 1,
+// a Hankel matrix A[m][t] = z[b + m + t] times the tap matrix.  Real and imaginary planes
+// give two real products per output column pair (re, im):
+//   D[m][2j]   = sum_t zr A_t cr_j - zi A_t ci_j,    D[m][2j+1] = sum_t zr ci_j + zi cr_j,
+// i.e. D = A_r B_r + A_i B_i with B_r = [cr ci], B_i = [-ci cr] per neighbour.
+//
+// The Hankel operand is never expanded: in the no-swizzle K-major layout an 8x8 BF16 core
+// matrix (8 rows of 16 bytes) at row block r and K block q holds z[b + 8(r + q) + a + e]
+// (a, e < 8), which depends on r + q only.  Shared memory keeps the distinct core matrices
+// H_d, d = r + q, back to back, and the descriptor uses the same 128-byte stride for the M
+// and K directions.
+//
+// Split precision: x = x0 + x1 + x2 with x_k = bf16(x - x0 - ... - x_{k-1}); the products
+// kept are (0,0) for BF16, + (0,1),(1,0) for x3, + (0,2),(1,1),(2,0) for x6, + (1,2),(2,1),(2,2)
+// for x9.  The tensor core's FP32 accumulation loses a fraction of an ulp of the running
+// sum at every MMA, so each chunk of GEMM_CK K steps accumulates into its own tensor-memory
+// tiles, one for the leading product (0,0) and one for the corrections; the epilogue adds
+// the tiles in FP32 registers (round to nearest).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <memory>
+
+#include "cplx.cuh"
+#include "rf_internal.h"
+
+namespace rf {
+
+namespace {
+
+constexpr int kGemmThreads = 128;
+constexpr int kGemmM = 128;
+constexpr int kGemmCK = 4;  // K steps (of 16 taps) per accumulator chunk
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: no swizzle, K-major, relative offsets.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 A and B (K-major), FP32 D, M = 128, N.
+__host__ __device__ constexpr uint32_t mma_idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kGemmM >> 4) << 24);
+}
+
+template <typename R>
+__device__ __forceinline__ void split3(R v, __nv_bfloat16& s0, __nv_bfloat16& s1, __nv_bfloat16& s2) {
+  s0 = __float2bfloat16_rn((float)v);
+  const R r1 = v - (R)__bfloat162float(s0);
+  s1 = __float2bfloat16_rn((float)r1);
+  const R r2 = r1 - (R)__bfloat162float(s1);
+  s2 = __float2bfloat16_rn((float)r2);
+}
+
+// Product pairs (A term, B term) of each precision, in issue order.
+__host__ __device__ constexpr int prec_products(int prec) {
+  return prec == RF_PREC_BF16 ? 1 : prec == RF_PREC_BF16X3 ? 3 : prec == RF_PREC_BF16X6 ? 6 : 9;
+}
+__host__ __device__ constexpr int prec_terms(int prec) {
+  return prec == RF_PREC_BF16 ? 1 : prec == RF_PREC_BF16X3 ? 2 : 3;
+}
+__device__ __forceinline__ void prec_pair(int q, int& a, int& b) {
+  constexpr int pa[9] = {0, 0, 1, 0, 1, 2, 1, 2, 2};
+  constexpr int pb[9] = {0, 1, 0, 2, 1, 0, 2, 1, 2};
+  a = pa[q];
+  b = pb[q];
+}
+
+// B operand of one neighbour group, prepared once per kernel set:
+// [plane (r, i)][term][N/8 row blocks][LP/8 K blocks][8 rows][8 BF16] with the taps in
+// reverse, columns (2j, 2j+1) = (re, im) of neighbour j of the group.
+template <typename V>
+__global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restrict__ off, const int* __restrict__ len,
+                              int k, int NJ, int LP, int terms, __nv_bfloat16* __restrict__ out) {
+  using R = typename real_of<V>::type;
+  const int g = blockIdx.y;
+  const int N = 2 * NJ;
+  const int64_t per_plane_term = (int64_t)N * LP;
+  __nv_bfloat16* og = out + (int64_t)g * 2 * terms * per_plane_term;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)N * LP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(e / LP), t = (int)(e % LP);
+    const int j = g * NJ + col / 2;
+    R cr = 0, ci = 0;
+    if (j < k) {
+      const int l = LP - 1 - t;
+      if (l < len[j]) {
+        const V c = taps[off[j] + l];
+        cr = c.x;
+        ci = c.y;
+      }
+    }
+    // plane r: (re, im) columns take (cr, ci); plane i: (-ci, cr)
+    const R vr = (col & 1) ? ci : cr;
+    const R vi = (col & 1) ? cr : -ci;
+    __nv_bfloat16 r0, r1, r2, i0, i1, i2;
+    split3<R>(vr, r0, r1, r2);
+    split3<R>(vi, i0, i1, i2);
+    const int64_t pos = (int64_t)(col / 8) * (LP / 8) * 64 + (t / 8) * 64 + (col % 8) * 8 + (t % 8);
+    const __nv_bfloat16 rr[3] = {r0, r1, r2}, ii[3] = {i0, i1, i2};
+    for (int s = 0; s < terms; ++s) {
+      og[(0 * terms + s) * per_plane_term + pos] = rr[s];
+      og[(1 * terms + s) * per_plane_term + pos] = ii[s];
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long gemm_key(float v, unsigned int i) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - i);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// One block: TM consecutive 128-output tiles of one neighbour group.
+template <typename V, int NJ, int PREC, bool WINMAX>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ z_ref, int64_t n,
+                                                          const __nv_bfloat16* __restrict__ Bg, int LP, int k,
+                                                          const int* __restrict__ lag0, int TM, V* __restrict__ z_out,
+                                                          unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
+                                                          int tmem_cols, int* __restrict__ status) {
+  using R = typename real_of<V>::type;
+  constexpr int N = 2 * NJ;
+  constexpr int TERMS = prec_terms(PREC);
+  constexpr int NPROD = prec_products(PREC);
+  static_assert(N == 16 || N == 32, "neighbours per group");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = blockIdx.y;
+  const int nH = 15 + LP / 8;                         // distinct Hankel core matrices
+  const int a_bytes = nH * 128;                       // per (plane, term)
+  const int b_bytes = N * LP * 2;                     // per (plane, term)
+  unsigned char* sA = smem;                           // [plane][term][nH][128 B]
+  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][N*LP BF16]
+  const int64_t mask = n - 1;
+
+  // B operand of the group, once per block (16-byte copies)
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Bg + (int64_t)g * 2 * TERMS * N * LP);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    const int cnt = 2 * TERMS * b_bytes / 16;
+    for (int e = tid; e < cnt; e += kGemmThreads) dst[e] = src[e];
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const int nchunk = (LP / 16 + kGemmCK - 1) / kGemmCK;
+  const int nacc = (NPROD > 1 ? 2 : 1) * nchunk;  // accumulator tiles of N columns
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = mma_idesc_bf16(N);
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int tile = 0; tile < TM && ok; ++tile) {
+    const int64_t i0 = ((int64_t)blockIdx.x * TM + tile) * kGemmM;
+    if (i0 >= n) break;
+    const int64_t b = i0 - LP + 1;
+    // Hankel core matrices: row a of H_d is z[b + 8d + a + e], e < 8, for each plane and term
+    for (int row = tid; row < nH * 8; row += kGemmThreads) {
+      const int d = row >> 3, a = row & 7;
+      __nv_bfloat16 hr[3][8], hi[3][8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const V v = z_ref[(b + 8 * d + a + e) & mask];
+        split3<R>(v.x, hr[0][e], hr[1][e], hr[2][e]);
+        split3<R>(v.y, hi[0][e], hi[1][e], hi[2][e]);
+      }
+#pragma unroll
+      for (int s = 0; s < TERMS; ++s) {
+        *reinterpret_cast<uint4*>(sA + (0 * TERMS + s) * a_bytes + d * 128 + a * 16) =
+            *reinterpret_cast<const uint4*>(hr[s]);
+        *reinterpret_cast<uint4*>(sA + (1 * TERMS + s) * a_bytes + d * 128 + a * 16) =
+            *reinterpret_cast<const uint4*>(hi[s]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int ks = 0; ks < LP / 16; ++ks) {
+        const int ch = ks / kGemmCK;
+        const bool chunk_start = (ks % kGemmCK) == 0;
+        for (int pl = 0; pl < 2; ++pl)
+          for (int q = 0; q < NPROD; ++q) {
+            int ta, tb;
+            prec_pair(q, ta, tb);
+            const uint64_t ad = smem_desc(smem_u32(sA + (pl * TERMS + ta) * a_bytes) + ks * 256, 128, 128);
+            const uint64_t bd = smem_desc(smem_u32(sB + (pl * TERMS + tb) * b_bytes) + ks * 256, 128, LP * 16);
+            // tile: leading product of chunk ch, or its corrections
+            const int tile_idx = (NPROD > 1 ? 2 * ch : ch) + (q > 0 ? 1 : 0);
+            const uint32_t d = tmem + (uint32_t)(tile_idx * N);
+            const bool first = chunk_start && pl == 0 && q <= 1;  // q == 0 / 1 open their tiles
+            const uint32_t acc = first ? 0u : 1u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)) : "memory");
+    }
+    // bounded wait for the tile's MMAs
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
+    }
+    phase ^= 1u;
+    if (!__syncthreads_and(done)) {
+      if (tid == 0) atomicExch(status, (int)RF_ETIMEOUT);
+      ok = false;
+      // give the tile's MMAs one more bounded wait before tensor memory is released
+      uint32_t late = 0;
+      for (int it = 0; it < (1 << 24) && !late; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(late) : "r"(smem_u32(&mbar)), "r"(phase ^ 1u) : "memory");
+      }
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w holds rows 32w..32w+31, thread = one row, all N columns
+    // sum the accumulator tiles of this row: corrections first, then the leading products
+    float r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int h = 0; h < N / 16; ++h) {
+      float big[16], small[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) big[c] = small[c] = 0.f;
+      for (int t = 0; t < nacc; ++t) {
+        uint32_t v[16];
+        tmem_ld16(taddr + (uint32_t)(t * N + 16 * h), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const bool is_small = (NPROD > 1) && (t & 1);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          if (is_small) small[c] += __uint_as_float(v[c]);
+          else big[c] += __uint_as_float(v[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) r[16 * h + c] = big[c] + small[c];
+    }
+    const int64_t ip = i0 + warp * 32 + lane;  // i'
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      const int j = g * NJ + jj;
+      if (j >= k) break;  // uniform across the block
+      const float re = r[2 * jj], im = r[2 * jj + 1];
+      const int64_t i = (ip + lag0[j]) & mask;
+      if (!WINMAX) {
+        z_out[(int64_t)j * n + i] = cmake<V>((R)re, (R)im);
+      } else {
+        const unsigned long long key = gemm_key(re * re + im * im, (unsigned int)i);
+        unsigned long long* kj = keys + (int64_t)j * nw;
+        const int64_t i_lane0 = __shfl_sync(0xffffffffu, i, 0);
+        const int64_t wA = i_lane0 / W;
+        const int64_t wB = (wA + 1 == nw) ? 0 : wA + 1;
+        const int64_t w = i / W;
+        const bool slow = !(w == wA || w == wB);
+        if (__any_sync(0xffffffffu, slow)) {
+          atomicMax(kj + w, key);
+        } else {
+          unsigned long long kA = (w == wA) ? key : 0ull, kB = (w == wB) ? key : 0ull;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
+            kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
+          }
+          if (lane == 0) {
+            if (kA) atomicMax(kj + wA, kA);
+            if (kB) atomicMax(kj + wB, kB);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // TMEM and the Hankel tiles are reused by the next tile
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+__global__ void k_gemm_unpack(const unsigned long long* __restrict__ keys, int64_t count, float* __restrict__ mx,
+                              int* __restrict__ arg) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const unsigned long long kk = keys[i];
+  mx[i] = __uint_as_float((unsigned int)(kk >> 32));
+  arg[i] = (int)(0xffffffffu - (unsigned int)(kk & 0xffffffffull));
+}
+
+size_t gemm_smem_bytes(int terms, int NJ, int LP) {
+  const int nH = 15 + LP / 8;
+  return (size_t)2 * terms * nH * 128 + (size_t)2 * terms * (2 * NJ) * LP * 2 + 1024;
+}
+
+// Tensor-memory columns: accumulator tiles of N columns, rounded up to a power of two >= 32.
+int gemm_tmem_cols(int prec, int NJ, int LP) {
+  const int nchunk = (LP / 16 + kGemmCK - 1) / kGemmCK;
+  const int need = (prec_products(prec) > 1 ? 2 : 1) * nchunk * 2 * NJ;
+  int cols = 32;
+  while (cols < need) cols *= 2;
+  return cols;
+}
+
+template <typename V, int NJ, int PREC, bool WINMAX>
+void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, unsigned long long* keys, int64_t W,
+                 int64_t nw, cudaStream_t s) {
+  const int LP = kern->gemm_LP;
+  const int cols = gemm_tmem_cols(PREC, NJ, LP);
+  RF_REQUIRE(cols <= 512, "tensor-core form: %d tensor-memory columns needed", cols);
+  // shared memory sized so that the blocks resident on one SM never ask for more than the
+  // 512 tensor-memory columns of the SM (an allocation would otherwise wait for a release)
+  const size_t smem_max = 227 * 1024;
+  const int max_blocks = 512 / cols;
+  size_t smem = gemm_smem_bytes(prec_terms(PREC), NJ, LP);
+  smem = std::max(smem, smem_max / (size_t)(max_blocks + 1) + 1024);
+  smem = std::min(smem, (size_t)220 * 1024);
+  auto fn = k_gemm<V, NJ, PREC, WINMAX>;
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGemmThreads, smem));
+  RF_REQUIRE(per_sm * cols <= 512, "tensor-core form: %d blocks per SM x %d columns exceed tensor memory", per_sm,
+             cols);
+  const int64_t tiles = c->n / kGemmM;
+  const int groups = (kern->k + NJ - 1) / NJ;
+  int TM = 1;
+  while (TM < 16 && (tiles / (TM * 2)) * groups >= 4LL * c->nsm) TM *= 2;
+  dim3 grid((unsigned)((tiles + TM - 1) / TM), (unsigned)groups);
+  fn<<<grid, kGemmThreads, smem, s>>>(z_ref, c->n, kern->gemm_B.as<__nv_bfloat16>(), LP, kern->k,
+                                      kern->lag0_d.as<int>(), TM, z_out, keys, W, nw, cols, c->status.as<int>());
+  RF_LAUNCHED();
+}
+
+template <typename V, int NJ, bool WINMAX>
+void launch_gemm_prec(rf_ctx* c, const rf_kernels* kern, int prec, const V* z_ref, V* z_out,
+                      unsigned long long* keys, int64_t W, int64_t nw, cudaStream_t s) {
+  switch (prec) {
+    case RF_PREC_BF16: launch_gemm<V, NJ, RF_PREC_BF16, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    case RF_PREC_BF16X3: launch_gemm<V, NJ, RF_PREC_BF16X3, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    case RF_PREC_BF16X6: launch_gemm<V, NJ, RF_PREC_BF16X6, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    default: launch_gemm<V, NJ, RF_PREC_BF16X9, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+  }
+}
+
+}  // namespace
+
+int gemm_max_len() { return 512; }
+
+void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
+  RF_REQUIRE(kern->max_len <= gemm_max_len(), "the tensor-core direct form takes kernels of at most %d taps (got %d)",
+             gemm_max_len(), kern->max_len);
+  const int terms = prec_terms(prec);
+  const int LP = std::max(16, (kern->max_len + 15) / 16 * 16);
+  int NJ = 16;
+  if (gemm_smem_bytes(terms, NJ, LP) > 220 * 1024) NJ = 8;
+  RF_REQUIRE(gemm_smem_bytes(terms, NJ, LP) <= 220 * 1024, "tensor-core direct form: %d taps do not fit", LP);
+  if (kern->gemm_ready && kern->gemm_terms == terms && kern->gemm_LP == LP && kern->gemm_NJ == NJ) return;
+  const int groups = std::max(1, (kern->k + NJ - 1) / NJ);
+  const size_t elems = (size_t)groups * 2 * terms * (2 * NJ) * LP;
+  kern->gemm_B.ensure(sizeof(__nv_bfloat16) * std::max<size_t>(elems, 8));
+  dim3 grid((unsigned)std::max<int64_t>(1, (2 * NJ * LP + 255) / 256), (unsigned)groups);
+  if (kern->dtype == RF_F64)
+    k_gemm_prep_b<double2><<<grid, 256, 0, s>>>(kern->taps.as<double2>(), kern->off_d.as<int64_t>(),
+                                                kern->len_d.as<int>(), kern->k, NJ, LP, terms,
+                                                kern->gemm_B.as<__nv_bfloat16>());
+  else
+    k_gemm_prep_b<float2><<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(),
+                                               kern->len_d.as<int>(), kern->k, NJ, LP, terms,
+                                               kern->gemm_B.as<__nv_bfloat16>());
+  RF_LAUNCHED();
+  RF_CUDA(cudaStreamSynchronize(s));
+  kern->gemm_ready = true;
+  kern->gemm_terms = terms;
+  kern->gemm_LP = LP;
+  kern->gemm_NJ = NJ;
+}
+
+void reconstruct_gemm(rf_ctx* c, const void* z_ref, rf_kernels* kern, int prec, void* z_out, int64_t W,
+                      float* max_out, int32_t* argmax_out, cudaStream_t s) {
+  if (kern->k == 0) return;
+  RF_REQUIRE(c->n % kGemmM == 0, "the tensor-core direct form needs n to be a multiple of 128");
+  gemm_prepare(c, kern, prec, s);  // no-op when the kernel set is prepared for this precision
+  const bool win = max_out != nullptr;
+  const int64_t nw = win ? (c->n + W - 1) / W : 0;
+  unsigned long long* keys = nullptr;
+  if (win) {
+    c->scratch.ensure(sizeof(unsigned long long) * (size_t)kern->k * nw + 256);
+    keys = c->scratch.as<unsigned long long>();
+    RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)kern->k * nw, s));
+  }
+  auto go = [&](auto vtag) {
+    using V = decltype(vtag);
+    const V* zr = static_cast<const V*>(z_ref);
+    V* zo = static_cast<V*>(z_out);
+    if (kern->gemm_NJ == 16) {
+      if (win) launch_gemm_prec<V, 16, true>(c, kern, prec, zr, nullptr, keys, W, nw, s);
+      else launch_gemm_prec<V, 16, false>(c, kern, prec, zr, zo, nullptr, 0, 0, s);
+    } else {
+      if (win) launch_gemm_prec<V, 8, true>(c, kern, prec, zr, nullptr, keys, W, nw, s);
+      else launch_gemm_prec<V, 8, false>(c, kern, prec, zr, zo, nullptr, 0, 0, s);
+    }
+  };
+  if (c->g.dtype == RF_F64) go(double2{});
+  else go(float2{});
+  if (win) {
+    const int64_t count = (int64_t)kern->k * nw;
+    k_gemm_unpack<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
+    RF_LAUNCHED();
+  }
+}
+
+}  // namespace rf

@@ -99,6 +99,7 @@ struct rf_ctx {
   rf::DevBuf red;      // FP64 reduction scratch
   rf::DevBuf scratch;  // growable: packed window keys, OS block spectra, builder chunks
   rf::DevBuf scratch2;
+  rf::DevBuf status;   // int: device-side error status (RF_ETIMEOUT from bounded waits), 0 if none
   size_t reserved = 0;
   int64_t max_chunk = 0;  // builder templates per chunk
   // Batched overlap-save plan (rf_reconstruct_batched): work items, reference pointers,
@@ -130,6 +131,11 @@ struct rf_kernels {
   rf::DevBuf os_spec;      // float2 [sum_j P_j][B]
   rf::DevBuf os_off_d;     // int64 [k+1]: element offset of kernel j's first partition spectrum
   rf::DevBuf os_parts_d;   // int32 [k]
+  // Tensor-core direct form: split-BF16 tap operands per group of gemm_NJ neighbours,
+  // taps padded to gemm_LP (see reconstruct_gemm.cu).
+  bool gemm_ready = false;
+  int gemm_terms = 0, gemm_LP = 0, gemm_NJ = 0;
+  rf::DevBuf gemm_B;
 };
 
 namespace rf {
@@ -176,5 +182,10 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
                     int32_t* argmax_out, cudaStream_t s);
 void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
                          float* max_out, int32_t* argmax_out, cudaStream_t s);
+// tensor-core direct form (reconstruct_gemm.cu); kernels of at most gemm_max_len() taps
+int gemm_max_len();
+void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s);
+void reconstruct_gemm(rf_ctx* c, const void* z_ref, rf_kernels* kern, int prec, void* z_out, int64_t W,
+                      float* max_out, int32_t* argmax_out, cudaStream_t s);
 
 }  // namespace rf

@@ -479,3 +479,74 @@ def test_batched_step_captures_in_a_cuda_graph(torch):
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(P, P0) and torch.equal(A, A0) and torch.equal(Pr, Pr0)
+
+
+# ---------------------------------------------------------------- tensor-core direct form
+
+# Error bars of the split-BF16 products relative to max|z| (x = x0 + x1 + x2, u = 2^-9 the BF16
+# unit roundoff of each term): the dropped products are O(u) for BF16, O(u^2) for x3, and O(u^3)
+# for x6/x9, where the FP32 accumulation (about 1e-7 of the running sum) dominates.
+GEMM_TOL = {"bf16": 2e-2, "bf16x3": 2e-4, "bf16x6": 2e-6, "bf16x9": 2e-6}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_reconstruct_gemm_edge_lengths(torch, dtype):
+    n = 1 << 13
+    rng = np.random.default_rng(17)
+    lengths = [1, 2, 15, 16, 17, 100, 255, 256, 257, 384, 0, 500, 31]
+    lags = [0, -5, 37, n // 2, -(n // 2) + 1, 100, -1000, 3, 2000, -2, 5, 11, -n // 4]
+    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype=dtype)
+    rf = _rf(cfg)
+    cdt = np.complex64 if dtype == "f32" else np.complex128
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(cdt)
+    taps = [((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(max(L, 1))).astype(cdt)
+            for L in lengths]
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    zt = torch.tensor(z, device="cuda")
+    zo = [reconstruct.reconstruct_direct(z.astype(np.complex128), lags[j], taps[j].astype(np.complex128))
+          for j in range(len(lengths))]
+    errs = {}
+    for prec, tol in GEMM_TOL.items():
+        out = rf.reconstruct(zt, kern, "gemm", prec=prec).cpu().numpy()
+        rf.device_status()
+        worst = 0.0
+        for j, L in enumerate(lengths):
+            if L == 0:
+                assert np.abs(out[j]).max() == 0.0
+                continue
+            worst = max(worst, _relerr(out[j], zo[j]))
+        errs[prec] = worst
+        assert worst < tol, (prec, worst)
+        P, A = rf.reconstruct_winmax(zt, kern, 1000, "gemm", prec=prec)
+        P, A = P.cpu().numpy(), A.cpu().numpy()
+        for j, L in enumerate(lengths):
+            if L == 0:
+                continue
+            Po, Ao = reconstruct.window_peaks(zo[j], 1000)
+            assert np.abs(P[j] - Po).max() <= 4 * tol * Po.max()
+            _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, 1000, 8 * tol * Po.max())
+    # each extra set of products improves the result
+    assert errs["bf16x3"] < errs["bf16"] / 10 and errs["bf16x6"] < errs["bf16x3"] / 10
+
+
+def test_reconstruct_gemm_precision_form_workload(torch):
+    """The precision-form workload: the FP64 small configuration's data and bank through the
+    tensor-core form, every split precision against the FP64 oracle."""
+    cfg = workload.config(3)
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    ipt = torch.tensor(ip, device="cuda")
+    z, _ = rf.mf_reference(torch.tensor(x, device="cuda"), ipt, [ref])
+    kern = rf.build_ratio_kernels(ref, nb, ipt, cfg.threshold)
+    zo, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    pk = ratio.build_ratio_kernels(ref, nb, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, cfg.threshold)
+    zh = [reconstruct.reconstruct_direct(zo, *pk.kernel(j)) for j in range(len(nb))]
+    for prec, tol in GEMM_TOL.items():
+        out = rf.reconstruct(z[0], kern, "gemm", prec=prec).cpu().numpy()
+        worst = max(_relerr(out[j], zh[j]) for j in range(len(nb)))
+        assert worst < tol, (prec, worst)
+    P, A = rf.reconstruct_winmax(z[0], kern, cfg.window, "gemm", prec="bf16x6")
+    inj = cfg.injections[0]
+    assert A[inj.template_index, inj.sample // cfg.window].item() == inj.sample
