@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2)
-    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "os"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "os", "gemm"])
+    ap.add_argument("--prec", default=None, choices=["native", "bf16", "bf16x3", "bf16x6", "bf16x9"],
+                    help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default 8192)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
@@ -218,6 +220,23 @@ def cpu_baseline(cfg, n_nbrs=4, slice_len=1 << 12, budget_s=20.0):
     }
 
 
+# --------------------------------------------------------------------------- ncu traffic
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
+    kernel's sources changed since that capture (or no capture exists)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+        m = hashlib.sha256()
+        for f in rec["sources"]:
+            m.update(open(os.path.join(ROOT, "paper_2511_12894_gb300", "csrc", f), "rb").read())
+        return rec["traffic_bytes_per_launch"] if m.hexdigest() == rec["sha256"] else None
+    except Exception:
+        return None
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args):
@@ -292,9 +311,11 @@ def main():
     if algo_used == "os":
         rf.reserve(rows)
 
+    prec = args.prec or ("bf16x6" if algo_used == "gemm" else "native")
+
     def recon():
         if G == 1:
-            rf.reconstruct_winmax(z[0], kerns[0], W, args.algo, max_out=Pn, arg_out=An)
+            rf.reconstruct_winmax(z[0], kerns[0], W, args.algo, max_out=Pn, arg_out=An, prec=prec)
         else:
             rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, args.algo, max_out=Pn, arg_out=An)
 
@@ -404,14 +425,43 @@ def main():
         flops = 8.0 * float(L.sum()) * n
     props = torch.cuda.get_device_properties(dev)
     sm_max = 2070.0
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = flops / (rec_avg_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": f"reconstruct ({algo_used}{', B=%d' % B if algo_used == 'os' else ''}, FP32 CUDA cores, "
-                          f"{'batched persistent' if G > 1 else 'one reference'})",
-                "peak_note": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                "kernel_ms": rec_avg_ms, "share_of_step": rec_avg_ms / ms_per_step}
+    if algo_used == "gemm":
+        # tensor-pipe work actually issued: per 128-output tile and group of NJ neighbours,
+        # LP/16 K steps x 2 planes x products, each 2 x 128 x (2 NJ) x 16 flops
+        terms = {"bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 3}[prec]
+        nprod = {"bf16": 1, "bf16x3": 3, "bf16x6": 6, "bf16x9": 9}[prec]
+        mma_flops = 0.0
+        for k in kerns:
+            L16 = max(16, -(-int(k.length.max()) // 16) * 16)
+            nck = -(-L16 // 256)
+            KC = -(-(-(-L16 // nck)) // 16) * 16
+            LP = KC * nck
+            NJ = 16 if (2 * terms * (15 + KC // 8) * 128 + 2 * terms * 32 * KC * 2 + 1024) <= 220 * 1024 else 8
+            groups = -(-k.k // NJ)
+            mma_flops += (n / 128) * groups * (LP / 16) * 2 * nprod * (2 * 128 * 2 * NJ * 16)
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak_tflops = float(peaks.get("bf16_tflops", 1900.0))
+        achieved = mma_flops / (rec_avg_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops, "traffic": ncu_traffic("k_gemm") if args.config == 3 else None,
+                    "kernel": f"reconstruct (tcgen05 Hankel GEMM, {prec}, one reference)",
+                    "peak_note": ("measured cuBLAS bf16 burst (MEASURED_PEAKS.json)" if peaks else "fallback 1.9 PF/s") +
+                                 "; achieved counts the MMA flops issued (split terms included)",
+                    "algorithmic_tflops": flops / (rec_avg_ms / 1e3) / 1e12,
+                    "kernel_ms": rec_avg_ms, "share_of_step": rec_avg_ms / ms_per_step}
+    else:
+        peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / (rec_avg_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops,
+                    "traffic": ncu_traffic("k_os") if (algo_used == "os" and G == 1 and args.config == 2
+                                                       and (args.block or 8192) == 8192) else None,
+                    "kernel": f"reconstruct ({algo_used}{', B=%d' % B if algo_used == 'os' else ''}, "
+                              f"{'FP64' if cfg.dtype == 'f64' and algo_used == 'direct' else 'FP32'} CUDA cores, "
+                              f"{'batched persistent' if G > 1 else 'one reference'})",
+                    "peak_note": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                    "kernel_ms": rec_avg_ms, "share_of_step": rec_avg_ms / ms_per_step}
 
     # ---------------- plain method on the same GPU, and the SNR error against it
     baseline = None
@@ -462,6 +512,7 @@ def main():
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
                        "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used,
+                       "prec": prec,
                        "graph": graph is not None, "parallelism": f"replicas x{world}"},
             "build_s": build_s, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "plain_mf_cufft": baseline, "err_vs_full_mf": err,

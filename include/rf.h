@@ -68,7 +68,7 @@ typedef enum {
   RF_ALGO_DIRECT = 1,    /* direct time-domain sum on CUDA cores (Eq. 8) */
   RF_ALGO_OS = 2,        /* overlap-save block FFT (frequency form, Eq. 7), FP32 */
   RF_ALGO_GEMM = 3       /* direct sum as a Hankel x taps complex GEMM on the tcgen05 tensor
-                            cores (kernels of at most 512 taps, n a multiple of 128) */
+                            cores (n a multiple of 128) */
 } rf_algo;
 
 /* Arithmetic of the reconstruction.  RF_PREC_NATIVE: the grid dtype on CUDA cores (direct,

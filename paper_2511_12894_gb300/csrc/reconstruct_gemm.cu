@@ -77,41 +77,43 @@ __device__ __forceinline__ void prec_pair(int q, int& a, int& b) {
   b = pb[q];
 }
 
-// B operand of one neighbour group, prepared once per kernel set:
-// [plane (r, i)][term][N/8 row blocks][LP/8 K blocks][8 rows][8 BF16] with the taps in
-// reverse, columns (2j, 2j+1) = (re, im) of neighbour j of the group.
+// Tap operands of one neighbour group, prepared once per kernel set, chunk by chunk:
+// [K chunk c][plane (r, i)][term][N/8 row blocks][KC/8 K blocks][8 rows][8 BF16], taps in
+// reverse (t = c KC + t_local, tap l = LP - 1 - t), columns (2j, 2j+1) = (re, im) of
+// neighbour j of the group; plane r holds (cr, ci), plane i holds (-ci, cr).
 template <typename V>
 __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restrict__ off, const int* __restrict__ len,
-                              int k, int NJ, int LP, int terms, __nv_bfloat16* __restrict__ out) {
+                              int k, int NJ, int KC, int NCK, int terms, __nv_bfloat16* __restrict__ out) {
   using R = typename real_of<V>::type;
   const int g = blockIdx.y;
   const int N = 2 * NJ;
-  const int64_t per_plane_term = (int64_t)N * LP;
-  __nv_bfloat16* og = out + (int64_t)g * 2 * terms * per_plane_term;
+  const int LP = KC * NCK;
+  const int64_t per_plane_term = (int64_t)N * KC;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)N * LP;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int col = (int)(e / LP), t = (int)(e % LP);
+    const int c = t / KC, tl = t % KC;
     const int j = g * NJ + col / 2;
     R cr = 0, ci = 0;
     if (j < k) {
       const int l = LP - 1 - t;
       if (l < len[j]) {
-        const V c = taps[off[j] + l];
-        cr = c.x;
-        ci = c.y;
+        const V v = taps[off[j] + l];
+        cr = v.x;
+        ci = v.y;
       }
     }
-    // plane r: (re, im) columns take (cr, ci); plane i: (-ci, cr)
     const R vr = (col & 1) ? ci : cr;
     const R vi = (col & 1) ? cr : -ci;
     __nv_bfloat16 r0, r1, r2, i0, i1, i2;
     split3<R>(vr, r0, r1, r2);
     split3<R>(vi, i0, i1, i2);
-    const int64_t pos = (int64_t)(col / 8) * (LP / 8) * 64 + (t / 8) * 64 + (col % 8) * 8 + (t % 8);
+    __nv_bfloat16* oc = out + ((int64_t)g * NCK + c) * 2 * terms * per_plane_term;
+    const int64_t pos = (int64_t)(col / 8) * (KC / 8) * 64 + (tl / 8) * 64 + (col % 8) * 8 + (tl % 8);
     const __nv_bfloat16 rr[3] = {r0, r1, r2}, ii[3] = {i0, i1, i2};
     for (int s = 0; s < terms; ++s) {
-      og[(0 * terms + s) * per_plane_term + pos] = rr[s];
-      og[(1 * terms + s) * per_plane_term + pos] = ii[s];
+      oc[(0 * terms + s) * per_plane_term + pos] = rr[s];
+      oc[(1 * terms + s) * per_plane_term + pos] = ii[s];
     }
   }
 }
@@ -128,13 +130,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
-// One block: TM consecutive 128-output tiles of one neighbour group.
+// Bounded wait for phase `phase` of an mbarrier; true when it completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar_addr, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(mbar_addr), "r"(phase) : "memory");
+  }
+  return done != 0;
+}
+
+// One block: TM consecutive 128-output tiles of one neighbour group.  The taps are
+// consumed in NCK chunks of KC taps: per chunk the block stages the Hankel core matrices
+// and (when there is more than one chunk) the chunk's tap operands, issues the chunk's
+// MMAs, and folds the chunk's accumulator tiles into FP32 register sums.
 template <typename V, int NJ, int PREC, bool WINMAX>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ z_ref, int64_t n,
-                                                          const __nv_bfloat16* __restrict__ Bg, int LP, int k,
-                                                          const int* __restrict__ lag0, int TM, V* __restrict__ z_out,
-                                                          unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
-                                                          int tmem_cols, int* __restrict__ status) {
+                                                          const __nv_bfloat16* __restrict__ Bg, int KC, int NCK,
+                                                          int k, const int* __restrict__ lag0, int TM,
+                                                          V* __restrict__ z_out, unsigned long long* __restrict__ keys,
+                                                          int64_t W, int64_t nw, int tmem_cols,
+                                                          int* __restrict__ status) {
   using R = typename real_of<V>::type;
   constexpr int N = 2 * NJ;
   constexpr int TERMS = prec_terms(PREC);
@@ -145,26 +162,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ 
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = blockIdx.y;
-  const int nH = 15 + LP / 8;                         // distinct Hankel core matrices
+  const int LP = KC * NCK;
+  const int nH = 15 + KC / 8;                         // distinct Hankel core matrices per chunk
   const int a_bytes = nH * 128;                       // per (plane, term)
-  const int b_bytes = N * LP * 2;                     // per (plane, term)
+  const int b_bytes = N * KC * 2;                     // per (plane, term)
   unsigned char* sA = smem;                           // [plane][term][nH][128 B]
-  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][N*LP BF16]
+  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][N/8][KC/8][128 B]
   const int64_t mask = n - 1;
+  const __nv_bfloat16* Bgrp = Bg + (int64_t)g * NCK * 2 * TERMS * N * KC;
+  const int nacc_chunks = (KC / 16 + kGemmCK - 1) / kGemmCK;
+  const int nacc = (NPROD > 1 ? 2 : 1) * nacc_chunks;  // accumulator tiles of N columns per K chunk
 
-  // B operand of the group, once per block (16-byte copies)
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(Bg + (int64_t)g * 2 * TERMS * N * LP);
+  auto stage_b = [&](int c) {
+    const uint4* src = reinterpret_cast<const uint4*>(Bgrp + (int64_t)c * 2 * TERMS * N * KC);
     uint4* dst = reinterpret_cast<uint4*>(sB);
     const int cnt = 2 * TERMS * b_bytes / 16;
     for (int e = tid; e < cnt; e += kGemmThreads) dst[e] = src[e];
-  }
+  };
+  if (NCK == 1) stage_b(0);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const int nchunk = (LP / 16 + kGemmCK - 1) / kGemmCK;
-  const int nacc = (NPROD > 1 ? 2 : 1) * nchunk;  // accumulator tiles of N columns
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(tmem_cols));
@@ -174,109 +193,101 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
+  const uint32_t mbar_addr = smem_u32(&mbar);
   constexpr uint32_t idesc = mma_idesc_bf16(N);
   uint32_t phase = 0;
   bool ok = true;
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
 
   for (int tile = 0; tile < TM && ok; ++tile) {
     const int64_t i0 = ((int64_t)blockIdx.x * TM + tile) * kGemmM;
     if (i0 >= n) break;
     const int64_t b = i0 - LP + 1;
-    // Hankel core matrices: row a of H_d is z[b + 8d + a + e], e < 8, for each plane and term
-    for (int row = tid; row < nH * 8; row += kGemmThreads) {
-      const int d = row >> 3, a = row & 7;
-      __nv_bfloat16 hr[3][8], hi[3][8];
+    float big[32], small[32];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const V v = z_ref[(b + 8 * d + a + e) & mask];
-        split3<R>(v.x, hr[0][e], hr[1][e], hr[2][e]);
-        split3<R>(v.y, hi[0][e], hi[1][e], hi[2][e]);
-      }
+    for (int cidx = 0; cidx < 32; ++cidx) big[cidx] = small[cidx] = 0.f;
+    for (int c = 0; c < NCK && ok; ++c) {
+      if (NCK > 1) stage_b(c);
+      // Hankel core matrices of the chunk: row a of H_d is z[b + c KC + 8d + a + e], e < 8
+      const int64_t bc = b + (int64_t)c * KC;
+      for (int row = tid; row < nH * 8; row += kGemmThreads) {
+        const int d = row >> 3, a = row & 7;
+        __nv_bfloat16 hr[3][8], hi[3][8];
 #pragma unroll
-      for (int s = 0; s < TERMS; ++s) {
-        *reinterpret_cast<uint4*>(sA + (0 * TERMS + s) * a_bytes + d * 128 + a * 16) =
-            *reinterpret_cast<const uint4*>(hr[s]);
-        *reinterpret_cast<uint4*>(sA + (1 * TERMS + s) * a_bytes + d * 128 + a * 16) =
-            *reinterpret_cast<const uint4*>(hi[s]);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int ks = 0; ks < LP / 16; ++ks) {
-        const int ch = ks / kGemmCK;
-        const bool chunk_start = (ks % kGemmCK) == 0;
-        for (int pl = 0; pl < 2; ++pl)
-          for (int q = 0; q < NPROD; ++q) {
-            int ta, tb;
-            prec_pair(q, ta, tb);
-            const uint64_t ad = smem_desc(smem_u32(sA + (pl * TERMS + ta) * a_bytes) + ks * 256, 128, 128);
-            const uint64_t bd = smem_desc(smem_u32(sB + (pl * TERMS + tb) * b_bytes) + ks * 256, 128, LP * 16);
-            // tile: leading product of chunk ch, or its corrections
-            const int tile_idx = (NPROD > 1 ? 2 * ch : ch) + (q > 0 ? 1 : 0);
-            const uint32_t d = tmem + (uint32_t)(tile_idx * N);
-            const bool first = chunk_start && pl == 0 && q <= 1;  // q == 0 / 1 open their tiles
-            const uint32_t acc = first ? 0u : 1u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&mbar)) : "memory");
-    }
-    // bounded wait for the tile's MMAs
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
-    }
-    phase ^= 1u;
-    if (!__syncthreads_and(done)) {
-      if (tid == 0) atomicExch(status, (int)RF_ETIMEOUT);
-      ok = false;
-      // give the tile's MMAs one more bounded wait before tensor memory is released
-      uint32_t late = 0;
-      for (int it = 0; it < (1 << 24) && !late; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(late) : "r"(smem_u32(&mbar)), "r"(phase ^ 1u) : "memory");
-      }
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w holds rows 32w..32w+31, thread = one row, all N columns
-    // sum the accumulator tiles of this row: corrections first, then the leading products
-    float r[32];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int e = 0; e < 8; ++e) {
+          const V v = z_ref[(bc + 8 * d + a + e) & mask];
+          split3<R>(v.x, hr[0][e], hr[1][e], hr[2][e]);
+          split3<R>(v.y, hi[0][e], hi[1][e], hi[2][e]);
+        }
 #pragma unroll
-    for (int h = 0; h < N / 16; ++h) {
-      float big[16], small[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) big[c] = small[c] = 0.f;
-      for (int t = 0; t < nacc; ++t) {
-        uint32_t v[16];
-        tmem_ld16(taddr + (uint32_t)(t * N + 16 * h), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const bool is_small = (NPROD > 1) && (t & 1);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          if (is_small) small[c] += __uint_as_float(v[c]);
-          else big[c] += __uint_as_float(v[c]);
+        for (int s = 0; s < TERMS; ++s) {
+          *reinterpret_cast<uint4*>(sA + (0 * TERMS + s) * a_bytes + d * 128 + a * 16) =
+              *reinterpret_cast<const uint4*>(hr[s]);
+          *reinterpret_cast<uint4*>(sA + (1 * TERMS + s) * a_bytes + d * 128 + a * 16) =
+              *reinterpret_cast<const uint4*>(hi[s]);
         }
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int ks = 0; ks < KC / 16; ++ks) {
+          const int ch = ks / kGemmCK;
+          const bool chunk_start = (ks % kGemmCK) == 0;
+          for (int pl = 0; pl < 2; ++pl)
+            for (int q = 0; q < NPROD; ++q) {
+              int ta, tb;
+              prec_pair(q, ta, tb);
+              const uint64_t ad = smem_desc(smem_u32(sA + (pl * TERMS + ta) * a_bytes) + ks * 256, 128, 128);
+              const uint64_t bd = smem_desc(smem_u32(sB + (pl * TERMS + tb) * b_bytes) + ks * 256, 128, KC * 16);
+              // tile: leading product of accumulator chunk ch, or its corrections
+              const int tile_idx = (NPROD > 1 ? 2 * ch : ch) + (q > 0 ? 1 : 0);
+              const uint32_t d = tmem + (uint32_t)(tile_idx * N);
+              const bool first = chunk_start && pl == 0 && q <= 1;  // q == 0 / 1 open their tiles
+              const uint32_t acc = first ? 0u : 1u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
+                     : "memory");
+      }
+      const bool done = mbar_wait(mbar_addr, phase);
+      phase ^= 1u;
+      if (!__syncthreads_and(done)) {
+        if (tid == 0) atomicExch(status, (int)RF_ETIMEOUT);
+        ok = false;
+        mbar_wait(mbar_addr, phase ^ 1u);  // one more bounded wait before tensor memory is released
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // fold the chunk's tiles into the row sums (thread = row 32 w + lane)
 #pragma unroll
-      for (int c = 0; c < 16; ++c) r[16 * h + c] = big[c] + small[c];
+      for (int h = 0; h < N / 16; ++h) {
+        for (int t = 0; t < nacc; ++t) {
+          uint32_t v[16];
+          tmem_ld16(taddr + (uint32_t)(t * N + 16 * h), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const bool is_small = (NPROD > 1) && (t & 1);
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            if (is_small) small[16 * h + cc] += __uint_as_float(v[cc]);
+            else big[16 * h + cc] += __uint_as_float(v[cc]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();  // shared tiles and tensor memory are rewritten by the next chunk
     }
+    if (!ok) break;
     const int64_t ip = i0 + warp * 32 + lane;  // i'
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
       const int j = g * NJ + jj;
       if (j >= k) break;  // uniform across the block
-      const float re = r[2 * jj], im = r[2 * jj + 1];
+      const float re = big[2 * jj] + small[2 * jj], im = big[2 * jj + 1] + small[2 * jj + 1];
       const int64_t i = (ip + lag0[j]) & mask;
       if (!WINMAX) {
         z_out[(int64_t)j * n + i] = cmake<V>((R)re, (R)im);
@@ -304,8 +315,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ 
         }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // TMEM and the Hankel tiles are reused by the next tile
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -321,14 +330,15 @@ __global__ void k_gemm_unpack(const unsigned long long* __restrict__ keys, int64
   arg[i] = (int)(0xffffffffu - (unsigned int)(kk & 0xffffffffull));
 }
 
-size_t gemm_smem_bytes(int terms, int NJ, int LP) {
-  const int nH = 15 + LP / 8;
-  return (size_t)2 * terms * nH * 128 + (size_t)2 * terms * (2 * NJ) * LP * 2 + 1024;
+size_t gemm_smem_bytes(int terms, int NJ, int KC) {
+  const int nH = 15 + KC / 8;
+  return (size_t)2 * terms * nH * 128 + (size_t)2 * terms * (2 * NJ) * KC * 2 + 1024;
 }
 
-// Tensor-memory columns: accumulator tiles of N columns, rounded up to a power of two >= 32.
-int gemm_tmem_cols(int prec, int NJ, int LP) {
-  const int nchunk = (LP / 16 + kGemmCK - 1) / kGemmCK;
+// Tensor-memory columns: accumulator tiles of N columns for one K chunk, rounded up to a
+// power of two >= 32.
+int gemm_tmem_cols(int prec, int NJ, int KC) {
+  const int nchunk = (KC / 16 + kGemmCK - 1) / kGemmCK;
   const int need = (prec_products(prec) > 1 ? 2 : 1) * nchunk * 2 * NJ;
   int cols = 32;
   while (cols < need) cols *= 2;
@@ -338,28 +348,28 @@ int gemm_tmem_cols(int prec, int NJ, int LP) {
 template <typename V, int NJ, int PREC, bool WINMAX>
 void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, unsigned long long* keys, int64_t W,
                  int64_t nw, cudaStream_t s) {
-  const int LP = kern->gemm_LP;
-  const int cols = gemm_tmem_cols(PREC, NJ, LP);
+  const int KC = kern->gemm_KC, NCK = kern->gemm_NCK;
+  const int cols = gemm_tmem_cols(PREC, NJ, KC);
   RF_REQUIRE(cols <= 512, "tensor-core form: %d tensor-memory columns needed", cols);
   // shared memory sized so that the blocks resident on one SM never ask for more than the
   // 512 tensor-memory columns of the SM (an allocation would otherwise wait for a release)
   const size_t smem_max = 227 * 1024;
   const int max_blocks = 512 / cols;
-  size_t smem = gemm_smem_bytes(prec_terms(PREC), NJ, LP);
+  size_t smem = gemm_smem_bytes(prec_terms(PREC), NJ, KC);
   smem = std::max(smem, smem_max / (size_t)(max_blocks + 1) + 1024);
   smem = std::min(smem, (size_t)220 * 1024);
   auto fn = k_gemm<V, NJ, PREC, WINMAX>;
   RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGemmThreads, smem));
-  RF_REQUIRE(per_sm * cols <= 512, "tensor-core form: %d blocks per SM x %d columns exceed tensor memory", per_sm,
-             cols);
+  RF_REQUIRE(per_sm >= 1 && per_sm * cols <= 512,
+             "tensor-core form: %d blocks per SM x %d columns exceed tensor memory", per_sm, cols);
   const int64_t tiles = c->n / kGemmM;
   const int groups = (kern->k + NJ - 1) / NJ;
   int TM = 1;
   while (TM < 16 && (tiles / (TM * 2)) * groups >= 4LL * c->nsm) TM *= 2;
   dim3 grid((unsigned)((tiles + TM - 1) / TM), (unsigned)groups);
-  fn<<<grid, kGemmThreads, smem, s>>>(z_ref, c->n, kern->gemm_B.as<__nv_bfloat16>(), LP, kern->k,
+  fn<<<grid, kGemmThreads, smem, s>>>(z_ref, c->n, kern->gemm_B.as<__nv_bfloat16>(), KC, NCK, kern->k,
                                       kern->lag0_d.as<int>(), TM, z_out, keys, W, nw, cols, c->status.as<int>());
   RF_LAUNCHED();
 }
@@ -377,34 +387,40 @@ void launch_gemm_prec(rf_ctx* c, const rf_kernels* kern, int prec, const V* z_re
 
 }  // namespace
 
-int gemm_max_len() { return 512; }
+int gemm_max_len() { return 1 << 16; }
 
 void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
-  RF_REQUIRE(kern->max_len <= gemm_max_len(), "the tensor-core direct form takes kernels of at most %d taps (got %d)",
-             gemm_max_len(), kern->max_len);
   const int terms = prec_terms(prec);
-  const int LP = std::max(16, (kern->max_len + 15) / 16 * 16);
+  // K chunks of at most 256 taps, a multiple of 16 each
+  const int L16 = std::max(16, (kern->max_len + 15) / 16 * 16);
+  const int NCK = (L16 + 255) / 256;
+  const int KC = ((L16 + NCK - 1) / NCK + 15) / 16 * 16;
   int NJ = 16;
-  if (gemm_smem_bytes(terms, NJ, LP) > 220 * 1024) NJ = 8;
-  RF_REQUIRE(gemm_smem_bytes(terms, NJ, LP) <= 220 * 1024, "tensor-core direct form: %d taps do not fit", LP);
-  if (kern->gemm_ready && kern->gemm_terms == terms && kern->gemm_LP == LP && kern->gemm_NJ == NJ) return;
+  if (gemm_smem_bytes(terms, NJ, KC) > 220 * 1024) NJ = 8;
+  RF_REQUIRE(gemm_smem_bytes(terms, NJ, KC) <= 220 * 1024, "tensor-core direct form: chunk of %d taps does not fit",
+             KC);
+  if (kern->gemm_ready && kern->gemm_terms == terms && kern->gemm_KC == KC && kern->gemm_NCK == NCK &&
+      kern->gemm_NJ == NJ)
+    return;
   const int groups = std::max(1, (kern->k + NJ - 1) / NJ);
+  const int LP = KC * NCK;
   const size_t elems = (size_t)groups * 2 * terms * (2 * NJ) * LP;
   kern->gemm_B.ensure(sizeof(__nv_bfloat16) * std::max<size_t>(elems, 8));
   dim3 grid((unsigned)std::max<int64_t>(1, (2 * NJ * LP + 255) / 256), (unsigned)groups);
   if (kern->dtype == RF_F64)
     k_gemm_prep_b<double2><<<grid, 256, 0, s>>>(kern->taps.as<double2>(), kern->off_d.as<int64_t>(),
-                                                kern->len_d.as<int>(), kern->k, NJ, LP, terms,
+                                                kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms,
                                                 kern->gemm_B.as<__nv_bfloat16>());
   else
     k_gemm_prep_b<float2><<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(),
-                                               kern->len_d.as<int>(), kern->k, NJ, LP, terms,
+                                               kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms,
                                                kern->gemm_B.as<__nv_bfloat16>());
   RF_LAUNCHED();
   RF_CUDA(cudaStreamSynchronize(s));
   kern->gemm_ready = true;
   kern->gemm_terms = terms;
-  kern->gemm_LP = LP;
+  kern->gemm_KC = KC;
+  kern->gemm_NCK = NCK;
   kern->gemm_NJ = NJ;
 }
 

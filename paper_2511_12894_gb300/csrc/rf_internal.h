@@ -131,10 +131,10 @@ struct rf_kernels {
   rf::DevBuf os_spec;      // float2 [sum_j P_j][B]
   rf::DevBuf os_off_d;     // int64 [k+1]: element offset of kernel j's first partition spectrum
   rf::DevBuf os_parts_d;   // int32 [k]
-  // Tensor-core direct form: split-BF16 tap operands per group of gemm_NJ neighbours,
-  // taps padded to gemm_LP (see reconstruct_gemm.cu).
+  // Tensor-core direct form: split-BF16 tap operands per group of gemm_NJ neighbours, taps
+  // padded to gemm_NCK chunks of gemm_KC (see reconstruct_gemm.cu).
   bool gemm_ready = false;
-  int gemm_terms = 0, gemm_LP = 0, gemm_NJ = 0;
+  int gemm_terms = 0, gemm_KC = 0, gemm_NCK = 0, gemm_NJ = 0;
   rf::DevBuf gemm_B;
 };
 

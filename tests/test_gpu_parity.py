@@ -493,8 +493,8 @@ GEMM_TOL = {"bf16": 2e-2, "bf16x3": 2e-4, "bf16x6": 2e-6, "bf16x9": 2e-6}
 def test_reconstruct_gemm_edge_lengths(torch, dtype):
     n = 1 << 13
     rng = np.random.default_rng(17)
-    lengths = [1, 2, 15, 16, 17, 100, 255, 256, 257, 384, 0, 500, 31]
-    lags = [0, -5, 37, n // 2, -(n // 2) + 1, 100, -1000, 3, 2000, -2, 5, 11, -n // 4]
+    lengths = [1, 2, 15, 16, 17, 100, 255, 256, 257, 384, 0, 500, 31, 1000, 600]
+    lags = [0, -5, 37, n // 2, -(n // 2) + 1, 100, -1000, 3, 2000, -2, 5, 11, -n // 4, -400, 4000]
     cfg = replace(workload.config(1, n_override=n, k_override=1), dtype=dtype)
     rf = _rf(cfg)
     cdt = np.complex64 if dtype == "f32" else np.complex128
