@@ -56,45 +56,62 @@ __host__ __device__ constexpr int block_table_size() {
 }
 
 // tw: the stage tables of B.  SIGN: -1 forward, +1 inverse (unnormalised).
+// Every access of a stage is base + t * stride in the padded index (the strides are
+// multiples of 16, so pad(base + t stride) = pad(base) + t (stride + stride / 16)), which
+// lets the compiler use one base register and immediate offsets.
 template <int B, int SIGN>
 __device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const float2* __restrict__ tw) {
   using S = BlockFFTShape<B>;
   constexpr int NT = S::NT;
   const int tid = threadIdx.x;
-  // first stage: Ns = 1, no twiddles, out[b*16 + t]
+  // first stage: Ns = 1, no twiddles, out[b*16 + t] at padded index 17 b + t
   dft<16, SIGN>(v);
+  {
+    float2* o = sm + 17 * tid;
 #pragma unroll
-  for (int t = 0; t < 16; ++t) sm[bf_pad(tid * 16 + t)] = v[t];
+    for (int t = 0; t < 16; ++t) o[t] = v[t];
+  }
   __syncthreads();
   int Ns = 16;
   // middle radix-16 stages (all but the last stage)
   constexpr int MID = block_mid_stages<B>();
+  constexpr int RSTR = B / 16 + B / 256;  // padded stride of the stage reads
 #pragma unroll
   for (int st = 0; st < MID; ++st) {
+    {
+      const float2* in = sm + bf_pad(tid);
 #pragma unroll
-    for (int t = 0; t < 16; ++t) v[t] = sm[bf_pad(tid + t * (B / 16))];
+      for (int t = 0; t < 16; ++t) v[t] = in[t * RSTR];
+    }
     __syncthreads();
     const int k = tid & (Ns - 1);
+    const float2* twk = tw + k;
 #pragma unroll
-    for (int t = 1; t < 16; ++t) v[t] = tw_apply<SIGN>(v[t], __ldg(tw + t * Ns + k));
+    for (int t = 1; t < 16; ++t) v[t] = tw_apply<SIGN>(v[t], __ldg(twk + t * Ns));
     dft<16, SIGN>(v);
-    const int base = (tid - k) * 16 + k;
+    {
+      float2* o = sm + bf_pad((tid - k) * 16 + k);
+      const int wstr = Ns + Ns / 16;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) sm[bf_pad(base + t * Ns)] = v[t];
+      for (int t = 0; t < 16; ++t) o[t * wstr] = v[t];
+    }
     __syncthreads();
     tw += 16 * Ns;
     Ns *= 16;
   }
   // last stage: radix RL, Ns = B / RL, every butterfly index b < Ns so k = b
   constexpr int RL = S::RL;
+  constexpr int LSTR = B / RL + B / (16 * RL);
 #pragma unroll
   for (int q = 0; q < 16 / RL; ++q) {
     const int b = tid + q * NT;
     float2 a[RL];
+    const float2* in = sm + bf_pad(b);
 #pragma unroll
-    for (int t = 0; t < RL; ++t) a[t] = sm[bf_pad(b + t * (B / RL))];
+    for (int t = 0; t < RL; ++t) a[t] = in[t * LSTR];
+    const float2* twb = tw + b;
 #pragma unroll
-    for (int t = 1; t < RL; ++t) a[t] = tw_apply<SIGN>(a[t], __ldg(tw + t * (B / RL) + b));
+    for (int t = 1; t < RL; ++t) a[t] = tw_apply<SIGN>(a[t], __ldg(twb + t * (B / RL)));
     dft<RL, SIGN>(a);
 #pragma unroll
     for (int t = 0; t < RL; ++t) v[q * RL + t] = a[t];

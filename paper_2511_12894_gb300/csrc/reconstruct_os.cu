@@ -137,32 +137,54 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
       __syncthreads();
       const int lane = tid & 31;
       const int qbase = tid * CH;
-      bool slow = !fastwin;
-      unsigned long long kA = 0, kB = 0;
-      int64_t wA = 0, wB = 0;
       float mv[CH];
 #pragma unroll
       for (int e = 0; e < CH; e += 4)
         *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + qbase + e);
-      if (fastwin) {
-        const int64_t i_warp = (base + (int64_t)(tid - lane) * CH) & mask;
-        wA = i_warp / W;
-        wB = (wA + 1 == nw) ? 0 : wA + 1;
+      // sample index and window of this thread's first output; later outputs step by one
+      // (wrapping at n), so one division per thread suffices
+      int i0 = (int)((base + qbase) & mask);
+      int w0 = i0 / (int)W;
+      int r0 = i0 - w0 * (int)W;
+      const int wA = __shfl_sync(0xffffffffu, w0, 0);
+      const int wB = (wA + 1 == (int)nw) ? 0 : wA + 1;
+      unsigned long long kA = 0, kB = 0;
+      bool slow = !fastwin;
+      {
+        int i = i0, w = w0, r = r0;
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
-          const int64_t i = (base + qbase + e) & mask;
-          const int64_t w = i / W;
           const unsigned long long key = pack_key(mv[e], (unsigned int)i);
           if (w == wA) kA = max(kA, key);
           else if (w == wB) kB = max(kB, key);
           else slow = true;
+          ++i;
+          ++r;
+          if (i == (int)n) {
+            i = 0;
+            w = 0;
+            r = 0;
+          } else if (r == (int)W) {
+            ++w;
+            r = 0;
+          }
         }
       }
       const bool any_slow = __any_sync(0xffffffffu, slow);
       if (any_slow) {
+        int i = i0, w = w0, r = r0;
         for (int e = 0; e < CH; ++e) {
-          const int64_t i = (base + qbase + e) & mask;
-          atomicMax(kj + i / W, pack_key(mv[e], (unsigned int)i));
+          atomicMax(kj + w, pack_key(mv[e], (unsigned int)i));
+          ++i;
+          ++r;
+          if (i == (int)n) {
+            i = 0;
+            w = 0;
+            r = 0;
+          } else if (r == (int)W) {
+            ++w;
+            r = 0;
+          }
         }
       } else {
 #pragma unroll
