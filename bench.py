@@ -332,7 +332,8 @@ def main():
         if G == 1:
             rf.reconstruct_winmax(z[0], kerns[0], W, args.algo, max_out=Pn, arg_out=An, prec=prec)
         else:
-            rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, args.algo, max_out=Pn, arg_out=An)
+            rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, args.algo, max_out=Pn, arg_out=An,
+                                      prec=prec)
 
     def step():
         rf.mf_reference(x, ip, refs, z_out=z, sigma_out=sig)
@@ -448,10 +449,9 @@ def main():
         mma_flops = 0.0
         for k in kerns:
             L16 = max(16, -(-int(k.length.max()) // 16) * 16)
-            nck = -(-L16 // 256)
-            KC = -(-(-(-L16 // nck)) // 16) * 16
-            LP = KC * nck
-            NJ = 16 if (2 * terms * (15 + KC // 8) * 128 + 2 * terms * 32 * KC * 2 + 1024) <= 220 * 1024 else 8
+            KC = min(128, L16)
+            LP = KC * (-(-L16 // KC))
+            NJ = 16 if k.k <= 16 else {"bf16": 128, "bf16x3": 48, "bf16x6": 40, "bf16x9": 24}[prec]
             groups = -(-k.k // NJ)
             mma_flops += (n / 128) * groups * (LP / 16) * 2 * nprod * (2 * 128 * 2 * NJ * 16)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

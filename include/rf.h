@@ -199,9 +199,11 @@ rf_status rf_reconstruct_winmax(rf_ctx* ctx, const void* z_ref, const rf_kernels
 /* Batched fused form for G references, each with its own neighbours (Sec. III.A: groups
  * are independent): per reference g, z_refs[g] is its z_ref (device complex[n]) and ks[g]
  * its kernel set; the rows of max_out/argmax_out ([sum_g k_g][ceil(n/W)]) follow the order
- * of the groups and, inside a group, of its neighbours.  Runs overlap-save (RF_F32 grid,
- * n >= 512; algo must be RF_ALGO_AUTO or RF_ALGO_OS) as one persistent launch over
- * (neighbour, output-block chunk) work units.  z_refs and ks are host arrays.  The first
+ * of the groups and, inside a group, of its neighbours.  algo and prec as in
+ * rf_reconstruct_winmax, one choice for all groups.  Overlap-save (AUTO on an RF_F32 grid
+ * with n >= 512, or RF_ALGO_OS) runs as one persistent launch over (neighbour, output-block
+ * chunk) work units; the direct and tensor-core forms run group after group, each writing
+ * its rows in place.  z_refs and ks are host arrays.  For overlap-save, the first
  * call with a given set of references and kernel sets (or after any of them is re-prepared)
  * builds and uploads the work list and allocates the per-reference segment spectra
  * (G x 2n complex64) and window keys, synchronously; later calls with the same arguments

@@ -293,7 +293,7 @@ class RatioFilter:
         return mo, ao
 
     def reconstruct_batched(self, z_refs: Sequence, kerns: Sequence[Kernels], W: int, algo: str = "auto",
-                            max_out=None, arg_out=None, stream=None):
+                            max_out=None, arg_out=None, stream=None, prec: str = "native"):
         """Fused window peaks of several references' neighbours in one persistent launch.
 
         z_refs: CUDA complex tensors of length n (one per reference); kerns: their kernel
@@ -308,7 +308,7 @@ class RatioFilter:
         zp = (ctypes.c_void_p * G)(*[z.data_ptr() for z in zs])
         kp = (ctypes.c_void_p * G)(*[k.handle.value if isinstance(k.handle, ctypes.c_void_p) else k.handle
                                      for k in kerns])
-        _check(_lib.rf_reconstruct_batched(self.handle, G, zp, kp, ALGOS[algo], 0, int(W),
+        _check(_lib.rf_reconstruct_batched(self.handle, G, zp, kp, ALGOS[algo], PRECS[prec], int(W),
                                            ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()),
                                            _stream(stream)))
         return mo, ao

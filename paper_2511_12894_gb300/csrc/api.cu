@@ -166,8 +166,11 @@ rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out) {
     // overlap-save segment spectra plus packed window keys for windows of >= 16 samples
     const size_t bytes = os_workspace_bytes(ctx, k_max, 16);
     ctx->scratch.ensure(bytes);
+    // BF16 planes of z_ref for the tensor-core path, for taps up to the segment length
+    const size_t planes = gemm_zplanes_bytes(ctx->n, ctx->n + 128, 3);
+    ctx->scratch2.ensure(planes);
     ctx->reserved = bytes;
-    if (bytes_out) *bytes_out = (int64_t)bytes;
+    if (bytes_out) *bytes_out = (int64_t)(bytes + planes);
   });
 }
 
@@ -349,15 +352,32 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
     RF_REQUIRE(z_refs != nullptr && ks != nullptr, "z_refs and ks must be non-NULL host arrays");
     RF_REQUIRE(W >= 1 && W <= ctx->n, "W=%lld must be in [1, n]", (long long)W);
     int64_t rows = 0;
+    int a = RF_ALGO_AUTO;
     for (int g = 0; g < G; ++g) {
-      const int a = check_recon(ctx, z_refs[g], ks[g], algo, prec);
-      RF_REQUIRE(a == RF_ALGO_OS, "the batched form runs overlap-save (RF_F32 grid, n >= 512)");
+      RF_REQUIRE(ks[g] != nullptr, "ks[%d] is NULL", g);
+      a = check_recon(ctx, z_refs[g], ks[g], algo, prec);  // the same for every group
       rows += ks[g]->k;
     }
     if (!rows) return;
     check_dev(max_out, "max_out");
     check_dev(argmax_out, "argmax_out");
-    reconstruct_batched(ctx, G, z_refs, ks, W, max_out, argmax_out, (cudaStream_t)stream);
+    if (a == RF_ALGO_OS) {
+      reconstruct_batched(ctx, G, z_refs, ks, W, max_out, argmax_out, (cudaStream_t)stream);
+      return;
+    }
+    const int64_t nw = (ctx->n + W - 1) / W;
+    int64_t row = 0;
+    for (int g = 0; g < G; ++g) {
+      if (ks[g]->k) {
+        if (a == RF_ALGO_GEMM)
+          reconstruct_gemm(ctx, z_refs[g], ks[g], prec, nullptr, W, max_out + row * nw, argmax_out + row * nw,
+                           (cudaStream_t)stream);
+        else
+          reconstruct_direct(ctx, z_refs[g], ks[g], nullptr, W, max_out + row * nw, argmax_out + row * nw,
+                             (cudaStream_t)stream);
+      }
+      row += ks[g]->k;
+    }
   });
 }
 

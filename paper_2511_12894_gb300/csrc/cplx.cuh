@@ -22,6 +22,23 @@ template <typename V> __host__ __device__ __forceinline__ V cmake(typename real_
 }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmake<V>(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmake<V>(a.x - b.x, a.y - b.y); }
+
+// FP32 complex add / subtract as one paired-FP32 instruction (sm_100 and later): the same
+// IEEE round-to-nearest results as two scalar operations, in one issue slot.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -88,11 +105,11 @@ template <int SIGN, typename V>
 __device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
   V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
   V d = csub(a1, a3);
-  V t3 = cmake<V>(-SIGN * d.y, SIGN * d.x);  // d * (SIGN i)
   a0 = cadd(t0, t2);
   a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  // t1 +- d * (SIGN i), written out so the quarter turn costs no moves
+  a1 = cmake<V>(t1.x - SIGN * d.y, t1.y + SIGN * d.x);
+  a3 = cmake<V>(t1.x + SIGN * d.y, t1.y - SIGN * d.x);
 }
 
 // R = R1 * R2 with n = n1 + R1 n2, k = k2 + R2 k1.

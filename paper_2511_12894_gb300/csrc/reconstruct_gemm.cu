@@ -18,9 +18,10 @@
 // Split precision: x = x0 + x1 + x2 with x_k = bf16(x - x0 - ... - x_{k-1}); the products
 // kept are (0,0) for BF16, + (0,1),(1,0) for x3, + (0,2),(1,1),(2,0) for x6, + (1,2),(2,1),(2,2)
 // for x9.  The tensor core's FP32 accumulation loses a fraction of an ulp of the running
-// sum at every MMA, so each chunk of GEMM_CK K steps accumulates into its own tensor-memory
-// tiles, one for the leading product (0,0) and one for the corrections; the epilogue adds
-// the tiles in FP32 registers (round to nearest).
+// sum at every MMA, so every product of every K chunk (at most 256 taps) accumulates into
+// its own tensor-memory tile, and the block adds the tiles in FP32 registers (round to
+// nearest), corrections apart from the leading product.  Separate tiles also keep
+// consecutive MMAs independent, which the tensor pipe needs to overlap short (N = 32) MMAs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -35,7 +36,6 @@ namespace {
 
 constexpr int kGemmThreads = 128;
 constexpr int kGemmM = 128;
-constexpr int kGemmCK = 4;  // K steps (of 16 taps) per accumulator chunk
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -69,12 +69,6 @@ __host__ __device__ constexpr int prec_products(int prec) {
 }
 __host__ __device__ constexpr int prec_terms(int prec) {
   return prec == RF_PREC_BF16 ? 1 : prec == RF_PREC_BF16X3 ? 2 : 3;
-}
-__device__ __forceinline__ void prec_pair(int q, int& a, int& b) {
-  constexpr int pa[9] = {0, 0, 1, 0, 1, 2, 1, 2, 2};
-  constexpr int pb[9] = {0, 1, 0, 2, 1, 0, 2, 1, 2};
-  a = pa[q];
-  b = pb[q];
 }
 
 // Tap operands of one neighbour group, prepared once per kernel set, chunk by chunk:
@@ -118,6 +112,29 @@ __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restr
   }
 }
 
+// z_ref split into BF16 planes once per call: plane (p, s) holds term s of the real (p = 0)
+// or imaginary (p = 1) part, element x of the circular sequence at index x + pad for
+// x in [-pad, n + tail); pad = 7 (mod 8) makes every Hankel row-block window 16-byte aligned.
+// The split runs in FP32 (complex128 inputs are rounded to FP32 first, well inside the
+// three-term resolution).
+static int64_t gemm_zpad(int64_t LP) { return ((LP + 8 + 7) / 8) * 8 + 7; }
+static int64_t gemm_zlen(int64_t n, int64_t LP) { return ((gemm_zpad(LP) + n + 160 + 7) / 8) * 8; }
+
+template <typename V>
+__global__ void k_gemm_split_z(const V* __restrict__ z, int64_t n, int64_t pad, int64_t len, int terms,
+                               __nv_bfloat16* __restrict__ planes) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= len) return;
+  const V v = z[(idx - pad) & (n - 1)];
+  __nv_bfloat16 r[3], i[3];
+  split3<float>((float)v.x, r[0], r[1], r[2]);
+  split3<float>((float)v.y, i[0], i[1], i[2]);
+  for (int s = 0; s < terms; ++s) {
+    planes[(int64_t)(0 * terms + s) * len + idx] = r[s];
+    planes[(int64_t)(1 * terms + s) * len + idx] = i[s];
+  }
+}
+
 __device__ __forceinline__ unsigned long long gemm_key(float v, unsigned int i) {
   return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - i);
 }
@@ -141,22 +158,35 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar_addr, uint32_t phase) {
   return done != 0;
 }
 
-// One block: TM consecutive 128-output tiles of one neighbour group.  The taps are
+// B terms multiplied with A term ta: x9 keeps all three, the others the terms tb <= TERMS-1-ta.
+__host__ __device__ constexpr int b_terms_for(int prec, int ta) {
+  return prec == RF_PREC_BF16X9 ? 3 : prec_terms(prec) - ta;
+}
+// Tensor-memory column of the tile of A term ta (tiles follow each other, N columns per B term).
+__host__ __device__ constexpr int tile_col(int prec, int ta, int N) {
+  int c = 0;
+  for (int t = 0; t < ta; ++t) c += N * b_terms_for(prec, t);
+  return c;
+}
+
+// One block: TM consecutive 128-output tiles of one group of NJ neighbours.  The taps are
 // consumed in NCK chunks of KC taps: per chunk the block stages the Hankel core matrices
-// and (when there is more than one chunk) the chunk's tap operands, issues the chunk's
-// MMAs, and folds the chunk's accumulator tiles into FP32 register sums.
+// and (when there is more than one chunk) the chunk's tap operands, issues one MMA per
+// (K step, plane, A term) whose N spans every B term paired with that A term, and folds
+// the chunk's tiles into FP32 register sums (plain BF16 accumulates in tensor memory).
 template <typename V, int NJ, int PREC, bool WINMAX>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ z_ref, int64_t n,
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __nv_bfloat16* __restrict__ zp, int64_t zpad,
+                                                          int64_t zlen, int64_t n,
                                                           const __nv_bfloat16* __restrict__ Bg, int KC, int NCK,
                                                           int k, const int* __restrict__ lag0, int TM,
                                                           V* __restrict__ z_out, unsigned long long* __restrict__ keys,
                                                           int64_t W, int64_t nw, int tmem_cols,
                                                           int* __restrict__ status) {
   using R = typename real_of<V>::type;
-  constexpr int N = 2 * NJ;
+  constexpr int N = 2 * NJ;                // columns per B term
   constexpr int TERMS = prec_terms(PREC);
-  constexpr int NPROD = prec_products(PREC);
-  static_assert(N == 16 || N == 32, "neighbours per group");
+  constexpr bool FOLD = PREC != RF_PREC_BF16;
+  static_assert(N % 16 == 0 && N * b_terms_for(PREC, 0) <= 256, "MMA width");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ uint32_t tmem_base;
@@ -170,8 +200,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ 
   unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][N/8][KC/8][128 B]
   const int64_t mask = n - 1;
   const __nv_bfloat16* Bgrp = Bg + (int64_t)g * NCK * 2 * TERMS * N * KC;
-  const int nacc_chunks = (KC / 16 + kGemmCK - 1) / kGemmCK;
-  const int nacc = (NPROD > 1 ? 2 : 1) * nacc_chunks;  // accumulator tiles of N columns per K chunk
 
   auto stage_b = [&](int c) {
     const uint4* src = reinterpret_cast<const uint4*>(Bgrp + (int64_t)c * 2 * TERMS * N * KC);
@@ -194,7 +222,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t mbar_addr = smem_u32(&mbar);
-  constexpr uint32_t idesc = mma_idesc_bf16(N);
   uint32_t phase = 0;
   bool ok = true;
   const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -203,52 +230,54 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ 
     const int64_t i0 = ((int64_t)blockIdx.x * TM + tile) * kGemmM;
     if (i0 >= n) break;
     const int64_t b = i0 - LP + 1;
-    float big[32], small[32];
+    float run[FOLD ? N : 1];
 #pragma unroll
-    for (int cidx = 0; cidx < 32; ++cidx) big[cidx] = small[cidx] = 0.f;
+    for (int cidx = 0; cidx < (FOLD ? N : 1); ++cidx) run[cidx] = 0.f;
     for (int c = 0; c < NCK && ok; ++c) {
       if (NCK > 1) stage_b(c);
-      // Hankel core matrices of the chunk: row a of H_d is z[b + c KC + 8d + a + e], e < 8
-      const int64_t bc = b + (int64_t)c * KC;
-      for (int row = tid; row < nH * 8; row += kGemmThreads) {
-        const int d = row >> 3, a = row & 7;
-        __nv_bfloat16 hr[3][8], hi[3][8];
+      // Hankel core matrices of the chunk: row a of H_d is z[b + c KC + 8d + a + e], e < 8.
+      // One task = one (plane, term, d): the aligned 16-element window starting at
+      // b + c KC + 8d gives all eight rows by funnel shifts.
+      const int64_t bc = b + (int64_t)c * KC + zpad;  // plane index of the chunk's first element
+      for (int task = tid; task < 2 * TERMS * nH; task += kGemmThreads) {
+        const int pt = task / nH, d = task - pt * nH;
+        const uint4* src = reinterpret_cast<const uint4*>(zp + (int64_t)pt * zlen + bc + 8 * d);
+        const uint4 lo = src[0], hi = src[1];
+        const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        unsigned char* dst = sA + pt * a_bytes + d * 128;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const V v = z_ref[(bc + 8 * d + a + e) & mask];
-          split3<R>(v.x, hr[0][e], hr[1][e], hr[2][e]);
-          split3<R>(v.y, hi[0][e], hi[1][e], hi[2][e]);
-        }
+        for (int a = 0; a < 8; ++a) {
+          uint32_t o[4];
 #pragma unroll
-        for (int s = 0; s < TERMS; ++s) {
-          *reinterpret_cast<uint4*>(sA + (0 * TERMS + s) * a_bytes + d * 128 + a * 16) =
-              *reinterpret_cast<const uint4*>(hr[s]);
-          *reinterpret_cast<uint4*>(sA + (1 * TERMS + s) * a_bytes + d * 128 + a * 16) =
-              *reinterpret_cast<const uint4*>(hi[s]);
+          for (int q = 0; q < 4; ++q) o[q] = __funnelshift_r(w[a / 2 + q], w[a / 2 + q + 1], (a & 1) * 16);
+          *reinterpret_cast<uint4*>(dst + a * 16) = make_uint4(o[0], o[1], o[2], o[3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // K step ks adds ks * 256 bytes to each start address, i.e. ks * 16 to the
+        // descriptor's low field (addresses stay below 256 KB, so the field never carries)
+        uint64_t adesc[2 * TERMS], bdesc[2];
+#pragma unroll
+        for (int i = 0; i < 2 * TERMS; ++i) adesc[i] = smem_desc(smem_u32(sA + i * a_bytes), 128, 128);
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) bdesc[pl] = smem_desc(smem_u32(sB + pl * TERMS * b_bytes), 128, KC * 16);
         for (int ks = 0; ks < KC / 16; ++ks) {
-          const int ch = ks / kGemmCK;
-          const bool chunk_start = (ks % kGemmCK) == 0;
+          const uint64_t koff = (uint64_t)(ks * 16);
+#pragma unroll
           for (int pl = 0; pl < 2; ++pl)
-            for (int q = 0; q < NPROD; ++q) {
-              int ta, tb;
-              prec_pair(q, ta, tb);
-              const uint64_t ad = smem_desc(smem_u32(sA + (pl * TERMS + ta) * a_bytes) + ks * 256, 128, 128);
-              const uint64_t bd = smem_desc(smem_u32(sB + (pl * TERMS + tb) * b_bytes) + ks * 256, 128, KC * 16);
-              // tile: leading product of accumulator chunk ch, or its corrections
-              const int tile_idx = (NPROD > 1 ? 2 * ch : ch) + (q > 0 ? 1 : 0);
-              const uint32_t d = tmem + (uint32_t)(tile_idx * N);
-              const bool first = chunk_start && pl == 0 && q <= 1;  // q == 0 / 1 open their tiles
+#pragma unroll
+            for (int ta = 0; ta < TERMS; ++ta) {
+              const uint32_t idesc = mma_idesc_bf16(N * b_terms_for(PREC, ta));
+              const uint32_t d = tmem + (uint32_t)tile_col(PREC, ta, N);
+              const bool first = (FOLD || c == 0) && ks == 0 && pl == 0;
               const uint32_t acc = first ? 0u : 1u;
               asm volatile(
                   "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                   "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                  "l"(adesc[pl * TERMS + ta] + koff), "l"(bdesc[pl] + koff), "r"(idesc), "r"(acc));
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
@@ -263,58 +292,84 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const V* __restrict__ 
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // fold the chunk's tiles into the row sums (thread = row 32 w + lane)
+      if constexpr (FOLD) {
+        // row sums of the chunk: the leading product (A term 0 x B term 0) plus the corrections
 #pragma unroll
-      for (int h = 0; h < N / 16; ++h) {
-        for (int t = 0; t < nacc; ++t) {
-          uint32_t v[16];
-          tmem_ld16(taddr + (uint32_t)(t * N + 16 * h), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const bool is_small = (NPROD > 1) && (t & 1);
+        for (int h = 0; h < N / 16; ++h) {
+          float big[16], small[16];
 #pragma unroll
-          for (int cc = 0; cc < 16; ++cc) {
-            if (is_small) small[16 * h + cc] += __uint_as_float(v[cc]);
-            else big[16 * h + cc] += __uint_as_float(v[cc]);
-          }
+          for (int cc = 0; cc < 16; ++cc) big[cc] = small[cc] = 0.f;
+#pragma unroll
+          for (int ta = 0; ta < TERMS; ++ta)
+#pragma unroll
+            for (int tb = 0; tb < b_terms_for(PREC, ta); ++tb) {
+              uint32_t v[16];
+              tmem_ld16(taddr + (uint32_t)(tile_col(PREC, ta, N) + tb * N + 16 * h), v);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+              for (int cc = 0; cc < 16; ++cc) {
+                if (ta == 0 && tb == 0) big[cc] += __uint_as_float(v[cc]);
+                else small[cc] += __uint_as_float(v[cc]);
+              }
+            }
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) run[16 * h + cc] += big[cc] + small[cc];
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();  // shared tiles and tensor memory are rewritten by the next chunk
     }
     if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int64_t ip = i0 + warp * 32 + lane;  // i'
 #pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-      const int j = g * NJ + jj;
-      if (j >= k) break;  // uniform across the block
-      const float re = big[2 * jj] + small[2 * jj], im = big[2 * jj + 1] + small[2 * jj + 1];
-      const int64_t i = (ip + lag0[j]) & mask;
-      if (!WINMAX) {
-        z_out[(int64_t)j * n + i] = cmake<V>((R)re, (R)im);
-      } else {
-        const unsigned long long key = gemm_key(re * re + im * im, (unsigned int)i);
-        unsigned long long* kj = keys + (int64_t)j * nw;
-        const int64_t i_lane0 = __shfl_sync(0xffffffffu, i, 0);
-        const int64_t wA = i_lane0 / W;
-        const int64_t wB = (wA + 1 == nw) ? 0 : wA + 1;
-        const int64_t w = i / W;
-        const bool slow = !(w == wA || w == wB);
-        if (__any_sync(0xffffffffu, slow)) {
-          atomicMax(kj + w, key);
-        } else {
-          unsigned long long kA = (w == wA) ? key : 0ull, kB = (w == wB) ? key : 0ull;
+    for (int h = 0; h < N / 16; ++h) {
+      float val[16];
+      if constexpr (FOLD) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
-            kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
-          }
-          if (lane == 0) {
-            if (kA) atomicMax(kj + wA, kA);
-            if (kB) atomicMax(kj + wB, kB);
+        for (int cc = 0; cc < 16; ++cc) val[cc] = run[16 * h + cc];
+      } else {
+        uint32_t v[16];
+        tmem_ld16(taddr + (uint32_t)(16 * h), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) val[cc] = __uint_as_float(v[cc]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = g * NJ + 8 * h + jj;
+        if (j >= k) break;  // uniform across the block
+        const float re = val[2 * jj], im = val[2 * jj + 1];
+        const int64_t i = (ip + lag0[j]) & mask;
+        if (!WINMAX) {
+          z_out[(int64_t)j * n + i] = cmake<V>((R)re, (R)im);
+        } else {
+          const unsigned long long key = gemm_key(re * re + im * im, (unsigned int)i);
+          unsigned long long* kj = keys + (int64_t)j * nw;
+          const int64_t i_lane0 = __shfl_sync(0xffffffffu, i, 0);
+          const int64_t wA = i_lane0 / W;
+          const int64_t wB = (wA + 1 == nw) ? 0 : wA + 1;
+          const int64_t w = i / W;
+          const bool slow = !(w == wA || w == wB);
+          if (__any_sync(0xffffffffu, slow)) {
+            atomicMax(kj + w, key);
+          } else {
+            unsigned long long kA = (w == wA) ? key : 0ull, kB = (w == wB) ? key : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
+              kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
+            }
+            if (lane == 0) {
+              if (kA) atomicMax(kj + wA, kA);
+              if (kB) atomicMax(kj + wB, kB);
+            }
           }
         }
       }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // tensor memory is rewritten by the next tile
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -335,21 +390,30 @@ size_t gemm_smem_bytes(int terms, int NJ, int KC) {
   return (size_t)2 * terms * nH * 128 + (size_t)2 * terms * (2 * NJ) * KC * 2 + 1024;
 }
 
-// Tensor-memory columns: accumulator tiles of N columns for one K chunk, rounded up to a
-// power of two >= 32.
-int gemm_tmem_cols(int prec, int NJ, int KC) {
-  const int nchunk = (KC / 16 + kGemmCK - 1) / kGemmCK;
-  const int need = (prec_products(prec) > 1 ? 2 : 1) * nchunk * 2 * NJ;
+// Tensor-memory columns: one column group of 2 NJ per product, rounded up to a power of two.
+int gemm_tmem_cols(int prec, int NJ) {
+  const int need = prec_products(prec) * 2 * NJ;
   int cols = 32;
   while (cols < need) cols *= 2;
   return cols;
+}
+
+// Neighbours per group: the widest MMA (all B terms of A term 0) must fit N <= 256, and the
+// tile columns of all products must fit the 512 of tensor memory.
+int gemm_nj_max(int prec) {
+  switch (prec) {
+    case RF_PREC_BF16: return 128;
+    case RF_PREC_BF16X3: return 48;
+    case RF_PREC_BF16X6: return 40;
+    default: return 24;
+  }
 }
 
 template <typename V, int NJ, int PREC, bool WINMAX>
 void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, unsigned long long* keys, int64_t W,
                  int64_t nw, cudaStream_t s) {
   const int KC = kern->gemm_KC, NCK = kern->gemm_NCK;
-  const int cols = gemm_tmem_cols(PREC, NJ, KC);
+  const int cols = gemm_tmem_cols(PREC, NJ);
   RF_REQUIRE(cols <= 512, "tensor-core form: %d tensor-memory columns needed", cols);
   // shared memory sized so that the blocks resident on one SM never ask for more than the
   // 512 tensor-memory columns of the SM (an allocation would otherwise wait for a release)
@@ -369,34 +433,53 @@ void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, un
   int TM = 1;
   while (TM < 16 && (tiles / (TM * 2)) * groups >= 4LL * c->nsm) TM *= 2;
   dim3 grid((unsigned)((tiles + TM - 1) / TM), (unsigned)groups);
-  fn<<<grid, kGemmThreads, smem, s>>>(z_ref, c->n, kern->gemm_B.as<__nv_bfloat16>(), KC, NCK, kern->k,
+  // z_ref split into BF16 planes, padded so that no Hankel window wraps
+  const int terms = prec_terms(PREC);
+  const int64_t LP = (int64_t)KC * NCK;
+  const int64_t zpad = gemm_zpad(LP), zlen = gemm_zlen(c->n, LP);
+  c->scratch2.ensure(gemm_zplanes_bytes(c->n, LP, terms));
+  __nv_bfloat16* zp = c->scratch2.as<__nv_bfloat16>();
+  k_gemm_split_z<V><<<(unsigned)((zlen + 255) / 256), 256, 0, s>>>(z_ref, c->n, zpad, zlen, terms, zp);
+  RF_LAUNCHED();
+  fn<<<grid, kGemmThreads, smem, s>>>(zp, zpad, zlen, c->n, kern->gemm_B.as<__nv_bfloat16>(), KC, NCK, kern->k,
                                       kern->lag0_d.as<int>(), TM, z_out, keys, W, nw, cols, c->status.as<int>());
   RF_LAUNCHED();
 }
 
-template <typename V, int NJ, bool WINMAX>
+template <typename V, int PREC, bool WINMAX>
+void launch_gemm_nj(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, unsigned long long* keys, int64_t W,
+                    int64_t nw, cudaStream_t s) {
+  constexpr int NJMAX = PREC == RF_PREC_BF16 ? 128 : PREC == RF_PREC_BF16X3 ? 48 : PREC == RF_PREC_BF16X6 ? 40 : 24;
+  if (kern->gemm_NJ == 16) launch_gemm<V, 16, PREC, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s);
+  else launch_gemm<V, NJMAX, PREC, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s);
+}
+
+template <typename V, bool WINMAX>
 void launch_gemm_prec(rf_ctx* c, const rf_kernels* kern, int prec, const V* z_ref, V* z_out,
                       unsigned long long* keys, int64_t W, int64_t nw, cudaStream_t s) {
   switch (prec) {
-    case RF_PREC_BF16: launch_gemm<V, NJ, RF_PREC_BF16, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
-    case RF_PREC_BF16X3: launch_gemm<V, NJ, RF_PREC_BF16X3, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
-    case RF_PREC_BF16X6: launch_gemm<V, NJ, RF_PREC_BF16X6, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
-    default: launch_gemm<V, NJ, RF_PREC_BF16X9, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    case RF_PREC_BF16: launch_gemm_nj<V, RF_PREC_BF16, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    case RF_PREC_BF16X3: launch_gemm_nj<V, RF_PREC_BF16X3, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    case RF_PREC_BF16X6: launch_gemm_nj<V, RF_PREC_BF16X6, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    default: launch_gemm_nj<V, RF_PREC_BF16X9, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
   }
 }
 
 }  // namespace
 
+size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int terms) {
+  return sizeof(__nv_bfloat16) * (size_t)(2 * terms) * (size_t)gemm_zlen(n, LP) + 256;
+}
+
 int gemm_max_len() { return 1 << 16; }
 
 void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
   const int terms = prec_terms(prec);
-  // K chunks of at most 256 taps, a multiple of 16 each
+  // K chunks of 128 taps; groups of 16 neighbours when the set is small, else the widest
   const int L16 = std::max(16, (kern->max_len + 15) / 16 * 16);
-  const int NCK = (L16 + 255) / 256;
-  const int KC = ((L16 + NCK - 1) / NCK + 15) / 16 * 16;
-  int NJ = 16;
-  if (gemm_smem_bytes(terms, NJ, KC) > 220 * 1024) NJ = 8;
+  const int KC = std::min(128, L16);
+  const int NCK = (L16 + KC - 1) / KC;
+  const int NJ = kern->k <= 16 ? 16 : gemm_nj_max(prec);
   RF_REQUIRE(gemm_smem_bytes(terms, NJ, KC) <= 220 * 1024, "tensor-core direct form: chunk of %d taps does not fit",
              KC);
   if (kern->gemm_ready && kern->gemm_terms == terms && kern->gemm_KC == KC && kern->gemm_NCK == NCK &&
@@ -441,13 +524,8 @@ void reconstruct_gemm(rf_ctx* c, const void* z_ref, rf_kernels* kern, int prec, 
     using V = decltype(vtag);
     const V* zr = static_cast<const V*>(z_ref);
     V* zo = static_cast<V*>(z_out);
-    if (kern->gemm_NJ == 16) {
-      if (win) launch_gemm_prec<V, 16, true>(c, kern, prec, zr, nullptr, keys, W, nw, s);
-      else launch_gemm_prec<V, 16, false>(c, kern, prec, zr, zo, nullptr, 0, 0, s);
-    } else {
-      if (win) launch_gemm_prec<V, 8, true>(c, kern, prec, zr, nullptr, keys, W, nw, s);
-      else launch_gemm_prec<V, 8, false>(c, kern, prec, zr, zo, nullptr, 0, 0, s);
-    }
+    if (win) launch_gemm_prec<V, true>(c, kern, prec, zr, nullptr, keys, W, nw, s);
+    else launch_gemm_prec<V, false>(c, kern, prec, zr, zo, nullptr, 0, 0, s);
   };
   if (c->g.dtype == RF_F64) go(double2{});
   else go(float2{});

@@ -178,6 +178,8 @@ void winmax_series(rf_ctx* c, const void* z, int32_t count, int64_t W, float* ma
 int os_default_block(const rf_ctx* c);
 void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W);
+// bytes of the BF16 planes of z_ref used by the tensor-core path (taps padded to LP)
+size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int terms);
 void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,
                     int32_t* argmax_out, cudaStream_t s);
 void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,

@@ -440,6 +440,27 @@ def test_reconstruct_batched_matches_per_group_and_oracle(torch):
     assert torch.allclose(P3, P, rtol=4 * TOL["f32"], atol=4 * TOL["f32"] * P.max().item())
 
 
+@pytest.mark.parametrize("algo,prec", [("direct", "native"), ("gemm", "bf16x6")])
+def test_reconstruct_batched_other_forms_match_per_group(torch, algo, prec):
+    """The batched entry with the direct or tensor-core form writes, group after group, the
+    same rows as the per-group calls."""
+    cfg = _batch_cfg()
+    ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
+    x = torch.tensor(data.strain(cfg), dtype=torch.float32, device="cuda")
+    rf = _rf(cfg)
+    refs = [g[0] for g in cfg.groups]
+    z, _ = rf.mf_reference(x, ip, refs)
+    kerns = [rf.build_ratio_kernels(r, nb, ip, cfg.threshold) for r, nb in cfg.groups]
+    W = cfg.window
+    P, A = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W, algo, prec=prec)
+    row = 0
+    for g, k in enumerate(kerns):
+        Pg, Ag = rf.reconstruct_winmax(z[g], k, W, algo, prec=prec)
+        assert torch.equal(P[row:row + k.k], Pg) and torch.equal(A[row:row + k.k], Ag)
+        row += k.k
+    assert row == P.shape[0]
+
+
 def test_batched_step_captures_in_a_cuda_graph(torch):
     """After a warm-up call, the whole online step (matched filter of every reference,
     reference peaks, batched reconstruction) replays from a CUDA graph with the same result."""
@@ -550,3 +571,32 @@ def test_reconstruct_gemm_precision_form_workload(torch):
     P, A = rf.reconstruct_winmax(z[0], kern, cfg.window, "gemm", prec="bf16x6")
     inj = cfg.injections[0]
     assert A[inj.template_index, inj.sample // cfg.window].item() == inj.sample
+
+
+def test_reconstruct_gemm_wide_groups(torch):
+    """More neighbours than one 16-wide group: the widest tensor-core tiles (all split terms of
+    a group side by side in N) against the oracle, with a ragged last group."""
+    n = 1 << 12
+    rng = np.random.default_rng(23)
+    k = 101
+    lengths = list(rng.integers(1, 300, k))
+    lags = list(rng.integers(-n // 2 + 1, n // 2, k))
+    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype="f32")
+    rf = _rf(cfg)
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    taps = [((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(L)).astype(np.complex64)
+            for L in lengths]
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    zt = torch.tensor(z, device="cuda")
+    zo = [reconstruct.reconstruct_direct(z.astype(np.complex128), int(lags[j]), taps[j].astype(np.complex128))
+          for j in range(k)]
+    for prec, tol in GEMM_TOL.items():
+        out = rf.reconstruct(zt, kern, "gemm", prec=prec).cpu().numpy()
+        worst = max(_relerr(out[j], zo[j]) for j in range(k))
+        assert worst < tol, (prec, worst)
+    P, A = rf.reconstruct_winmax(zt, kern, 512, "gemm", prec="bf16x6")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    for j in range(0, k, 7):
+        Po, Ao = reconstruct.window_peaks(zo[j], 512)
+        assert np.abs(P[j] - Po).max() <= 4 * GEMM_TOL["bf16x6"] * Po.max()
+        _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, 512, 8 * GEMM_TOL["bf16x6"] * Po.max())
