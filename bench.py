@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--prec", default=None, choices=["native", "bf16", "bf16x3", "bf16x6", "bf16x9"],
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
-    ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default 8192)")
+    ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default)")
+    ap.add_argument("--part", type=int, default=0,
+                    help="overlap-save partition length: block/2, /4 or /8 (0: library default)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--kernels", type=int, default=None, help="neighbours per group (default: the config's)")
@@ -222,13 +224,15 @@ def cpu_baseline(cfg, n_nbrs=4, slice_len=1 << 12, budget_s=20.0):
 
 # --------------------------------------------------------------------------- ncu traffic
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, layout: str = None):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
-    kernel's sources changed since that capture (or no capture exists)."""
+    kernel's sources (or its layout) changed since that capture, or no capture exists."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))[kernel]
+        if layout is not None and rec.get("layout") != layout:
+            return None
         m = hashlib.sha256()
         for f in rec["sources"]:
             m.update(open(os.path.join(ROOT, "paper_2511_12894_gb300", "csrc", f), "rb").read())
@@ -308,12 +312,12 @@ def main():
     algo_used = args.algo if args.algo != "auto" else ("os" if cfg.dtype == "f32" else "direct")
     if algo_used == "os":
         for k in kerns:
-            k.prepare(args.block)
+            k.prepare(args.block, args.part)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     L = np.concatenate([k.length for k in kerns]).astype(np.float64)
     rows = int(L.size)
-    B = args.block or 8192
+    B, Lp = kerns[0].os_layout() if algo_used == "os" else (0, 0)
 
     nw = -(-n // W)
     z = torch.empty((G, n), dtype=rf.cdtype, device=dev)
@@ -432,10 +436,11 @@ def main():
 
     # ---------------- roofline of the dominant kernel (the neighbour reconstruction)
     if algo_used == "os":
-        # per output block of H = B/2 samples: one inverse B-point FFT (5 B log2 B) and
-        # P_j complex multiply-adds per bin (8 P_j B); the segment spectra are shared
-        H = B // 2
-        P = np.maximum(1, np.ceil(L / H))
+        # per output block of H = B - Lp samples: one inverse B-point FFT (5 B log2 B) and
+        # P_j = ceil(L_j / Lp) complex multiply-adds per bin (8 P_j B); the segment spectra
+        # are shared by all neighbours of a reference
+        H = B - Lp
+        P = np.maximum(1, np.ceil(L / Lp))
         flops = float(np.sum((5.0 * B * math.log2(B) + 8.0 * P * B) / H)) * n
     else:
         flops = 8.0 * float(L.sum()) * n
@@ -470,9 +475,9 @@ def main():
         achieved = flops / (rec_avg_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops,
-                    "traffic": ncu_traffic("k_os") if (algo_used == "os" and G == 1 and args.config == 2
-                                                       and (args.block or 8192) == 8192) else None,
-                    "kernel": f"reconstruct ({algo_used}{', B=%d' % B if algo_used == 'os' else ''}, "
+                    "traffic": ncu_traffic("k_os", f"B={B},Lp={Lp}") if (algo_used == "os" and G == 1
+                                                                            and args.config == 2) else None,
+                    "kernel": f"reconstruct ({algo_used}{', B=%d, Lp=%d' % (B, Lp) if algo_used == 'os' else ''}, "
                               f"{'FP64' if cfg.dtype == 'f64' and algo_used == 'direct' else 'FP32'} CUDA cores, "
                               f"{'batched persistent' if G > 1 else 'one reference'})",
                     "peak_note": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",

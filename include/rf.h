@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RF_ABI_VERSION 1
+#define RF_ABI_VERSION 2
 
 typedef struct rf_ctx rf_ctx;
 typedef struct rf_kernels rf_kernels;
@@ -164,12 +164,20 @@ rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** le
                           const int32_t** lag0, const int64_t** offset, const double** df_low,
                           const void** taps_dev);
 
-/* Prepare a kernel set for overlap-save reconstruction (RF_F32 grids, n >= 512): block
- * size B (a power of two in [512, 16384], <= n; 0 picks the default 8192), partitions of
- * B/2 taps, and their spectra FFT_B(taps)/B computed in FP64 and stored as complex64 inside
- * the kernel set.  The first overlap-save reconstruction prepares with the default block if
- * this was not called.  Allocates; SYNCHRONISES `stream`. */
-rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, rf_stream stream);
+/* Prepare a kernel set for overlap-save reconstruction (Eq. 7 in blocks; RF_F32 grids,
+ * n >= 512): block size B (a power of two in [512, 16384], <= n) and partition length Lp
+ * (B/2, B/4 or B/8 taps); 0 for either picks, among the allowed layouts, the one of least
+ * modelled cost for this set's kernel lengths (a per-block cost table measured on GB300,
+ * plus a penalty for launches too small to fill the GPU).  Computes the partition spectra
+ * FFT_B(taps)/B in FP64 and stores them as complex64 inside the kernel set
+ * (sum_j ceil(L_j / Lp) x B complex64).  Each output block transform then keeps B - Lp
+ * outputs.  The first overlap-save reconstruction prepares with the modelled choice if this
+ * was not called.  Allocates; SYNCHRONISES `stream`.  RF_EINVAL for other sizes. */
+rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, int32_t part, rf_stream stream);
+
+/* Overlap-save layout a kernel set is prepared for: block size and partition length (both 0
+ * when not prepared).  Either output pointer may be NULL. */
+rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* part);
 
 /* Copy the packed taps (sum(len) complex entries, grid dtype) into caller device memory
  * `dst`.  Async on stream. */
@@ -182,8 +190,8 @@ void rf_kernels_free(rf_kernels* kern);
  * z_ref: complex[n]; z_out: complex[k][n] (grid dtype).  algo: rf_algo.  RF_ALGO_OS needs an
  * RF_F32 grid with n >= 512 (else RF_EUNSUPPORTED) and evaluates the same sum through the
  * frequency form (Eq. 7) in overlap-save blocks; RF_ALGO_AUTO takes OS on RF_F32 grids and the
- * direct sum on RF_F64 grids.  The context's workspace grows on first use (2 n complex64 for
- * OS; see rf_reserve).  Async on stream, except that an OS call on a kernel set that was not
+ * direct sum on RF_F64 grids.  The context's workspace grows on first use ((B / Lp) n
+ * complex64 for OS; see rf_reserve).  Async on stream, except that an OS call on a kernel set that was not
  * prepared prepares it first (see rf_kernels_prepare). */
 rf_status rf_reconstruct(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo,
                          int32_t prec, void* z_out, rf_stream stream);

@@ -30,6 +30,7 @@ PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
 EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
+    "rf_kernels_os_layout",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status",
 )
@@ -79,7 +80,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_kernels_import": (i32, [vp, i32, P(i32), P(i32), vp, P(vp)]),
         "rf_kernels_info": (i32, [vp, P(i32), P(P(i32)), P(P(i32)), P(P(i64)), P(P(dbl)), P(vp)]),
         "rf_kernels_copy_taps": (i32, [vp, vp, vp]),
-        "rf_kernels_prepare": (i32, [vp, vp, i32, vp]),
+        "rf_kernels_prepare": (i32, [vp, vp, i32, i32, vp]),
+        "rf_kernels_os_layout": (i32, [vp, P(i32), P(i32)]),
         "rf_kernels_free": (None, [vp]),
         "rf_reconstruct": (i32, [vp, vp, vp, i32, i32, vp, vp]),
         "rf_reconstruct_winmax": (i32, [vp, vp, vp, i32, i32, i64, vp, vp, vp]),
@@ -153,9 +155,16 @@ class Kernels:
             _check(_lib.rf_kernels_copy_taps(self.handle, ctypes.c_void_p(t.data_ptr()), _stream()))
         return t
 
-    def prepare(self, block: int = 0, stream=None) -> None:
-        """Overlap-save preparation with block size ``block`` (0: default); synchronises."""
-        _check(_lib.rf_kernels_prepare(self.ctx.handle, self.handle, int(block), _stream(stream)))
+    def prepare(self, block: int = 0, part: int = 0, stream=None) -> None:
+        """Overlap-save preparation with block size ``block`` and partition length ``part``
+        (0: defaults); synchronises."""
+        _check(_lib.rf_kernels_prepare(self.ctx.handle, self.handle, int(block), int(part), _stream(stream)))
+
+    def os_layout(self):
+        """(block size, partition length) of the overlap-save preparation, (0, 0) if none."""
+        b, p = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(_lib.rf_kernels_os_layout(self.handle, ctypes.byref(b), ctypes.byref(p)))
+        return b.value, p.value
 
     def free(self) -> None:
         if self.handle:

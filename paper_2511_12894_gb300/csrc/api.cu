@@ -164,7 +164,7 @@ rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out) {
     check_ctx(ctx);
     RF_REQUIRE(k_max >= 0, "k_max must be non-negative");
     // overlap-save segment spectra plus packed window keys for windows of >= 16 samples
-    const size_t bytes = os_workspace_bytes(ctx, k_max, 16);
+    const size_t bytes = os_workspace_bytes(ctx, k_max, 16, 8);  // the largest partition ratio
     ctx->scratch.ensure(bytes);
     // BF16 planes of z_ref for the tensor-core path, for taps up to the segment length
     const size_t planes = gemm_zplanes_bytes(ctx->n, ctx->n + 128, 3);
@@ -252,7 +252,7 @@ rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** le
   });
 }
 
-rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, rf_stream stream) {
+rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, int32_t part, rf_stream stream) {
   return guard([&] {
     check_ctx(ctx);
     RF_REQUIRE(kern != nullptr, "kern is NULL");
@@ -261,7 +261,16 @@ rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, rf_st
       set_error("overlap-save needs an RF_F32 grid with n >= 512");
       throw Fail{RF_EUNSUPPORTED};
     }
-    os_prepare(ctx, kern, block ? block : os_default_block(ctx), (cudaStream_t)stream);
+    RF_REQUIRE(block >= 0 && part >= 0, "block and part must be non-negative");
+    os_prepare(ctx, kern, block, part, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* part) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    if (block) *block = kern->os_ready ? kern->os_B : 0;
+    if (part) *part = kern->os_ready ? kern->os_Lp : 0;
   });
 }
 

@@ -1,15 +1,19 @@
 // Overlap-save reconstruction (frequency form of the ratio identity, Eq. 7) with
 // uniformly partitioned kernels, FP32.
 //
-// With block size B and hop H = B/2:
-//   segment spectra (once per reference, shared by all neighbours)
-//     Zs[s] = FFT_B( z_ref[(s H - H + t) mod n], t < B ),          s < NS = n / H
+// Block size B, partition length Lp = B / Q (Q = 2, 4 or 8) and hop H = B - Lp:
+//   segment spectra (once per reference, shared by all neighbours), NQ = n / Lp of them
+//     Zs[q] = FFT_B( z_ref[(q Lp + t) mod n], t < B )
 //   kernel partition spectra (once per kernel set, FP64 then rounded)
-//     C[j][p] = FFT_B( c_j[p H + u] for u < H, zero above ) / B,   p < P_j = ceil(L_j / H)
-//   output block s of neighbour j
-//     y = IFFT_B( sum_p Zs[(s - p) mod NS] C[j][p] ),  w_j[s H + t - H] = y[t] for H <= t < B,
-// which is w_j[i'] = sum_l c_j[l] z_ref[(i' - l) mod n], and z_j[i] = w_j[(i - m0_j) mod n]:
-// the first lag is applied by relabelling outputs, so every neighbour shares Zs.
+//     C[j][p] = FFT_B( c_j[p Lp + u] for u < Lp, zero above ) / B,   p < P_j = ceil(L_j / Lp)
+//   output block s of neighbour j (s < NB = ceil(n / H))
+//     y = IFFT_B( sum_p Zs[(s (Q - 1) - p - 1) mod NQ] C[j][p] ),
+//     w_j[s H + t - Lp] = y[t] for Lp <= t < B (and s H + t - Lp < n),
+// which is w_j[i'] = sum_l c_j[l] z_ref[(i' - l) mod n] (the circular product of a B-point
+// segment with a partition of Lp taps is free of wrap-around from t = Lp - 1 on), and
+// z_j[i] = w_j[(i - m0_j) mod n]: the first lag is applied by relabelling outputs, so every
+// neighbour shares Zs.  Q = 2 is the classic half-overlap form; larger Q keeps more outputs
+// per block transform at the price of more (cheap) partition products.
 // The window peaks are reduced per warp and merged across blocks with 64-bit
 // atomicMax on (float bits of |z|^2) << 32 | (2^32 - 1 - i), which orders by value
 // and then by the smallest index.
@@ -29,17 +33,16 @@ __device__ __forceinline__ unsigned long long pack_key(float v, unsigned int i) 
 }
 
 template <int B>
-__global__ void __launch_bounds__(B / 16) k_os_segments(const float2* __restrict__ z_ref, int64_t n,
+__global__ void __launch_bounds__(B / 16) k_os_segments(const float2* __restrict__ z_ref, int64_t n, int Lp,
                                                         const float2* __restrict__ tw, float2* __restrict__ Zs) {
   using S = BlockFFTShape<B>;
   extern __shared__ float2 sm[];
-  constexpr int H = B / 2;
   const int64_t s = blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t mask = n - 1;
   float2 v[16];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) v[t] = z_ref[(s * H - H + tid + t * (B / 16)) & mask];
+  for (int t = 0; t < 16; ++t) v[t] = z_ref[(s * Lp + tid + t * (B / 16)) & mask];
   block_fft<B, -1>(v, sm, tw);
   float2* out = Zs + s * B;
 #pragma unroll
@@ -48,43 +51,44 @@ __global__ void __launch_bounds__(B / 16) k_os_segments(const float2* __restrict
     for (int t = 0; t < S::RL; ++t) out[tid + q * S::NT + t * (B / S::RL)] = v[q * S::RL + t];
 }
 
-// One neighbour's output blocks [s0, s1): spectral products, inverse block FFT, then either
-// the series (zrow != nullptr) or the window peaks (keys row kj).
 // Segment spectra of several references: block (s, g) transforms segment s of z_refs[g].
 template <int B>
 __global__ void __launch_bounds__(B / 16) k_os_segments_batched(const float2* const* __restrict__ z_refs, int64_t n,
-                                                                const float2* __restrict__ tw,
+                                                                int Lp, const float2* __restrict__ tw,
                                                                 float2* __restrict__ Zs_all) {
   using S = BlockFFTShape<B>;
   extern __shared__ float2 sm[];
-  constexpr int H = B / 2;
   const int64_t s = blockIdx.x;
   const int64_t g = blockIdx.y;
-  const int64_t NS = n / H;
+  const int64_t NQ = n / Lp;
   const float2* z_ref = z_refs[g];
   const int tid = threadIdx.x;
   const int64_t mask = n - 1;
   float2 v[16];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) v[t] = z_ref[(s * H - H + tid + t * (B / 16)) & mask];
+  for (int t = 0; t < 16; ++t) v[t] = z_ref[(s * Lp + tid + t * (B / 16)) & mask];
   block_fft<B, -1>(v, sm, tw);
-  float2* out = Zs_all + (g * NS + s) * B;
+  float2* out = Zs_all + (g * NQ + s) * B;
 #pragma unroll
   for (int q = 0; q < 16 / S::RL; ++q)
 #pragma unroll
     for (int t = 0; t < S::RL; ++t) out[tid + q * S::NT + t * (B / S::RL)] = v[q * S::RL + t];
 }
 
-template <int B, bool WINMAX>
+// One neighbour's output blocks [s0, s1): spectral products, inverse block FFT, then either
+// the series (zrow != nullptr) or the window peaks (keys row kj).
+template <int B, int Q, bool WINMAX>
 __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const float2* __restrict__ C, int P,
-                                          int64_t m0, const float2* __restrict__ tw, int64_t n, int NS, int s0,
+                                          int64_t m0, const float2* __restrict__ tw, int64_t n, int NQ, int s0,
                                           int s1, float2* __restrict__ zrow, unsigned long long* __restrict__ kj,
                                           int64_t W, int64_t nw, int fastwin, float2* sm) {
   using S = BlockFFTShape<B>;
   constexpr int NT = S::NT;
-  constexpr int H = B / 2;
+  constexpr int LP = B / Q;   // partition length: outputs start at block position LP
+  constexpr int H = B - LP;   // outputs per block
   constexpr int RL = S::RL;
-  constexpr int CH = H / NT;  // outputs per thread in the peak reduction (8)
+  constexpr int CH = H / NT;  // outputs per thread in the peak reduction (8, 12 or 14)
+  static_assert(Q == 2 || Q == 4 || Q == 8, "partition ratio");
   const int tid = threadIdx.x;
   const int64_t mask = n - 1;
   for (int s = s0; s < s1; ++s) {
@@ -92,10 +96,10 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
 #pragma unroll
     for (int t = 0; t < 16; ++t) v[t] = make_float2(0.f, 0.f);
     // partitions outermost: each pass issues all 32 loads of the thread's bins at once
-    for (int p = 0; p < P; ++p) {
-      int sp = s - p;
-      sp += (sp < 0) ? NS : 0;
-      const float2* zp = Zs + (int64_t)sp * B + tid;
+    int sp = s * (Q - 1) - 1;  // segment of partition 0; always < NQ
+    for (int p = 0; p < P; ++p, --sp) {
+      const int q = sp + ((sp < 0) ? NQ : 0);  // sp >= -NQ because P <= NQ
+      const float2* zp = Zs + (int64_t)q * B + tid;
       const float2* cp = C + (int64_t)p * B + tid;
 #pragma unroll
       for (int h = 0; h < 16; h += 8) {
@@ -113,14 +117,16 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
       }
     }
     block_fft<B, +1>(v, sm, tw);
-    const int64_t base = ((int64_t)s * H + m0) & mask;  // output index of block position H
+    const int64_t o0 = (int64_t)s * H;                // pre-relabel index of block position LP
+    const int64_t base = (o0 + m0) & mask;            // its output index
+    const int64_t lim = n - o0;                       // block positions LP + t with t < lim exist
     if (!WINMAX) {
 #pragma unroll
       for (int q = 0; q < 16 / RL; ++q)
 #pragma unroll
-        for (int t = RL / 2; t < RL; ++t) {
-          const int idx = tid + q * NT + t * (B / RL);  // >= H
-          zrow[(base + idx - H) & mask] = v[q * RL + t];
+        for (int t = 0; t < RL; ++t) {
+          const int idx = tid + q * NT + t * (B / RL);
+          if (idx >= LP && idx - LP < lim) zrow[(base + idx - LP) & mask] = v[q * RL + t];
         }
       __syncthreads();  // the next block's FFT overwrites the shared memory read above
     } else {
@@ -129,18 +135,29 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
 #pragma unroll
       for (int q = 0; q < 16 / RL; ++q)
 #pragma unroll
-        for (int t = RL / 2; t < RL; ++t) {
+        for (int t = 0; t < RL; ++t) {
           const int idx = tid + q * NT + t * (B / RL);
-          const float2 y = v[q * RL + t];
-          mag[idx - H] = y.x * y.x + y.y * y.y;
+          if (idx >= LP) {
+            const float2 y = v[q * RL + t];
+            mag[idx - LP] = y.x * y.x + y.y * y.y;
+          }
         }
       __syncthreads();
       const int lane = tid & 31;
       const int qbase = tid * CH;
       float mv[CH];
+      if constexpr (CH % 4 == 0) {
 #pragma unroll
-      for (int e = 0; e < CH; e += 4)
-        *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + qbase + e);
+        for (int e = 0; e < CH; e += 4)
+          *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + qbase + e);
+      } else {
+#pragma unroll
+        for (int e = 0; e < CH; e += 2)
+          *reinterpret_cast<float2*>(mv + e) = *reinterpret_cast<const float2*>(mag + qbase + e);
+      }
+      // outputs of this thread that exist (all but possibly in the last block)
+      const int64_t avail = lim - qbase;
+      const int cnt = avail <= 0 ? 0 : (avail >= CH ? CH : (int)avail);
       // sample index and window of this thread's first output; later outputs step by one
       // (wrapping at n), so one division per thread suffices
       int i0 = (int)((base + qbase) & mask);
@@ -154,10 +171,10 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
         int i = i0, w = w0, r = r0;
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
-          const unsigned long long key = pack_key(mv[e], (unsigned int)i);
+          const unsigned long long key = e < cnt ? pack_key(mv[e], (unsigned int)i) : 0ull;
           if (w == wA) kA = max(kA, key);
           else if (w == wB) kB = max(kB, key);
-          else slow = true;
+          else if (e < cnt) slow = true;
           ++i;
           ++r;
           if (i == (int)n) {
@@ -173,8 +190,9 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
       const bool any_slow = __any_sync(0xffffffffu, slow);
       if (any_slow) {
         int i = i0, w = w0, r = r0;
+#pragma unroll
         for (int e = 0; e < CH; ++e) {
-          atomicMax(kj + w, pack_key(mv[e], (unsigned int)i));
+          if (e < cnt) atomicMax(kj + w, pack_key(mv[e], (unsigned int)i));
           ++i;
           ++r;
           if (i == (int)n) {
@@ -202,18 +220,18 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
   }
 }
 
-template <int B, bool WINMAX>
+template <int B, int Q, bool WINMAX>
 __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restrict__ Zs, const float2* __restrict__ Cs,
                                               const int64_t* __restrict__ spec_off, const int* __restrict__ parts,
                                               const int* __restrict__ lag0, const float2* __restrict__ tw, int64_t n,
-                                              int NS, int SC, float2* __restrict__ z_out,
+                                              int NQ, int NB, int SC, float2* __restrict__ z_out,
                                               unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
                                               int fastwin) {
   extern __shared__ float2 sm[];
   const int j = blockIdx.y;
   const int s0 = blockIdx.x * SC;
-  const int s1 = min(NS, s0 + SC);
-  os_blocks<B, WINMAX>(Zs, Cs + spec_off[j], parts[j], lag0[j], tw, n, NS, s0, s1,
+  const int s1 = min(NB, s0 + SC);
+  os_blocks<B, Q, WINMAX>(Zs, Cs + spec_off[j], parts[j], lag0[j], tw, n, NQ, s0, s1,
                        WINMAX ? nullptr : z_out + (int64_t)j * n, WINMAX ? keys + (int64_t)j * nw : nullptr, W, nw,
                        fastwin, sm);
 }
@@ -231,10 +249,11 @@ struct OsItem {
   long long row;
 };
 
-template <int B>
+template <int B, int Q>
 __global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* __restrict__ items, int64_t units,
                                                                  int nchunk, const float2* __restrict__ tw, int64_t n,
-                                                                 int NS, int SC, unsigned long long* __restrict__ keys,
+                                                                 int NQ, int NB, int SC,
+                                                                 unsigned long long* __restrict__ keys,
                                                                  int64_t W, int64_t nw, int fastwin,
                                                                  unsigned long long* __restrict__ counter) {
   extern __shared__ float2 sm[];
@@ -247,8 +266,9 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* 
     if (u >= units) break;
     const OsItem it = items[u / nchunk];
     const int s0 = (int)(u % nchunk) * SC;
-    const int s1 = min(NS, s0 + SC);
-    os_blocks<B, true>(it.Zs, it.C, it.P, it.lag0, tw, n, NS, s0, s1, nullptr, keys + it.row * nw, W, nw, fastwin, sm);
+    const int s1 = min(NB, s0 + SC);
+    os_blocks<B, Q, true>(it.Zs, it.C, it.P, it.lag0, tw, n, NQ, s0, s1, nullptr, keys + it.row * nw, W, nw, fastwin,
+                          sm);
   }
 }
 
@@ -261,17 +281,16 @@ __global__ void k_unpack_keys(const unsigned long long* __restrict__ keys, int64
   arg[i] = (int)(0xffffffffu - (unsigned int)(k & 0xffffffffull));
 }
 
-// rows[g][u] = taps of partition (j, p) = g, promoted to FP64, zero above H or L_j
+// rows[g][u] = taps of partition (j, p) = g, promoted to FP64, zero from u = Lp or l = L_j on
 __global__ void k_os_fill(const float2* __restrict__ taps, const int64_t* __restrict__ off,
                           const int* __restrict__ len, const int* __restrict__ gj, const int* __restrict__ gp,
-                          int B, double2* __restrict__ rows) {
+                          int B, int Lp, double2* __restrict__ rows) {
   const int g = blockIdx.y;
   const int j = gj[g], p = gp[g];
-  const int H = B / 2;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < B; u += gridDim.x * blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
-    const int l = p * H + u;
-    if (u < H && l < len[j]) {
+    const int64_t l = (int64_t)p * Lp + u;
+    if (u < Lp && l < len[j]) {
       const float2 c = taps[off[j] + l];
       v = make_double2((double)c.x, (double)c.y);
     }
@@ -290,27 +309,35 @@ size_t os_smem() {
 }
 
 template <int B>
-void launch_os_segments(rf_ctx* c, const float2* z_ref, float2* Zs, cudaStream_t s) {
-  const int NS = (int)(c->n / (B / 2));
+void launch_os_segments(rf_ctx* c, const float2* z_ref, int Lp, float2* Zs, cudaStream_t s) {
+  const int NQ = (int)(c->n / Lp);
   const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<B>::LOGB];
   auto fn = k_os_segments<B>;
   RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<B>()));
-  fn<<<NS, B / 16, os_smem<B>(), s>>>(z_ref, c->n, tw, Zs);
+  fn<<<NQ, B / 16, os_smem<B>(), s>>>(z_ref, c->n, Lp, tw, Zs);
   RF_LAUNCHED();
 }
 
-template <int B, bool WINMAX>
+// outputs of a window that one warp's epilogue covers (32 threads x H / (B / 16) outputs)
+template <int B, int Q>
+constexpr int os_warp_span() {
+  return 32 * ((B - B / Q) / (B / 16));
+}
+
+template <int B, int Q, bool WINMAX>
 void launch_os(rf_ctx* c, const rf_kernels* kern, const float2* Zs, float2* z_out, unsigned long long* keys,
                int64_t W, cudaStream_t s) {
-  const int NS = (int)(c->n / (B / 2));
+  constexpr int Lp = B / Q, H = B - Lp;
+  const int NQ = (int)(c->n / Lp);
+  const int NB = (int)((c->n + H - 1) / H);
   const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<B>::LOGB];
   const int64_t nw = WINMAX ? (c->n + W - 1) / W : 0;
-  // segments per block: enough blocks for every SM several times over
+  // output blocks per CTA: enough CTAs for every SM several times over
   int SC = 8;
-  while (SC > 1 && (int64_t)kern->k * ((NS + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
-  const int nchunk = (NS + SC - 1) / SC;
-  const int fastwin = (WINMAX && W >= 256) ? 1 : 0;  // a warp's 256 outputs span <= 2 windows
-  auto fn = k_os<B, WINMAX>;
+  while (SC > 1 && (int64_t)kern->k * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
+  const int nchunk = (NB + SC - 1) / SC;
+  const int fastwin = (WINMAX && W >= os_warp_span<B, Q>()) ? 1 : 0;  // a warp's outputs span <= 2 windows
+  auto fn = k_os<B, Q, WINMAX>;
   RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<B>()));
   int64_t done = 0;
   while (done < kern->k) {
@@ -318,7 +345,7 @@ void launch_os(rf_ctx* c, const rf_kernels* kern, const float2* Zs, float2* z_ou
     dim3 grid((unsigned)nchunk, (unsigned)cnt);
     fn<<<grid, B / 16, os_smem<B>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>() + done,
                                           kern->os_parts_d.as<int>() + done, kern->lag0_d.as<int>() + done, tw, c->n,
-                                          NS, SC, z_out ? z_out + done * c->n : nullptr,
+                                          NQ, NB, SC, z_out ? z_out + done * c->n : nullptr,
                                           keys ? keys + done * nw : nullptr, W, nw, fastwin);
     RF_LAUNCHED();
     done += cnt;
@@ -336,6 +363,18 @@ void dispatch_b(int B, F&& f) {
     case 16384: f(std::integral_constant<int, 16384>{}); break;
     default: RF_REQUIRE(false, "overlap-save block size %d is not supported", B);
   }
+}
+
+template <typename F>
+void dispatch_bq(int B, int Q, F&& f) {
+  dispatch_b(B, [&](auto bc) {
+    switch (Q) {
+      case 2: f(bc, std::integral_constant<int, 2>{}); break;
+      case 4: f(bc, std::integral_constant<int, 4>{}); break;
+      case 8: f(bc, std::integral_constant<int, 8>{}); break;
+      default: RF_REQUIRE(false, "overlap-save partition ratio %d is not supported", Q);
+    }
+  });
 }
 
 }  // namespace
@@ -386,24 +425,61 @@ std::vector<float2> block_fft_tables(int64_t off[16]) {
   return out;
 }
 
-int os_default_block(const rf_ctx* c) {
-  int B = 8192;
-  while (B > 512 && B > c->n) B /= 2;
-  return B;
+// Layout choice by a cost model.  Per neighbour, a layout (B, Lp) runs NB = ceil(n / (B - Lp))
+// output blocks, each one inverse block transform plus P = ceil(L / Lp) spectral
+// multiply-adds; the model charges F(B) + P M(B) per block, with F and M the throughput
+// costs per block (ns, whole GPU) measured on a GB300 for B >= 4096 on the 3.5PN
+// 2^20-sample workload and scaled by B log B (F) and B (M) below that, and a fill penalty
+// when the launch has fewer blocks than the GPU holds at once.
+double os_layout_cost(const rf_ctx* c, const std::vector<int>& lengths, int B, int Lp) {
+  static const double F[6] = {0.9, 1.9, 4.2, 9.9, 29.5, 70.3};   // B = 512 .. 16384
+  static const double M[6] = {0.37, 0.73, 1.47, 2.93, 5.1, 10.8};
+  int b = 0;
+  while ((512 << b) < B) ++b;
+  const int64_t H = B - Lp;
+  const int64_t NB = (c->n + H - 1) / H;
+  double cost = 0.0;
+  for (const int L : lengths) cost += (double)NB * (F[b] + (double)std::max(1, (L + Lp - 1) / Lp) * M[b]);
+  const double blocks = (double)NB * (double)lengths.size();
+  const double slots = (double)c->nsm * (16384 / B);
+  return blocks < slots ? cost * slots / blocks : cost;
 }
 
-void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s) {
+void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, int* B_out, int* Lp_out) {
+  double best = 0.0;
+  int bB = 0, bL = 0;
+  for (int B = 512; B <= 16384; B *= 2) {
+    if (B > c->n || (block && B != block)) continue;
+    for (int Q = 2; Q <= 8; Q *= 2) {
+      const double cost = os_layout_cost(c, lengths, B, B / Q);
+      if (!bB || cost < best) {
+        best = cost;
+        bB = B;
+        bL = B / Q;
+      }
+    }
+  }
+  RF_REQUIRE(bB, "no overlap-save layout for block %d and n=%lld", block, (long long)c->n);
+  *B_out = bB;
+  *Lp_out = bL;
+}
+
+void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s) {
   RF_REQUIRE(kern->dtype == RF_F32, "overlap-save needs the FP32 grid");
-  RF_REQUIRE(B >= 512 && B <= 16384 && (B & (B - 1)) == 0 && B <= c->n, "overlap-save block %d invalid for n=%lld", B,
-             (long long)c->n);
-  if (kern->os_ready && kern->os_B == B) return;
-  const int H = B / 2;
+  RF_REQUIRE(B == 0 || (B >= 512 && B <= 16384 && (B & (B - 1)) == 0 && B <= c->n),
+             "overlap-save block %d invalid for n=%lld", B, (long long)c->n);
+  if (!B || !Lp) {
+    RF_REQUIRE(Lp == 0, "a partition length needs a block size");
+    os_choose_layout(c, kern->len, B, &B, &Lp);
+  }
+  RF_REQUIRE(Lp == B / 2 || Lp == B / 4 || Lp == B / 8, "overlap-save partition length %d must be B/2, B/4 or B/8", Lp);
+  if (kern->os_ready && kern->os_B == B && kern->os_Lp == Lp) return;
   const int k = kern->k;
   std::vector<int> parts(k);
   std::vector<int64_t> off(k + 1, 0);
   std::vector<int> gj, gp;
   for (int j = 0; j < k; ++j) {
-    parts[j] = std::max(1, (kern->len[j] + H - 1) / H);
+    parts[j] = std::max(1, (kern->len[j] + Lp - 1) / Lp);
     off[j + 1] = off[j] + (int64_t)parts[j] * B;
     for (int p = 0; p < parts[j]; ++p) {
       gj.push_back(j);
@@ -436,7 +512,7 @@ void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s) {
     const int cnt = std::min(chunk, G - g0);
     dim3 grid((unsigned)((B + 255) / 256), (unsigned)cnt);
     k_os_fill<<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(), kern->len_d.as<int>(),
-                                   gjd.as<int>() + g0, gpd.as<int>() + g0, B, in);
+                                   gjd.as<int>() + g0, gpd.as<int>() + g0, B, Lp, in);
     RF_LAUNCHED();
     fft_c2c_f64(in, out, tmp, B, cnt, -1, c->tw64.as<double2>(), c->n, s);
     const int64_t count = (int64_t)cnt * B;
@@ -447,35 +523,37 @@ void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s) {
   RF_CUDA(cudaStreamSynchronize(s));  // the row buffers are released on return
   kern->os_parts = parts;
   kern->os_B = B;
+  kern->os_Lp = Lp;
   kern->os_ready = true;
   static unsigned long long version = 0;
   kern->os_version = ++version;
 }
 
-size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W) {
+// Segment spectra (Q n complex64 for partition ratio Q = B / Lp) plus packed window keys.
+size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q) {
   const int64_t nw = W > 0 ? (c->n + W - 1) / W : 0;
-  return sizeof(float2) * (size_t)(2 * c->n) + sizeof(unsigned long long) * (size_t)k * (size_t)nw + 256;
+  return sizeof(float2) * (size_t)Q * (size_t)c->n + sizeof(unsigned long long) * (size_t)k * (size_t)nw + 256;
 }
 
 void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,
                     int32_t* argmax_out, cudaStream_t s) {
   if (kern->k == 0) return;
-  const int B = kern->os_ready ? kern->os_B : os_default_block(c);
-  if (!kern->os_ready) os_prepare(c, kern, B, s);
+  if (!kern->os_ready) os_prepare(c, kern, 0, 0, s);
+  const int B = kern->os_B, Lp = kern->os_Lp, Q = B / Lp;
   const bool win = max_out != nullptr;
-  const size_t need = os_workspace_bytes(c, kern->k, win ? W : 0);
+  const size_t need = os_workspace_bytes(c, kern->k, win ? W : 0, Q);
   c->scratch.ensure(need);
   float2* Zs = c->scratch.as<float2>();
-  unsigned long long* keys = reinterpret_cast<unsigned long long*>(Zs + 2 * c->n);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(Zs + (int64_t)Q * c->n);
   const int64_t nw = win ? (c->n + W - 1) / W : 0;
   if (win) RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)kern->k * nw, s));
-  dispatch_b(B, [&](auto bc) {
-    constexpr int BB = decltype(bc)::value;
-    launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), Zs, s);
+  dispatch_bq(B, Q, [&](auto bc, auto qc) {
+    constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
+    launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), Lp, Zs, s);
     if (win)
-      launch_os<BB, true>(c, kern, Zs, nullptr, keys, W, s);
+      launch_os<BB, QQ, true>(c, kern, Zs, nullptr, keys, W, s);
     else
-      launch_os<BB, false>(c, kern, Zs, static_cast<float2*>(z_out), nullptr, 0, s);
+      launch_os<BB, QQ, false>(c, kern, Zs, static_cast<float2*>(z_out), nullptr, 0, s);
   });
   if (win) {
     const int64_t count = (int64_t)kern->k * nw;
@@ -486,20 +564,29 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
 
 void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
                          float* max_out, int32_t* argmax_out, cudaStream_t s) {
-  // one block size for the whole batch (the first prepared kernel set decides)
-  int B = 0;
+  // one layout for the whole batch (the first prepared kernel set decides)
+  int B = 0, Lp = 0;
   for (int g = 0; g < G && !B; ++g)
-    if (ks[g]->os_ready) B = ks[g]->os_B;
-  if (!B) B = os_default_block(c);
+    if (ks[g]->os_ready) {
+      B = ks[g]->os_B;
+      Lp = ks[g]->os_Lp;
+    }
+  if (!B) {
+    std::vector<int> all;
+    for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
+    os_choose_layout(c, all, 0, &B, &Lp);
+  }
   for (int g = 0; g < G; ++g)
-    if (!ks[g]->os_ready || ks[g]->os_B != B) os_prepare(c, ks[g], B, s);
-  const int H = B / 2;
+    if (!ks[g]->os_ready || ks[g]->os_B != B || ks[g]->os_Lp != Lp) os_prepare(c, ks[g], B, Lp, s);
+  const int Q = B / Lp;
   const int64_t n = c->n;
-  const int NS = (int)(n / H);
+  const int NQ = (int)(n / Lp);
+  const int NB = (int)((n + (B - Lp) - 1) / (B - Lp));
   const int64_t nw = (n + W - 1) / W;
-  // plan key: block size, window, references and kernel sets with their spectra versions
+  // plan key: layout, window, references and kernel sets with their spectra versions
   std::vector<unsigned long long> key;
   key.push_back((unsigned long long)B);
+  key.push_back((unsigned long long)Lp);
   key.push_back((unsigned long long)W);
   for (int g = 0; g < G; ++g) {
     key.push_back((unsigned long long)(uintptr_t)z_refs[g]);
@@ -511,14 +598,14 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   if (key != c->batch_key) {
     std::vector<OsItem> items;
     items.reserve((size_t)rows);
-    c->batch_zs.ensure(sizeof(float2) * (size_t)G * NS * B);
+    c->batch_zs.ensure(sizeof(float2) * (size_t)G * NQ * B);
     const float2* zs_all = c->batch_zs.as<float2>();
     int64_t row = 0;
     for (int g = 0; g < G; ++g) {
       const rf_kernels* k = ks[g];
       int64_t off = 0;
       for (int j = 0; j < k->k; ++j) {
-        items.push_back(OsItem{k->os_spec.as<float2>() + off, zs_all + (int64_t)g * NS * B, k->os_parts[j],
+        items.push_back(OsItem{k->os_spec.as<float2>() + off, zs_all + (int64_t)g * NQ * B, k->os_parts[j],
                                k->lag0[j], (long long)row++});
         off += (int64_t)k->os_parts[j] * B;
       }
@@ -542,26 +629,26 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   unsigned long long* counter = keys + rows * nw;
   RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * ((size_t)rows * nw + 1), s));
   int SC = 8;
-  while (SC > 1 && rows * ((NS + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
-  const int nchunk = (NS + SC - 1) / SC;
+  while (SC > 1 && rows * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
+  const int nchunk = (NB + SC - 1) / SC;
   const int64_t units = rows * nchunk;
-  const int fastwin = (W >= 256) ? 1 : 0;  // a warp's 256 outputs span <= 2 windows
-  dispatch_b(B, [&](auto bc) {
-    constexpr int BB = decltype(bc)::value;
+  dispatch_bq(B, Q, [&](auto bc, auto qc) {
+    constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
+    const int fastwin = (W >= os_warp_span<BB, QQ>()) ? 1 : 0;  // a warp's outputs span <= 2 windows
     const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<BB>::LOGB];
     auto seg = k_os_segments_batched<BB>;
     RF_CUDA(cudaFuncSetAttribute(seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
     RF_REQUIRE(G <= 65535, "at most 65535 references per batch");
-    seg<<<dim3((unsigned)NS, (unsigned)G), BB / 16, os_smem<BB>(), s>>>(c->batch_zptr.as<const float2*>(), n, tw,
+    seg<<<dim3((unsigned)NQ, (unsigned)G), BB / 16, os_smem<BB>(), s>>>(c->batch_zptr.as<const float2*>(), n, Lp, tw,
                                                                        c->batch_zs.as<float2>());
     RF_LAUNCHED();
-    auto fn = k_os_batched<BB>;
+    auto fn = k_os_batched<BB, QQ>;
     RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
     int per_sm = 0;
     RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BB / 16, os_smem<BB>()));
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * c->nsm, units));
-    fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>(), units, nchunk, tw, n, NS, SC,
-                                                      keys, W, nw, fastwin, counter);
+    fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>(), units, nchunk, tw, n, NQ, NB,
+                                                      SC, keys, W, nw, fastwin, counter);
     RF_LAUNCHED();
   });
   const int64_t count = rows * nw;

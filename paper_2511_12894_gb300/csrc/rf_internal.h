@@ -126,6 +126,7 @@ struct rf_kernels {
   // and the partition spectra FFT_B(taps) / B, kernel after kernel.
   bool os_ready = false;
   int os_B = 0;
+  int os_Lp = 0;                      // partition length (B/2, B/4 or B/8)
   unsigned long long os_version = 0;  // changes whenever the spectra are rebuilt
   std::vector<int32_t> os_parts;
   rf::DevBuf os_spec;      // float2 [sum_j P_j][B]
@@ -175,9 +176,12 @@ void reconstruct_direct(rf_ctx* c, const void* z_ref, const rf_kernels* kern, vo
 void winmax_series(rf_ctx* c, const void* z, int32_t count, int64_t W, float* max_out,
                    int32_t* argmax_out, cudaStream_t s);
 // overlap-save (reconstruct_os.cu); FP32 grids, block sizes 512..16384
-int os_default_block(const rf_ctx* c);
-void os_prepare(rf_ctx* c, rf_kernels* kern, int B, cudaStream_t s);
-size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W);
+// Overlap-save layout (block size, partition length) of least modelled cost for kernels of
+// the given lengths; block != 0 fixes the block size.
+void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, int* B, int* Lp);
+// B = 0 and/or Lp = 0 take the modelled choice.
+void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s);
+size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
 // bytes of the BF16 planes of z_ref used by the tensor-core path (taps padded to LP)
 size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int terms);
 void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,

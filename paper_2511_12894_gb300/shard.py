@@ -15,13 +15,13 @@ import heapq
 from typing import List, Sequence
 
 
-def group_cost(n: int, kernel_lengths: Sequence[int], block: int = 8192) -> float:
+def group_cost(n: int, kernel_lengths: Sequence[int], block: int = 16384, part: int = 4096) -> float:
     """Relative cost of one group: (1 + K) n for the matched filter and peaks, plus the
-    overlap-save work of each neighbour, proportional to log2(B) + P_j (P_j = ceil(L_j / (B/2)))."""
+    overlap-save work of each neighbour: per output block of B - Lp samples, one block
+    transform (~ log2 B) and P_j = ceil(L_j / Lp) spectral products."""
     import math
-    h = block // 2
-    recon = sum(math.log2(block) + max(1, -(-int(L) // h)) for L in kernel_lengths)
-    return float(n) * (1 + len(kernel_lengths) + recon / math.log2(block))
+    recon = sum(math.log2(block) + max(1, -(-int(L) // part)) for L in kernel_lengths)
+    return float(n) * (1 + len(kernel_lengths) + recon / math.log2(block) * block / (block - part))
 
 
 def assign(costs: Sequence[float], world: int) -> List[List[int]]:

@@ -269,31 +269,48 @@ def test_winmax_series(torch):
 
 # ---------------------------------------------------------------- overlap-save
 
-@pytest.mark.parametrize("B", [512, 1024, 8192, 16384])
-def test_reconstruct_os_edge_lengths(torch, B):
-    """Overlap-save against the oracle's direct sum: lengths around the partition size
-    H = B/2, lengths above n/2, lags of both signs and wrapping, windows down to 1 sample."""
-    n = 1 << 15
-    H = B // 2
-    rng = np.random.default_rng(B)
-    lengths = [1, 2, 31, 255, 256, 257, H - 1, H, H + 1, 2 * H + 7, 1000, n // 2 + 3, 0]
-    lags = [0, -5, 37, n // 2, -(n // 2) + 1, 100, -1000, 3, 7000, -2, 11, -n // 4, 5]
-    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype="f32")
-    rf = _rf(cfg)
+_OS_N = 1 << 15
+
+
+@pytest.fixture(scope="module")
+def os_case():
+    """Random z and kernels whose lengths sit around every partition length tested (Lp - 1,
+    Lp, Lp + 1, 2 Lp + 7), above n/2, and zero; lags of both signs and wrapping; with the
+    oracle's direct sums, computed once for every layout."""
+    n = _OS_N
+    rng = np.random.default_rng(1515)
+    lengths = [1, 2, 31, 63, 64, 65, 135, 255, 256, 257, 519, 1023, 1024, 1025, 2055, 2047, 2048, 2049,
+               4095, 4096, 4097, 8199, 8191, 8192, 8193, 16391, n // 2 + 3, 0]
+    lags = [int(v) for v in rng.integers(-n // 2 + 1, n // 2 + 1, len(lengths))]
+    lags[:4] = [0, -5, n // 2, -(n // 2) + 1]
     z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
     taps = [((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(max(L, 1))).astype(np.complex64)
             for L in lengths]
-    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
-    kern.prepare(B)
-    zt = torch.tensor(z, device="cuda")
-    out = rf.reconstruct(zt, kern, "os").cpu().numpy()
     zo = [reconstruct.reconstruct_direct(z.astype(np.complex128), lags[j], taps[j].astype(np.complex128))
           for j in range(len(lengths))]
+    return z, lengths, lags, taps, zo
+
+
+@pytest.mark.parametrize("B,Lp", [(512, 256), (512, 128), (512, 64), (1024, 512), (8192, 4096), (8192, 2048),
+                                  (8192, 1024), (16384, 8192), (16384, 4096), (16384, 2048)])
+def test_reconstruct_os_edge_lengths(torch, os_case, B, Lp):
+    """Overlap-save with block B and partitions of Lp taps (hop B - Lp, which does not divide
+    n for Lp < B/2, so the last block is partial) against the oracle's direct sum; window
+    peaks for windows down to 1 sample."""
+    z, lengths, lags, taps, zo = os_case
+    n = _OS_N
+    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype="f32")
+    rf = _rf(cfg)
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    kern.prepare(B, Lp)
+    assert kern.os_layout() == (B, Lp)
+    zt = torch.tensor(z, device="cuda")
+    out = rf.reconstruct(zt, kern, "os").cpu().numpy()
     for j, L in enumerate(lengths):
         if L == 0:
             assert np.abs(out[j]).max() == 0.0
             continue
-        assert _relerr(out[j], zo[j]) < TOL["f32"], (B, j, L)
+        assert _relerr(out[j], zo[j]) < TOL["f32"], (B, Lp, j, L)
     for W in (1, 3, 1000, 2048, n):
         P, A = rf.reconstruct_winmax(zt, kern, W, "os")
         P, A = P.cpu().numpy(), A.cpu().numpy()
@@ -302,7 +319,7 @@ def test_reconstruct_os_edge_lengths(torch, B):
             if L == 0:
                 assert np.all(P[j] == 0)
                 continue
-            assert np.abs(P[j] - Po).max() <= 4 * TOL["f32"] * Po.max()
+            assert np.abs(P[j] - Po).max() <= 4 * TOL["f32"] * Po.max(), (B, Lp, W, j)
             _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, W, 8 * TOL["f32"] * Po.max())
 
 
@@ -328,13 +345,17 @@ def test_reconstruct_os_paper_shaped_kernels(torch):
     rf = _rf(cfg)
     z32 = zo_ref.astype(np.complex64)
     kern = rf.kernels_import(pk.lag0, pk.length, pk.taps.astype(np.complex64))
-    for B in (2048, 8192):
-        kern.prepare(B)
+    zh = [reconstruct.reconstruct_direct(z32.astype(np.complex128), pk.kernel(j)[0],
+                                         pk.kernel(j)[1].astype(np.complex64)) for j in range(len(nb))]
+    for B, Lp in ((2048, 1024), (8192, 4096), (8192, 2048), (16384, 2048)):
+        kern.prepare(B, Lp)
         out = rf.reconstruct(torch.tensor(z32, device="cuda"), kern, "os").cpu().numpy()
         for j in range(len(nb)):
-            m0, c = pk.kernel(j)
-            zh = reconstruct.reconstruct_direct(z32.astype(np.complex128), m0, c.astype(np.complex64))
-            assert _relerr(out[j], zh) < TOL["f32"], (B, j)
+            assert _relerr(out[j], zh[j]) < TOL["f32"], (B, Lp, j)
+    # the modelled layout choice is one of the allowed layouts
+    kern.prepare()
+    B, Lp = kern.os_layout()
+    assert B in (512, 1024, 2048, 4096, 8192, 16384) and B <= cfg.n and Lp in (B // 2, B // 4, B // 8)
     # whole path
     ipt = torch.tensor(ip, device="cuda")
     zg, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), ipt, [ref])
