@@ -4,11 +4,13 @@
 One step = the whole online path for one data segment of the paper-shaped FP32
 workload (fs 2048 Hz, f_low 20 Hz, 512 s, n = 2^20, one reference and 256
 TaylorF2 3.5PN neighbours):
-    mf_reference (data FFT, reference matched filter)  ->  z_ref
+    mf_filtered (data FFT, reference matched filter)   ->  z_ref
     winmax of z_ref                                     ->  reference peaks
     reconstruct_winmax (all neighbours, fused peaks)    ->  neighbour peaks
 Units per step: (1 + K) * n template-samples.  Kernel building is offline
-(its time is reported as `build_s`, outside the metric).
+(its time is reported as `build_s`, outside the metric), and so is the stored
+reference filter conj(h~_ref) / S_n / N_ref of each reference, which depends on
+the template and the PSD only (`--mf onthefly` regenerates it in every step).
 
 Also measured in the same run: per-template full-length cuFFT matched
 filtering of every template (the plain method) and the SNR error of our
@@ -51,6 +53,8 @@ def parse():
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default)")
+    ap.add_argument("--mf", default="filtered", choices=["filtered", "onthefly"],
+                    help="reference matched filter from stored filters, or template regenerated every step")
     ap.add_argument("--part", type=int, default=0,
                     help="overlap-save partition length: block/2, /4 or /8 (0: library default)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
@@ -309,6 +313,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     kerns = [rf.build_ratio_kernels(r, nb, ip, thr) for r, nb in cfg.groups]
+    filt, sig = rf.reference_filters(ip, refs)
     algo_used = args.algo if args.algo != "auto" else ("os" if cfg.dtype == "f32" else "direct")
     if algo_used == "os":
         for k in kerns:
@@ -321,7 +326,6 @@ def main():
 
     nw = -(-n // W)
     z = torch.empty((G, n), dtype=rf.cdtype, device=dev)
-    sig = torch.empty(G, dtype=torch.float64, device=dev)
     Pn = torch.empty((rows, nw), dtype=torch.float32, device=dev)
     An = torch.empty((rows, nw), dtype=torch.int32, device=dev)
     Pr = torch.empty((G, nw), dtype=torch.float32, device=dev)
@@ -339,8 +343,14 @@ def main():
             rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, args.algo, max_out=Pn, arg_out=An,
                                       prec=prec)
 
+    def mf_step(xs):
+        if args.mf == "filtered":
+            rf.mf_filtered(xs, filt, z_out=z)
+        else:
+            rf.mf_reference(xs, ip, refs, z_out=z, sigma_out=sig)
+
     def step():
-        rf.mf_reference(x, ip, refs, z_out=z, sigma_out=sig)
+        mf_step(x)
         rf.winmax(z, W, max_out=Pr, arg_out=Ar)
         recon()
 
@@ -417,7 +427,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         x_dev.copy_(x_host, non_blocking=True)
-        rf.mf_reference(x_dev, ip, refs, z_out=z, sigma_out=sig)
+        mf_step(x_dev)
         rf.winmax(z, W, max_out=Pr, arg_out=Ar)
         recon()
         P_host[:G].copy_(Pr, non_blocking=True)
@@ -432,7 +442,7 @@ def main():
     e2e = {"value": (units_total if sharded else world * units_step) / (e2e_ms / 1e3), "unit": "template*samples/s",
            "h2d_bytes_per_step": int(x_host.numel() * x_host.element_size()),
            "d2h_bytes_per_step": int(P_host.numel() * 4 + A_host.numel() * 4), "ms_per_step": e2e_ms,
-           "path": "pinned host x -> mf_reference -> winmax -> reconstruct (eager calls) -> pinned host peaks"}
+           "path": f"pinned host x -> mf_{args.mf} -> winmax -> reconstruct (eager calls) -> pinned host peaks"}
 
     # ---------------- roofline of the dominant kernel (the neighbour reconstruction)
     if algo_used == "os":
@@ -532,7 +542,7 @@ def main():
                                    f"f_low={cfg.f_low:g}; {G} ref + {rows} TaylorF2 nbrs; thr={thr:g} rel; W={W}",
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
-                       "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used,
+                       "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf,
                        "prec": prec,
                        "graph": graph is not None,
                        "parallelism": (f"groups sharded over {world} ranks" if sharded else f"replicas x{world}")},

@@ -137,6 +137,24 @@ rf_status rf_template_fd(rf_ctx* ctx, const rf_template* tmpl, void* h_out, rf_s
 rf_status rf_mf_reference(rf_ctx* ctx, const void* x, const double* inv_psd, int32_t nref,
                           const rf_template* refs, void* z_out, double* sigma_out, rf_stream stream);
 
+/* Stored reference filters for rf_mf_filtered (the data-independent half of Eq. 2, kept like
+ * the ratio kernels): per reference r and bin k = 0..n/2,
+ *   filt[r][k] = (4 / (n N_r)) conj(h~_r(f_k)) inv_psd[k] on [f_low, f_high], 0 elsewhere,
+ * with N_r as in rf_mf_reference (Eq. 3, FP64) and the phase in FP64, rounded once to the
+ * grid dtype.  filt_out: complex[nref][n/2+1] (grid dtype); sigma_out: double[nref] (device,
+ * may be NULL).  refs: host.  Async on stream. */
+rf_status rf_reference_filters(rf_ctx* ctx, const double* inv_psd, int32_t nref, const rf_template* refs,
+                               void* filt_out, double* sigma_out, rf_stream stream);
+
+/* Reference matched filter from stored filters: X = DFT(x) once (unnormalised, Eq. 1), then
+ * for each reference z_r[i] = sum_{k=0}^{n/2} X[k] filt[r][k] exp(+2 pi i i k / n), which is
+ * z_ref of rf_mf_reference (Eqs. 2, 6).  The product is formed inside the first pass of the
+ * inverse transform.  x: real[n]; filt: complex[nref][n/2+1]; z_out: complex[nref][n] (grid
+ * dtype).  The first call allocates a temporary of up to min(nref, 2^27 / n) x n complex
+ * values (later calls with as many references reuse it, so a warmed-up call can be captured
+ * in a CUDA graph).  Async on stream. */
+rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* filt, void* z_out, rf_stream stream);
+
 /* Ratio kernels of k neighbours of one reference (Sec. II.B-II.D).  Per neighbour j, in FP64:
  *   K~_k = (N_ref/N_j) W(f_k) conj(h~_j(f_k) / h~_ref(f_k))   (Eqs. 5, 7 and window Eq. 9)
  *   rho[m] = (1/n) sum_{k=0}^{n/2} K~_k exp(+2 pi i k m / n),  m = 0..n-1

@@ -32,7 +32,7 @@ EXPORTED = (
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
     "rf_kernels_os_layout",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
-    "rf_mf_reference_noalloc", "rf_device_status",
+    "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
 )
 
 
@@ -88,6 +88,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_winmax": (i32, [vp, vp, i32, i64, vp, vp, vp]),
         "rf_reconstruct_batched": (i32, [vp, i32, P(vp), P(vp), i32, i32, i64, vp, vp, vp]),
         "rf_mf_reference_noalloc": (i32, [P(rf_grid), vp, vp, P(rf_template), vp, vp, vp]),
+        "rf_reference_filters": (i32, [vp, vp, i32, P(rf_template), vp, vp, vp]),
+        "rf_mf_filtered": (i32, [vp, vp, i32, vp, vp, vp]),
         "rf_device_status": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -239,6 +241,31 @@ class RatioFilter:
                                     nref, _templates(refs), ctypes.c_void_p(z.data_ptr()),
                                     ctypes.c_void_p(sg.data_ptr()), _stream(stream)))
         return z, sg
+
+    def reference_filters(self, inv_psd, refs: Sequence, filt_out=None, sigma_out=None, stream=None):
+        """Stored filters [nref, n/2+1] (complex) and N[nref] of each reference (Sec. II.A)."""
+        import torch
+        ip = _dev(inv_psd, torch.float64, "inv_psd")
+        nref = len(refs)
+        f = filt_out if filt_out is not None else torch.empty((nref, self.n // 2 + 1), dtype=self.cdtype,
+                                                               device="cuda")
+        sg = sigma_out if sigma_out is not None else torch.empty(nref, dtype=torch.float64, device="cuda")
+        _check(_lib.rf_reference_filters(self.handle, ctypes.c_void_p(ip.data_ptr()), nref, _templates(refs),
+                                         ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(sg.data_ptr()),
+                                         _stream(stream)))
+        return f, sg
+
+    def mf_filtered(self, x, filt, z_out=None, stream=None):
+        """z_ref[nref, n] from stored filters ``filt`` [nref, n/2+1]."""
+        import torch
+        x = _dev(x, self.rdtype, "x")
+        filt = _dev(filt, self.cdtype, "filt")
+        f2 = filt.reshape(-1, self.n // 2 + 1)
+        nref = f2.shape[0]
+        z = z_out if z_out is not None else torch.empty((nref, self.n), dtype=self.cdtype, device="cuda")
+        _check(_lib.rf_mf_filtered(self.handle, ctypes.c_void_p(x.data_ptr()), nref, ctypes.c_void_p(f2.data_ptr()),
+                                   ctypes.c_void_p(z.data_ptr()), _stream(stream)))
+        return z
 
     def _wrap_kernels(self, h: ctypes.c_void_p) -> Kernels:
         k = ctypes.c_int32()

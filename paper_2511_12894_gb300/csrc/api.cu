@@ -199,6 +199,32 @@ rf_status rf_mf_reference(rf_ctx* ctx, const void* x, const double* inv_psd, int
   });
 }
 
+rf_status rf_reference_filters(rf_ctx* ctx, const double* inv_psd, int32_t nref, const rf_template* refs,
+                               void* filt_out, double* sigma_out, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(nref >= 1, "nref must be >= 1");
+    check_host(refs, "refs");
+    for (int r = 0; r < nref; ++r) check_template(refs[r], "refs[r]");
+    check_dev(inv_psd, "inv_psd");
+    check_dev(filt_out, "filt_out");
+    check_dev(sigma_out, "sigma_out", true);
+    reference_filters_impl(ctx, inv_psd, nref, refs, filt_out, sigma_out, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* filt, void* z_out, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(nref >= 1, "nref must be >= 1");
+    RF_REQUIRE(ctx->n >= 16, "the stored-filter form needs n >= 16");
+    check_dev(x, "x");
+    check_dev(filt, "filt");
+    check_dev(z_out, "z_out");
+    mf_filtered_impl(ctx, x, nref, filt, z_out, (cudaStream_t)stream);
+  });
+}
+
 rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_template* nbrs, int32_t k,
                                  const double* inv_psd, double threshold, int32_t relative, rf_kernels** out,
                                  rf_stream stream) {

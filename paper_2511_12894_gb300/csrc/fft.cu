@@ -45,6 +45,28 @@ __global__ void __launch_bounds__(256) k_stockham(const V* __restrict__ in, V* _
   for (int t = 0; t < R; ++t) out[base + t * Ns] = a[t];
 }
 
+// First pass of a transform whose input is the one-sided product X[k] F[k] for k <= n/2 and
+// zero above (the matched-filter integrand of Eq. 2): the product is formed on load.
+template <typename V, int R, int SIGN>
+__global__ void __launch_bounds__(256) k_stockham_first_mul(const V* __restrict__ X, const V* __restrict__ F,
+                                                            int64_t fstride, V* __restrict__ out, int64_t n) {
+  const int64_t nb = n / R;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  F += (int64_t)blockIdx.y * fstride;
+  out += (int64_t)blockIdx.y * n;
+  const int64_t half = n / 2;
+  V a[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t k = j + t * nb;
+    a[t] = k <= half ? cmul(X[k], F[k]) : cmake<V>(0, 0);
+  }
+  dft<R, SIGN>(a);
+#pragma unroll
+  for (int t = 0; t < R; ++t) out[j * R + t] = a[t];
+}
+
 template <typename V, int R>
 void launch_pass(const V* in, V* out, int64_t n, int64_t Ns, int batch, int sign, const V* tw,
                  int64_t tw_stride, cudaStream_t s) {
@@ -60,7 +82,7 @@ void launch_pass(const V* in, V* out, int64_t n, int64_t Ns, int batch, int sign
 
 template <typename V>
 void fft_c2c(const V* in, V* out, V* tmp, int64_t n, int batch, int sign, const V* tw,
-             int64_t table_n, cudaStream_t s) {
+             int64_t table_n, cudaStream_t s, const V* mulF = nullptr, int64_t fstride = 0) {
   RF_REQUIRE(n >= 2 && (n & (n - 1)) == 0, "fft: n=%lld is not a power of two", (long long)n);
   RF_REQUIRE(table_n % n == 0, "fft: twiddle table too small");
   RF_REQUIRE(batch >= 1 && batch <= 65535, "fft: batch %d out of range", batch);
@@ -79,6 +101,15 @@ void fft_c2c(const V* in, V* out, V* tmp, int64_t n, int batch, int sign, const 
   int64_t Ns = 1;
   for (int p = 0; p < P; ++p) {
     V* dst = ((P - 1 - p) % 2 == 0) ? out : tmp;
+    if (p == 0 && mulF) {
+      RF_REQUIRE(radix[0] == 16 && sign > 0, "fft: the product pass needs n >= 16 and an inverse transform");
+      dim3 grid((unsigned)((n / 16 + 255) / 256), (unsigned)batch);
+      k_stockham_first_mul<V, 16, +1><<<grid, 256, 0, s>>>(in, mulF, fstride, dst, n);
+      RF_LAUNCHED();
+      Ns *= radix[p];
+      src = dst;
+      continue;
+    }
     switch (radix[p]) {
       case 16: launch_pass<V, 16>(src, dst, n, Ns, batch, sign, tw, tw_stride, s); break;
       case 8: launch_pass<V, 8>(src, dst, n, Ns, batch, sign, tw, tw_stride, s); break;
@@ -106,6 +137,16 @@ void fft_c2c_f64(const double2* in, double2* out, double2* tmp, int64_t n, int b
 void fft_c2c_f32(const float2* in, float2* out, float2* tmp, int64_t n, int batch, int sign,
                  const float2* tw, int64_t table_n, cudaStream_t s) {
   fft_c2c<float2>(in, out, tmp, n, batch, sign, tw, table_n, s);
+}
+
+void ifft_product_f64(const double2* X, const double2* F, int64_t fstride, double2* out, double2* tmp, int64_t n,
+                      int batch, const double2* tw, int64_t table_n, cudaStream_t s) {
+  fft_c2c<double2>(X, out, tmp, n, batch, +1, tw, table_n, s, F, fstride);
+}
+
+void ifft_product_f32(const float2* X, const float2* F, int64_t fstride, float2* out, float2* tmp, int64_t n,
+                      int batch, const float2* tw, int64_t table_n, cudaStream_t s) {
+  fft_c2c<float2>(X, out, tmp, n, batch, +1, tw, table_n, s, F, fstride);
 }
 
 void real_to_complex_f64(const double* x, double2* out, int64_t n, cudaStream_t s) {

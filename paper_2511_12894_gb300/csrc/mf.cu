@@ -1,4 +1,5 @@
 // Reference matched filter (Sec. II.A, Eqs. 2-4 and 6) and template spectra.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -114,6 +115,28 @@ __global__ void __launch_bounds__(256) k_mf_pointwise(const V* __restrict__ X, c
   Z[k] = out;
 }
 
+// Stored reference filter: F[k] = (4 / (n N)) conj(h~_k) inv_psd[k] on the band, 0 elsewhere,
+// k = 0..n/2, phase and scale in FP64 and rounded once.  With X the unnormalised DFT of the
+// data, X[k] F[k] is the integrand of Eq. 2 (4 df dt = 4 / n).
+template <typename V>
+__global__ void __launch_bounds__(256) k_ref_filter(const double* __restrict__ ip, const double* __restrict__ sigma2,
+                                                    Tf2 p, int64_t n, double df, double f_low, double f_high,
+                                                    V* __restrict__ F, double* __restrict__ sigma_out) {
+  using R = typename real_of<V>::type;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0 && sigma_out) sigma_out[0] = sqrt(sigma2[0]);
+  if (k > n / 2) return;
+  const double f = (double)k * df;
+  V out = cmake<V>((R)0, (R)0);
+  if (k > 0 && f >= f_low && f <= f_high) {
+    double sn, cs;
+    sincos(tf2_phase(p, f), &sn, &cs);
+    const double a = 4.0 / ((double)n * sqrt(sigma2[0])) * tf2_amp(f) * ip[k];
+    out = cmake<V>((R)(a * cs), (R)(a * sn));  // conj(h~) = B exp(+i Psi)
+  }
+  F[k] = out;
+}
+
 template <typename V>
 __global__ void __launch_bounds__(256) k_template_fd(Tf2 p, int64_t nbins, double df, V* __restrict__ h) {
   using R = typename real_of<V>::type;
@@ -185,6 +208,60 @@ void mf_reference_impl(rf_ctx* c, const void* x, const double* inv_psd, int32_t 
       RF_LAUNCHED();
       fft_c2c_f32(c->fa.as<float2>(), static_cast<float2*>(z_out) + (int64_t)r * n, c->fb.as<float2>(), n, 1, +1,
                   c->tw32.as<float2>(), n, s);
+    }
+  }
+}
+
+void reference_filters_impl(rf_ctx* c, const double* inv_psd, int32_t nref, const rf_template* refs, void* filt,
+                            double* sigma_out, cudaStream_t s) {
+  const int64_t n = c->n;
+  const int64_t nb = n / 2 + 1;
+  const double df = c->g.fs / (double)n;
+  c->red.ensure(sizeof(double) * (kRedBlocks + 8));
+  double* sig2 = c->red.as<double>() + kRedBlocks;
+  k_sigma2_partial<<<kRedBlocks, kRedThreads, 0, s>>>(inv_psd, nb, df, c->g.f_low, c->g.f_high, c->red.as<double>());
+  RF_LAUNCHED();
+  k_sum_partials<<<1, kRedThreads, 0, s>>>(c->red.as<double>(), kRedBlocks, sig2);
+  RF_LAUNCHED();
+  const unsigned grid = (unsigned)((nb + 255) / 256);
+  for (int r = 0; r < nref; ++r) {
+    const Tf2 p = make_tf2(refs[r], c->g.pn_order);
+    double* so = sigma_out ? sigma_out + r : nullptr;
+    if (c->g.dtype == RF_F64)
+      k_ref_filter<double2><<<grid, 256, 0, s>>>(inv_psd, sig2, p, n, df, c->g.f_low, c->g.f_high,
+                                                 static_cast<double2*>(filt) + (int64_t)r * nb, so);
+    else
+      k_ref_filter<float2><<<grid, 256, 0, s>>>(inv_psd, sig2, p, n, df, c->g.f_low, c->g.f_high,
+                                                static_cast<float2*>(filt) + (int64_t)r * nb, so);
+    RF_LAUNCHED();
+  }
+}
+
+void mf_filtered_impl(rf_ctx* c, const void* x, int32_t nref, const void* filt, void* z_out, cudaStream_t s) {
+  const int64_t n = c->n;
+  const int64_t nb = n / 2 + 1;
+  // references per batched inverse transform, bounded by the temporary buffer
+  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(nref, std::min<int64_t>(65535, (int64_t)(1 << 27) / n)));
+  if (c->g.dtype == RF_F64) {
+    c->mf_tmp.ensure(sizeof(double2) * (size_t)chunk * n);
+    real_to_complex_f64(static_cast<const double*>(x), c->fa.as<double2>(), n, s);
+    fft_c2c_f64(c->fa.as<double2>(), c->xf.as<double2>(), c->fb.as<double2>(), n, 1, -1, c->tw64.as<double2>(), n,
+                s);
+    for (int r0 = 0; r0 < nref; r0 += chunk) {
+      const int cnt = std::min(chunk, nref - r0);
+      ifft_product_f64(c->xf.as<double2>(), static_cast<const double2*>(filt) + (int64_t)r0 * nb, nb,
+                       static_cast<double2*>(z_out) + (int64_t)r0 * n, c->mf_tmp.as<double2>(), n, cnt,
+                       c->tw64.as<double2>(), n, s);
+    }
+  } else {
+    c->mf_tmp.ensure(sizeof(float2) * (size_t)chunk * n);
+    real_to_complex_f32(static_cast<const float*>(x), c->fa.as<float2>(), n, s);
+    fft_c2c_f32(c->fa.as<float2>(), c->xf.as<float2>(), c->fb.as<float2>(), n, 1, -1, c->tw32.as<float2>(), n, s);
+    for (int r0 = 0; r0 < nref; r0 += chunk) {
+      const int cnt = std::min(chunk, nref - r0);
+      ifft_product_f32(c->xf.as<float2>(), static_cast<const float2*>(filt) + (int64_t)r0 * nb, nb,
+                       static_cast<float2*>(z_out) + (int64_t)r0 * n, c->mf_tmp.as<float2>(), n, cnt,
+                       c->tw32.as<float2>(), n, s);
     }
   }
 }

@@ -99,6 +99,7 @@ struct rf_ctx {
   rf::DevBuf red;      // FP64 reduction scratch
   rf::DevBuf scratch;  // growable: packed window keys, OS block spectra, builder chunks
   rf::DevBuf scratch2;
+  rf::DevBuf mf_tmp;   // inverse-transform temporaries of the stored-filter matched filter
   rf::DevBuf status;   // int: device-side error status (RF_ETIMEOUT from bounded waits), 0 if none
   size_t reserved = 0;
   int64_t max_chunk = 0;  // builder templates per chunk
@@ -147,6 +148,12 @@ namespace rf {
 // (same size as in/out) as the ping-pong buffer.  in, out, tmp must be distinct.
 void fft_c2c_f64(const double2* in, double2* out, double2* tmp, int64_t n, int batch, int sign,
                  const double2* tw_table, int64_t table_n, cudaStream_t s);
+// Inverse transform (unnormalised) of the one-sided product X[k] F_b[k] (k <= n/2, zero
+// above) for `batch` filters F_b = F + b fstride; the product is formed in the first pass.
+void ifft_product_f64(const double2* X, const double2* F, int64_t fstride, double2* out, double2* tmp, int64_t n,
+                      int batch, const double2* tw, int64_t table_n, cudaStream_t s);
+void ifft_product_f32(const float2* X, const float2* F, int64_t fstride, float2* out, float2* tmp, int64_t n,
+                      int batch, const float2* tw, int64_t table_n, cudaStream_t s);
 void fft_c2c_f32(const float2* in, float2* out, float2* tmp, int64_t n, int batch, int sign,
                  const float2* tw_table, int64_t table_n, cudaStream_t s);
 void real_to_complex_f64(const double* x, double2* out, int64_t n, cudaStream_t s);
@@ -158,6 +165,9 @@ std::vector<double2> host_twiddles(int64_t n);
 std::vector<float2> block_fft_tables(int64_t off[16]);
 
 // ---------------------------------------------------------------- MF (mf.cu)
+void reference_filters_impl(rf_ctx* c, const double* inv_psd, int32_t nref, const rf_template* refs, void* filt,
+                            double* sigma_out, cudaStream_t s);
+void mf_filtered_impl(rf_ctx* c, const void* x, int32_t nref, const void* filt, void* z_out, cudaStream_t s);
 void mf_reference_impl(rf_ctx* c, const void* x, const double* inv_psd, int32_t nref,
                        const rf_template* refs, void* z_out, double* sigma_out, cudaStream_t s);
 void template_fd_impl(rf_ctx* c, const rf_template& t, void* h_out, cudaStream_t s);

@@ -106,6 +106,30 @@ def test_mf_reference_f32(torch, n):
     assert _relerr(z[0].cpu().numpy(), zo) < TOL["f32"]
 
 
+@pytest.mark.parametrize("dtype,n", [("f64", 1 << 12), ("f64", 1 << 15), ("f32", 1 << 13), ("f32", 1 << 17)])
+def test_mf_filtered_matches_oracle(torch, dtype, n):
+    """Stored reference filters (Eqs. 2-4 split into a data-independent filter) give the
+    oracle's matched filter for several references in one batched call."""
+    cfg = workload.config(1, n_override=n, k_override=3) if dtype == "f64" else _small_f32_cfg(n, 3)
+    ref, nb = cfg.groups[0]
+    refs = [ref] + list(nb[:2])
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    ipt = torch.tensor(ip, device="cuda")
+    filt, sg = rf.reference_filters(ipt, refs)
+    assert filt.shape == (3, n // 2 + 1)
+    xt = torch.tensor(x, dtype=torch.float64 if dtype == "f64" else torch.float32, device="cuda")
+    z = rf.mf_filtered(xt, filt)
+    for r, t in enumerate(refs):
+        zo, No = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, t.m1, t.m2, cfg.pn_order)
+        assert _relerr(z[r].cpu().numpy(), zo) < TOL[dtype], (r, dtype, n)
+        assert abs(sg[r].item() / No - 1) < 1e-13
+    # a single reference (its own filter row) gives the same row
+    z1 = rf.mf_filtered(xt, filt[1:2])
+    assert torch.equal(z1[0], z[1])
+
+
 def test_zero_noise_injection_optimal_snr(torch):
     cfg = workload.config(1, n_override=1 << 14, k_override=3)
     inj = workload.Injection(-1, 0, 5000, 10.0)
