@@ -474,7 +474,7 @@ def main():
         peak_tflops = float(peaks.get("bf16_tflops", 1900.0))
         achieved = mma_flops / (rec_avg_ms / 1e3) / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops, "traffic": ncu_traffic("k_gemm") if args.config == 3 else None,
+                    "frac": achieved / peak_tflops, "traffic": ncu_traffic("k_gemm", prec) if args.config == 3 else None,
                     "kernel": f"reconstruct (tcgen05 Hankel GEMM, {prec}, one reference)",
                     "peak_note": ("measured cuBLAS bf16 burst (MEASURED_PEAKS.json)" if peaks else "fallback 1.9 PF/s") +
                                  "; achieved counts the MMA flops issued (split terms included)",

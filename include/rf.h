@@ -244,6 +244,13 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
  * are then incomplete), and clears it. */
 rf_status rf_device_status(rf_ctx* ctx);
 
+/* Health check of the timeout path (the paper has no counterpart): launches one small kernel
+ * that waits, with a short iteration limit, on a barrier nothing arrives on, and records
+ * RF_ETIMEOUT in the context's status word as a timed-out tensor-core wait does.  The next
+ * rf_device_status then returns RF_ETIMEOUT and clears it; the context stays usable.  Async
+ * on stream. */
+rf_status rf_selftest_bounded_wait(rf_ctx* ctx, rf_stream stream);
+
 /* Window peaks of `count` series already in memory (e.g. z_ref itself): z: complex[count][n];
  * max_out/argmax_out: [count][ceil(n/W)], same definition as rf_reconstruct_winmax. */
 rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float* max_out,

@@ -33,6 +33,7 @@ EXPORTED = (
     "rf_kernels_os_layout",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
+    "rf_selftest_bounded_wait",
 )
 
 
@@ -90,6 +91,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_mf_reference_noalloc": (i32, [P(rf_grid), vp, vp, P(rf_template), vp, vp, vp]),
         "rf_reference_filters": (i32, [vp, vp, i32, P(rf_template), vp, vp, vp]),
         "rf_mf_filtered": (i32, [vp, vp, i32, vp, vp, vp]),
+        "rf_selftest_bounded_wait": (i32, [vp, vp]),
         "rf_device_status": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -314,6 +316,10 @@ class RatioFilter:
     def device_status(self) -> None:
         """Raise if a bounded device-side wait of an earlier call ran out (synchronises)."""
         _check(_lib.rf_device_status(self.handle))
+
+    def selftest_bounded_wait(self, stream=None) -> None:
+        """Exercise the timeout path: the next device_status() raises RF_ETIMEOUT."""
+        _check(_lib.rf_selftest_bounded_wait(self.handle, _stream(stream)))
 
     def reconstruct_winmax(self, z_ref, kern: Kernels, W: int, algo: str = "auto", max_out=None, arg_out=None,
                            stream=None, prec: str = "native"):

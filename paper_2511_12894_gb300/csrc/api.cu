@@ -416,6 +416,13 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
   });
 }
 
+rf_status rf_selftest_bounded_wait(rf_ctx* ctx, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    wait_selftest(ctx, (cudaStream_t)stream);
+  });
+}
+
 rf_status rf_device_status(rf_ctx* ctx) {
   rf_status out = RF_OK;
   const rf_status st = guard([&] {

@@ -14,7 +14,8 @@
 //
 // Twiddles come from per-stage tables laid out in thread order: the stage with
 // radix R and Ns has a table of R*Ns entries, entry t*Ns + k = exp(-2 pi i t k / (R Ns)),
-// so the loads of a warp are contiguous.  The tables of the middle stages and of the
+// so the loads of a warp are contiguous.  A last stage of radix 2 or 4 reads only the
+// t = 1 row and forms the other powers by complex products.  The tables of the middle stages and of the
 // last stage follow each other; a block size B needs block_table_size<B>() entries
 // (built on the host by block_fft_tables).
 #pragma once
@@ -109,9 +110,21 @@ __device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const flo
     const float2* in = sm + bf_pad(b);
 #pragma unroll
     for (int t = 0; t < RL; ++t) a[t] = in[t * LSTR];
-    const float2* twb = tw + b;
+    if constexpr (RL <= 4) {
+      // w^t for t < RL from the table's t = 1 row: the row of B/RL entries stays in L1,
+      // and the square (and cube) cost a complex product each (about 1 ulp more error)
+      const float2 w1 = __ldg(tw + (B / RL) + b);
+      a[1] = tw_apply<SIGN>(a[1], w1);
+      if constexpr (RL == 4) {
+        const float2 w2 = cmul(w1, w1);
+        a[2] = tw_apply<SIGN>(a[2], w2);
+        a[3] = tw_apply<SIGN>(a[3], cmul(w2, w1));
+      }
+    } else {
+      const float2* twb = tw + b;
 #pragma unroll
-    for (int t = 1; t < RL; ++t) a[t] = tw_apply<SIGN>(a[t], __ldg(twb + t * (B / RL)));
+      for (int t = 1; t < RL; ++t) a[t] = tw_apply<SIGN>(a[t], __ldg(twb + t * (B / RL)));
+    }
     dft<RL, SIGN>(a);
 #pragma unroll
     for (int t = 0; t < RL; ++t) v[q * RL + t] = a[t];

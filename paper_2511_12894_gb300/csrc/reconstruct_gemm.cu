@@ -148,9 +148,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 // Bounded wait for phase `phase` of an mbarrier; true when it completed.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar_addr, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar_addr, uint32_t phase, int limit = 1 << 24) {
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 24) && !done; ++it) {
+  for (int it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done) : "r"(mbar_addr), "r"(phase) : "memory");
@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __nv_bfloat16* _
       if (NCK > 1) stage_b(c);
       // Hankel core matrices of the chunk: row a of H_d is z[b + c KC + 8d + a + e], e < 8.
       // One task = one (plane, term, d): the aligned 16-element window starting at
-      // b + c KC + 8d gives all eight rows by funnel shifts.
+      // b + c KC + 8d gives all eight rows by funnel shifts.  (One 16-byte row per thread
+      // avoids the shared-memory bank conflicts of these stores but measured slower: five
+      // scalar loads per row instead of two vector loads per eight rows.)
       const int64_t bc = b + (int64_t)c * KC + zpad;  // plane index of the chunk's first element
       for (int task = tid; task < 2 * TERMS * nH; task += kGemmThreads) {
         const int pt = task / nH, d = task - pt * nH;
@@ -465,7 +467,27 @@ void launch_gemm_prec(rf_ctx* c, const rf_kernels* kern, int prec, const V* z_re
   }
 }
 
+// Health check of the timeout path: waits, with a short limit, on an mbarrier that nothing
+// arrives on, and records RF_ETIMEOUT in the status word exactly as a timed-out wait of the
+// tensor-core kernel does.  Holds no tensor memory and issues no asynchronous copies.
+__global__ void k_wait_selftest(int limit, int* __restrict__ status) {
+  __shared__ __align__(8) unsigned long long mbar;
+  const uint32_t addr = smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(addr));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool done = mbar_wait(addr, 0u, limit);
+  if (!__syncthreads_and(done) && threadIdx.x == 0) atomicExch(status, (int)RF_ETIMEOUT);
+}
+
 }  // namespace
+
+void wait_selftest(rf_ctx* c, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(1024, c->status.as<int>());
+  RF_LAUNCHED();
+}
 
 size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int terms) {
   return sizeof(__nv_bfloat16) * (size_t)(2 * terms) * (size_t)gemm_zlen(n, LP) + 256;

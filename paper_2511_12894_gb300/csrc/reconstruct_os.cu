@@ -95,7 +95,9 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
     float2 v[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) v[t] = make_float2(0.f, 0.f);
-    // partitions outermost: each pass issues all 32 loads of the thread's bins at once
+    // partitions outermost: each pass issues all 32 loads of the thread's bins at once.
+    // The spectra stream through L2 only (ld.global.cg), so they do not evict the
+    // twiddle tables from L1.
     int sp = s * (Q - 1) - 1;  // segment of partition 0; always < NQ
     for (int p = 0; p < P; ++p, --sp) {
       const int q = sp + ((sp < 0) ? NQ : 0);  // sp >= -NQ because P <= NQ
@@ -106,8 +108,8 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
         float2 z[8], c[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-          z[t] = __ldg(zp + (h + t) * (B / 16));
-          c[t] = __ldg(cp + (h + t) * (B / 16));
+          z[t] = __ldcg(zp + (h + t) * (B / 16));
+          c[t] = __ldcg(cp + (h + t) * (B / 16));
         }
 #pragma unroll
         for (int t = 0; t < 8; ++t) {

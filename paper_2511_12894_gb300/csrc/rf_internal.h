@@ -192,6 +192,8 @@ void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int bloc
 // B = 0 and/or Lp = 0 take the modelled choice.
 void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
+// launches the bounded-wait health check (reconstruct_gemm.cu)
+void wait_selftest(rf_ctx* c, cudaStream_t s);
 // bytes of the BF16 planes of z_ref used by the tensor-core path (taps padded to LP)
 size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int terms);
 void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,

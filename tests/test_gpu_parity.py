@@ -645,3 +645,23 @@ def test_reconstruct_gemm_wide_groups(torch):
         Po, Ao = reconstruct.window_peaks(zo[j], 512)
         assert np.abs(P[j] - Po).max() <= 4 * GEMM_TOL["bf16x6"] * Po.max()
         _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, 512, 8 * GEMM_TOL["bf16x6"] * Po.max())
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(torch):
+    """A device-side wait that runs out (a barrier nothing arrives on, short limit) is
+    reported as RF_ETIMEOUT by the next status call, cleared, and the context keeps working."""
+    from paper_2511_12894_gb300 import RF_ETIMEOUT, RFError
+    cfg = _small_f32_cfg(1 << 12, 2)
+    rf = _rf(cfg)
+    rf.device_status()                       # clean to begin with
+    rf.selftest_bounded_wait()
+    with pytest.raises(RFError) as e:
+        rf.device_status()
+    assert e.value.status == RF_ETIMEOUT
+    rf.device_status()                       # cleared
+    ref = cfg.groups[0][0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    z, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), torch.tensor(ip, device="cuda"), [ref])
+    zo, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    assert _relerr(z[0].cpu().numpy(), zo) < TOL["f32"]
