@@ -53,6 +53,8 @@ def parse():
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (with --algo auto: the cost-model overlap-save layout)")
     ap.add_argument("--mf", default="filtered", choices=["filtered", "onthefly"],
                     help="reference matched filter from stored filters, or template regenerated every step")
     ap.add_argument("--part", type=int, default=0,
@@ -314,10 +316,21 @@ def main():
     t0 = time.perf_counter()
     kerns = [rf.build_ratio_kernels(r, nb, ip, thr) for r, nb in cfg.groups]
     filt, sig = rf.reference_filters(ip, refs)
-    algo_used = args.algo if args.algo != "auto" else ("os" if cfg.dtype == "f32" else "direct")
-    if algo_used == "os":
-        for k in kerns:
-            k.prepare(args.block, args.part)
+    tune, tune_s = None, 0.0
+    if args.algo == "auto" and not args.no_autotune and args.block == 0 and args.part == 0:
+        # the autotuner times candidate forms on a z_ref of this segment (offline, like the kernels)
+        t1 = time.perf_counter()
+        zt = rf.mf_filtered(x, filt)
+        tune = rf.autotune([zt[g] for g in range(G)], kerns, W, allow_split=cfg.dtype == "f32")
+        del zt
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t1
+        algo_used = tune[0]["algo"]
+    else:
+        algo_used = args.algo if args.algo != "auto" else ("os" if cfg.dtype == "f32" else "direct")
+        if algo_used == "os":
+            for k in kerns:
+                k.prepare(args.block, args.part)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     L = np.concatenate([k.length for k in kerns]).astype(np.float64)
@@ -334,14 +347,15 @@ def main():
     if algo_used == "os":
         rf.reserve(rows)
 
-    prec = args.prec or ("bf16x6" if algo_used == "gemm" else "native")
+    call_prec = args.prec or ("bf16x6" if args.algo == "gemm" else "native")
+    prec = tune[0]["prec"] if tune else call_prec   # the precision the reconstruction runs at
 
     def recon():
         if G == 1:
-            rf.reconstruct_winmax(z[0], kerns[0], W, args.algo, max_out=Pn, arg_out=An, prec=prec)
+            rf.reconstruct_winmax(z[0], kerns[0], W, args.algo, max_out=Pn, arg_out=An, prec=call_prec)
         else:
             rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, args.algo, max_out=Pn, arg_out=An,
-                                      prec=prec)
+                                      prec=call_prec)
 
     def mf_step(xs):
         if args.mf == "filtered":
@@ -543,6 +557,7 @@ def main():
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
                        "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf,
+                       "autotune": ({"seconds": tune_s, "timed": tune} if tune else None),
                        "prec": prec,
                        "graph": graph is not None,
                        "parallelism": (f"groups sharded over {world} ranks" if sharded else f"replicas x{world}")},

@@ -239,6 +239,31 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
                                  int32_t algo, int32_t prec, int64_t W, float* max_out,
                                  int32_t* argmax_out, rf_stream stream);
 
+/* Autotuner flags. */
+enum { RF_TUNE_ALLOW_SPLIT = 1 }; /* the tensor-core form (bf16x6, error about 3e-7 of max|z|) may
+                                     be chosen; without it only exact-arithmetic forms compete */
+
+/* One timed candidate of rf_autotune: form (rf_algo), overlap-save block size and partition
+ * length (0 for the other forms), precision (rf_prec) and the best of three timings (ms) of the
+ * fused window-peak reconstruction of the whole batch. */
+typedef struct {
+  int32_t algo, block, part, prec;
+  float ms;
+} rf_tune_entry;
+
+/* Autotuner for a batch of G references (z_refs[g], kernel sets ks[g], windows of W samples):
+ * times candidate forms on the device and records the fastest in every kernel set, so that
+ * RF_ALGO_AUTO uses it from then on (with its precision when it is the tensor-core form).
+ * Candidates: on RF_F32 grids the max_os overlap-save layouts of least modelled cost (the batch
+ * runs them as in rf_reconstruct_batched), the tensor-core form at RF_PREC_BF16X6 when flags has
+ * RF_TUNE_ALLOW_SPLIT and the mean kernel length is at most 4096 taps, and the direct sum when the
+ * grid is RF_F64 or no kernel is longer than 1024 taps.  out (host, may be NULL): up to max_out entries, the winner first; *n_out (host, may
+ * be NULL) the number written.  Overlap-save kernel sets end up prepared for the winning layout
+ * (or the last one timed when another form wins).  Allocates; SYNCHRONISES `stream`. */
+rf_status rf_autotune(rf_ctx* ctx, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
+                      int32_t flags, int32_t max_os, rf_tune_entry* out, int32_t max_out, int32_t* n_out,
+                      rf_stream stream);
+
 /* Device-side status of the context: waits for the device, then returns RF_OK, or
  * RF_ETIMEOUT if a bounded device-side wait of an earlier call ran out (that call's outputs
  * are then incomplete), and clears it. */

@@ -33,8 +33,13 @@ EXPORTED = (
     "rf_kernels_os_layout",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
-    "rf_selftest_bounded_wait",
+    "rf_selftest_bounded_wait", "rf_autotune",
 )
+
+
+class rf_tune_entry(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("block", ctypes.c_int32), ("part", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class RFError(RuntimeError):
@@ -92,6 +97,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_reference_filters": (i32, [vp, vp, i32, P(rf_template), vp, vp, vp]),
         "rf_mf_filtered": (i32, [vp, vp, i32, vp, vp, vp]),
         "rf_selftest_bounded_wait": (i32, [vp, vp]),
+        "rf_autotune": (i32, [vp, i32, P(vp), P(vp), i64, i32, i32, P(rf_tune_entry), i32, P(i32), vp]),
         "rf_device_status": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -317,6 +323,25 @@ class RatioFilter:
         """Raise if a bounded device-side wait of an earlier call ran out (synchronises)."""
         _check(_lib.rf_device_status(self.handle))
 
+    def autotune(self, z_refs: Sequence, kerns: Sequence[Kernels], W: int, allow_split: bool = False,
+                 max_os: int = 4, stream=None):
+        """Time candidate forms for this batch and record the fastest in every kernel set.
+
+        Returns the timed candidates, the winner first: dicts with algo, block, part, prec, ms."""
+        G = len(z_refs)
+        zs = [_dev(z, self.cdtype, "z_refs[g]") for z in z_refs]
+        zp = (ctypes.c_void_p * G)(*[z.data_ptr() for z in zs])
+        kp = (ctypes.c_void_p * G)(*[k.handle.value if isinstance(k.handle, ctypes.c_void_p) else k.handle
+                                     for k in kerns])
+        out = (rf_tune_entry * 64)()
+        n = ctypes.c_int32(0)
+        _check(_lib.rf_autotune(self.handle, G, zp, kp, int(W), 1 if allow_split else 0, int(max_os), out, 64,
+                                ctypes.byref(n), _stream(stream)))
+        names = {v: k for k, v in ALGOS.items()}
+        pnames = {v: k for k, v in PRECS.items()}
+        return [{"algo": names[e.algo], "block": e.block, "part": e.part, "prec": pnames[e.prec], "ms": e.ms}
+                for e in out[:n.value]]
+
     def selftest_bounded_wait(self, stream=None) -> None:
         """Exercise the timeout path: the next device_status() raises RF_ETIMEOUT."""
         _check(_lib.rf_selftest_bounded_wait(self.handle, _stream(stream)))
@@ -389,4 +414,4 @@ def mf_reference_noalloc(grid: rf_grid, x, inv_psd, ref, z_out, sigma_out=None, 
                                        ctypes.c_void_p(z_out.data_ptr()), sp, _stream(stream)))
 
 
-__all__ = ["mf_reference_noalloc", "rf_grid", "RatioFilter", "Kernels", "RFError", "load_library", "launch_count", "EXPORTED", "LIB_PATH"]
+__all__ = ["mf_reference_noalloc", "rf_grid", "rf_tune_entry", "RatioFilter", "Kernels", "RFError", "load_library", "launch_count", "EXPORTED", "LIB_PATH"]

@@ -317,7 +317,10 @@ void rf_kernels_free(rf_kernels* kern) {
   delete kern;
 }
 
-static int check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t prec) {
+// Validates a reconstruction call and resolves RF_ALGO_AUTO: the autotuned form of the kernel
+// set (with its precision) when there is one, else overlap-save on FP32 grids with n >= 512 and
+// the direct sum otherwise.
+static int check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, int32_t algo, int32_t& prec) {
   check_ctx(ctx);
   RF_REQUIRE(kern != nullptr, "kern is NULL");
   RF_REQUIRE(kern->n == ctx->n && kern->dtype == ctx->g.dtype, "kernels were made for another grid");
@@ -325,6 +328,10 @@ static int check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, i
   RF_REQUIRE(algo == RF_ALGO_AUTO || algo == RF_ALGO_DIRECT || algo == RF_ALGO_OS || algo == RF_ALGO_GEMM,
              "unknown algo %d", algo);
   RF_REQUIRE(prec >= RF_PREC_NATIVE && prec <= RF_PREC_BF16X9, "unknown prec %d", prec);
+  if (algo == RF_ALGO_AUTO && kern->tuned_algo && prec == RF_PREC_NATIVE) {
+    algo = kern->tuned_algo;
+    prec = kern->tuned_prec;
+  }
   if (algo == RF_ALGO_GEMM) {
     RF_REQUIRE(prec != RF_PREC_NATIVE, "the tensor-core form needs a split precision (RF_PREC_BF16*)");
     if (kern->max_len > gemm_max_len() || ctx->n % 128 != 0) {
@@ -388,11 +395,18 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
     RF_REQUIRE(W >= 1 && W <= ctx->n, "W=%lld must be in [1, n]", (long long)W);
     int64_t rows = 0;
     int a = RF_ALGO_AUTO;
+    int32_t pa = prec;
     for (int g = 0; g < G; ++g) {
       RF_REQUIRE(ks[g] != nullptr, "ks[%d] is NULL", g);
-      a = check_recon(ctx, z_refs[g], ks[g], algo, prec);  // the same for every group
+      int32_t pg = prec;
+      const int ag = check_recon(ctx, z_refs[g], ks[g], algo, pg);
+      RF_REQUIRE(g == 0 || (ag == a && pg == pa),
+                 "the groups resolve to different forms (tune them together with rf_autotune)");
+      a = ag;
+      pa = pg;
       rows += ks[g]->k;
     }
+    prec = pa;
     if (!rows) return;
     check_dev(max_out, "max_out");
     check_dev(argmax_out, "argmax_out");
@@ -413,6 +427,25 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
       }
       row += ks[g]->k;
     }
+  });
+}
+
+rf_status rf_autotune(rf_ctx* ctx, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
+                      int32_t flags, int32_t max_os, rf_tune_entry* out, int32_t max_out, int32_t* n_out,
+                      rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(G >= 1, "G must be >= 1");
+    RF_REQUIRE(z_refs != nullptr && ks != nullptr, "z_refs and ks must be non-NULL host arrays");
+    RF_REQUIRE(W >= 1 && W <= ctx->n, "W=%lld must be in [1, n]", (long long)W);
+    RF_REQUIRE(max_out >= 0 && max_os >= 0, "max_out and max_os must be >= 0");
+    RF_REQUIRE((flags & ~RF_TUNE_ALLOW_SPLIT) == 0, "unknown flags %d", flags);
+    for (int g = 0; g < G; ++g) {
+      RF_REQUIRE(ks[g] != nullptr, "ks[%d] is NULL", g);
+      RF_REQUIRE(ks[g]->n == ctx->n && ks[g]->dtype == ctx->g.dtype, "kernels were made for another grid");
+      check_dev(z_refs[g], "z_refs[g]");
+    }
+    autotune_impl(ctx, G, z_refs, ks, W, flags, max_os, out, max_out, n_out, (cudaStream_t)stream);
   });
 }
 

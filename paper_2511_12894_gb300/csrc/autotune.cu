@@ -1,0 +1,127 @@
+// Autotuner: picks, for a batch of kernel sets, the reconstruction form and its shape by timing
+// candidates on the device.  Candidates: overlap-save layouts (block size B, partition length
+// Lp; the cost model of reconstruct_os.cu ranks them and the best few are timed), the
+// tensor-core form at the cheapest split precision that meets the FP32-equivalent accuracy
+// (bf16x6) when the kernels are short enough for it to compete, and the direct sum for short
+// kernels.  Each candidate runs the fused window-peak
+// form once to warm up and then three times between CUDA events; the fastest wins and is
+// recorded in every kernel set, so that RF_ALGO_AUTO follows it.
+#include <algorithm>
+#include <vector>
+
+#include "rf_internal.h"
+
+namespace rf {
+
+namespace {
+
+struct Cand {
+  int algo, block, part, prec;
+  double model;
+};
+
+// layouts of least modelled cost over all kernel lengths of the batch
+std::vector<Cand> os_candidates(const rf_ctx* c, int G, rf_kernels* const* ks, int max_os) {
+  std::vector<int> all;
+  for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
+  std::vector<Cand> out;
+  for (int B = 512; B <= 16384; B *= 2) {
+    if (B > c->n) continue;
+    for (int Q = 2; Q <= 8; Q *= 2) out.push_back(Cand{RF_ALGO_OS, B, B / Q, RF_PREC_NATIVE,
+                                                        os_layout_cost(c, all, B, B / Q)});
+  }
+  std::sort(out.begin(), out.end(), [](const Cand& a, const Cand& b) { return a.model < b.model; });
+  if ((int)out.size() > max_os) out.resize(max_os);
+  return out;
+}
+
+}  // namespace
+
+void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
+                   int32_t flags, int32_t max_os, rf_tune_entry* out, int32_t max_out, int32_t* n_out,
+                   cudaStream_t s) {
+  int64_t rows = 0, taps = 0;
+  int32_t max_len = 0;
+  for (int g = 0; g < G; ++g) {
+    rows += ks[g]->k;
+    taps += ks[g]->offset[ks[g]->k];
+    max_len = std::max(max_len, ks[g]->max_len);
+  }
+  const double mean_len = rows ? (double)taps / (double)rows : 0.0;
+  std::vector<Cand> cands;
+  const bool f32 = c->g.dtype == RF_F32;
+  if (f32 && c->n >= 512) cands = os_candidates(c, G, ks, std::max(1, max_os));
+  // the tensor-core form costs 8 L flops per output times the split products, so it is timed
+  // only for short kernels (mean length <= 4096 taps)
+  if ((flags & RF_TUNE_ALLOW_SPLIT) && max_len <= gemm_max_len() && c->n % 128 == 0 && mean_len <= 4096.0)
+    cands.push_back(Cand{RF_ALGO_GEMM, 0, 0, RF_PREC_BF16X6, 0.0});
+  if (!f32 || max_len <= 1024) cands.push_back(Cand{RF_ALGO_DIRECT, 0, 0, RF_PREC_NATIVE, 0.0});
+  RF_REQUIRE(!cands.empty(), "no reconstruction form to tune");
+  const int64_t nw = (c->n + W - 1) / W;
+  DevBuf pk, ak;
+  pk.ensure(sizeof(float) * (size_t)std::max<int64_t>(1, rows * nw));
+  ak.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(1, rows * nw));
+  cudaEvent_t e0, e1;
+  RF_CUDA(cudaEventCreate(&e0));
+  RF_CUDA(cudaEventCreate(&e1));
+  auto run = [&](const Cand& cd) {
+    if (cd.algo == RF_ALGO_OS && G > 1) {
+      reconstruct_batched(c, G, z_refs, ks, W, pk.as<float>(), ak.as<int32_t>(), s);
+      return;
+    }
+    int64_t row = 0;
+    for (int g = 0; g < G; ++g) {
+      rf_kernels* k = ks[g];
+      if (k->k) {
+        float* mo = pk.as<float>() + row * nw;
+        int32_t* ao = ak.as<int32_t>() + row * nw;
+        if (cd.algo == RF_ALGO_OS) reconstruct_os(c, z_refs[g], k, nullptr, W, mo, ao, s);
+        else if (cd.algo == RF_ALGO_GEMM) reconstruct_gemm(c, z_refs[g], k, cd.prec, nullptr, W, mo, ao, s);
+        else reconstruct_direct(c, z_refs[g], k, nullptr, W, mo, ao, s);
+      }
+      row += k->k;
+    }
+  };
+  std::vector<float> ms(cands.size(), 0.f);
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const Cand& cd = cands[i];
+    if (cd.algo == RF_ALGO_OS)
+      for (int g = 0; g < G; ++g) os_prepare(c, ks[g], cd.block, cd.part, s);
+    run(cd);  // warm-up (and the tensor-core operand preparation)
+    float best = 0.f;
+    for (int r = 0; r < 3; ++r) {
+      RF_CUDA(cudaEventRecord(e0, s));
+      run(cd);
+      RF_CUDA(cudaEventRecord(e1, s));
+      RF_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      RF_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      best = r == 0 ? t : std::min(best, t);
+    }
+    ms[i] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  size_t win = 0;
+  for (size_t i = 1; i < cands.size(); ++i)
+    if (ms[i] < ms[win]) win = i;
+  const Cand& w = cands[win];
+  for (int g = 0; g < G; ++g) {
+    if (w.algo == RF_ALGO_OS) os_prepare(c, ks[g], w.block, w.part, s);
+    ks[g]->tuned_algo = w.algo;
+    ks[g]->tuned_prec = w.prec;
+  }
+  RF_CUDA(cudaStreamSynchronize(s));
+  // the winner first, then the others in the order they were timed
+  int32_t n = 0;
+  auto put = [&](size_t i) {
+    if (n < max_out && out) out[n] = rf_tune_entry{cands[i].algo, cands[i].block, cands[i].part, cands[i].prec, ms[i]};
+    ++n;
+  };
+  put(win);
+  for (size_t i = 0; i < cands.size(); ++i)
+    if (i != win) put(i);
+  if (n_out) *n_out = std::min(n, max_out);
+}
+
+}  // namespace rf

@@ -135,6 +135,8 @@ struct rf_kernels {
   rf::DevBuf os_parts_d;   // int32 [k]
   // Tensor-core direct form: split-BF16 tap operands per group of gemm_NJ neighbours, taps
   // padded to gemm_NCK chunks of gemm_KC (see reconstruct_gemm.cu).
+  // Form chosen by rf_autotune (RF_ALGO_AUTO then follows it; 0 when not tuned).
+  int tuned_algo = 0, tuned_prec = 0;
   bool gemm_ready = false;
   int gemm_terms = 0, gemm_KC = 0, gemm_NCK = 0, gemm_NJ = 0;
   rf::DevBuf gemm_B;
@@ -189,6 +191,12 @@ void winmax_series(rf_ctx* c, const void* z, int32_t count, int64_t W, float* ma
 // Overlap-save layout (block size, partition length) of least modelled cost for kernels of
 // the given lengths; block != 0 fixes the block size.
 void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, int* B, int* Lp);
+// modelled cost (ns, whole GPU) of one layout for kernels of the given lengths
+double os_layout_cost(const rf_ctx* c, const std::vector<int>& lengths, int B, int Lp);
+// autotune.cu
+void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
+                   int32_t flags, int32_t max_os, rf_tune_entry* out, int32_t max_out, int32_t* n_out,
+                   cudaStream_t s);
 // B = 0 and/or Lp = 0 take the modelled choice.
 void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);

@@ -665,3 +665,38 @@ def test_bounded_wait_timeout_is_reported_and_context_survives(torch):
     z, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), torch.tensor(ip, device="cuda"), [ref])
     zo, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
     assert _relerr(z[0].cpu().numpy(), zo) < TOL["f32"]
+
+
+def test_autotune_records_the_fastest_form_and_auto_follows_it(torch):
+    """The autotuner times overlap-save layouts, the tensor-core form and the direct sum on a
+    batch, records the fastest, and AUTO then gives the same rows as that form called
+    explicitly; on an FP64 grid without split precisions only the exact direct sum competes."""
+    cfg = _batch_cfg()
+    ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
+    x = torch.tensor(data.strain(cfg), dtype=torch.float32, device="cuda")
+    rf = _rf(cfg)
+    refs = [g[0] for g in cfg.groups]
+    z, _ = rf.mf_reference(x, ip, refs)
+    kerns = [rf.build_ratio_kernels(r, nb, ip, cfg.threshold) for r, nb in cfg.groups]
+    W = cfg.window
+    zs = [z[g] for g in range(len(refs))]
+    table = rf.autotune(zs, kerns, W, allow_split=True, max_os=3)
+    assert len(table) >= 3 and all(e["ms"] > 0 for e in table)
+    assert sum(e["algo"] == "os" for e in table) == 3
+    assert {e["algo"] for e in table} <= {"os", "gemm", "direct"}
+    win = table[0]
+    assert win["ms"] == min(e["ms"] for e in table)
+    if win["algo"] == "os":
+        assert all(k.os_layout() == (win["block"], win["part"]) for k in kerns)
+    P, A = rf.reconstruct_batched(zs, kerns, W)                       # AUTO -> the tuned form
+    P2, A2 = rf.reconstruct_batched(zs, kerns, W, win["algo"], prec=win["prec"])
+    assert torch.equal(P, P2) and torch.equal(A, A2)
+    # FP64 grid, exact forms only
+    c1 = workload.config(1, n_override=1 << 13, k_override=3)
+    r1 = _rf(c1)
+    ref, nb = c1.groups[0]
+    ip1 = torch.tensor(workload.inv_psd(c1), device="cuda")
+    z1, _ = r1.mf_reference(torch.tensor(data.strain(c1), device="cuda"), ip1, [ref])
+    k1 = r1.build_ratio_kernels(ref, nb, ip1, c1.threshold)
+    t1 = r1.autotune([z1[0]], [k1], c1.window)
+    assert [e["algo"] for e in t1] == ["direct"]
