@@ -335,7 +335,8 @@ def main():
     build_s = time.perf_counter() - t0
     L = np.concatenate([k.length for k in kerns]).astype(np.float64)
     rows = int(L.size)
-    B, Lp = kerns[0].os_layout() if algo_used == "os" else (0, 0)
+    buckets = kerns[0].os_buckets() if algo_used == "os" else []   # [(cut, B, Lp), ...]
+    layout = ",".join(f"B={b},Lp={p}" + (f"@{c}" if c else "") for c, b, p in buckets)
 
     nw = -(-n // W)
     z = torch.empty((G, n), dtype=rf.cdtype, device=dev)
@@ -463,9 +464,12 @@ def main():
         # per output block of H = B - Lp samples: one inverse B-point FFT (5 B log2 B) and
         # P_j = ceil(L_j / Lp) complex multiply-adds per bin (8 P_j B); the segment spectra
         # are shared by all neighbours of a reference
-        H = B - Lp
-        P = np.maximum(1, np.ceil(L / Lp))
-        flops = float(np.sum((5.0 * B * math.log2(B) + 8.0 * P * B) / H)) * n
+        cuts = np.array([c for c, _, _ in buckets])
+        bi = np.searchsorted(cuts, L, side="right") - 1          # bucket of each kernel
+        Bj = np.array([b for _, b, _ in buckets], dtype=np.float64)[bi]
+        Lpj = np.array([p for _, _, p in buckets], dtype=np.float64)[bi]
+        P = np.maximum(1, np.ceil(L / Lpj))
+        flops = float(np.sum((5.0 * Bj * np.log2(Bj) + 8.0 * P * Bj) / (Bj - Lpj))) * n
     else:
         flops = 8.0 * float(L.sum()) * n
     props = torch.cuda.get_device_properties(dev)
@@ -499,9 +503,9 @@ def main():
         achieved = flops / (rec_avg_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops,
-                    "traffic": ncu_traffic("k_os", f"B={B},Lp={Lp}") if (algo_used == "os" and G == 1
+                    "traffic": ncu_traffic("k_os", layout) if (algo_used == "os" and G == 1
                                                                             and args.config == 2) else None,
-                    "kernel": f"reconstruct ({algo_used}{', B=%d, Lp=%d' % (B, Lp) if algo_used == 'os' else ''}, "
+                    "kernel": f"reconstruct ({algo_used}{', ' + layout if algo_used == 'os' else ''}, "
                               f"{'FP64' if cfg.dtype == 'f64' and algo_used == 'direct' else 'FP32'} CUDA cores, "
                               f"{'batched persistent' if G > 1 else 'one reference'})",
                     "peak_note": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",

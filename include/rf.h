@@ -193,9 +193,23 @@ rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** le
  * was not called.  Allocates; SYNCHRONISES `stream`.  RF_EINVAL for other sizes. */
 rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, int32_t part, rf_stream stream);
 
-/* Overlap-save layout a kernel set is prepared for: block size and partition length (both 0
- * when not prepared).  Either output pointer may be NULL. */
+/* Overlap-save layout a kernel set is prepared for: block size and partition length of its
+ * first length bucket (both 0 when not prepared).  Either output pointer may be NULL. */
 rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* part);
+
+/* Overlap-save preparation with a layout per kernel-length bucket: bucket b takes the
+ * neighbours with cuts[b] <= L < cuts[b+1] (cuts[0] = 0, increasing; the last bucket is open)
+ * and runs with block size blocks[b] and partition length parts[b] (each as in
+ * rf_kernels_prepare, both non-zero).  A reconstruction then makes one segment transform and
+ * one launch per bucket; rows keep the neighbour order.  1 <= nb <= 8; cuts, blocks, parts are
+ * host arrays.  Allocates; SYNCHRONISES `stream`. */
+rf_status rf_kernels_prepare_buckets(rf_ctx* ctx, rf_kernels* kern, int32_t nb, const int32_t* cuts,
+                                     const int32_t* blocks, const int32_t* parts, rf_stream stream);
+
+/* The bucket layout of a prepared kernel set: up to max_nb buckets into the host arrays cuts,
+ * blocks, parts (any may be NULL) and their number into *nb (0 when not prepared). */
+rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t* cuts, int32_t* blocks,
+                                int32_t* parts, int32_t* nb);
 
 /* Copy the packed taps (sum(len) complex entries, grid dtype) into caller device memory
  * `dst`.  Async on stream. */
@@ -243,11 +257,12 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
 enum { RF_TUNE_ALLOW_SPLIT = 1 }; /* the tensor-core form (bf16x6, error about 3e-7 of max|z|) may
                                      be chosen; without it only exact-arithmetic forms compete */
 
-/* One timed candidate of rf_autotune: form (rf_algo), overlap-save block size and partition
- * length (0 for the other forms), precision (rf_prec) and the best of three timings (ms) of the
- * fused window-peak reconstruction of the whole batch. */
+/* One timed candidate of rf_autotune: form (rf_algo), precision (rf_prec), overlap-save block
+ * size and partition length (0 for the other forms) of the kernels shorter than `cut` taps, and
+ * block2 / part2 for the others (cut = block2 = part2 = 0: one layout for all), and the best of
+ * three timings (ms) of the fused window-peak reconstruction of the whole batch. */
 typedef struct {
-  int32_t algo, block, part, prec;
+  int32_t algo, block, part, prec, cut, block2, part2;
   float ms;
 } rf_tune_entry;
 
@@ -255,7 +270,9 @@ typedef struct {
  * times candidate forms on the device and records the fastest in every kernel set, so that
  * RF_ALGO_AUTO uses it from then on (with its precision when it is the tensor-core form).
  * Candidates: on RF_F32 grids the max_os overlap-save layouts of least modelled cost (the batch
- * runs them as in rf_reconstruct_batched), the tensor-core form at RF_PREC_BF16X6 when flags has
+ * runs them as in rf_reconstruct_batched) and two-bucket variants (kernels shorter than 2048,
+ * 4096 or 8192 taps with one of the two layouts of least modelled cost for them, the others with
+ * the fastest single layout), the tensor-core form at RF_PREC_BF16X6 when flags has
  * RF_TUNE_ALLOW_SPLIT and the mean kernel length is at most 4096 taps, and the direct sum when the
  * grid is RF_F64 or no kernel is longer than 1024 taps.  out (host, may be NULL): up to max_out entries, the winner first; *n_out (host, may
  * be NULL) the number written.  Overlap-save kernel sets end up prepared for the winning layout

@@ -30,7 +30,7 @@ PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
 EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
-    "rf_kernels_os_layout",
+    "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_os_buckets",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
     "rf_selftest_bounded_wait", "rf_autotune",
@@ -39,7 +39,8 @@ EXPORTED = (
 
 class rf_tune_entry(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("block", ctypes.c_int32), ("part", ctypes.c_int32),
-                ("prec", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("prec", ctypes.c_int32), ("cut", ctypes.c_int32), ("block2", ctypes.c_int32),
+                ("part2", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class RFError(RuntimeError):
@@ -88,6 +89,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_kernels_copy_taps": (i32, [vp, vp, vp]),
         "rf_kernels_prepare": (i32, [vp, vp, i32, i32, vp]),
         "rf_kernels_os_layout": (i32, [vp, P(i32), P(i32)]),
+        "rf_kernels_prepare_buckets": (i32, [vp, vp, i32, P(i32), P(i32), P(i32), vp]),
+        "rf_kernels_os_buckets": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
         "rf_kernels_free": (None, [vp]),
         "rf_reconstruct": (i32, [vp, vp, vp, i32, i32, vp, vp]),
         "rf_reconstruct_winmax": (i32, [vp, vp, vp, i32, i32, i64, vp, vp, vp]),
@@ -169,6 +172,20 @@ class Kernels:
         """Overlap-save preparation with block size ``block`` and partition length ``part``
         (0: defaults); synchronises."""
         _check(_lib.rf_kernels_prepare(self.ctx.handle, self.handle, int(block), int(part), _stream(stream)))
+
+    def prepare_buckets(self, cuts: Sequence[int], blocks: Sequence[int], parts: Sequence[int], stream=None) -> None:
+        """Overlap-save layout per kernel-length bucket: bucket b takes cuts[b] <= L < cuts[b+1]."""
+        nb = len(cuts)
+        arr = lambda v: (ctypes.c_int32 * nb)(*[int(x) for x in v])
+        _check(_lib.rf_kernels_prepare_buckets(self.ctx.handle, self.handle, nb, arr(cuts), arr(blocks), arr(parts),
+                                               _stream(stream)))
+
+    def os_buckets(self):
+        """[(cut, block, part), ...] of the overlap-save preparation ([] if none)."""
+        c, b, p = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)()
+        nb = ctypes.c_int32(0)
+        _check(_lib.rf_kernels_os_buckets(self.handle, 8, c, b, p, ctypes.byref(nb)))
+        return [(c[i], b[i], p[i]) for i in range(nb.value)]
 
     def os_layout(self):
         """(block size, partition length) of the overlap-save preparation, (0, 0) if none."""
@@ -339,8 +356,8 @@ class RatioFilter:
                                 ctypes.byref(n), _stream(stream)))
         names = {v: k for k, v in ALGOS.items()}
         pnames = {v: k for k, v in PRECS.items()}
-        return [{"algo": names[e.algo], "block": e.block, "part": e.part, "prec": pnames[e.prec], "ms": e.ms}
-                for e in out[:n.value]]
+        return [{"algo": names[e.algo], "block": e.block, "part": e.part, "prec": pnames[e.prec], "cut": e.cut,
+                 "block2": e.block2, "part2": e.part2, "ms": e.ms} for e in out[:n.value]]
 
     def selftest_bounded_wait(self, stream=None) -> None:
         """Exercise the timeout path: the next device_status() raises RF_ETIMEOUT."""

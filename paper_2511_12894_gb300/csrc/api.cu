@@ -292,6 +292,39 @@ rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, int32
   });
 }
 
+rf_status rf_kernels_prepare_buckets(rf_ctx* ctx, rf_kernels* kern, int32_t nb, const int32_t* cuts,
+                                     const int32_t* blocks, const int32_t* parts, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    RF_REQUIRE(kern->n == ctx->n && kern->dtype == ctx->g.dtype, "kernels were made for another grid");
+    if (ctx->g.dtype != RF_F32 || ctx->n < 512) {
+      set_error("overlap-save needs an RF_F32 grid with n >= 512");
+      throw Fail{RF_EUNSUPPORTED};
+    }
+    RF_REQUIRE(nb >= 1 && nb <= 8, "nb must be in [1, 8]");
+    check_host(cuts, "cuts");
+    check_host(blocks, "blocks");
+    check_host(parts, "parts");
+    os_prepare_buckets(ctx, kern, nb, cuts, blocks, parts, (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t* cuts, int32_t* blocks,
+                                int32_t* parts, int32_t* nb) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    RF_REQUIRE(max_nb >= 0, "max_nb must be >= 0");
+    const int cnt = kern->os_ready ? (int)kern->os_buckets.size() : 0;
+    for (int b = 0; b < std::min(cnt, (int)max_nb); ++b) {
+      if (cuts) cuts[b] = kern->os_buckets[b].cut_lo;
+      if (blocks) blocks[b] = kern->os_buckets[b].B;
+      if (parts) parts[b] = kern->os_buckets[b].Lp;
+    }
+    if (nb) *nb = std::min(cnt, (int)max_nb);
+  });
+}
+
 rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* part) {
   return guard([&] {
     RF_REQUIRE(kern != nullptr, "kern is NULL");

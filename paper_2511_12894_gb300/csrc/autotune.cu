@@ -1,6 +1,7 @@
 // Autotuner: picks, for a batch of kernel sets, the reconstruction form and its shape by timing
 // candidates on the device.  Candidates: overlap-save layouts (block size B, partition length
-// Lp; the cost model of reconstruct_os.cu ranks them and the best few are timed), the
+// Lp; the cost model of reconstruct_os.cu ranks them and the best few are timed), two-bucket
+// overlap-save (short kernels with their own layout, the rest with the fastest single one), the
 // tensor-core form at the cheapest split precision that meets the FP32-equivalent accuracy
 // (bf16x6) when the kernels are short enough for it to compete, and the direct sum for short
 // kernels.  Each candidate runs the fused window-peak
@@ -18,21 +19,27 @@ namespace {
 struct Cand {
   int algo, block, part, prec;
   double model;
+  int cut = 0, block2 = 0, part2 = 0;  // two-bucket overlap-save: (block, part) below cut
 };
 
-// layouts of least modelled cost over all kernel lengths of the batch
-std::vector<Cand> os_candidates(const rf_ctx* c, int G, rf_kernels* const* ks, int max_os) {
-  std::vector<int> all;
-  for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
+// layouts of least modelled cost for kernels of the given lengths
+std::vector<Cand> os_candidates_for(const rf_ctx* c, const std::vector<int>& all, int max_os) {
   std::vector<Cand> out;
   for (int B = 512; B <= 16384; B *= 2) {
     if (B > c->n) continue;
-    for (int Q = 2; Q <= 8; Q *= 2) out.push_back(Cand{RF_ALGO_OS, B, B / Q, RF_PREC_NATIVE,
-                                                        os_layout_cost(c, all, B, B / Q)});
+    for (int Q = 2; Q <= 8; Q *= 2)
+      out.push_back(Cand{RF_ALGO_OS, B, B / Q, RF_PREC_NATIVE, os_layout_cost(c, all, B, B / Q)});
   }
   std::sort(out.begin(), out.end(), [](const Cand& a, const Cand& b) { return a.model < b.model; });
   if ((int)out.size() > max_os) out.resize(max_os);
   return out;
+}
+
+// the same over all kernel lengths of the batch
+std::vector<Cand> os_candidates(const rf_ctx* c, int G, rf_kernels* const* ks, int max_os) {
+  std::vector<int> all;
+  for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
+  return os_candidates_for(c, all, max_os);
 }
 
 }  // namespace
@@ -82,11 +89,17 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
       row += k->k;
     }
   };
-  std::vector<float> ms(cands.size(), 0.f);
-  for (size_t i = 0; i < cands.size(); ++i) {
-    const Cand& cd = cands[i];
-    if (cd.algo == RF_ALGO_OS)
+  auto prepare = [&](const Cand& cd) {
+    if (cd.algo != RF_ALGO_OS) return;
+    if (!cd.cut) {
       for (int g = 0; g < G; ++g) os_prepare(c, ks[g], cd.block, cd.part, s);
+    } else {
+      const int32_t cuts[2] = {0, cd.cut}, Bs[2] = {cd.block, cd.block2}, Lps[2] = {cd.part, cd.part2};
+      for (int g = 0; g < G; ++g) os_prepare_buckets(c, ks[g], 2, cuts, Bs, Lps, s);
+    }
+  };
+  auto time_cand = [&](const Cand& cd) {
+    prepare(cd);
     run(cd);  // warm-up (and the tensor-core operand preparation)
     float best = 0.f;
     for (int r = 0; r < 3; ++r) {
@@ -98,7 +111,42 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
       RF_CUDA(cudaEventElapsedTime(&t, e0, e1));
       best = r == 0 ? t : std::min(best, t);
     }
-    ms[i] = best;
+    return best;
+  };
+  std::vector<float> ms;
+  for (const Cand& cd : cands) ms.push_back(time_cand(cd));
+  // two-bucket variants around the fastest single layout: the kernels below a cut run with
+  // one of the two layouts of least modelled cost for them
+  if (f32 && c->n >= 512 && max_os > 0) {
+    size_t best_os = cands.size();
+    for (size_t i = 0; i < cands.size(); ++i)
+      if (cands[i].algo == RF_ALGO_OS && (best_os == cands.size() || ms[i] < ms[best_os])) best_os = i;
+    if (best_os < cands.size()) {
+      const Cand lead = cands[best_os];
+      std::vector<Cand> extra;
+      for (const int cut : {2048, 4096, 8192}) {
+        std::vector<int> shortL;
+        bool any_long = false;
+        for (int g = 0; g < G; ++g)
+          for (const int L : ks[g]->len) {
+            if (L < cut) shortL.push_back(L);
+            else any_long = true;
+          }
+        if (shortL.empty() || !any_long) continue;
+        std::vector<Cand> sc = os_candidates_for(c, shortL, 2);
+        for (Cand cd : sc) {
+          if (cd.block == lead.block && cd.part == lead.part) continue;
+          cd.cut = cut;
+          cd.block2 = lead.block;
+          cd.part2 = lead.part;
+          extra.push_back(cd);
+        }
+      }
+      for (const Cand& cd : extra) {
+        cands.push_back(cd);
+        ms.push_back(time_cand(cd));
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -106,8 +154,8 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   for (size_t i = 1; i < cands.size(); ++i)
     if (ms[i] < ms[win]) win = i;
   const Cand& w = cands[win];
+  prepare(w);
   for (int g = 0; g < G; ++g) {
-    if (w.algo == RF_ALGO_OS) os_prepare(c, ks[g], w.block, w.part, s);
     ks[g]->tuned_algo = w.algo;
     ks[g]->tuned_prec = w.prec;
   }
@@ -115,7 +163,9 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   // the winner first, then the others in the order they were timed
   int32_t n = 0;
   auto put = [&](size_t i) {
-    if (n < max_out && out) out[n] = rf_tune_entry{cands[i].algo, cands[i].block, cands[i].part, cands[i].prec, ms[i]};
+    const Cand& cd = cands[i];
+    if (n < max_out && out)
+      out[n] = rf_tune_entry{cd.algo, cd.block, cd.part, cd.prec, cd.cut, cd.block2, cd.part2, ms[i]};
     ++n;
   };
   put(win);

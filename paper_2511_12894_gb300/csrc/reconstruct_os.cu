@@ -222,15 +222,17 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
   }
 }
 
+// Neighbours idx[y0 + blockIdx.y] of one layout bucket; blockIdx.x takes SC output blocks.
 template <int B, int Q, bool WINMAX>
 __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restrict__ Zs, const float2* __restrict__ Cs,
                                               const int64_t* __restrict__ spec_off, const int* __restrict__ parts,
-                                              const int* __restrict__ lag0, const float2* __restrict__ tw, int64_t n,
+                                              const int* __restrict__ lag0, const int* __restrict__ idx, int y0,
+                                              const float2* __restrict__ tw, int64_t n,
                                               int NQ, int NB, int SC, float2* __restrict__ z_out,
                                               unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
                                               int fastwin) {
   extern __shared__ float2 sm[];
-  const int j = blockIdx.y;
+  const int j = idx[y0 + blockIdx.y];
   const int s0 = blockIdx.x * SC;
   const int s1 = min(NB, s0 + SC);
   os_blocks<B, Q, WINMAX>(Zs, Cs + spec_off[j], parts[j], lag0[j], tw, n, NQ, s0, s1,
@@ -327,30 +329,28 @@ constexpr int os_warp_span() {
 }
 
 template <int B, int Q, bool WINMAX>
-void launch_os(rf_ctx* c, const rf_kernels* kern, const float2* Zs, float2* z_out, unsigned long long* keys,
-               int64_t W, cudaStream_t s) {
+void launch_os(rf_ctx* c, const rf_kernels* kern, const OsBucket& bk, const float2* Zs, float2* z_out,
+               unsigned long long* keys, int64_t W, cudaStream_t s) {
   constexpr int Lp = B / Q, H = B - Lp;
   const int NQ = (int)(c->n / Lp);
   const int NB = (int)((c->n + H - 1) / H);
+  const int count = (int)bk.idx.size();
   const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<B>::LOGB];
   const int64_t nw = WINMAX ? (c->n + W - 1) / W : 0;
   // output blocks per CTA: enough CTAs for every SM several times over
   int SC = 8;
-  while (SC > 1 && (int64_t)kern->k * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
+  while (SC > 1 && (int64_t)count * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
   const int nchunk = (NB + SC - 1) / SC;
   const int fastwin = (WINMAX && W >= os_warp_span<B, Q>()) ? 1 : 0;  // a warp's outputs span <= 2 windows
   auto fn = k_os<B, Q, WINMAX>;
   RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<B>()));
-  int64_t done = 0;
-  while (done < kern->k) {
-    const int cnt = (int)std::min<int64_t>(65535, kern->k - done);
+  for (int done = 0; done < count; done += 65535) {
+    const int cnt = std::min(65535, count - done);
     dim3 grid((unsigned)nchunk, (unsigned)cnt);
-    fn<<<grid, B / 16, os_smem<B>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>() + done,
-                                          kern->os_parts_d.as<int>() + done, kern->lag0_d.as<int>() + done, tw, c->n,
-                                          NQ, NB, SC, z_out ? z_out + done * c->n : nullptr,
-                                          keys ? keys + done * nw : nullptr, W, nw, fastwin);
+    fn<<<grid, B / 16, os_smem<B>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>(),
+                                          kern->os_parts_d.as<int>(), kern->lag0_d.as<int>(), bk.idx_d.as<int>(), done,
+                                          tw, c->n, NQ, NB, SC, z_out, keys, W, nw, fastwin);
     RF_LAUNCHED();
-    done += cnt;
   }
 }
 
@@ -466,6 +466,114 @@ void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int bloc
   *Lp_out = bL;
 }
 
+static void check_layout(const rf_ctx* c, int B, int Lp) {
+  RF_REQUIRE(B >= 512 && B <= 16384 && (B & (B - 1)) == 0 && B <= c->n, "overlap-save block %d invalid for n=%lld", B,
+             (long long)c->n);
+  RF_REQUIRE(Lp == B / 2 || Lp == B / 4 || Lp == B / 8, "overlap-save partition length %d must be B/2, B/4 or B/8",
+             Lp);
+}
+
+void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts, const int32_t* Bs,
+                        const int32_t* Lps, cudaStream_t s) {
+  RF_REQUIRE(kern->dtype == RF_F32, "overlap-save needs the FP32 grid");
+  RF_REQUIRE(nb >= 1 && nb <= 8, "between 1 and 8 layout buckets");
+  RF_REQUIRE(cuts[0] == 0, "the first bucket starts at length 0");
+  for (int b = 0; b < nb; ++b) {
+    check_layout(c, Bs[b], Lps[b]);
+    RF_REQUIRE(b == 0 || cuts[b] > cuts[b - 1], "bucket cuts must increase");
+  }
+  if (kern->os_ready && (int)kern->os_buckets.size() == nb) {
+    bool same = true;
+    for (int b = 0; b < nb; ++b) {
+      const OsBucket& o = kern->os_buckets[b];
+      same = same && o.cut_lo == cuts[b] && o.B == Bs[b] && o.Lp == Lps[b];
+    }
+    if (same) return;
+  }
+  const int k = kern->k;
+  std::vector<OsBucket> bk(nb);
+  for (int b = 0; b < nb; ++b) {
+    bk[b].cut_lo = cuts[b];
+    bk[b].B = Bs[b];
+    bk[b].Lp = Lps[b];
+  }
+  std::vector<int> bucket_of(k);
+  for (int j = 0; j < k; ++j) {
+    int b = nb - 1;
+    while (b > 0 && kern->len[j] < cuts[b]) --b;
+    bucket_of[j] = b;
+    bk[b].idx.push_back(j);
+  }
+  // spectra bucket after bucket, kernels in index order inside a bucket
+  std::vector<int> parts(k);
+  std::vector<int64_t> off(k, 0);
+  int64_t total = 0;
+  for (int b = 0; b < nb; ++b)
+    for (const int j : bk[b].idx) {
+      parts[j] = std::max(1, (kern->len[j] + bk[b].Lp - 1) / bk[b].Lp);
+      off[j] = total;
+      total += (int64_t)parts[j] * bk[b].B;
+    }
+  kern->os_ready = false;
+  kern->os_spec.ensure(std::max<size_t>(16, sizeof(float2) * (size_t)total));
+  kern->os_off_d.ensure(std::max<size_t>(16, sizeof(int64_t) * k));
+  kern->os_parts_d.ensure(std::max<size_t>(16, sizeof(int) * k));
+  if (k) {
+    RF_CUDA(cudaMemcpyAsync(kern->os_off_d.p, off.data(), sizeof(int64_t) * k, cudaMemcpyHostToDevice, s));
+    RF_CUDA(cudaMemcpyAsync(kern->os_parts_d.p, parts.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  }
+  for (int b = 0; b < nb; ++b) {
+    OsBucket& o = bk[b];
+    o.idx_d.ensure(std::max<size_t>(16, sizeof(int32_t) * o.idx.size()));
+    if (!o.idx.empty())
+      RF_CUDA(cudaMemcpyAsync(o.idx_d.p, o.idx.data(), sizeof(int32_t) * o.idx.size(), cudaMemcpyHostToDevice, s));
+    // partition rows (kernel, partition) of this bucket, contiguous in os_spec
+    std::vector<int> gj, gp;
+    for (const int j : o.idx)
+      for (int p = 0; p < parts[j]; ++p) {
+        gj.push_back(j);
+        gp.push_back(p);
+      }
+    const int G = (int)gj.size();
+    if (!G) continue;
+    const int B = o.B, Lp = o.Lp;
+    DevBuf gjd, gpd, rows;
+    gjd.ensure(sizeof(int) * G);
+    gpd.ensure(sizeof(int) * G);
+    RF_CUDA(cudaMemcpyAsync(gjd.p, gj.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s));
+    RF_CUDA(cudaMemcpyAsync(gpd.p, gp.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s));
+    float2* dst = kern->os_spec.as<float2>() + off[o.idx[0]];
+    // FP64 transforms of the partitions, a bounded number of rows at a time
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)256 << 20) / (3LL * B * 16)));
+    rows.ensure((size_t)3 * chunk * B * sizeof(double2));
+    double2* in = rows.as<double2>();
+    double2* out = in + (int64_t)chunk * B;
+    double2* tmp = out + (int64_t)chunk * B;
+    for (int g0 = 0; g0 < G; g0 += chunk) {
+      const int cnt = std::min(chunk, G - g0);
+      dim3 grid((unsigned)((B + 255) / 256), (unsigned)cnt);
+      k_os_fill<<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(), kern->len_d.as<int>(),
+                                     gjd.as<int>() + g0, gpd.as<int>() + g0, B, Lp, in);
+      RF_LAUNCHED();
+      fft_c2c_f64(in, out, tmp, B, cnt, -1, c->tw64.as<double2>(), c->n, s);
+      const int64_t count = (int64_t)cnt * B;
+      k_os_round<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, count, 1.0 / (double)B,
+                                                                  dst + (int64_t)g0 * B);
+      RF_LAUNCHED();
+    }
+    RF_CUDA(cudaStreamSynchronize(s));  // the row buffers are released at the end of the iteration
+  }
+  RF_CUDA(cudaStreamSynchronize(s));
+  kern->os_parts = parts;
+  kern->os_off = off;
+  kern->os_buckets = std::move(bk);
+  kern->os_B = Bs[0];
+  kern->os_Lp = Lps[0];
+  kern->os_ready = true;
+  static unsigned long long version = 0;
+  kern->os_version = ++version;
+}
+
 void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s) {
   RF_REQUIRE(kern->dtype == RF_F32, "overlap-save needs the FP32 grid");
   RF_REQUIRE(B == 0 || (B >= 512 && B <= 16384 && (B & (B - 1)) == 0 && B <= c->n),
@@ -474,61 +582,8 @@ void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s) {
     RF_REQUIRE(Lp == 0, "a partition length needs a block size");
     os_choose_layout(c, kern->len, B, &B, &Lp);
   }
-  RF_REQUIRE(Lp == B / 2 || Lp == B / 4 || Lp == B / 8, "overlap-save partition length %d must be B/2, B/4 or B/8", Lp);
-  if (kern->os_ready && kern->os_B == B && kern->os_Lp == Lp) return;
-  const int k = kern->k;
-  std::vector<int> parts(k);
-  std::vector<int64_t> off(k + 1, 0);
-  std::vector<int> gj, gp;
-  for (int j = 0; j < k; ++j) {
-    parts[j] = std::max(1, (kern->len[j] + Lp - 1) / Lp);
-    off[j + 1] = off[j] + (int64_t)parts[j] * B;
-    for (int p = 0; p < parts[j]; ++p) {
-      gj.push_back(j);
-      gp.push_back(p);
-    }
-  }
-  const int G = (int)gj.size();
-  kern->os_ready = false;
-  kern->os_spec.ensure(std::max<size_t>(16, sizeof(float2) * (size_t)off[k]));
-  kern->os_off_d.ensure(sizeof(int64_t) * (k + 1));
-  kern->os_parts_d.ensure(std::max<size_t>(16, sizeof(int) * k));
-  if (k) {
-    RF_CUDA(cudaMemcpyAsync(kern->os_off_d.p, off.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, s));
-    RF_CUDA(cudaMemcpyAsync(kern->os_parts_d.p, parts.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s));
-  }
-  DevBuf gjd, gpd, rows;
-  gjd.ensure(std::max<size_t>(16, sizeof(int) * G));
-  gpd.ensure(std::max<size_t>(16, sizeof(int) * G));
-  if (G) {
-    RF_CUDA(cudaMemcpyAsync(gjd.p, gj.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s));
-    RF_CUDA(cudaMemcpyAsync(gpd.p, gp.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s));
-  }
-  // FP64 transforms of the partitions, a bounded number of rows at a time
-  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)256 << 20) / (3LL * B * 16)));
-  rows.ensure((size_t)3 * chunk * B * sizeof(double2));
-  double2* in = rows.as<double2>();
-  double2* out = in + (int64_t)chunk * B;
-  double2* tmp = out + (int64_t)chunk * B;
-  for (int g0 = 0; g0 < G; g0 += chunk) {
-    const int cnt = std::min(chunk, G - g0);
-    dim3 grid((unsigned)((B + 255) / 256), (unsigned)cnt);
-    k_os_fill<<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(), kern->len_d.as<int>(),
-                                   gjd.as<int>() + g0, gpd.as<int>() + g0, B, Lp, in);
-    RF_LAUNCHED();
-    fft_c2c_f64(in, out, tmp, B, cnt, -1, c->tw64.as<double2>(), c->n, s);
-    const int64_t count = (int64_t)cnt * B;
-    k_os_round<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, count, 1.0 / (double)B,
-                                                                kern->os_spec.as<float2>() + (int64_t)g0 * B);
-    RF_LAUNCHED();
-  }
-  RF_CUDA(cudaStreamSynchronize(s));  // the row buffers are released on return
-  kern->os_parts = parts;
-  kern->os_B = B;
-  kern->os_Lp = Lp;
-  kern->os_ready = true;
-  static unsigned long long version = 0;
-  kern->os_version = ++version;
+  const int32_t cut = 0;
+  os_prepare_buckets(c, kern, 1, &cut, &B, &Lp, s);
 }
 
 // Segment spectra (Q n complex64 for partition ratio Q = B / Lp) plus packed window keys.
@@ -541,22 +596,27 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
                     int32_t* argmax_out, cudaStream_t s) {
   if (kern->k == 0) return;
   if (!kern->os_ready) os_prepare(c, kern, 0, 0, s);
-  const int B = kern->os_B, Lp = kern->os_Lp, Q = B / Lp;
+  int Qmax = 2;
+  for (const OsBucket& bk : kern->os_buckets) Qmax = std::max(Qmax, bk.B / bk.Lp);
   const bool win = max_out != nullptr;
-  const size_t need = os_workspace_bytes(c, kern->k, win ? W : 0, Q);
+  const size_t need = os_workspace_bytes(c, kern->k, win ? W : 0, Qmax);
   c->scratch.ensure(need);
   float2* Zs = c->scratch.as<float2>();
-  unsigned long long* keys = reinterpret_cast<unsigned long long*>(Zs + (int64_t)Q * c->n);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(Zs + (int64_t)Qmax * c->n);
   const int64_t nw = win ? (c->n + W - 1) / W : 0;
   if (win) RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)kern->k * nw, s));
-  dispatch_bq(B, Q, [&](auto bc, auto qc) {
-    constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
-    launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), Lp, Zs, s);
-    if (win)
-      launch_os<BB, QQ, true>(c, kern, Zs, nullptr, keys, W, s);
-    else
-      launch_os<BB, QQ, false>(c, kern, Zs, static_cast<float2*>(z_out), nullptr, 0, s);
-  });
+  // one segment transform and one launch per layout bucket (stream order keeps Zs consistent)
+  for (const OsBucket& bk : kern->os_buckets) {
+    if (bk.idx.empty()) continue;
+    dispatch_bq(bk.B, bk.B / bk.Lp, [&](auto bc, auto qc) {
+      constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
+      launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), bk.Lp, Zs, s);
+      if (win)
+        launch_os<BB, QQ, true>(c, kern, bk, Zs, nullptr, keys, W, s);
+      else
+        launch_os<BB, QQ, false>(c, kern, bk, Zs, static_cast<float2*>(z_out), nullptr, 0, s);
+    });
+  }
   if (win) {
     const int64_t count = (int64_t)kern->k * nw;
     k_unpack_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
@@ -566,29 +626,34 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
 
 void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
                          float* max_out, int32_t* argmax_out, cudaStream_t s) {
-  // one layout for the whole batch (the first prepared kernel set decides)
-  int B = 0, Lp = 0;
-  for (int g = 0; g < G && !B; ++g)
-    if (ks[g]->os_ready) {
-      B = ks[g]->os_B;
-      Lp = ks[g]->os_Lp;
+  // one bucket configuration for the whole batch: the first prepared kernel set decides,
+  // else the modelled single layout over all kernel lengths
+  const rf_kernels* lead = nullptr;
+  for (int g = 0; g < G && !lead; ++g)
+    if (ks[g]->os_ready) lead = ks[g];
+  std::vector<int32_t> cuts, Bs, Lps;
+  if (lead) {
+    for (const OsBucket& b : lead->os_buckets) {
+      cuts.push_back(b.cut_lo);
+      Bs.push_back(b.B);
+      Lps.push_back(b.Lp);
     }
-  if (!B) {
+  } else {
     std::vector<int> all;
     for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
+    int B = 0, Lp = 0;
     os_choose_layout(c, all, 0, &B, &Lp);
+    cuts.push_back(0);
+    Bs.push_back(B);
+    Lps.push_back(Lp);
   }
-  for (int g = 0; g < G; ++g)
-    if (!ks[g]->os_ready || ks[g]->os_B != B || ks[g]->os_Lp != Lp) os_prepare(c, ks[g], B, Lp, s);
-  const int Q = B / Lp;
+  const int nb = (int)cuts.size();
+  for (int g = 0; g < G; ++g) os_prepare_buckets(c, ks[g], nb, cuts.data(), Bs.data(), Lps.data(), s);
   const int64_t n = c->n;
-  const int NQ = (int)(n / Lp);
-  const int NB = (int)((n + (B - Lp) - 1) / (B - Lp));
   const int64_t nw = (n + W - 1) / W;
-  // plan key: layout, window, references and kernel sets with their spectra versions
+  // plan key: window, references and kernel sets with their spectra versions (which change
+  // whenever a layout changes)
   std::vector<unsigned long long> key;
-  key.push_back((unsigned long long)B);
-  key.push_back((unsigned long long)Lp);
   key.push_back((unsigned long long)W);
   for (int g = 0; g < G; ++g) {
     key.push_back((unsigned long long)(uintptr_t)z_refs[g]);
@@ -597,62 +662,74 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   }
   int64_t rows = 0;
   for (int g = 0; g < G; ++g) rows += ks[g]->k;
+  size_t zs_need = 16;
+  for (int b = 0; b < nb; ++b) zs_need = std::max(zs_need, sizeof(float2) * (size_t)G * (size_t)(n / Lps[b]) * Bs[b]);
   if (key != c->batch_key) {
+    // work items bucket after bucket (the reference's segment spectra of that bucket's layout)
     std::vector<OsItem> items;
     items.reserve((size_t)rows);
-    c->batch_zs.ensure(sizeof(float2) * (size_t)G * NQ * B);
+    c->batch_zs.ensure(zs_need);
     const float2* zs_all = c->batch_zs.as<float2>();
-    int64_t row = 0;
-    for (int g = 0; g < G; ++g) {
-      const rf_kernels* k = ks[g];
-      int64_t off = 0;
-      for (int j = 0; j < k->k; ++j) {
-        items.push_back(OsItem{k->os_spec.as<float2>() + off, zs_all + (int64_t)g * NQ * B, k->os_parts[j],
-                               k->lag0[j], (long long)row++});
-        off += (int64_t)k->os_parts[j] * B;
+    c->batch_lay_off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+      const int64_t zstride = (n / Lps[b]) * Bs[b];
+      int64_t row0 = 0;
+      for (int g = 0; g < G; ++g) {
+        const rf_kernels* k = ks[g];
+        for (const int j : k->os_buckets[b].idx)
+          items.push_back(OsItem{k->os_spec.as<float2>() + k->os_off[j], zs_all + (int64_t)g * zstride,
+                                 k->os_parts[j], k->lag0[j], (long long)(row0 + j)});
+        row0 += k->k;
       }
+      c->batch_lay_off[b + 1] = (int64_t)items.size();
     }
     std::vector<const float2*> zp(G);
     for (int g = 0; g < G; ++g) zp[g] = static_cast<const float2*>(z_refs[g]);
     c->batch_key.clear();
     c->batch_items.ensure(std::max<size_t>(16, sizeof(OsItem) * items.size()));
     c->batch_zptr.ensure(sizeof(const float2*) * G);
-    c->batch_keys.ensure(sizeof(unsigned long long) * ((size_t)rows * nw + 1));
+    c->batch_keys.ensure(sizeof(unsigned long long) * ((size_t)rows * nw + nb));
     if (!items.empty())
       RF_CUDA(cudaMemcpy(c->batch_items.p, items.data(), sizeof(OsItem) * items.size(), cudaMemcpyHostToDevice));
     RF_CUDA(cudaMemcpy(c->batch_zptr.p, zp.data(), sizeof(const float2*) * G, cudaMemcpyHostToDevice));
     c->batch_key = key;
-    c->batch_B = B;
     c->batch_rows = rows;
     c->batch_nw = nw;
   }
   if (!rows) return;
   unsigned long long* keys = c->batch_keys.as<unsigned long long>();
-  unsigned long long* counter = keys + rows * nw;
-  RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * ((size_t)rows * nw + 1), s));
-  int SC = 8;
-  while (SC > 1 && rows * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
-  const int nchunk = (NB + SC - 1) / SC;
-  const int64_t units = rows * nchunk;
-  dispatch_bq(B, Q, [&](auto bc, auto qc) {
-    constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
-    const int fastwin = (W >= os_warp_span<BB, QQ>()) ? 1 : 0;  // a warp's outputs span <= 2 windows
-    const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<BB>::LOGB];
-    auto seg = k_os_segments_batched<BB>;
-    RF_CUDA(cudaFuncSetAttribute(seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
-    RF_REQUIRE(G <= 65535, "at most 65535 references per batch");
-    seg<<<dim3((unsigned)NQ, (unsigned)G), BB / 16, os_smem<BB>(), s>>>(c->batch_zptr.as<const float2*>(), n, Lp, tw,
-                                                                       c->batch_zs.as<float2>());
-    RF_LAUNCHED();
-    auto fn = k_os_batched<BB, QQ>;
-    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
-    int per_sm = 0;
-    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BB / 16, os_smem<BB>()));
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * c->nsm, units));
-    fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>(), units, nchunk, tw, n, NQ, NB,
-                                                      SC, keys, W, nw, fastwin, counter);
-    RF_LAUNCHED();
-  });
+  RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * ((size_t)rows * nw + nb), s));
+  RF_REQUIRE(G <= 65535, "at most 65535 references per batch");
+  for (int b = 0; b < nb; ++b) {
+    const int64_t first = c->batch_lay_off[b], cnt = c->batch_lay_off[b + 1] - first;
+    if (!cnt) continue;
+    const int B = Bs[b], Lp = Lps[b];
+    const int NQ = (int)(n / Lp);
+    const int NB = (int)((n + (B - Lp) - 1) / (B - Lp));
+    int SC = 8;
+    while (SC > 1 && cnt * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
+    const int nchunk = (NB + SC - 1) / SC;
+    const int64_t units = cnt * nchunk;
+    unsigned long long* counter = keys + rows * nw + b;
+    dispatch_bq(B, B / Lp, [&](auto bc, auto qc) {
+      constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
+      const int fastwin = (W >= os_warp_span<BB, QQ>()) ? 1 : 0;  // a warp's outputs span <= 2 windows
+      const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<BB>::LOGB];
+      auto seg = k_os_segments_batched<BB>;
+      RF_CUDA(cudaFuncSetAttribute(seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
+      seg<<<dim3((unsigned)NQ, (unsigned)G), BB / 16, os_smem<BB>(), s>>>(c->batch_zptr.as<const float2*>(), n, Lp,
+                                                                         tw, c->batch_zs.as<float2>());
+      RF_LAUNCHED();
+      auto fn = k_os_batched<BB, QQ>;
+      RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
+      int per_sm = 0;
+      RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BB / 16, os_smem<BB>()));
+      const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * c->nsm, units));
+      fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>() + first, units, nchunk, tw, n,
+                                                        NQ, NB, SC, keys, W, nw, fastwin, counter);
+      RF_LAUNCHED();
+    });
+  }
   const int64_t count = rows * nw;
   k_unpack_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
   RF_LAUNCHED();

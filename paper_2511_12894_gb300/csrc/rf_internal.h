@@ -107,9 +107,18 @@ struct rf_ctx {
   // segment spectra of every reference and packed window keys, kept while the same
   // references and kernel sets come back (so repeated calls allocate and copy nothing).
   std::vector<unsigned long long> batch_key;
-  int batch_B = 0;
+  std::vector<int64_t> batch_lay_off;  // work items of layout bucket b: [off[b], off[b+1])
   int64_t batch_rows = 0, batch_nw = 0;
   rf::DevBuf batch_items, batch_zptr, batch_zs, batch_keys;
+};
+
+// One overlap-save layout bucket of a kernel set: the neighbours whose lengths fall in
+// [cut_lo, next bucket's cut_lo) run with block size B and partitions of Lp taps.
+struct OsBucket {
+  int32_t cut_lo = 0;
+  int B = 0, Lp = 0;
+  std::vector<int32_t> idx;  // neighbour indices, increasing
+  rf::DevBuf idx_d;          // int32 copy of idx
 };
 
 struct rf_kernels {
@@ -123,15 +132,18 @@ struct rf_kernels {
   rf::DevBuf taps;             // packed taps (grid dtype complex)
   rf::DevBuf len_d, lag0_d;    // int32[k]
   rf::DevBuf off_d;            // int64[k+1]
-  // Overlap-save preparation (FP32 only): block size B, partitions P_j = ceil(L_j / (B/2)),
-  // and the partition spectra FFT_B(taps) / B, kernel after kernel.
+  // Overlap-save preparation (FP32 only): one or more layout buckets by kernel length; kernel j
+  // of a bucket with (B, Lp) has P_j = ceil(L_j / Lp) partition spectra FFT_B(taps) / B,
+  // stored bucket after bucket.
   bool os_ready = false;
-  int os_B = 0;
+  int os_B = 0;                       // layout of the first bucket
   int os_Lp = 0;                      // partition length (B/2, B/4 or B/8)
+  std::vector<OsBucket> os_buckets;
   unsigned long long os_version = 0;  // changes whenever the spectra are rebuilt
   std::vector<int32_t> os_parts;
-  rf::DevBuf os_spec;      // float2 [sum_j P_j][B]
-  rf::DevBuf os_off_d;     // int64 [k+1]: element offset of kernel j's first partition spectrum
+  std::vector<int64_t> os_off;
+  rf::DevBuf os_spec;      // float2, sum_j P_j B_j values
+  rf::DevBuf os_off_d;     // int64 [k]: element offset of kernel j's first partition spectrum
   rf::DevBuf os_parts_d;   // int32 [k]
   // Tensor-core direct form: split-BF16 tap operands per group of gemm_NJ neighbours, taps
   // padded to gemm_NCK chunks of gemm_KC (see reconstruct_gemm.cu).
@@ -199,6 +211,10 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
                    cudaStream_t s);
 // B = 0 and/or Lp = 0 take the modelled choice.
 void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s);
+// Several layout buckets: bucket b takes the kernels with cuts[b] <= L < cuts[b + 1]
+// (cuts[0] = 0, increasing) and runs with (Bs[b], Lps[b]).
+void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts, const int32_t* Bs,
+                        const int32_t* Lps, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
 // launches the bounded-wait health check (reconstruct_gemm.cu)
 void wait_selftest(rf_ctx* c, cudaStream_t s);

@@ -347,6 +347,63 @@ def test_reconstruct_os_edge_lengths(torch, os_case, B, Lp):
             _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, W, 8 * TOL["f32"] * Po.max())
 
 
+@pytest.mark.parametrize("cuts,blocks,parts", [([0, 1000], [4096, 16384], [1024, 4096]),
+                                               ([0, 64, 2048, 8192], [1024, 512, 8192, 16384],
+                                                [128, 256, 2048, 8192])])
+def test_reconstruct_os_length_buckets(torch, os_case, cuts, blocks, parts):
+    """A layout per kernel-length bucket (one segment transform and launch per bucket) gives
+    the oracle's direct sums in the original row order, and the same window peaks."""
+    z, lengths, lags, taps, zo = os_case
+    n = _OS_N
+    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype="f32")
+    rf = _rf(cfg)
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    kern.prepare_buckets(cuts, blocks, parts)
+    assert kern.os_buckets() == list(zip(cuts, blocks, parts))
+    zt = torch.tensor(z, device="cuda")
+    out = rf.reconstruct(zt, kern, "os").cpu().numpy()
+    for j, L in enumerate(lengths):
+        if L == 0:
+            assert np.abs(out[j]).max() == 0.0
+            continue
+        assert _relerr(out[j], zo[j]) < TOL["f32"], (cuts, j, L)
+    P, A = rf.reconstruct_winmax(zt, kern, 1000, "os")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    for j, L in enumerate(lengths):
+        if L == 0:
+            continue
+        Po, Ao = reconstruct.window_peaks(zo[j], 1000)
+        assert np.abs(P[j] - Po).max() <= 4 * TOL["f32"] * Po.max()
+        _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, 1000, 8 * TOL["f32"] * Po.max())
+    with pytest.raises(Exception):
+        kern.prepare_buckets([5, 100], [4096, 4096], [1024, 1024])      # first cut must be 0
+    with pytest.raises(Exception):
+        kern.prepare_buckets([0, 100], [4096, 4096], [1024, 3000])      # partition not B/2, B/4, B/8
+
+
+def test_batched_length_buckets_match_per_group(torch):
+    """The persistent batched launch runs one pass per layout bucket and writes the same rows
+    as the per-group bucketed reconstruction."""
+    cfg = _batch_cfg()
+    ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
+    x = torch.tensor(data.strain(cfg), dtype=torch.float32, device="cuda")
+    rf = _rf(cfg)
+    refs = [g[0] for g in cfg.groups]
+    z, _ = rf.mf_reference(x, ip, refs)
+    kerns = [rf.build_ratio_kernels(r, nb, ip, cfg.threshold) for r, nb in cfg.groups]
+    allL = np.concatenate([k.length for k in kerns])
+    cut = int(np.median(allL)) + 1
+    for k in kerns:
+        k.prepare_buckets([0, cut], [4096, 16384], [1024, 4096])
+    W = cfg.window
+    P, A = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W)
+    row = 0
+    for g, k in enumerate(kerns):
+        Pg, Ag = rf.reconstruct_winmax(z[g], k, W, "os")
+        assert torch.equal(P[row:row + k.k], Pg) and torch.equal(A[row:row + k.k], Ag)
+        row += k.k
+
+
 def _cfg2_long(n=1 << 17, k=8, dmax=4.0):
     cfg = workload.config(2, n_override=n, k_override=k)
     ref = cfg.groups[0][0]
@@ -682,12 +739,14 @@ def test_autotune_records_the_fastest_form_and_auto_follows_it(torch):
     zs = [z[g] for g in range(len(refs))]
     table = rf.autotune(zs, kerns, W, allow_split=True, max_os=3)
     assert len(table) >= 3 and all(e["ms"] > 0 for e in table)
-    assert sum(e["algo"] == "os" for e in table) == 3
+    assert sum(e["algo"] == "os" and e["cut"] == 0 for e in table) == 3       # single layouts
+    assert all(e["block2"] and e["part2"] for e in table if e["cut"])          # two-bucket variants
     assert {e["algo"] for e in table} <= {"os", "gemm", "direct"}
     win = table[0]
     assert win["ms"] == min(e["ms"] for e in table)
     if win["algo"] == "os":
-        assert all(k.os_layout() == (win["block"], win["part"]) for k in kerns)
+        want = [(0, win["block"], win["part"])] + ([(win["cut"], win["block2"], win["part2"])] if win["cut"] else [])
+        assert all(k.os_buckets() == want for k in kerns)
     P, A = rf.reconstruct_batched(zs, kerns, W)                       # AUTO -> the tuned form
     P2, A2 = rf.reconstruct_batched(zs, kerns, W, win["algo"], prec=win["prec"])
     assert torch.equal(P, P2) and torch.equal(A, A2)
