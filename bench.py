@@ -57,6 +57,9 @@ def parse():
                     help="skip the autotuner (with --algo auto: the cost-model overlap-save layout)")
     ap.add_argument("--mf", default="filtered", choices=["filtered", "onthefly"],
                     help="reference matched filter from stored filters, or template regenerated every step")
+    ap.add_argument("--buckets", default="",
+                    help="overlap-save layout per kernel-length bucket, 'cut:block:part,...' (first cut 0); "
+                         "skips the autotuner")
     ap.add_argument("--part", type=int, default=0,
                     help="overlap-save partition length: block/2, /4 or /8 (0: library default)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
@@ -247,6 +250,14 @@ def ncu_traffic(kernel: str, layout: str = None):
         return None
 
 
+def workload_label(cfg, config: int, thr: float) -> str:
+    """The workload name both arms print in config.workload."""
+    G = len(cfg.groups)
+    rows = sum(len(nb) for _, nb in cfg.groups)
+    return (f"cfg{config}: {cfg.name}; n=2^{int(math.log2(cfg.n))} fs={cfg.fs:g} f_low={cfg.f_low:g}; "
+            f"{G} ref + {rows} TaylorF2 nbrs; thr={thr:g} rel; W={cfg.window}")
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args):
@@ -264,7 +275,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "template*samples/s", "value": v, "unit": "template*samples/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"cfg{args.config}: {cfg.name}, n={cfg.n}, 1 ref + {len(cfg.groups[0][1])} nbrs",
+            "config": {"workload": workload_label(cfg, args.config,
+                                                  args.threshold if args.threshold is not None else GATE_THRESHOLD),
                        "parallelism": "host"},
             "cpu_baseline": {**cb, "value": v},
             "e2e": {"value": v, "unit": "template*samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -302,6 +314,7 @@ def main():
         from dataclasses import replace as _replace
         cfg = _replace(cfg, groups=tuple(all_groups[g] for g in mine))
     units_total = sum(1 + len(nb) for _, nb in all_groups) * cfg.n
+    full_cfg = workload.config(args.config, k_override=args.kernels)   # the whole workload, for its label
     # relative truncation threshold: the largest of 1e-3, 1e-4, 3e-5 whose window peaks stay
     # within 1e-4 of the loudest SNR against full matched filtering on this workload
     thr = args.threshold if args.threshold is not None else GATE_THRESHOLD
@@ -317,7 +330,12 @@ def main():
     kerns = [rf.build_ratio_kernels(r, nb, ip, thr) for r, nb in cfg.groups]
     filt, sig = rf.reference_filters(ip, refs)
     tune, tune_s = None, 0.0
-    if args.algo == "auto" and not args.no_autotune and args.block == 0 and args.part == 0:
+    if args.buckets:
+        spec = [tuple(int(v) for v in b.split(":")) for b in args.buckets.split(",")]
+        for k in kerns:
+            k.prepare_buckets([c for c, _, _ in spec], [b for _, b, _ in spec], [p for _, _, p in spec])
+        algo_used = "os"
+    elif args.algo == "auto" and not args.no_autotune and args.block == 0 and args.part == 0:
         # the autotuner times candidate forms on a z_ref of this segment (offline, like the kernels)
         t1 = time.perf_counter()
         zt = rf.mf_filtered(x, filt)
@@ -556,8 +574,7 @@ def main():
             "scaling": "strong" if sharded else "weak", "vs_baseline": None,
             "dtype": "f32" if cfg.dtype == "f32" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"cfg{args.config}: {cfg.name}; n=2^{int(math.log2(n))} fs={cfg.fs:g} "
-                                   f"f_low={cfg.f_low:g}; {G} ref + {rows} TaylorF2 nbrs; thr={thr:g} rel; W={W}",
+            "config": {"workload": workload_label(full_cfg, args.config, thr),
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
                        "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf,
