@@ -58,6 +58,21 @@ def snr_series(xf: np.ndarray, h: np.ndarray, inv_psd_band: np.ndarray, n: int, 
     return _fft.ifft_unnormalised(spec), N
 
 
+def snr_at(xf: np.ndarray, h: np.ndarray, inv_psd_band: np.ndarray, n: int, fs: float,
+           idx: np.ndarray) -> np.ndarray:
+    """z[i] of Eq. (2) for the sample indices ``idx`` only, each by the defining sum over the
+    one-sided bins (for segments too long to transform in the oracle)."""
+    df = fs / n
+    N = sigma(h, inv_psd_band, df)
+    w = (4.0 * df / N) * np.asarray(xf) * np.conj(h) * inv_psd_band
+    out = np.empty(len(idx), dtype=np.complex128)
+    for q, i in enumerate(np.asarray(idx, dtype=np.int64)):
+        # exp(2 pi i i k / n) with the product i k reduced modulo n exactly (integers)
+        ph = ((int(i) * np.arange(w.shape[0], dtype=np.int64)) % n).astype(np.float64) * (2.0 * np.pi / n)
+        out[q] = np.sum(w * (np.cos(ph) + 1j * np.sin(ph)))
+    return out
+
+
 def matched_filter(x: np.ndarray, inv_psd: np.ndarray, n: int, fs: float, f_low: float, f_high: float,
                    m1: float, m2: float, pn_order: int, tc: float = 0.0, phic: float = 0.0):
     """Full matched filter of real data x with one template: (z, N)."""

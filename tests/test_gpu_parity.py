@@ -465,8 +465,11 @@ def test_full_size_paper_workload_sampled(torch):
     x = data.strain(cfg)
     rf = _rf(cfg)
     ipt = torch.tensor(ip, device="cuda")
-    zg, _ = rf.mf_reference(torch.tensor(x, dtype=torch.float32, device="cuda"), ipt, [ref])
+    # as the benchmark runs it: stored reference filter, autotuned layout, AUTO reconstruction
+    filt, _ = rf.reference_filters(ipt, [ref])
+    zg = rf.mf_filtered(torch.tensor(x, dtype=torch.float32, device="cuda"), filt)
     kern = rf.build_ratio_kernels(ref, nb, ipt, cfg.threshold)
+    rf.autotune([zg[0]], [kern], cfg.window, allow_split=True)
     P, A = rf.reconstruct_winmax(zg[0], kern, cfg.window, "auto")
     P, A = P.cpu().numpy(), A.cpu().numpy()
     zo_ref, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
@@ -492,6 +495,50 @@ def test_full_size_paper_workload_sampled(torch):
     for inj in cfg.injections:
         w = inj.sample // cfg.window
         assert abs(int(A[inj.template_index, w]) - inj.sample) <= 1
+
+
+def test_long_segment_2p23_sampled(torch):
+    """The long-duration workload's segment (n = 2^23, f_low = 5 Hz) for one reference and two
+    neighbours 40-120 s away in duration (kernels of tens of thousands of taps): z_ref on sampled indices by the defining sum of
+    Eq. 2, and the reconstructed window peaks at sampled windows by the defining sum of Eq. 8
+    over the library's own z_ref and taps."""
+    base = workload.config(5, k_override=2)
+    ref = base.groups[0][0]
+    nb = workload.duration_lattice(ref, base.f_low, 2, 40.0, 120.0, np.random.default_rng(55), n_eta=1,
+                                   eta_range=(0.24, 0.25), mrange=(2.0, 3.0))
+    cfg = replace(base, groups=((ref, nb),) + base.groups[1:])
+    n, fs, W = cfg.n, cfg.fs, cfg.window
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    rf = _rf(cfg)
+    ipt = torch.tensor(ip, device="cuda")
+    filt, _ = rf.reference_filters(ipt, [ref])
+    zg = rf.mf_filtered(torch.tensor(x, dtype=torch.float32, device="cuda"), filt)
+    kern = rf.build_ratio_kernels(ref, nb, ipt, 3e-5)    # the benchmark's relative threshold
+    assert kern.length.max() > 1 << 15                    # many partitions at any layout
+    rf.autotune([zg[0]], [kern], W)
+    P, A = rf.reconstruct_winmax(zg[0], kern, W, "auto")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    z = zg[0].cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(5)
+    # z_ref against Eq. 2 on sampled indices (the data spectrum as constructed)
+    xf = workload.noise_spectrum(cfg, 0) + data.injection_spectrum(cfg, ip)
+    ipb = mf.band_limited_inv_psd(ip, n, fs, cfg.f_low, cfg.f_high)
+    h = mf.template(n, fs, ref.m1, ref.m2, cfg.pn_order)
+    idx = rng.choice(n, 8, replace=False)
+    zs = mf.snr_at(xf, h, ipb, n, fs, idx)
+    assert np.abs(z[idx] - zs).max() <= 4 * TOL["f32"] * np.abs(z).max()
+    # reconstruction against Eq. 8 on sampled windows
+    taps = kern.taps().cpu().numpy().astype(np.complex128)
+    for j in range(kern.k):
+        c = taps[kern.offset[j]:kern.offset[j + 1]]
+        wins = rng.choice(P.shape[1], 6, replace=False)
+        vals = reconstruct.reconstruct_at(z, int(kern.lag0[j]), c, A[j, wins])
+        assert np.abs(P[j, wins] - np.abs(vals) ** 2).max() <= 4 * TOL["f32"] * P[j].max()
+        for w in wins[:2]:
+            ii = w * W + rng.choice(min(W, n - w * W), 16, replace=False)
+            v = np.abs(reconstruct.reconstruct_at(z, int(kern.lag0[j]), c, ii)) ** 2
+            assert np.all(v <= P[j, w] + 4 * TOL["f32"] * P[j].max())
 
 
 # ---------------------------------------------------------------- batched form

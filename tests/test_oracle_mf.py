@@ -75,3 +75,20 @@ def test_sigma_closed_form_flat_psd():
     fb = f[ipb > 0]
     expect = np.sqrt(4 * (fs / n) * np.sum(fb ** (-7 / 3)))
     assert abs(mf.sigma(h, ipb, fs / n) / expect - 1) < 1e-13
+
+
+def test_snr_at_equals_the_series_at_those_samples():
+    """The sampled form of Eq. 2 agrees with the transform-based series (a different route:
+    per-sample sums with exact integer phase reduction against the radix-2 inverse FFT)."""
+    cfg = workload.config(1, n_override=1 << 12, k_override=2)
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    ref = cfg.groups[0][0]
+    n, fs = cfg.n, cfg.fs
+    xf = mf.data_spectrum(x, fs)
+    ipb = mf.band_limited_inv_psd(ip, n, fs, cfg.f_low, cfg.f_high)
+    h = mf.template(n, fs, ref.m1, ref.m2, cfg.pn_order)
+    z, _ = mf.snr_series(xf, h, ipb, n, fs)
+    idx = np.array([0, 1, 17, n // 2, n - 1, 2049])
+    zs = mf.snr_at(xf, h, ipb, n, fs, idx)
+    assert np.abs(zs - z[idx]).max() <= 1e-10 * np.abs(z).max()
