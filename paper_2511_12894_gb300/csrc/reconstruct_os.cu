@@ -160,37 +160,47 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
       // outputs of this thread that exist (all but possibly in the last block)
       const int64_t avail = lim - qbase;
       const int cnt = avail <= 0 ? 0 : (avail >= CH ? CH : (int)avail);
-      // sample index and window of this thread's first output; later outputs step by one
-      // (wrapping at n), so one division per thread suffices
-      int i0 = (int)((base + qbase) & mask);
-      int w0 = i0 / (int)W;
-      int r0 = i0 - w0 * (int)W;
+      // sample index and window of this thread's first output; its outputs i0 + e (wrapping to
+      // 0 at n) lie in window w0 below e_b = min(W - r0, n - i0) and in the next window w1 (w0 + 1,
+      // or 0 after the wrap) from e_b on: at most two windows when W >= CH, which fastwin implies
+      const int i0 = (int)((base + qbase) & mask);
+      const int w0 = i0 / (int)W;
+      const int r0 = i0 - w0 * (int)W;
+      const int to_wrap = (int)n - i0;
+      const int e_b = min((int)W - r0, to_wrap);
+      const int w1 = to_wrap <= (int)W - r0 ? 0 : w0 + 1;
       const int wA = __shfl_sync(0xffffffffu, w0, 0);
       const int wB = (wA + 1 == (int)nw) ? 0 : wA + 1;
-      unsigned long long kA = 0, kB = 0;
-      bool slow = !fastwin;
-      {
-        int i = i0, w = w0, r = r0;
+      // per window the largest |z|^2 and its first position (strict > keeps the first of equals)
+      float b0 = -1.f, b1 = -1.f;
+      int e0 = 0, e1 = 0;
 #pragma unroll
-        for (int e = 0; e < CH; ++e) {
-          const unsigned long long key = e < cnt ? pack_key(mv[e], (unsigned int)i) : 0ull;
-          if (w == wA) kA = max(kA, key);
-          else if (w == wB) kB = max(kB, key);
-          else if (e < cnt) slow = true;
-          ++i;
-          ++r;
-          if (i == (int)n) {
-            i = 0;
-            w = 0;
-            r = 0;
-          } else if (r == (int)W) {
-            ++w;
-            r = 0;
+      for (int e = 0; e < CH; ++e) {
+        const float m = mv[e];
+        if (e < cnt) {
+          if (e < e_b) {
+            if (m > b0) {
+              b0 = m;
+              e0 = e;
+            }
+          } else if (m > b1) {
+            b1 = m;
+            e1 = e;
           }
         }
       }
+      unsigned long long kA = 0, kB = 0;
+      bool slow = !fastwin;
+      auto put = [&](int w, unsigned long long k) {
+        if (w == wA) kA = max(kA, k);
+        else if (w == wB) kB = max(kB, k);
+        else slow = true;
+      };
+      if (b0 >= 0.f) put(w0, pack_key(b0, (unsigned int)(i0 + e0)));
+      if (b1 >= 0.f) put(w1, pack_key(b1, (unsigned int)(i0 + e1 >= (int)n ? i0 + e1 - (int)n : i0 + e1)));
       const bool any_slow = __any_sync(0xffffffffu, slow);
       if (any_slow) {
+        // per output, stepping the index and window by one (wrapping at n)
         int i = i0, w = w0, r = r0;
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
