@@ -14,8 +14,8 @@
 //
 // Twiddles come from per-stage tables laid out in thread order: the stage with
 // radix R and Ns has a table of R*Ns entries, entry t*Ns + k = exp(-2 pi i t k / (R Ns)),
-// so the loads of a warp are contiguous.  A last stage of radix 2 or 4 reads only the
-// t = 1 row and forms the other powers by complex products.  The tables of the middle stages and of the
+// so the loads of a warp are contiguous.  A stage reads the rows t = 1, 2, 4 and 8 and forms
+// the other powers by complex products (a last stage of radix 2 or 4 reads only row 1).  The tables of the middle stages and of the
 // last stage follow each other; a block size B needs block_table_size<B>() entries
 // (built on the host by block_fft_tables).
 #pragma once
@@ -25,6 +25,30 @@
 namespace rf {
 
 __device__ __forceinline__ int bf_pad(int p) { return p + (p >> 4); }
+
+// Multiplies a[t], 0 < t < R (R = 8 or 16), by w^t (conjugated for SIGN = +1) where w^t is
+// table entry t * stride: the entries t = 1, 2, 4 and 8 are loaded and the others formed by
+// at most two complex products of loaded entries (about 3 ulp), which takes 11 of the 15
+// table loads of a radix-16 stage off the load/store pipe.
+template <int R, int SIGN>
+__device__ __forceinline__ void apply_stage_twiddles(float2* a, const float2* __restrict__ tw, int stride) {
+  static_assert(R == 8 || R == 16, "radix");
+  float2 w[R];
+  w[1] = __ldg(tw + stride);
+  w[2] = __ldg(tw + 2 * stride);
+  w[4] = __ldg(tw + 4 * stride);
+  w[3] = cmul(w[2], w[1]);
+  w[5] = cmul(w[4], w[1]);
+  w[6] = cmul(w[4], w[2]);
+  w[7] = cmul(w[4], w[3]);
+  if constexpr (R == 16) {
+    w[8] = __ldg(tw + 8 * stride);
+#pragma unroll
+    for (int t = 9; t < 16; ++t) w[t] = cmul(w[8], w[t - 8]);
+  }
+#pragma unroll
+  for (int t = 1; t < R; ++t) a[t] = tw_apply<SIGN>(a[t], w[t]);
+}
 
 template <int B>
 struct BlockFFTShape {
@@ -86,9 +110,7 @@ __device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const flo
     }
     __syncthreads();
     const int k = tid & (Ns - 1);
-    const float2* twk = tw + k;
-#pragma unroll
-    for (int t = 1; t < 16; ++t) v[t] = tw_apply<SIGN>(v[t], __ldg(twk + t * Ns));
+    apply_stage_twiddles<16, SIGN>(v, tw + k, Ns);
     dft<16, SIGN>(v);
     {
       float2* o = sm + bf_pad((tid - k) * 16 + k);
@@ -121,9 +143,7 @@ __device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const flo
         a[3] = tw_apply<SIGN>(a[3], cmul(w2, w1));
       }
     } else {
-      const float2* twb = tw + b;
-#pragma unroll
-      for (int t = 1; t < RL; ++t) a[t] = tw_apply<SIGN>(a[t], __ldg(twb + t * (B / RL)));
+      apply_stage_twiddles<RL, SIGN>(a, tw + b, B / RL);
     }
     dft<RL, SIGN>(a);
 #pragma unroll
