@@ -57,3 +57,31 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rf_kernels_copy_taps(None, None, None) == RF_EINVAL
     lib.rf_destroy(None)
     lib.rf_kernels_free(None)
+
+
+def test_null_context_and_handles_are_rejected_by_every_entry_point(lib):
+    """Every call that takes a context or a kernel set refuses NULL with RF_EINVAL before any
+    device work (host validation; no GPU needed)."""
+    from paper_2511_12894_gb300 import RF_EINVAL
+    i32 = ctypes.c_int32
+    vp = ctypes.c_void_p
+    cuts = (i32 * 1)(0)
+    assert lib.rf_reserve(None, 4, None) == RF_EINVAL
+    assert lib.rf_template_fd(None, None, None, None) == RF_EINVAL
+    assert lib.rf_mf_reference(None, None, None, 1, None, None, None, None) == RF_EINVAL
+    assert lib.rf_reference_filters(None, None, 1, None, None, None, None) == RF_EINVAL
+    assert lib.rf_mf_filtered(None, None, 1, None, None, None) == RF_EINVAL
+    assert lib.rf_build_ratio_kernels(None, None, None, 0, None, 1e-3, 1, None, None) == RF_EINVAL
+    assert lib.rf_kernels_prepare(None, None, 0, 0, None) == RF_EINVAL
+    assert lib.rf_kernels_prepare_buckets(None, None, 1, cuts, cuts, cuts, None) == RF_EINVAL
+    assert lib.rf_kernels_os_layout(None, None, None) == RF_EINVAL
+    assert lib.rf_kernels_os_buckets(None, 1, None, None, None, None) == RF_EINVAL
+    assert lib.rf_reconstruct(None, None, None, 0, 0, None, None) == RF_EINVAL
+    assert lib.rf_reconstruct_winmax(None, None, None, 0, 0, 16, None, None, None) == RF_EINVAL
+    zs = (vp * 1)(None)
+    assert lib.rf_reconstruct_batched(None, 1, zs, zs, 0, 0, 16, None, None, None) == RF_EINVAL
+    assert lib.rf_autotune(None, 1, zs, zs, 16, 0, 4, None, 0, None, None) == RF_EINVAL
+    assert lib.rf_winmax(None, None, 1, 16, None, None, None) == RF_EINVAL
+    assert lib.rf_device_status(None) == RF_EINVAL
+    assert lib.rf_selftest_bounded_wait(None, None) == RF_EINVAL
+    assert b"NULL" in lib.rf_last_error() or len(lib.rf_last_error()) > 0
