@@ -21,6 +21,14 @@ Sec. II.B-II.D and App. A.
   circular arc [m0, m0 + L) that covers every above-threshold lag (sub-threshold
   lags inside it are kept); ties go to the arc whose start, mapped to
   (-n/2, n/2], is smallest.
+* Sec. II.D, build grid: the kernels may be built on a coarser frequency grid
+  f_k = k fs / n_b (n_b a power of two <= n) as long as 1/df of that grid exceeds
+  the kernel's duration; rho is then the n_b-point inverse transform (the same
+  (1/n_b) normalisation, so both approximate dt r(t)) and lags are signed on the
+  n_b circle.  The rule (a reading: the paper asks only for a grid longer than
+  the duration difference) takes the smallest power of two of at least four
+  times the lag extent between the window edges' time offsets (Eq. A2) plus the
+  low taper's spread 4 fs / df_low.  N_ref / N stays on the data grid.
 """
 from __future__ import annotations
 
@@ -61,24 +69,44 @@ def df_low_rule(ref, tgt, pn_order: int, f_low: float, df_low_max: float) -> flo
 
 def kernel_spectrum(ref, tgt, n: int, fs: float, f_low: float, f_high: float, pn_order: int,
                     inv_psd: np.ndarray, df_low_max: float = 5.0, df_high: float = 53.0,
-                    df_low: float = None) -> Tuple[np.ndarray, float]:
-    """K~_k, k = 0..n/2 (Eq. 7 with the Eq. 9 window); returns (K~, df_low)."""
+                    df_low: float = None, n_build: int = None) -> Tuple[np.ndarray, float]:
+    """K~_k, k = 0..n_b/2 (Eq. 7 with the Eq. 9 window) on the build grid f_k = k fs / n_b
+    (n_b = n_build, default n); N_ref / N (Eq. 3) on the data grid of n samples.  Returns
+    (K~, df_low)."""
+    nb = n if n_build is None else n_build
     f = freqs(n, fs)
     if df_low is None:
         df_low = df_low_rule(ref, tgt, pn_order, f_low, df_low_max)
-    w = window(f, f_low, f_high, df_low, df_high)
-    sup = w > 0
     ipb = band_limited_inv_psd(inv_psd, n, fs, f_low, f_high)
     df = fs / n
     h_ref = taylorf2.template_fd(f, ref.m1, ref.m2, pn_order, ref.tc, ref.phic)
     h_tgt = taylorf2.template_fd(f, tgt.m1, tgt.m2, pn_order, tgt.tc, tgt.phic)
     norm = sigma(h_ref, ipb, df) / sigma(h_tgt, ipb, df)            # N_ref / N
-    dpsi = taylorf2.phase(f[sup], tgt.m1, tgt.m2, pn_order, tgt.tc, tgt.phic) - \
-        taylorf2.phase(f[sup], ref.m1, ref.m2, pn_order, ref.tc, ref.phic)
-    R = taylorf2.amplitude(f[sup]) / taylorf2.amplitude(f[sup])     # B / B_ref (same law)
-    K = np.zeros(n // 2 + 1, dtype=np.complex128)
+    fb = freqs(nb, fs)
+    w = window(fb, f_low, f_high, df_low, df_high)
+    sup = w > 0
+    dpsi = taylorf2.phase(fb[sup], tgt.m1, tgt.m2, pn_order, tgt.tc, tgt.phic) - \
+        taylorf2.phase(fb[sup], ref.m1, ref.m2, pn_order, ref.tc, ref.phic)
+    R = taylorf2.amplitude(fb[sup]) / taylorf2.amplitude(fb[sup])   # B / B_ref (same law)
+    K = np.zeros(nb // 2 + 1, dtype=np.complex128)
     K[sup] = norm * R * w[sup] * np.exp(1j * dpsi)
     return K, df_low
+
+
+def build_grid_rule(ref, tgt, n: int, fs: float, f_low: float, f_high: float, pn_order: int,
+                    df_low: float, df_high: float = 53.0) -> int:
+    """Build grid of a kernel (Sec. II.D: 1/df of the build grid must exceed the duration
+    difference).  The kernel lives between the lags of the time offsets at the window edges,
+    dt(f) = (Psi_tgt'(f) - Psi_ref'(f)) / (2 pi) (Eq. A2) at f_low - df_low and
+    f_high + df_high, widened by the taper's spread 4 fs / df_low; the grid is the smallest
+    power of two of at least four times that extent, capped at n."""
+    fe = np.array([f_low - df_low, f_high + df_high])
+    d = (taylorf2.dphase(fe, tgt.m1, tgt.m2, pn_order) - taylorf2.dphase(fe, ref.m1, ref.m2, pn_order)) / (2 * math.pi)
+    extent = float(np.abs(d).max()) * fs + 4.0 * fs / df_low
+    nb = 16
+    while nb < 4.0 * extent and nb < n:
+        nb *= 2
+    return min(nb, n)
 
 
 def kernel_full(K: np.ndarray, n: int) -> np.ndarray:
@@ -136,6 +164,7 @@ class PackedKernels:
     offset: np.ndarray    # int64 [K+1]
     taps: np.ndarray      # complex128 [offset[-1]]
     df_low: np.ndarray    # float64 [K]
+    grid: np.ndarray = None  # int64 [K] build grid (lags are signed on it)
 
     def kernel(self, j: int) -> Tuple[int, np.ndarray]:
         return int(self.lag0[j]), self.taps[self.offset[j]:self.offset[j + 1]]
@@ -143,20 +172,29 @@ class PackedKernels:
 
 def build_ratio_kernels(ref, targets: Sequence, n: int, fs: float, f_low: float, f_high: float,
                         pn_order: int, inv_psd: np.ndarray, thr: float, relative: bool = True,
-                        df_low_max: float = 5.0, df_high: float = 53.0) -> PackedKernels:
-    """Kernel spectrum -> full kernel -> threshold truncation, per target."""
+                        df_low_max: float = 5.0, df_high: float = 53.0, n_build: int = 0) -> PackedKernels:
+    """Kernel spectrum -> full kernel -> threshold truncation, per target.
+
+    n_build: 0 builds on the data grid (n lags); a power of two builds every kernel on that
+    grid; -1 takes build_grid_rule per target.  Lags are signed on the build grid."""
     lag0: List[int] = []
     length: List[int] = []
     taps: List[np.ndarray] = []
     dfl: List[float] = []
+    grids: List[int] = []
     for t in targets:
-        K, d = kernel_spectrum(ref, t, n, fs, f_low, f_high, pn_order, inv_psd, df_low_max, df_high)
-        rho = kernel_full(K, n)
+        d = df_low_rule(ref, t, pn_order, f_low, df_low_max)
+        nb = n if n_build == 0 else (n_build if n_build > 0 else
+                                     build_grid_rule(ref, t, n, fs, f_low, f_high, pn_order, d, df_high))
+        K, _ = kernel_spectrum(ref, t, n, fs, f_low, f_high, pn_order, inv_psd, df_low_max, df_high, d, nb)
+        rho = kernel_full(K, nb)
         m0, L, c = truncate(rho, thr, relative)
         lag0.append(m0)
         length.append(L)
         taps.append(c)
         dfl.append(d)
+        grids.append(nb)
     offset = np.concatenate([[0], np.cumsum(length)]).astype(np.int64)
     return PackedKernels(n, np.array(lag0, np.int64), np.array(length, np.int64), offset,
-                         np.concatenate(taps) if taps else np.zeros(0, np.complex128), np.array(dfl))
+                         np.concatenate(taps) if taps else np.zeros(0, np.complex128), np.array(dfl),
+                         np.array(grids, np.int64))

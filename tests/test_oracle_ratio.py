@@ -206,3 +206,31 @@ def test_truncation_degenerate_inputs():
     assert (m0, L) == (-1, 1) and c[0] == 2.0
     m0, L, c = ratio.truncate(np.ones(16, complex), 1e-3)
     assert L == 16
+
+
+def test_coarse_build_grid_reproduces_the_data_grid_kernels():
+    """Built on the rule's coarser grid, every kernel keeps the span of the data-grid kernel
+    (the paper's exact object) and its taps to 1e-7 of their maximum; a grid equal to the
+    data grid reproduces it exactly; the rule's grid is a power of two below n that grows
+    with the duration difference."""
+    n = 1 << 16
+    cfg = workload.config(1, n_override=n, k_override=4)
+    ref = cfg.groups[0][0]
+    nb = list(cfg.groups[0][1]) + list(workload.duration_lattice(ref, cfg.f_low, 4, 0.2, 3.0,
+                                                                  np.random.default_rng(9), n_eta=1,
+                                                                  mrange=(1.0, 4.5)))
+    ip = workload.inv_psd(cfg)
+    args = (ref, nb, n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 1e-4)
+    fine = ratio.build_ratio_kernels(*args)
+    same = ratio.build_ratio_kernels(*args, n_build=n)
+    assert np.array_equal(fine.taps, same.taps) and np.array_equal(fine.lag0, same.lag0)
+    coarse = ratio.build_ratio_kernels(*args, n_build=-1)
+    assert np.all(coarse.grid < n) and np.all((coarse.grid & (coarse.grid - 1)) == 0)
+    assert len(np.unique(coarse.grid)) > 1
+    for j in range(len(nb)):
+        assert coarse.lag0[j] == fine.lag0[j] and coarse.length[j] == fine.length[j]
+        cf, cc = fine.kernel(j)[1], coarse.kernel(j)[1]
+        assert np.abs(cc - cf).max() <= 1e-7 * np.abs(cf).max()
+    # longer kernels get grids at least as large
+    order = np.argsort(fine.length)
+    assert np.all(np.diff(coarse.grid[order]) >= 0)
