@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RF_ABI_VERSION 2
+#define RF_ABI_VERSION 3
 
 typedef struct rf_ctx rf_ctx;
 typedef struct rf_kernels rf_kernels;
@@ -162,11 +162,18 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
  * (relative != 0) or |rho|^2 >= thr^2 (relative == 0); the kernel is the shortest circular
  * arc [m0, m0+L) covering them (ties: smallest m0 in (-n/2, n/2]).  Taps c[l] = rho[m0+l]
  * are stored packed (grid dtype) with int32 signed m0 and length L per neighbour.
+ * Build grid (Sec. II.D: a kernel needs a frequency grid only as fine as its duration):
+ * n_build = 0 builds on the data grid (n bins, the definition above); a power of two in
+ * [16, n] builds every kernel on that grid (K~ at f_k = k fs / n_b, an n_b-point inverse
+ * transform with the 1/n_b factor, lags signed in (-n_b/2, n_b/2]); -1 picks per neighbour the
+ * smallest power of two of at least four times its lag extent (time offsets (Psi_j' -
+ * Psi_ref')/(2 pi) at f_low - df_low and f_high + df_high, times fs, plus 4 fs / df_low),
+ * capped at n.  N_ref / N_j stays on the data grid.  RF_EINVAL for other n_build.
  * refs/nbrs: host; inv_psd: device double[n/2+1].  SYNCHRONISES `stream` (the lengths are
  * read back).  *out is freed with rf_kernels_free. */
 rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_template* nbrs,
                                  int32_t k, const double* inv_psd, double threshold,
-                                 int32_t relative, rf_kernels** out, rf_stream stream);
+                                 int32_t relative, int64_t n_build, rf_kernels** out, rf_stream stream);
 
 /* Import k kernels computed earlier and kept on disk or in host memory (Sec. II.B keeps the
  * truncated ratio waveforms between analyses):
@@ -214,6 +221,9 @@ rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t*
 /* Copy the packed taps (sum(len) complex entries, grid dtype) into caller device memory
  * `dst`.  Async on stream. */
 rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream);
+
+/* Borrowed view of the build grid of each kernel (host int64[k]; n for imported kernels). */
+rf_status rf_kernels_grids(const rf_kernels* kern, const int64_t** grids);
 
 /* Release a kernel set.  NULL is a no-op. */
 void rf_kernels_free(rf_kernels* kern);

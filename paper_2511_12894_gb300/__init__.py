@@ -30,7 +30,7 @@ PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
 EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
-    "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_os_buckets",
+    "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_os_buckets", "rf_kernels_grids",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
     "rf_selftest_bounded_wait", "rf_autotune",
@@ -83,7 +83,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_reserve": (i32, [vp, i32, P(i64)]),
         "rf_template_fd": (i32, [vp, P(rf_template), vp, vp]),
         "rf_mf_reference": (i32, [vp, vp, vp, i32, P(rf_template), vp, vp, vp]),
-        "rf_build_ratio_kernels": (i32, [vp, P(rf_template), P(rf_template), i32, vp, dbl, i32, P(vp), vp]),
+        "rf_build_ratio_kernels": (i32, [vp, P(rf_template), P(rf_template), i32, vp, dbl, i32, i64, P(vp), vp]),
+        "rf_kernels_grids": (i32, [vp, P(P(i64))]),
         "rf_kernels_import": (i32, [vp, i32, P(i32), P(i32), vp, P(vp)]),
         "rf_kernels_info": (i32, [vp, P(i32), P(P(i32)), P(P(i32)), P(P(i64)), P(P(dbl)), P(vp)]),
         "rf_kernels_copy_taps": (i32, [vp, vp, vp]),
@@ -159,6 +160,7 @@ class Kernels:
     lag0: np.ndarray
     offset: np.ndarray
     df_low: np.ndarray
+    grid: np.ndarray = None   # build grid of each kernel
 
     def taps(self):
         """Packed taps as a new CUDA tensor (complex, sum(length) entries)."""
@@ -302,18 +304,22 @@ class RatioFilter:
                                     ctypes.byref(dl), None))
         kk = k.value
         arr = lambda p, m, dt: np.ctypeslib.as_array(p, shape=(m,)).astype(dt).copy() if m else np.zeros(m, dt)
+        gp = ctypes.POINTER(ctypes.c_int64)()
+        _check(_lib.rf_kernels_grids(h, ctypes.byref(gp)))
         return Kernels(h, self, kk, arr(ln, kk, np.int64), arr(lg, kk, np.int64), arr(of, kk + 1, np.int64),
-                       arr(dl, kk, np.float64))
+                       arr(dl, kk, np.float64), arr(gp, kk, np.int64))
 
     def build_ratio_kernels(self, ref, nbrs: Sequence, inv_psd, threshold: float = 1e-3, relative: bool = True,
-                            stream=None) -> Kernels:
-        """Truncated ratio kernels of ``nbrs`` against ``ref`` (Sec. II.B-II.D); synchronises."""
+                            stream=None, n_build: int = 0) -> Kernels:
+        """Truncated ratio kernels of ``nbrs`` against ``ref`` (Sec. II.B-II.D); synchronises.
+
+        n_build: 0 on the data grid, a power of two for that build grid, -1 per neighbour."""
         import torch
         ip = _dev(inv_psd, torch.float64, "inv_psd")
         h = ctypes.c_void_p()
         _check(_lib.rf_build_ratio_kernels(self.handle, _templates([ref]), _templates(nbrs), len(nbrs),
                                            ctypes.c_void_p(ip.data_ptr()), float(threshold), int(bool(relative)),
-                                           ctypes.byref(h), _stream(stream)))
+                                           int(n_build), ctypes.byref(h), _stream(stream)))
         return self._wrap_kernels(h)
 
     def kernels_import(self, lag0: Iterable[int], length: Iterable[int], taps: np.ndarray) -> Kernels:

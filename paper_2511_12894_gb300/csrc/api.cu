@@ -226,8 +226,8 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
 }
 
 rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_template* nbrs, int32_t k,
-                                 const double* inv_psd, double threshold, int32_t relative, rf_kernels** out,
-                                 rf_stream stream) {
+                                 const double* inv_psd, double threshold, int32_t relative, int64_t n_build,
+                                 rf_kernels** out, rf_stream stream) {
   return guard([&] {
     RF_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
@@ -239,7 +239,10 @@ rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_t
     for (int j = 0; j < k; ++j) check_template(nbrs[j], "nbrs[j]");
     check_dev(inv_psd, "inv_psd");
     RF_REQUIRE(std::isfinite(threshold) && threshold >= 0, "threshold must be finite and >= 0");
-    *out = build_impl(ctx, *ref, nbrs, k, inv_psd, threshold, relative, (cudaStream_t)stream);
+    RF_REQUIRE(n_build == 0 || n_build == -1 ||
+                   (n_build >= 16 && n_build <= ctx->n && (n_build & (n_build - 1)) == 0),
+               "n_build=%lld must be 0, -1 or a power of two in [16, n]", (long long)n_build);
+    *out = build_impl(ctx, *ref, nbrs, k, inv_psd, threshold, relative, n_build, (cudaStream_t)stream);
   });
 }
 
@@ -322,6 +325,14 @@ rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t*
       if (parts) parts[b] = kern->os_buckets[b].Lp;
     }
     if (nb) *nb = std::min(cnt, (int)max_nb);
+  });
+}
+
+rf_status rf_kernels_grids(const rf_kernels* kern, const int64_t** grids) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    RF_REQUIRE(grids != nullptr, "grids is NULL");
+    *grids = kern->grid.data();
   });
 }
 

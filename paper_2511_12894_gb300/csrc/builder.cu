@@ -1,12 +1,17 @@
 // Ratio-kernel builder (Sec. II.B-II.D; Eqs. 5, 7, 9, 10), FP64 throughout.
 //
-// Per neighbour j of the reference:
+// Per neighbour j of the reference, on its build grid of n_b bins (f_k = k fs / n_b; n_b = n
+// unless a coarser grid is asked for, Sec. II.D):
 //   df_low_j = min(df_low_max, f_low / 2, 1 / sqrt(|dPsi''(f_low)| / (2 pi)))          (Eq. 10)
-//   K~_j[k]  = (N_ref / N_j) R(f_k) W_j(f_k) exp(+i (Psi_j(f_k) - Psi_ref(f_k))) / n     (Eqs. 5, 7, 9)
-//   rho_j    = unnormalised inverse DFT of K~_j (zero for k > n/2)
+//   K~_j[k]  = (N_ref / N_j) R(f_k) W_j(f_k) exp(+i (Psi_j(f_k) - Psi_ref(f_k))) / n_b   (Eqs. 5, 7, 9)
+//   rho_j    = unnormalised n_b-point inverse DFT of K~_j (zero for k > n_b/2)
 //   kept     = { m : |rho_j[m]|^2 >= thr^2 a_j },  a_j = max |rho_j|^2 (relative) or 1
 //   [m0, m0 + L) = shortest circular arc covering `kept`, ties to the smallest signed m0
-//   taps c_j[l] = rho_j[(m0 + l) mod n]
+//   taps c_j[l] = rho_j[(m0 + l) mod n_b]
+// The automatic grid is the smallest power of two of at least four times the lag extent
+// between the time offsets dt(f) = (Psi_j' - Psi_ref')(f) / (2 pi) (Eq. A2) at the window
+// edges f_low - df_low_j and f_high + df_high, plus the taper spread 4 fs / df_low_j
+// (capped at n); neighbours are processed grouped by grid.
 // The templates share the amplitude law B = f^-7/6, so R = 1 and N_ref / N_j = 1;
 // both factors are still formed from their definitions.
 #include <algorithm>
@@ -31,6 +36,17 @@ __global__ void k_df_low(Tf2 ref, const Tf2* __restrict__ tg, int count, double 
   double v = fmin(df_low_max, 0.5 * f_low);
   if (dtp > 0.0) v = fmin(v, 1.0 / sqrt(dtp));
   out[j] = v;
+}
+
+// Lag extent of each kernel for the automatic build grid (samples).
+__global__ void k_grid_extent(Tf2 ref, const Tf2* __restrict__ tg, const double* __restrict__ dfl, int count,
+                              double fs, double f_low, double f_high, double df_high, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= count) return;
+  const double fa = f_low - dfl[j], fb = f_high + df_high;
+  const double ta = (tf2_dphase(tg[j], fa) - tf2_dphase(ref, fa)) / kTwoPi;
+  const double tb = (tf2_dphase(tg[j], fb) - tf2_dphase(ref, fb)) / kTwoPi;
+  out[j] = fmax(fabs(ta), fabs(tb)) * fs + 4.0 * fs / dfl[j];
 }
 
 __global__ void __launch_bounds__(256) k_ref_phase(Tf2 ref, int64_t nbins, double df, double* __restrict__ psi) {
@@ -163,10 +179,8 @@ __global__ void __launch_bounds__(256) k_pack(const double2* __restrict__ rho, i
 }  // namespace
 
 rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbrs, int32_t k, const double* inv_psd,
-                       double thr, int relative, cudaStream_t s) {
+                       double thr, int relative, int64_t n_build, cudaStream_t s) {
   const int64_t n = c->n;
-  const int64_t nbins = n / 2 + 1;
-  const double df = c->g.fs / (double)n;
   const bool f64 = c->g.dtype == RF_F64;
   const size_t esz = f64 ? sizeof(double2) : sizeof(float2);
 
@@ -179,6 +193,7 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
   kern->lag0.assign(k, 0);
   kern->offset.assign((size_t)k + 1, 0);
   kern->df_low.assign(k, 0.0);
+  kern->grid.assign(k, n);
   if (k == 0) {
     kern->taps.ensure(16);
     kern->len_d.ensure(16);
@@ -189,15 +204,13 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
     return owner.release();
   }
 
-  // templates per chunk: three complex128 rows of n per template, about 1.5 GB in total
-  const int64_t per = 3 * n * (int64_t)sizeof(double2);
-  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>((int64_t)1536 << 20, (int64_t)1 << 40) / per);
-  chunk = std::min<int64_t>(chunk, std::min<int64_t>(k, 4096));
-
-  // device scratch: [Tf2 chunk][dfl][psi_ref][sig2][amax2][m0][len] + 3 rows of chunk x n complex128
+  // device scratch: [Tf2 k][dfl k][extent k][Tf2 k, grid order][dfl k, grid order][psi_ref][sig2]
+  // [amax2][m0][len]
+  const int64_t nbins = n / 2 + 1;
+  const int64_t kmax_chunk = std::min<int64_t>(k, 4096);
   DevBuf meta;
-  const size_t meta_bytes = sizeof(Tf2) * (size_t)k + sizeof(double) * ((size_t)k + nbins + 8 + chunk) +
-                            2 * sizeof(int) * (size_t)chunk + 4096;
+  const size_t meta_bytes = 2 * sizeof(Tf2) * (size_t)k + sizeof(double) * (3 * (size_t)k + nbins + 8 + kmax_chunk) +
+                            2 * sizeof(int) * (size_t)kmax_chunk + 8192;
   meta.ensure(meta_bytes);
   char* mp = static_cast<char*>(meta.p);
   auto carve = [&](size_t bytes) {
@@ -207,12 +220,15 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
   };
   Tf2* d_tg = reinterpret_cast<Tf2*>(carve(sizeof(Tf2) * k));
   double* d_dfl = reinterpret_cast<double*>(carve(sizeof(double) * k));
+  double* d_ext = reinterpret_cast<double*>(carve(sizeof(double) * k));
+  Tf2* d_tgs = reinterpret_cast<Tf2*>(carve(sizeof(Tf2) * k));
+  double* d_dfls = reinterpret_cast<double*>(carve(sizeof(double) * k));
   double* d_psi = reinterpret_cast<double*>(carve(sizeof(double) * nbins));
   double* d_sig2 = reinterpret_cast<double*>(carve(sizeof(double) * 2));
-  double* d_amax = reinterpret_cast<double*>(carve(sizeof(double) * chunk));
-  int* d_m0 = reinterpret_cast<int*>(carve(sizeof(int) * chunk));
-  int* d_len = reinterpret_cast<int*>(carve(sizeof(int) * chunk));
-  RF_REQUIRE((size_t)(mp - static_cast<char*>(meta.p)) <= meta_bytes + 4096, "builder: scratch layout");
+  double* d_amax = reinterpret_cast<double*>(carve(sizeof(double) * kmax_chunk));
+  int* d_m0 = reinterpret_cast<int*>(carve(sizeof(int) * kmax_chunk));
+  int* d_len = reinterpret_cast<int*>(carve(sizeof(int) * kmax_chunk));
+  RF_REQUIRE((size_t)(mp - static_cast<char*>(meta.p)) <= meta_bytes, "builder: scratch layout");
 
   std::vector<Tf2> tg(k);
   for (int j = 0; j < k; ++j) tg[j] = make_tf2(nbrs[j], c->g.pn_order);
@@ -220,40 +236,87 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
   const Tf2 pr = make_tf2(ref, c->g.pn_order);
   k_df_low<<<(k + 127) / 128, 128, 0, s>>>(pr, d_tg, k, c->g.f_low, c->g.df_low_max, d_dfl);
   RF_LAUNCHED();
-  k_ref_phase<<<(unsigned)((nbins + 255) / 256), 256, 0, s>>>(pr, nbins, df, d_psi);
-  RF_LAUNCHED();
-  // N_ref^2 and N_j^2 (Eq. 3): one FP64 sum serves both (same amplitude law)
+  RF_CUDA(cudaMemcpyAsync(kern->df_low.data(), d_dfl, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  // build grid per neighbour
+  if (n_build < 0) {
+    std::vector<double> ext(k);
+    k_grid_extent<<<(k + 127) / 128, 128, 0, s>>>(pr, d_tg, d_dfl, k, c->g.fs, c->g.f_low, c->g.f_high, c->g.df_high,
+                                                  d_ext);
+    RF_LAUNCHED();
+    RF_CUDA(cudaMemcpyAsync(ext.data(), d_ext, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    RF_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < k; ++j) {
+      int64_t nb = 16;
+      while ((double)nb < 4.0 * ext[j] && nb < n) nb *= 2;
+      kern->grid[j] = std::min<int64_t>(nb, n);
+    }
+  } else if (n_build > 0) {
+    for (int j = 0; j < k; ++j) kern->grid[j] = n_build;
+  }
+  RF_CUDA(cudaStreamSynchronize(s));  // df_low is on the host
+  // neighbours in grid order (stable), chunks of one grid
+  std::vector<int> order(k);
+  for (int j = 0; j < k; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kern->grid[a] < kern->grid[b]; });
+  {
+    std::vector<Tf2> tgs(k);
+    std::vector<double> dfls(k);
+    for (int q = 0; q < k; ++q) {
+      tgs[q] = tg[order[q]];
+      dfls[q] = kern->df_low[order[q]];
+    }
+    RF_CUDA(cudaMemcpyAsync(d_tgs, tgs.data(), sizeof(Tf2) * k, cudaMemcpyHostToDevice, s));
+    RF_CUDA(cudaMemcpyAsync(d_dfls, dfls.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    RF_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  }
+  // N_ref^2 and N_j^2 (Eq. 3) on the data grid: one FP64 sum serves both (same amplitude law)
   sigma2_impl(c, inv_psd, 1, d_sig2, s);
 
-  DevBuf rows;
-  rows.ensure((size_t)3 * chunk * n * sizeof(double2));
-  double2* bufK = rows.as<double2>();
-  double2* bufR = bufK + chunk * n;
-  double2* bufT = bufR + chunk * n;
-
+  // per kernel: its taps in a part buffer (one per chunk) and its place there
   std::vector<std::unique_ptr<DevBuf>> parts;
-  std::vector<int64_t> part_elems;
-  int64_t total = 0;
-  std::vector<int> hm0(chunk), hlen(chunk);
-  for (int64_t j0 = 0; j0 < k; j0 += chunk) {
-    const int cnt = (int)std::min<int64_t>(chunk, k - j0);
-    dim3 g1((unsigned)((n + 255) / 256), (unsigned)cnt);
-    k_kernel_spectrum<<<g1, 256, 0, s>>>(d_tg + j0, d_dfl + j0, d_psi, d_sig2, d_sig2, n, df, c->g.f_low,
+  std::vector<int> part_of(k);
+  std::vector<int64_t> at_in_part(k);
+  std::vector<int> hm0(kmax_chunk), hlen(kmax_chunk);
+  DevBuf rows;
+  int64_t psi_grid = 0;
+  for (int q0 = 0; q0 < k;) {
+    const int64_t nb = kern->grid[order[q0]];
+    // templates per chunk: three complex128 rows of nb per template, about 1.5 GB in total
+    const int64_t per = 3 * nb * (int64_t)sizeof(double2);
+    int64_t chunk = std::max<int64_t>(1, ((int64_t)1536 << 20) / per);
+    chunk = std::min<int64_t>(chunk, kmax_chunk);
+    int cnt = 0;
+    while (q0 + cnt < k && cnt < chunk && kern->grid[order[q0 + cnt]] == nb) ++cnt;
+    const double dfb = c->g.fs / (double)nb;
+    if (psi_grid != nb) {
+      k_ref_phase<<<(unsigned)((nb / 2 + 1 + 255) / 256), 256, 0, s>>>(pr, nb / 2 + 1, dfb, d_psi);
+      RF_LAUNCHED();
+      psi_grid = nb;
+    }
+    rows.ensure((size_t)3 * cnt * nb * sizeof(double2));
+    double2* bufK = rows.as<double2>();
+    double2* bufR = bufK + cnt * nb;
+    double2* bufT = bufR + cnt * nb;
+    dim3 g1((unsigned)((nb + 255) / 256), (unsigned)cnt);
+    k_kernel_spectrum<<<g1, 256, 0, s>>>(d_tgs + q0, d_dfls + q0, d_psi, d_sig2, d_sig2, nb, dfb, c->g.f_low,
                                          c->g.f_high, c->g.df_high, bufK);
     RF_LAUNCHED();
-    fft_c2c_f64(bufK, bufR, bufT, n, cnt, +1, c->tw64.as<double2>(), n, s);
-    k_row_max2<<<cnt, 1024, 0, s>>>(bufR, n, d_amax);
+    fft_c2c_f64(bufK, bufR, bufT, nb, cnt, +1, c->tw64.as<double2>(), n, s);
+    k_row_max2<<<cnt, 1024, 0, s>>>(bufR, nb, d_amax);
     RF_LAUNCHED();
-    const int nt = (int)std::min<int64_t>(1024, n);
-    k_arc<<<cnt, nt, 0, s>>>(bufR, n, d_amax, thr, relative, d_m0, d_len);
+    const int nt = (int)std::min<int64_t>(1024, nb);
+    k_arc<<<cnt, nt, 0, s>>>(bufR, nb, d_amax, thr, relative, d_m0, d_len);
     RF_LAUNCHED();
     RF_CUDA(cudaMemcpyAsync(hm0.data(), d_m0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
     RF_CUDA(cudaMemcpyAsync(hlen.data(), d_len, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
     RF_CUDA(cudaStreamSynchronize(s));
     std::vector<int64_t> off(cnt + 1, 0);
     for (int q = 0; q < cnt; ++q) {
-      kern->lag0[j0 + q] = hm0[q];
-      kern->len[j0 + q] = hlen[q];
+      const int j = order[q0 + q];
+      kern->lag0[j] = hm0[q];
+      kern->len[j] = hlen[q];
+      part_of[j] = (int)parts.size();
+      at_in_part[j] = off[q];
       off[q + 1] = off[q] + hlen[q];
     }
     std::unique_ptr<DevBuf> part(new DevBuf());
@@ -263,25 +326,38 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
     RF_CUDA(cudaMemcpyAsync(offd.p, off.data(), sizeof(int64_t) * (cnt + 1), cudaMemcpyHostToDevice, s));
     dim3 g2(64, (unsigned)cnt);
     if (f64)
-      k_pack<double2><<<g2, 256, 0, s>>>(bufR, n, d_m0, d_len, offd.as<int64_t>(), part->as<double2>());
+      k_pack<double2><<<g2, 256, 0, s>>>(bufR, nb, d_m0, d_len, offd.as<int64_t>(), part->as<double2>());
     else
-      k_pack<float2><<<g2, 256, 0, s>>>(bufR, n, d_m0, d_len, offd.as<int64_t>(), part->as<float2>());
+      k_pack<float2><<<g2, 256, 0, s>>>(bufR, nb, d_m0, d_len, offd.as<int64_t>(), part->as<float2>());
     RF_LAUNCHED();
     RF_CUDA(cudaStreamSynchronize(s));  // offd and the rows are reused
     parts.push_back(std::move(part));
-    part_elems.push_back(off[cnt]);
-    total += off[cnt];
-  }
-  RF_CUDA(cudaMemcpyAsync(kern->df_low.data(), d_dfl, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-  kern->taps.ensure(std::max<size_t>(16, (size_t)total * esz));
-  int64_t at = 0;
-  for (size_t q = 0; q < parts.size(); ++q) {
-    if (part_elems[q])
-      RF_CUDA(cudaMemcpyAsync(static_cast<char*>(kern->taps.p) + at * esz, parts[q]->p, part_elems[q] * esz,
-                              cudaMemcpyDeviceToDevice, s));
-    at += part_elems[q];
+    q0 += cnt;
   }
   for (int j = 0; j < k; ++j) kern->offset[j + 1] = kern->offset[j] + kern->len[j];
+  const int64_t total = kern->offset[k];
+  kern->taps.ensure(std::max<size_t>(16, (size_t)total * esz));
+  // taps in neighbour order: one copy per part when the order is unchanged, else one per kernel
+  bool identity = true;
+  for (int q = 0; q < k && identity; ++q) identity = order[q] == q;
+  if (identity) {
+    int64_t at = 0;
+    for (size_t pi = 0; pi < parts.size(); ++pi) {
+      int64_t elems = 0;
+      for (int j = 0; j < k; ++j)
+        if (part_of[j] == (int)pi) elems += kern->len[j];
+      if (elems)
+        RF_CUDA(cudaMemcpyAsync(static_cast<char*>(kern->taps.p) + at * esz, parts[pi]->p, elems * esz,
+                                cudaMemcpyDeviceToDevice, s));
+      at += elems;
+    }
+  } else {
+    for (int j = 0; j < k; ++j)
+      if (kern->len[j])
+        RF_CUDA(cudaMemcpyAsync(static_cast<char*>(kern->taps.p) + kern->offset[j] * esz,
+                                static_cast<char*>(parts[part_of[j]]->p) + at_in_part[j] * esz,
+                                (size_t)kern->len[j] * esz, cudaMemcpyDeviceToDevice, s));
+  }
   kern->max_len = *std::max_element(kern->len.begin(), kern->len.end());
   kern->len_d.ensure(sizeof(int32_t) * k);
   kern->lag0_d.ensure(sizeof(int32_t) * k);
@@ -301,6 +377,7 @@ rf_kernels* import_impl(rf_ctx* c, int32_t k, const int32_t* lag0, const int32_t
   kern->k = k;
   kern->n = c->n;
   kern->dtype = c->g.dtype;
+  kern->grid.assign(k, c->n);
   kern->len.assign(len, len + k);
   kern->lag0.assign(lag0, lag0 + k);
   kern->offset.assign((size_t)k + 1, 0);

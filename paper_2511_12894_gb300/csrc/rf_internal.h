@@ -128,6 +128,7 @@ struct rf_kernels {
   std::vector<int32_t> len, lag0;
   std::vector<int64_t> offset;
   std::vector<double> df_low;
+  std::vector<int64_t> grid;   // build grid of each kernel (its lags are signed on it)
   int32_t max_len = 0;
   rf::DevBuf taps;             // packed taps (grid dtype complex)
   rf::DevBuf len_d, lag0_d;    // int32[k]
@@ -190,7 +191,7 @@ void sigma2_impl(rf_ctx* c, const double* inv_psd, int count, double* out, cudaS
 
 // ---------------------------------------------------------------- builder (builder.cu)
 rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbrs, int32_t k,
-                       const double* inv_psd, double thr, int relative, cudaStream_t s);
+                       const double* inv_psd, double thr, int relative, int64_t n_build, cudaStream_t s);
 rf_kernels* import_impl(rf_ctx* c, int32_t k, const int32_t* lag0, const int32_t* len,
                         const void* taps);
 

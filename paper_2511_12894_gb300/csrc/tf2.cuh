@@ -51,6 +51,14 @@ __device__ __forceinline__ void tf2_series_d(const Tf2& p, double v, double& g1,
   }
 }
 
+// Psi'(f) = 2 pi tc + 3/(128 eta) g'(v) dv/df = 2 pi t(f) (Eq. A2)
+__device__ __forceinline__ double tf2_dphase(const Tf2& p, double f) {
+  const double v = cbrt(kPi * p.M * f);
+  double g1, g2;
+  tf2_series_d(p, v, g1, g2);
+  return kTwoPi * p.tc + p.pref * g1 * (kPi * p.M / (3.0 * v * v));
+}
+
 // Psi''(f) = (pi M / (128 eta)) (g'' v^-2 - 2 g' v^-3) dv/df,  dv/df = pi M / (3 v^2)
 __device__ __forceinline__ double tf2_d2phase(const Tf2& p, double f) {
   const double v = cbrt(kPi * p.M * f);

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_error_string(lib):
-    assert lib.rf_version() == 2
+    assert lib.rf_version() == 3
     assert isinstance(lib.rf_last_error(), bytes)
 
 
@@ -71,7 +71,8 @@ def test_null_context_and_handles_are_rejected_by_every_entry_point(lib):
     assert lib.rf_mf_reference(None, None, None, 1, None, None, None, None) == RF_EINVAL
     assert lib.rf_reference_filters(None, None, 1, None, None, None, None) == RF_EINVAL
     assert lib.rf_mf_filtered(None, None, 1, None, None, None) == RF_EINVAL
-    assert lib.rf_build_ratio_kernels(None, None, None, 0, None, 1e-3, 1, None, None) == RF_EINVAL
+    assert lib.rf_build_ratio_kernels(None, None, None, 0, None, 1e-3, 1, 0, None, None) == RF_EINVAL
+    assert lib.rf_kernels_grids(None, None) == RF_EINVAL
     assert lib.rf_kernels_prepare(None, None, 0, 0, None) == RF_EINVAL
     assert lib.rf_kernels_prepare_buckets(None, None, 1, cuts, cuts, cuts, None) == RF_EINVAL
     assert lib.rf_kernels_os_layout(None, None, None) == RF_EINVAL

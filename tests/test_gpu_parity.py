@@ -162,6 +162,30 @@ def test_build_ratio_kernels_f64(torch, n, k, thr, rel):
     assert _relerr(taps, pk.taps) < TOL["f64"]
 
 
+@pytest.mark.parametrize("n_build", [-1, 1 << 13])
+def test_build_ratio_kernels_coarse_grid(torch, n_build):
+    """Kernels built on a coarser grid (fixed, or per neighbour by the extent rule; Sec. II.D)
+    against the oracle's same definition: grids, spans and signed lags exact, taps to FP64
+    rounding; neighbours spanning several grids come back in their own order."""
+    n = 1 << 16
+    cfg = workload.config(1, n_override=n, k_override=4)
+    ref = cfg.groups[0][0]
+    nb = list(cfg.groups[0][1]) + list(workload.duration_lattice(ref, cfg.f_low, 4, 0.2, 3.0,
+                                                                  np.random.default_rng(9), n_eta=1,
+                                                                  mrange=(1.0, 4.5)))
+    nb = [nb[i] for i in (4, 0, 7, 1, 5, 2, 6, 3)]     # grids out of order
+    ip = workload.inv_psd(cfg)
+    rf = _rf(cfg)
+    kern = rf.build_ratio_kernels(ref, nb, torch.tensor(ip, device="cuda"), 1e-4, n_build=n_build)
+    pk = ratio.build_ratio_kernels(ref, nb, n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 1e-4,
+                                   n_build=n_build)
+    assert np.array_equal(kern.grid, pk.grid)
+    if n_build < 0:
+        assert len(np.unique(kern.grid)) > 1
+    assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
+    assert _relerr(kern.taps().cpu().numpy(), pk.taps) < TOL["f64"]
+
+
 def test_build_ratio_kernels_f32_long(torch):
     cfg = _small_f32_cfg(1 << 17, 6)
     ref = cfg.groups[0][0]
