@@ -53,6 +53,9 @@ def parse():
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default)")
+    ap.add_argument("--n-build", type=int, default=None,
+                    help="kernel build grid: 0 the data grid, -1 per neighbour, or a power of two "
+                         "(default: -1 for the 2^23-sample workload, else 0)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (with --algo auto: the cost-model overlap-save layout)")
     ap.add_argument("--mf", default="filtered", choices=["filtered", "onthefly"],
@@ -327,7 +330,8 @@ def main():
     # ---------------- offline: ratio kernels (and their overlap-save spectra)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    kerns = [rf.build_ratio_kernels(r, nb, ip, thr) for r, nb in cfg.groups]
+    n_build = args.n_build if args.n_build is not None else (-1 if cfg.n > (1 << 20) else 0)
+    kerns = [rf.build_ratio_kernels(r, nb, ip, thr, n_build=n_build) for r, nb in cfg.groups]
     filt, sig = rf.reference_filters(ip, refs)
     tune, tune_s = None, 0.0
     if args.buckets:
@@ -577,7 +581,7 @@ def main():
             "config": {"workload": workload_label(full_cfg, args.config, thr),
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
-                       "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf,
+                       "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf, "n_build": n_build,
                        "autotune": ({"seconds": tune_s, "timed": tune} if tune else None),
                        "prec": prec,
                        "graph": graph is not None,
