@@ -190,8 +190,9 @@ rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** le
                           const void** taps_dev);
 
 /* Prepare a kernel set for overlap-save reconstruction (Eq. 7 in blocks; RF_F32 grids,
- * n >= 512): block size B (a power of two in [512, 16384], <= n) and partition length Lp
- * (B/2, B/4 or B/8 taps); 0 for either picks, among the allowed layouts, the one of least
+ * n >= 512): block size B (a power of two in [512, 32768], <= n) and partition length Lp
+ * (B/2, B/4 or B/8 taps; B/2 or B/4 at 32768, whose blocks run on pairs of CTAs of a thread
+ * block cluster, each transforming the bins of one parity); 0 for either picks, among the allowed layouts, the one of least
  * modelled cost for this set's kernel lengths (a per-block cost table measured on GB300,
  * plus a penalty for launches too small to fill the GPU).  Computes the partition spectra
  * FFT_B(taps)/B in FP64 and stores them as complex64 inside the kernel set

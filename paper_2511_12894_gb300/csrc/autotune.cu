@@ -25,9 +25,9 @@ struct Cand {
 // layouts of least modelled cost for kernels of the given lengths
 std::vector<Cand> os_candidates_for(const rf_ctx* c, const std::vector<int>& all, int max_os) {
   std::vector<Cand> out;
-  for (int B = 512; B <= 16384; B *= 2) {
+  for (int B = 512; B <= 32768; B *= 2) {  // 32768: the CTA-pair layout (partitions B/2 or B/4)
     if (B > c->n) continue;
-    for (int Q = 2; Q <= 8; Q *= 2)
+    for (int Q = 2; Q <= (B == 32768 ? 4 : 8); Q *= 2)
       out.push_back(Cand{RF_ALGO_OS, B, B / Q, RF_PREC_NATIVE, os_layout_cost(c, all, B, B / Q)});
   }
   std::sort(out.begin(), out.end(), [](const Cand& a, const Cand& b) { return a.model < b.model; });

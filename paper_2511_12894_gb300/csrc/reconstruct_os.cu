@@ -75,6 +75,81 @@ __global__ void __launch_bounds__(B / 16) k_os_segments_batched(const float2* co
     for (int t = 0; t < S::RL; ++t) out[tid + q * S::NT + t * (B / S::RL)] = v[q * S::RL + t];
 }
 
+// Window peaks of this thread's CH consecutive outputs mv[0..cnt) whose first sample index is
+// i0 (later ones step by one and wrap to 0 at n), merged into the packed keys kj[window].
+// Warp-wide: every lane of the warp calls it (lanes without outputs pass cnt = 0).
+template <int CH>
+__device__ __forceinline__ void window_keys(const float (&mv)[CH], int cnt, int i0, int64_t n, int64_t W,
+                                            int64_t nw, int fastwin, unsigned long long* __restrict__ kj) {
+  const int lane = threadIdx.x & 31;
+  // sample index and window of this thread's first output; its outputs i0 + e (wrapping to
+  // 0 at n) lie in window w0 below e_b = min(W - r0, n - i0) and in the next window w1 (w0 + 1,
+  // or 0 after the wrap) from e_b on: at most two windows when W >= CH, which fastwin implies
+  const int w0 = i0 / (int)W;
+  const int r0 = i0 - w0 * (int)W;
+  const int to_wrap = (int)n - i0;
+  const int e_b = min((int)W - r0, to_wrap);
+  const int w1 = to_wrap <= (int)W - r0 ? 0 : w0 + 1;
+  const int wA = __shfl_sync(0xffffffffu, w0, 0);
+  const int wB = (wA + 1 == (int)nw) ? 0 : wA + 1;
+  // per window the largest |z|^2 and its first position (strict > keeps the first of equals)
+  float b0 = -1.f, b1 = -1.f;
+  int e0 = 0, e1 = 0;
+#pragma unroll
+  for (int e = 0; e < CH; ++e) {
+    const float m = mv[e];
+    if (e < cnt) {
+      if (e < e_b) {
+        if (m > b0) {
+          b0 = m;
+          e0 = e;
+        }
+      } else if (m > b1) {
+        b1 = m;
+        e1 = e;
+      }
+    }
+  }
+  unsigned long long kA = 0, kB = 0;
+  bool slow = !fastwin;
+  auto put = [&](int w, unsigned long long k) {
+    if (w == wA) kA = max(kA, k);
+    else if (w == wB) kB = max(kB, k);
+    else slow = true;
+  };
+  if (b0 >= 0.f) put(w0, pack_key(b0, (unsigned int)(i0 + e0)));
+  if (b1 >= 0.f) put(w1, pack_key(b1, (unsigned int)(i0 + e1 >= (int)n ? i0 + e1 - (int)n : i0 + e1)));
+  const bool any_slow = __any_sync(0xffffffffu, slow);
+  if (any_slow) {
+    // per output, stepping the index and window by one (wrapping at n)
+    int i = i0, w = w0, r = r0;
+#pragma unroll
+    for (int e = 0; e < CH; ++e) {
+      if (e < cnt) atomicMax(kj + w, pack_key(mv[e], (unsigned int)i));
+      ++i;
+      ++r;
+      if (i == (int)n) {
+        i = 0;
+        w = 0;
+        r = 0;
+      } else if (r == (int)W) {
+        ++w;
+        r = 0;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
+      kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
+    }
+    if (lane == 0) {
+      if (kA) atomicMax(kj + wA, kA);
+      if (kB) atomicMax(kj + wB, kB);
+    }
+  }
+}
+
 // One neighbour's output blocks [s0, s1): spectral products, inverse block FFT, then either
 // the series (zrow != nullptr) or the window peaks (keys row kj).
 template <int B, int Q, bool WINMAX>
@@ -145,7 +220,6 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
           }
         }
       __syncthreads();
-      const int lane = tid & 31;
       const int qbase = tid * CH;
       float mv[CH];
       if constexpr (CH % 4 == 0) {
@@ -160,73 +234,7 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
       // outputs of this thread that exist (all but possibly in the last block)
       const int64_t avail = lim - qbase;
       const int cnt = avail <= 0 ? 0 : (avail >= CH ? CH : (int)avail);
-      // sample index and window of this thread's first output; its outputs i0 + e (wrapping to
-      // 0 at n) lie in window w0 below e_b = min(W - r0, n - i0) and in the next window w1 (w0 + 1,
-      // or 0 after the wrap) from e_b on: at most two windows when W >= CH, which fastwin implies
-      const int i0 = (int)((base + qbase) & mask);
-      const int w0 = i0 / (int)W;
-      const int r0 = i0 - w0 * (int)W;
-      const int to_wrap = (int)n - i0;
-      const int e_b = min((int)W - r0, to_wrap);
-      const int w1 = to_wrap <= (int)W - r0 ? 0 : w0 + 1;
-      const int wA = __shfl_sync(0xffffffffu, w0, 0);
-      const int wB = (wA + 1 == (int)nw) ? 0 : wA + 1;
-      // per window the largest |z|^2 and its first position (strict > keeps the first of equals)
-      float b0 = -1.f, b1 = -1.f;
-      int e0 = 0, e1 = 0;
-#pragma unroll
-      for (int e = 0; e < CH; ++e) {
-        const float m = mv[e];
-        if (e < cnt) {
-          if (e < e_b) {
-            if (m > b0) {
-              b0 = m;
-              e0 = e;
-            }
-          } else if (m > b1) {
-            b1 = m;
-            e1 = e;
-          }
-        }
-      }
-      unsigned long long kA = 0, kB = 0;
-      bool slow = !fastwin;
-      auto put = [&](int w, unsigned long long k) {
-        if (w == wA) kA = max(kA, k);
-        else if (w == wB) kB = max(kB, k);
-        else slow = true;
-      };
-      if (b0 >= 0.f) put(w0, pack_key(b0, (unsigned int)(i0 + e0)));
-      if (b1 >= 0.f) put(w1, pack_key(b1, (unsigned int)(i0 + e1 >= (int)n ? i0 + e1 - (int)n : i0 + e1)));
-      const bool any_slow = __any_sync(0xffffffffu, slow);
-      if (any_slow) {
-        // per output, stepping the index and window by one (wrapping at n)
-        int i = i0, w = w0, r = r0;
-#pragma unroll
-        for (int e = 0; e < CH; ++e) {
-          if (e < cnt) atomicMax(kj + w, pack_key(mv[e], (unsigned int)i));
-          ++i;
-          ++r;
-          if (i == (int)n) {
-            i = 0;
-            w = 0;
-            r = 0;
-          } else if (r == (int)W) {
-            ++w;
-            r = 0;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
-          kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
-        }
-        if (lane == 0) {
-          if (kA) atomicMax(kj + wA, kA);
-          if (kB) atomicMax(kj + wB, kB);
-        }
-      }
+      window_keys<CH>(mv, cnt, (int)((base + qbase) & mask), n, W, nw, fastwin, kj);
       __syncthreads();  // mag (shared memory) is reused by the next block's FFT
     }
   }
@@ -317,6 +325,199 @@ __global__ void k_os_round(const double2* __restrict__ spec, int64_t count, doub
   if (i < count) out[i] = make_float2((float)(spec[i].x * scale), (float)(spec[i].y * scale));
 }
 
+// ------------------------------------------------------- 32768-point blocks on CTA pairs
+// A block of B2 = 32768 points is split by the parity of its bins between the two CTAs of a
+// cluster: CTA r holds Y[2k' + r], k' < BH = 16384, and transforms it with the 16384-point
+// block FFT; the halves combine as
+//   y[t] = E0[t] + w^t E1[t],  y[t + BH] = E0[t] - w^t E1[t],  t < BH,  w = exp(+2 pi i / B2),
+// each CTA computing half of the t and reading the other CTA's half from distributed shared
+// memory.  Spectra of this layout are stored parity-split: bin 2k' + r at r BH + k'.
+constexpr int kBH = 16384;
+constexpr int kB2 = 2 * kBH;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of both CTAs arrives; memory written before is visible after (release/acquire).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_peer_addr(const void* p, unsigned rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ float2 ld_peer_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+// Segment spectra of the B2 layout (no cluster needed): block (q, r, g) transforms
+//   u_0[m] = x[m] + x[m + BH],  u_1[m] = (x[m] - x[m + BH]) exp(-2 pi i m / B2),
+// x[m] = z_ref_g[(q Lp + m) mod n], giving the bins of parity r (decimation in frequency).
+__global__ void __launch_bounds__(kBH / 16) k_os2_segments(const float2* __restrict__ z_one,
+                                                          const float2* const* __restrict__ z_many, int64_t n, int Lp,
+                                                          int NQ, const float2* __restrict__ tw,
+                                                          const float2* __restrict__ twc, float2* __restrict__ Zs_all) {
+  using S = BlockFFTShape<kBH>;
+  extern __shared__ float2 sm[];
+  const int64_t q = blockIdx.x;
+  const int r = blockIdx.y;
+  const int64_t g = blockIdx.z;
+  const float2* z = z_many ? z_many[g] : z_one;
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  float2 v[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int m = tid + t * S::NT;
+    const float2 a = z[(q * Lp + m) & mask];
+    const float2 b = z[(q * Lp + m + kBH) & mask];
+    v[t] = r == 0 ? cadd(a, b) : cmul(csub(a, b), __ldg(twc + m));
+  }
+  block_fft<kBH, -1>(v, sm, tw);
+  float2* out = Zs_all + ((int64_t)g * NQ + q) * kB2 + (int64_t)r * kBH;
+#pragma unroll
+  for (int qq = 0; qq < 16 / S::RL; ++qq)
+#pragma unroll
+    for (int t = 0; t < S::RL; ++t) out[tid + qq * S::NT + t * (kBH / S::RL)] = v[qq * S::RL + t];
+}
+
+// Output blocks [s0, s1) of one neighbour on a CTA pair (both CTAs run the same blocks, so
+// they pass the same cluster barriers).  Zs: the reference's segment spectra [NQ][B2]; C: the
+// neighbour's partition spectra [P][B2], both parity-split.
+template <int Q, bool WINMAX>
+__device__ __forceinline__ void os2_blocks(const float2* __restrict__ Zs, const float2* __restrict__ C, int P,
+                                           int64_t m0, const float2* __restrict__ tw, const float2* __restrict__ twc,
+                                           int64_t n, int NQ, int s0, int s1, float2* __restrict__ zrow,
+                                           unsigned long long* __restrict__ kj, int64_t W, int64_t nw, int fastwin,
+                                           float2* sm) {
+  using S = BlockFFTShape<kBH>;
+  constexpr int NT = S::NT;
+  constexpr int RL = S::RL;
+  constexpr int LP = kB2 / Q;  // outputs start at block position LP (<= BH)
+  constexpr int H = kB2 - LP;
+  static_assert(Q == 2 || Q == 4, "partition ratio");
+  const unsigned r = cluster_rank();
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  const uint32_t peer = cluster_peer_addr(sm, r ^ 1u);
+  const int tb = (int)r * (kBH / 2) + tid * 8;  // this thread's first combined position t
+  for (int s = s0; s < s1; ++s) {
+    float2 v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = make_float2(0.f, 0.f);
+    int sp = s * (Q - 1) - 1;  // segment of partition 0; always < NQ
+    for (int p = 0; p < P; ++p, --sp) {
+      const int q = sp + ((sp < 0) ? NQ : 0);  // sp >= -NQ because P <= NQ
+      const float2* zp = Zs + (int64_t)q * kB2 + (int64_t)r * kBH + tid;
+      const float2* cp = C + (int64_t)p * kB2 + (int64_t)r * kBH + tid;
+#pragma unroll
+      for (int h = 0; h < 16; h += 8) {
+        float2 z[8], c[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          z[t] = __ldcg(zp + (h + t) * NT);
+          c[t] = __ldcg(cp + (h + t) * NT);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          v[h + t].x = fmaf(z[t].x, c[t].x, fmaf(-z[t].y, c[t].y, v[h + t].x));
+          v[h + t].y = fmaf(z[t].x, c[t].y, fmaf(z[t].y, c[t].x, v[h + t].y));
+        }
+      }
+    }
+    block_fft<kBH, +1>(v, sm, tw);
+    __syncthreads();  // the last stage has read shared memory
+#pragma unroll
+    for (int qq = 0; qq < 16 / RL; ++qq)
+#pragma unroll
+      for (int t = 0; t < RL; ++t) sm[tid + qq * NT + t * (kBH / RL)] = v[qq * RL + t];
+    cluster_sync_all();  // both halves in shared memory
+    float2 ylo[8], yhi[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int t = tb + e;
+      const float2 eo = sm[t];
+      const float2 ep = ld_peer_f2(peer + (uint32_t)t * 8u);
+      const float2 e0 = r ? ep : eo;
+      const float2 e1 = r ? eo : ep;
+      const float2 x = cmulc(e1, __ldg(twc + t));  // w^t E1, twc = exp(-2 pi i t / B2)
+      ylo[e] = cadd(e0, x);
+      yhi[e] = csub(e0, x);
+    }
+    cluster_sync_all();  // the peer has read this CTA's half: shared memory may be rewritten
+    const int64_t o0 = (int64_t)s * H;  // pre-relabel index of block position LP
+    const int64_t lim = n - o0;         // positions LP + u with u < lim exist
+    if (!WINMAX) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int tl = tb + e, th = tb + e + kBH;
+        if (tl >= LP && tl - LP < lim) zrow[(o0 + m0 + tl - LP) & mask] = ylo[e];
+        if (th - LP < lim) zrow[(o0 + m0 + th - LP) & mask] = yhi[e];
+      }
+    } else {
+      float ml[8], mh[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        ml[e] = ylo[e].x * ylo[e].x + ylo[e].y * ylo[e].y;
+        mh[e] = yhi[e].x * yhi[e].x + yhi[e].y * yhi[e].y;
+      }
+      // runs of 8 positions: t = tb + e (kept when tb >= LP; LP and tb are multiples of 8)
+      // and t = tb + BH + e (always kept since LP <= BH)
+      auto count = [&](int64_t u0) { return u0 >= lim ? 0 : (lim - u0 >= 8 ? 8 : (int)(lim - u0)); };
+      const int cl = tb >= LP ? count(tb - LP) : 0;
+      const int ch = count(tb + kBH - LP);
+      window_keys<8>(ml, cl, (int)((o0 + m0 + tb - LP) & mask), n, W, nw, fastwin, kj);
+      window_keys<8>(mh, ch, (int)((o0 + m0 + tb + kBH - LP) & mask), n, W, nw, fastwin, kj);
+    }
+  }
+}
+
+template <int Q, bool WINMAX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBH / 16, 1)
+    k_os2(const float2* __restrict__ Zs, const float2* __restrict__ Cs, const int64_t* __restrict__ spec_off,
+          const int* __restrict__ parts, const int* __restrict__ lag0, const int* __restrict__ idx, int y0,
+          const float2* __restrict__ tw, const float2* __restrict__ twc, int64_t n, int NQ, int NB, int SC,
+          float2* __restrict__ z_out, unsigned long long* __restrict__ keys, int64_t W, int64_t nw, int fastwin) {
+  extern __shared__ float2 sm[];
+  const int j = idx[y0 + blockIdx.y];
+  const int s0 = (int)(blockIdx.x >> 1) * SC;
+  const int s1 = min(NB, s0 + SC);
+  os2_blocks<Q, WINMAX>(Zs, Cs + spec_off[j], parts[j], lag0[j], tw, twc, n, NQ, s0, s1,
+                        WINMAX ? nullptr : z_out + (int64_t)j * n, WINMAX ? keys + (int64_t)j * nw : nullptr, W, nw,
+                        fastwin, sm);
+}
+
+// Batched form: cluster (chunk, item) of a grid of (2 nchunk, count) CTAs.
+template <int Q>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBH / 16, 1)
+    k_os2_batched(const OsItem* __restrict__ items, int nchunk, const float2* __restrict__ tw,
+                  const float2* __restrict__ twc, int64_t n, int NQ, int NB, int SC,
+                  unsigned long long* __restrict__ keys, int64_t W, int64_t nw, int fastwin) {
+  extern __shared__ float2 sm[];
+  const OsItem it = items[blockIdx.y];
+  const int s0 = (int)(blockIdx.x >> 1) * SC;
+  const int s1 = min(NB, s0 + SC);
+  os2_blocks<Q, true>(it.Zs, it.C, it.P, it.lag0, tw, twc, n, NQ, s0, s1, nullptr, keys + it.row * nw, W, nw, fastwin,
+                      sm);
+}
+
+// partition spectra of the B2 layout: rows of B2 bins, rounded and stored parity-split
+__global__ void k_os2_round(const double2* __restrict__ spec, int64_t count, double scale, float2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int k = (int)(i & (kB2 - 1));
+  out[(i - k) + (k & 1) * kBH + (k >> 1)] = make_float2((float)(spec[i].x * scale), (float)(spec[i].y * scale));
+}
+
 template <int B>
 size_t os_smem() {
   return sizeof(float2) * BlockFFTShape<B>::SMEM;
@@ -360,6 +561,47 @@ void launch_os(rf_ctx* c, const rf_kernels* kern, const OsBucket& bk, const floa
     fn<<<grid, B / 16, os_smem<B>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>(),
                                           kern->os_parts_d.as<int>(), kern->lag0_d.as<int>(), bk.idx_d.as<int>(), done,
                                           tw, c->n, NQ, NB, SC, z_out, keys, W, nw, fastwin);
+    RF_LAUNCHED();
+  }
+}
+
+// Segment spectra of the pair layout for one reference (z_many == nullptr) or G of them.
+void launch_os2_segments(rf_ctx* c, const float2* z_one, const float2* const* z_many, int G, int Lp, float2* Zs,
+                         cudaStream_t s) {
+  const int NQ = (int)(c->n / Lp);
+  const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
+  const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
+  RF_REQUIRE(G <= 65535, "at most 65535 references per batch");
+  RF_CUDA(cudaFuncSetAttribute(k_os2_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<kBH>()));
+  k_os2_segments<<<dim3((unsigned)NQ, 2, (unsigned)G), kBH / 16, os_smem<kBH>(), s>>>(z_one, z_many, c->n, Lp, NQ, tw,
+                                                                                      twc, Zs);
+  RF_LAUNCHED();
+}
+
+// One layout bucket on CTA pairs: clusters (chunk of SC output blocks, neighbour).
+template <int Q, bool WINMAX>
+void launch_os2(rf_ctx* c, const rf_kernels* kern, const OsBucket& bk, const float2* Zs, float2* z_out,
+                unsigned long long* keys, int64_t W, cudaStream_t s) {
+  constexpr int Lp = kB2 / Q, H = kB2 - Lp;
+  const int NQ = (int)(c->n / Lp);
+  const int NB = (int)((c->n + H - 1) / H);
+  const int count = (int)bk.idx.size();
+  const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
+  const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
+  const int64_t nw = WINMAX ? (c->n + W - 1) / W : 0;
+  // output blocks per cluster: enough clusters for every SM pair several times over
+  int SC = 8;
+  while (SC > 1 && (int64_t)count * ((NB + SC - 1) / SC) < 4LL * c->nsm) SC /= 2;
+  const int nchunk = (NB + SC - 1) / SC;
+  const int fastwin = (WINMAX && W >= 256) ? 1 : 0;  // a warp's 256 outputs of a run span <= 2 windows
+  auto fn = k_os2<Q, WINMAX>;
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<kBH>()));
+  for (int done = 0; done < count; done += 65535) {
+    const int cnt = std::min(65535, count - done);
+    dim3 grid((unsigned)(2 * nchunk), (unsigned)cnt);
+    fn<<<grid, kBH / 16, os_smem<kBH>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>(),
+                                              kern->os_parts_d.as<int>(), kern->lag0_d.as<int>(), bk.idx_d.as<int>(),
+                                              done, tw, twc, c->n, NQ, NB, SC, z_out, keys, W, nw, fastwin);
     RF_LAUNCHED();
   }
 }
@@ -434,6 +676,12 @@ std::vector<float2> block_fft_tables(int64_t off[16]) {
   append_tables<8192>(out);
   off[14] = (int64_t)out.size();
   append_tables<16384>(out);
+  // the pair layout's twiddles exp(-2 pi i m / 32768), m < 16384 (segment split and combine)
+  off[15] = (int64_t)out.size();
+  {
+    const std::vector<double2> w = host_twiddles(kB2);
+    for (int m = 0; m < kBH; ++m) out.push_back(make_float2((float)w[(size_t)m].x, (float)w[(size_t)m].y));
+  }
   return out;
 }
 
@@ -444,8 +692,10 @@ std::vector<float2> block_fft_tables(int64_t off[16]) {
 // 2^20-sample workload and scaled by B log B (F) and B (M) below that, and a fill penalty
 // when the launch has fewer blocks than the GPU holds at once.
 double os_layout_cost(const rf_ctx* c, const std::vector<int>& lengths, int B, int Lp) {
-  static const double F[6] = {0.9, 1.9, 4.2, 9.9, 29.5, 70.3};   // B = 512 .. 16384
-  static const double M[6] = {0.37, 0.73, 1.47, 2.93, 5.1, 10.8};
+  // B = 512 .. 32768; the 32768-point block runs on a CTA pair (two 16384-point transforms
+  // plus the exchange, estimated)
+  static const double F[7] = {0.9, 1.9, 4.2, 9.9, 29.5, 70.3, 155.0};
+  static const double M[7] = {0.37, 0.73, 1.47, 2.93, 5.1, 10.8, 21.6};
   int b = 0;
   while ((512 << b) < B) ++b;
   const int64_t H = B - Lp;
@@ -453,16 +703,16 @@ double os_layout_cost(const rf_ctx* c, const std::vector<int>& lengths, int B, i
   double cost = 0.0;
   for (const int L : lengths) cost += (double)NB * (F[b] + (double)std::max(1, (L + Lp - 1) / Lp) * M[b]);
   const double blocks = (double)NB * (double)lengths.size();
-  const double slots = (double)c->nsm * (16384 / B);
+  const double slots = B > 16384 ? (double)c->nsm / 2 : (double)c->nsm * (16384 / B);
   return blocks < slots ? cost * slots / blocks : cost;
 }
 
 void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, int* B_out, int* Lp_out) {
   double best = 0.0;
   int bB = 0, bL = 0;
-  for (int B = 512; B <= 16384; B *= 2) {
+  for (int B = 512; B <= kB2; B *= 2) {
     if (B > c->n || (block && B != block)) continue;
-    for (int Q = 2; Q <= 8; Q *= 2) {
+    for (int Q = 2; Q <= (B == kB2 ? 4 : 8); Q *= 2) {
       const double cost = os_layout_cost(c, lengths, B, B / Q);
       if (!bB || cost < best) {
         best = cost;
@@ -477,10 +727,10 @@ void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int bloc
 }
 
 static void check_layout(const rf_ctx* c, int B, int Lp) {
-  RF_REQUIRE(B >= 512 && B <= 16384 && (B & (B - 1)) == 0 && B <= c->n, "overlap-save block %d invalid for n=%lld", B,
+  RF_REQUIRE(B >= 512 && B <= kB2 && (B & (B - 1)) == 0 && B <= c->n, "overlap-save block %d invalid for n=%lld", B,
              (long long)c->n);
-  RF_REQUIRE(Lp == B / 2 || Lp == B / 4 || Lp == B / 8, "overlap-save partition length %d must be B/2, B/4 or B/8",
-             Lp);
+  RF_REQUIRE(Lp == B / 2 || Lp == B / 4 || (Lp == B / 8 && B < kB2),
+             "overlap-save partition length %d must be B/2, B/4 or (below 32768) B/8", Lp);
 }
 
 void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts, const int32_t* Bs,
@@ -567,8 +817,12 @@ void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts
       RF_LAUNCHED();
       fft_c2c_f64(in, out, tmp, B, cnt, -1, c->tw64.as<double2>(), c->n, s);
       const int64_t count = (int64_t)cnt * B;
-      k_os_round<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, count, 1.0 / (double)B,
-                                                                  dst + (int64_t)g0 * B);
+      if (B == kB2)
+        k_os2_round<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, count, 1.0 / (double)B,
+                                                                     dst + (int64_t)g0 * B);
+      else
+        k_os_round<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, count, 1.0 / (double)B,
+                                                                    dst + (int64_t)g0 * B);
       RF_LAUNCHED();
     }
     RF_CUDA(cudaStreamSynchronize(s));  // the row buffers are released at the end of the iteration
@@ -586,7 +840,7 @@ void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts
 
 void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s) {
   RF_REQUIRE(kern->dtype == RF_F32, "overlap-save needs the FP32 grid");
-  RF_REQUIRE(B == 0 || (B >= 512 && B <= 16384 && (B & (B - 1)) == 0 && B <= c->n),
+  RF_REQUIRE(B == 0 || (B >= 512 && B <= kB2 && (B & (B - 1)) == 0 && B <= c->n),
              "overlap-save block %d invalid for n=%lld", B, (long long)c->n);
   if (!B || !Lp) {
     RF_REQUIRE(Lp == 0, "a partition length needs a block size");
@@ -618,6 +872,18 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
   // one segment transform and one launch per layout bucket (stream order keeps Zs consistent)
   for (const OsBucket& bk : kern->os_buckets) {
     if (bk.idx.empty()) continue;
+    if (bk.B == kB2) {
+      launch_os2_segments(c, static_cast<const float2*>(z_ref), nullptr, 1, bk.Lp, Zs, s);
+      const bool q2 = bk.B / bk.Lp == 2;
+      if (win) {
+        if (q2) launch_os2<2, true>(c, kern, bk, Zs, nullptr, keys, W, s);
+        else launch_os2<4, true>(c, kern, bk, Zs, nullptr, keys, W, s);
+      } else {
+        if (q2) launch_os2<2, false>(c, kern, bk, Zs, static_cast<float2*>(z_out), nullptr, 0, s);
+        else launch_os2<4, false>(c, kern, bk, Zs, static_cast<float2*>(z_out), nullptr, 0, s);
+      }
+      continue;
+    }
     dispatch_bq(bk.B, bk.B / bk.Lp, [&](auto bc, auto qc) {
       constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
       launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), bk.Lp, Zs, s);
@@ -716,6 +982,28 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     const int B = Bs[b], Lp = Lps[b];
     const int NQ = (int)(n / Lp);
     const int NB = (int)((n + (B - Lp) - 1) / (B - Lp));
+    if (B == kB2) {
+      // CTA pairs: one cluster per (chunk of output blocks, work item), no work counter
+      int SC = 8;
+      while (SC > 1 && cnt * ((NB + SC - 1) / SC) < 4LL * c->nsm) SC /= 2;
+      const int nchunk = (NB + SC - 1) / SC;
+      launch_os2_segments(c, nullptr, c->batch_zptr.as<const float2*>(), G, Lp, c->batch_zs.as<float2>(), s);
+      const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
+      const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
+      const int fastwin = (W >= 256) ? 1 : 0;
+      auto run = [&](auto fn) {
+        RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<kBH>()));
+        for (int64_t done = 0; done < cnt; done += 65535) {
+          const int part = (int)std::min<int64_t>(65535, cnt - done);
+          fn<<<dim3((unsigned)(2 * nchunk), (unsigned)part), kBH / 16, os_smem<kBH>(), s>>>(
+              c->batch_items.as<OsItem>() + first + done, nchunk, tw, twc, n, NQ, NB, SC, keys, W, nw, fastwin);
+          RF_LAUNCHED();
+        }
+      };
+      if (B / Lp == 2) run(k_os2_batched<2>);
+      else run(k_os2_batched<4>);
+      continue;
+    }
     int SC = 8;
     while (SC > 1 && cnt * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
     const int nchunk = (NB + SC - 1) / SC;

@@ -340,7 +340,8 @@ def os_case():
 
 
 @pytest.mark.parametrize("B,Lp", [(512, 256), (512, 128), (512, 64), (1024, 512), (8192, 4096), (8192, 2048),
-                                  (8192, 1024), (16384, 8192), (16384, 4096), (16384, 2048)])
+                                  (8192, 1024), (16384, 8192), (16384, 4096), (16384, 2048), (32768, 16384),
+                                  (32768, 8192)])
 def test_reconstruct_os_edge_lengths(torch, os_case, B, Lp):
     """Overlap-save with block B and partitions of Lp taps (hop B - Lp, which does not divide
     n for Lp < B/2, so the last block is partial) against the oracle's direct sum; window
@@ -372,6 +373,7 @@ def test_reconstruct_os_edge_lengths(torch, os_case, B, Lp):
 
 
 @pytest.mark.parametrize("cuts,blocks,parts", [([0, 1000], [4096, 16384], [1024, 4096]),
+                                               ([0, 2000, 8000], [4096, 16384, 32768], [1024, 4096, 16384]),
                                                ([0, 64, 2048, 8192], [1024, 512, 8192, 16384],
                                                 [128, 256, 2048, 8192])])
 def test_reconstruct_os_length_buckets(torch, os_case, cuts, blocks, parts):
@@ -418,7 +420,7 @@ def test_batched_length_buckets_match_per_group(torch):
     allL = np.concatenate([k.length for k in kerns])
     cut = int(np.median(allL)) + 1
     for k in kerns:
-        k.prepare_buckets([0, cut], [4096, 16384], [1024, 4096])
+        k.prepare_buckets([0, cut], [4096, 32768], [1024, 8192])   # the long bucket on CTA pairs
     W = cfg.window
     P, A = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W)
     row = 0
