@@ -390,9 +390,42 @@ __global__ void __launch_bounds__(kBH / 16) k_os2_segments(const float2* __restr
     for (int t = 0; t < S::RL; ++t) out[tid + qq * S::NT + t * (kBH / S::RL)] = v[qq * S::RL + t];
 }
 
-// Output blocks [s0, s1) of one neighbour on a CTA pair (both CTAs run the same blocks, so
-// they pass the same cluster barriers).  Zs: the reference's segment spectra [NQ][B2]; C: the
-// neighbour's partition spectra [P][B2], both parity-split.
+// Spectral products of one output block for the bins of parity r (as os_blocks, on the
+// parity-split spectra).
+template <int Q>
+__device__ __forceinline__ void os2_products(float2 (&v)[16], const float2* __restrict__ Zs,
+                                             const float2* __restrict__ C, int P, int NQ, int s, unsigned r, int tid) {
+  constexpr int NT = kBH / 16;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) v[t] = make_float2(0.f, 0.f);
+  int sp = s * (Q - 1) - 1;  // segment of partition 0; always < NQ
+  for (int p = 0; p < P; ++p, --sp) {
+    const int q = sp + ((sp < 0) ? NQ : 0);  // sp >= -NQ because P <= NQ
+    const float2* zp = Zs + (int64_t)q * kB2 + (int64_t)r * kBH + tid;
+    const float2* cp = C + (int64_t)p * kB2 + (int64_t)r * kBH + tid;
+#pragma unroll
+    for (int h = 0; h < 16; h += 8) {
+      float2 z[8], c[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        z[t] = __ldcg(zp + (h + t) * NT);
+        c[t] = __ldcg(cp + (h + t) * NT);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        v[h + t].x = fmaf(z[t].x, c[t].x, fmaf(-z[t].y, c[t].y, v[h + t].x));
+        v[h + t].y = fmaf(z[t].x, c[t].y, fmaf(z[t].y, c[t].x, v[h + t].y));
+      }
+    }
+  }
+}
+
+// Output blocks [s0, s1) of one neighbour on a CTA pair.  Both CTAs run the same blocks and
+// so pass the same cluster barriers: per block, transform, store the half in shared memory,
+// barrier, combine (reading the peer's half), barrier (the peer is done with this CTA's half,
+// so the next transform may rewrite it), window scan.
+// Zs: the reference's segment spectra [NQ][B2]; C: the neighbour's partition spectra [P][B2],
+// both parity-split.
 template <int Q, bool WINMAX>
 __device__ __forceinline__ void os2_blocks(const float2* __restrict__ Zs, const float2* __restrict__ C, int P,
                                            int64_t m0, const float2* __restrict__ tw, const float2* __restrict__ twc,
@@ -409,31 +442,12 @@ __device__ __forceinline__ void os2_blocks(const float2* __restrict__ Zs, const 
   const int tid = threadIdx.x;
   const int64_t mask = n - 1;
   const uint32_t peer = cluster_peer_addr(sm, r ^ 1u);
-  const int tb = (int)r * (kBH / 2) + tid * 8;  // this thread's first combined position t
+  const int tb = (int)r * (kBH / 2) + tid * 8;  // this thread's first position in the scan
+  float* mag_lo = reinterpret_cast<float*>(sm + S::SMEM);  // |y|^2 of t, per CTA range
+  float* mag_hi = mag_lo + kBH / 2;                         // |y|^2 of t + BH
   for (int s = s0; s < s1; ++s) {
     float2 v[16];
-#pragma unroll
-    for (int t = 0; t < 16; ++t) v[t] = make_float2(0.f, 0.f);
-    int sp = s * (Q - 1) - 1;  // segment of partition 0; always < NQ
-    for (int p = 0; p < P; ++p, --sp) {
-      const int q = sp + ((sp < 0) ? NQ : 0);  // sp >= -NQ because P <= NQ
-      const float2* zp = Zs + (int64_t)q * kB2 + (int64_t)r * kBH + tid;
-      const float2* cp = C + (int64_t)p * kB2 + (int64_t)r * kBH + tid;
-#pragma unroll
-      for (int h = 0; h < 16; h += 8) {
-        float2 z[8], c[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          z[t] = __ldcg(zp + (h + t) * NT);
-          c[t] = __ldcg(cp + (h + t) * NT);
-        }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          v[h + t].x = fmaf(z[t].x, c[t].x, fmaf(-z[t].y, c[t].y, v[h + t].x));
-          v[h + t].y = fmaf(z[t].x, c[t].y, fmaf(z[t].y, c[t].x, v[h + t].y));
-        }
-      }
-    }
+    os2_products<Q>(v, Zs, C, P, NQ, s, r, tid);
     block_fft<kBH, +1>(v, sm, tw);
     __syncthreads();  // the last stage has read shared memory
 #pragma unroll
@@ -441,37 +455,35 @@ __device__ __forceinline__ void os2_blocks(const float2* __restrict__ Zs, const 
 #pragma unroll
       for (int t = 0; t < RL; ++t) sm[tid + qq * NT + t * (kBH / RL)] = v[qq * RL + t];
     cluster_sync_all();  // both halves in shared memory
-    float2 ylo[8], yhi[8];
+    // combine: this CTA takes t = r BH/2 + e NT + tid, e < 8 (consecutive lanes, consecutive t)
+    const int64_t o0 = (int64_t)s * H;  // pre-relabel index of block position LP
+    const int64_t lim = n - o0;         // positions LP + u with u < lim exist
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int t = tb + e;
+      const int t = (int)r * (kBH / 2) + e * NT + tid;
       const float2 eo = sm[t];
       const float2 ep = ld_peer_f2(peer + (uint32_t)t * 8u);
       const float2 e0 = r ? ep : eo;
       const float2 e1 = r ? eo : ep;
       const float2 x = cmulc(e1, __ldg(twc + t));  // w^t E1, twc = exp(-2 pi i t / B2)
-      ylo[e] = cadd(e0, x);
-      yhi[e] = csub(e0, x);
+      const float2 ylo = cadd(e0, x), yhi = csub(e0, x);
+      if (!WINMAX) {
+        if (t >= LP && t - LP < lim) zrow[(o0 + m0 + t - LP) & mask] = ylo;
+        if (t + kBH - LP < lim) zrow[(o0 + m0 + t + kBH - LP) & mask] = yhi;
+      } else {
+        mag_lo[e * NT + tid] = ylo.x * ylo.x + ylo.y * ylo.y;
+        mag_hi[e * NT + tid] = yhi.x * yhi.x + yhi.y * yhi.y;
+      }
     }
-    cluster_sync_all();  // the peer has read this CTA's half: shared memory may be rewritten
-    const int64_t o0 = (int64_t)s * H;  // pre-relabel index of block position LP
-    const int64_t lim = n - o0;         // positions LP + u with u < lim exist
-    if (!WINMAX) {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int tl = tb + e, th = tb + e + kBH;
-        if (tl >= LP && tl - LP < lim) zrow[(o0 + m0 + tl - LP) & mask] = ylo[e];
-        if (th - LP < lim) zrow[(o0 + m0 + th - LP) & mask] = yhi[e];
-      }
-    } else {
+    cluster_sync_all();  // the peer has read this CTA's half; the magnitudes are in place
+    if (WINMAX) {
+      // runs of 8 consecutive positions per thread: t = tb + e (kept when tb >= LP; LP and tb
+      // are multiples of 8) and t = tb + BH + e (always kept since LP <= BH)
       float ml[8], mh[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        ml[e] = ylo[e].x * ylo[e].x + ylo[e].y * ylo[e].y;
-        mh[e] = yhi[e].x * yhi[e].x + yhi[e].y * yhi[e].y;
-      }
-      // runs of 8 positions: t = tb + e (kept when tb >= LP; LP and tb are multiples of 8)
-      // and t = tb + BH + e (always kept since LP <= BH)
+      *reinterpret_cast<float4*>(ml) = *reinterpret_cast<const float4*>(mag_lo + tid * 8);
+      *reinterpret_cast<float4*>(ml + 4) = *reinterpret_cast<const float4*>(mag_lo + tid * 8 + 4);
+      *reinterpret_cast<float4*>(mh) = *reinterpret_cast<const float4*>(mag_hi + tid * 8);
+      *reinterpret_cast<float4*>(mh + 4) = *reinterpret_cast<const float4*>(mag_hi + tid * 8 + 4);
       auto count = [&](int64_t u0) { return u0 >= lim ? 0 : (lim - u0 >= 8 ? 8 : (int)(lim - u0)); };
       const int cl = tb >= LP ? count(tb - LP) : 0;
       const int ch = count(tb + kBH - LP);
@@ -517,6 +529,10 @@ __global__ void k_os2_round(const double2* __restrict__ spec, int64_t count, dou
   const int k = (int)(i & (kB2 - 1));
   out[(i - k) + (k & 1) * kBH + (k >> 1)] = make_float2((float)(spec[i].x * scale), (float)(spec[i].y * scale));
 }
+
+// dynamic shared memory of the pair kernels: the 16384-point transform plus two 8192-float
+// |y|^2 staging rows
+size_t os2_smem();
 
 template <int B>
 size_t os_smem() {
@@ -565,6 +581,8 @@ void launch_os(rf_ctx* c, const rf_kernels* kern, const OsBucket& bk, const floa
   }
 }
 
+size_t os2_smem() { return os_smem<kBH>() + sizeof(float) * kBH; }
+
 // Segment spectra of the pair layout for one reference (z_many == nullptr) or G of them.
 void launch_os2_segments(rf_ctx* c, const float2* z_one, const float2* const* z_many, int G, int Lp, float2* Zs,
                          cudaStream_t s) {
@@ -595,11 +613,11 @@ void launch_os2(rf_ctx* c, const rf_kernels* kern, const OsBucket& bk, const flo
   const int nchunk = (NB + SC - 1) / SC;
   const int fastwin = (WINMAX && W >= 256) ? 1 : 0;  // a warp's 256 outputs of a run span <= 2 windows
   auto fn = k_os2<Q, WINMAX>;
-  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<kBH>()));
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os2_smem()));
   for (int done = 0; done < count; done += 65535) {
     const int cnt = std::min(65535, count - done);
     dim3 grid((unsigned)(2 * nchunk), (unsigned)cnt);
-    fn<<<grid, kBH / 16, os_smem<kBH>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>(),
+    fn<<<grid, kBH / 16, os2_smem(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>(),
                                               kern->os_parts_d.as<int>(), kern->lag0_d.as<int>(), bk.idx_d.as<int>(),
                                               done, tw, twc, c->n, NQ, NB, SC, z_out, keys, W, nw, fastwin);
     RF_LAUNCHED();
@@ -992,10 +1010,10 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
       const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
       const int fastwin = (W >= 256) ? 1 : 0;
       auto run = [&](auto fn) {
-        RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<kBH>()));
+        RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os2_smem()));
         for (int64_t done = 0; done < cnt; done += 65535) {
           const int part = (int)std::min<int64_t>(65535, cnt - done);
-          fn<<<dim3((unsigned)(2 * nchunk), (unsigned)part), kBH / 16, os_smem<kBH>(), s>>>(
+          fn<<<dim3((unsigned)(2 * nchunk), (unsigned)part), kBH / 16, os2_smem(), s>>>(
               c->batch_items.as<OsItem>() + first + done, nchunk, tw, twc, n, NQ, NB, SC, keys, W, nw, fastwin);
           RF_LAUNCHED();
         }
