@@ -39,6 +39,7 @@ import workload  # noqa: E402
 L2_BYTES = 129 * 1024 * 1024
 GATE_THRESHOLD = 3e-5
 FP32_LANES_PER_SM = 128
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 : BF16 tensor rates of the part
 
 
 def parse():
@@ -49,7 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--algo", default="auto", choices=["auto", "direct", "os", "gemm"])
-    ap.add_argument("--prec", default=None, choices=["native", "bf16", "bf16x3", "bf16x6", "bf16x9"],
+    ap.add_argument("--prec", default=None, choices=["native", "bf16", "bf16x3", "bf16x6", "bf16x9", "3xtf32"],
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default)")
@@ -285,7 +286,8 @@ def ncu_traffic(kernel: str, layout: str = None):
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
-        rec = json.load(open(path))[kernel]
+        recs = json.load(open(path))
+        rec = recs.get(f"{kernel}@{layout}", recs[kernel])
         if layout is not None and rec.get("layout") != layout:
             return None
         m = hashlib.sha256()
@@ -541,25 +543,33 @@ def main():
     sm_max = 2070.0
     if algo_used == "gemm":
         # tensor-pipe work actually issued: per 128-output tile and group of NJ neighbours,
-        # LP/16 K steps x 2 planes x products, each 2 x 128 x (2 NJ) x 16 flops
-        terms = {"bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 3}[prec]
-        nprod = {"bf16": 1, "bf16x3": 3, "bf16x6": 6, "bf16x9": 9}[prec]
+        # LP taps x 2 planes x products, each 2 x 128 x (2 NJ) flops per tap (the chunk KC
+        # and group width NJ follow the library's choice for the precision)
+        terms = {"bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 3, "3xtf32": 2}[prec]
+        nprod = {"bf16": 1, "bf16x3": 3, "bf16x6": 6, "bf16x9": 9, "3xtf32": 3}[prec]
+        ebytes = 4 if prec == "3xtf32" else 2
         mma_flops = 0.0
         for k in kerns:
             L16 = max(16, -(-int(k.length.max()) // 16) * 16)
+            NJ = 16 if k.k <= 16 else {"bf16": 128, "bf16x3": 48, "bf16x6": 40, "bf16x9": 24, "3xtf32": 48}[prec]
             KC = min(128, L16)
+            while KC > 16 and (2 * terms * ((30 + KC // 4) if ebytes == 4 else (15 + KC // 8)) * 128
+                               + 2 * terms * 2 * NJ * KC * ebytes + 1024) > 160 * 1024:
+                KC //= 2
             LP = KC * (-(-L16 // KC))
-            NJ = 16 if k.k <= 16 else {"bf16": 128, "bf16x3": 48, "bf16x6": 40, "bf16x9": 24}[prec]
             groups = -(-k.k // NJ)
-            mma_flops += (n / 128) * groups * (LP / 16) * 2 * nprod * (2 * 128 * 2 * NJ * 16)
+            mma_flops += (n / 128) * groups * LP * 2 * nprod * (2 * 128 * 2 * NJ)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak_tflops = float(peaks.get("bf16_tflops", 1900.0))
+        if prec == "3xtf32":
+            peak_tflops *= TF32_PER_BF16   # the TF32 pipe's own peak: measured BF16 x nominal ratio
         achieved = mma_flops / (rec_avg_ms / 1e3) / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": ncu_traffic("k_gemm", prec) if args.config == 3 else None,
                     "kernel": f"reconstruct (tcgen05 Hankel GEMM, {prec}, one reference)",
                     "peak_note": ("measured cuBLAS bf16 burst (MEASURED_PEAKS.json)" if peaks else "fallback 1.9 PF/s") +
+                                 (" x 1.1/2.25 nominal TF32:BF16" if prec == "3xtf32" else "") +
                                  "; achieved counts the MMA flops issued (split terms included)",
                     "algorithmic_tflops": flops / (rec_avg_ms / 1e3) / 1e12,
                     "kernel_ms": rec_avg_ms, "share_of_step": rec_avg_ms / ms_per_step}

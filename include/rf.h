@@ -75,13 +75,16 @@ typedef enum {
  * overlap-save).  The tensor-core form (RF_ALGO_GEMM) splits every z_ref and tap value into
  * BF16 terms x = x0 + x1 + x2 (x_k = bf16 of the remainder) and accumulates in FP32:
  * RF_PREC_BF16 keeps x0 y0 (plain BF16, about 3 significant digits), RF_PREC_BF16X3 adds
- * x0 y1 + x1 y0, RF_PREC_BF16X6 adds x0 y2 + x1 y1 + x2 y0, RF_PREC_BF16X9 all nine products. */
+ * x0 y1 + x1 y0, RF_PREC_BF16X6 adds x0 y2 + x1 y1 + x2 y0, RF_PREC_BF16X9 all nine products.
+ * RF_PREC_3XTF32 splits into two TF32 terms (x0 = tf32(x), x1 = tf32(x - x0), round to
+ * nearest) and keeps x0 y0 + x0 y1 + x1 y0 on the TF32 tensor pipe (half the BF16 rate). */
 typedef enum {
   RF_PREC_NATIVE = 0,
   RF_PREC_BF16 = 1,
   RF_PREC_BF16X3 = 2,
   RF_PREC_BF16X6 = 3,
-  RF_PREC_BF16X9 = 4
+  RF_PREC_BF16X9 = 4,
+  RF_PREC_3XTF32 = 5
 } rf_prec;
 
 /* A non-spinning stationary-phase inspiral (App. A, Eq. A1): h(f) = B(f) exp(-i Psi(f)),

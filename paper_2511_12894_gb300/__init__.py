@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "librf.so")
 RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ETIMEOUT, RF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 RF_F64, RF_F32 = 0, 1
 ALGOS = {"auto": 0, "direct": 1, "os": 2, "gemm": 3}
-PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
+PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4, "3xtf32": 5}
 
 EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",

@@ -166,8 +166,9 @@ rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out) {
     // overlap-save segment spectra plus packed window keys for windows of >= 16 samples
     const size_t bytes = os_workspace_bytes(ctx, k_max, 16, 8);  // the largest partition ratio
     ctx->scratch.ensure(bytes);
-    // BF16 planes of z_ref for the tensor-core path, for taps up to the segment length
-    const size_t planes = gemm_zplanes_bytes(ctx->n, ctx->n + 128, 3);
+    // split planes of z_ref for the tensor-core path, for taps up to the segment length
+    const size_t planes = std::max(gemm_zplanes_bytes(ctx->n, ctx->n + 128, RF_PREC_BF16X9),
+                                   gemm_zplanes_bytes(ctx->n, ctx->n + 128, RF_PREC_3XTF32));
     ctx->scratch2.ensure(planes);
     ctx->reserved = bytes;
     if (bytes_out) *bytes_out = (int64_t)(bytes + planes);
@@ -371,13 +372,13 @@ static int check_recon(rf_ctx* ctx, const void* z_ref, const rf_kernels* kern, i
   check_dev(z_ref, "z_ref");
   RF_REQUIRE(algo == RF_ALGO_AUTO || algo == RF_ALGO_DIRECT || algo == RF_ALGO_OS || algo == RF_ALGO_GEMM,
              "unknown algo %d", algo);
-  RF_REQUIRE(prec >= RF_PREC_NATIVE && prec <= RF_PREC_BF16X9, "unknown prec %d", prec);
+  RF_REQUIRE(prec >= RF_PREC_NATIVE && prec <= RF_PREC_3XTF32, "unknown prec %d", prec);
   if (algo == RF_ALGO_AUTO && kern->tuned_algo && prec == RF_PREC_NATIVE) {
     algo = kern->tuned_algo;
     prec = kern->tuned_prec;
   }
   if (algo == RF_ALGO_GEMM) {
-    RF_REQUIRE(prec != RF_PREC_NATIVE, "the tensor-core form needs a split precision (RF_PREC_BF16*)");
+    RF_REQUIRE(prec != RF_PREC_NATIVE, "the tensor-core form needs a split precision (RF_PREC_BF16* or RF_PREC_3XTF32)");
     if (kern->max_len > gemm_max_len() || ctx->n % 128 != 0) {
       set_error("the tensor-core form takes kernels of at most %d taps and n a multiple of 128", gemm_max_len());
       throw Fail{RF_EUNSUPPORTED};

@@ -22,6 +22,13 @@
 // its own tensor-memory tile, and the block adds the tiles in FP32 registers (round to
 // nearest), corrections apart from the leading product.  Separate tiles also keep
 // consecutive MMAs independent, which the tensor pipe needs to overlap short (N = 32) MMAs.
+//
+// 3xTF32 runs the same tiles with kind::tf32 MMAs: x = x0 + x1, x0 = tf32(x) and
+// x1 = tf32(x - x0) (each TF32 term carries 11 significant bits, so x1 resolves x to about
+// 2^-22), products (0,0), (0,1), (1,0).  A TF32 core matrix row is 16 bytes = 4 values and
+// an MMA spans K = 8, so the Hankel core matrix at row block r and K block q starts at
+// z[b + 8r + 4q], i.e. depends on d = 2r + q: consecutive d are the K neighbours and d + 2
+// the next row block.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -49,9 +56,25 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
-// kind::f16 instruction descriptor: BF16 A and B (K-major), FP32 D, M = 128, N.
-__host__ __device__ constexpr uint32_t mma_idesc_bf16(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kGemmM >> 4) << 24);
+// Instruction descriptor: FP32 D, K-major A and B of format fmt (kind::f16: 1 = BF16;
+// kind::tf32: 2 = TF32), M = 128, N.
+__host__ __device__ constexpr uint32_t mma_idesc(int N, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kGemmM >> 4) << 24);
+}
+
+// Operand format of a split precision: TF32 terms are 4-byte words (core-matrix rows of 4
+// values, K = 8 per MMA), BF16 terms 2-byte (rows of 8 values, K = 16 per MMA).
+__host__ __device__ constexpr bool prec_tf32(int prec) { return prec == RF_PREC_3XTF32; }
+__host__ __device__ constexpr int prec_ebytes(int prec) { return prec_tf32(prec) ? 4 : 2; }
+// distinct Hankel core matrices of a K chunk of KC taps (d = r + q, or 2r + q for TF32)
+__host__ __device__ constexpr int hankel_cores(int prec, int KC) {
+  return prec_tf32(prec) ? 30 + KC / 4 : 15 + KC / 8;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 template <typename R>
@@ -63,21 +86,28 @@ __device__ __forceinline__ void split3(R v, __nv_bfloat16& s0, __nv_bfloat16& s1
   s2 = __float2bfloat16_rn((float)r2);
 }
 
+template <typename R>
+__device__ __forceinline__ void split2_tf32(R v, float& s0, float& s1) {
+  s0 = tf32_rna((float)v);
+  s1 = tf32_rna((float)(v - (R)s0));
+}
+
 // Product pairs (A term, B term) of each precision, in issue order.
 __host__ __device__ constexpr int prec_products(int prec) {
-  return prec == RF_PREC_BF16 ? 1 : prec == RF_PREC_BF16X3 ? 3 : prec == RF_PREC_BF16X6 ? 6 : 9;
+  return prec == RF_PREC_BF16 ? 1 : (prec == RF_PREC_BF16X3 || prec == RF_PREC_3XTF32) ? 3 : prec == RF_PREC_BF16X6 ? 6 : 9;
 }
 __host__ __device__ constexpr int prec_terms(int prec) {
-  return prec == RF_PREC_BF16 ? 1 : prec == RF_PREC_BF16X3 ? 2 : 3;
+  return prec == RF_PREC_BF16 ? 1 : (prec == RF_PREC_BF16X3 || prec == RF_PREC_3XTF32) ? 2 : 3;
 }
 
 // Tap operands of one neighbour group, prepared once per kernel set, chunk by chunk:
-// [K chunk c][plane (r, i)][term][N/8 row blocks][KC/8 K blocks][8 rows][8 BF16], taps in
-// reverse (t = c KC + t_local, tap l = LP - 1 - t), columns (2j, 2j+1) = (re, im) of
-// neighbour j of the group; plane r holds (cr, ci), plane i holds (-ci, cr).
+// [K chunk c][plane (r, i)][term][N/8 row blocks][KC/8 K blocks][8 rows][8 BF16] (TF32:
+// [KC/4 K blocks][8 rows][4 words]), taps in reverse (t = c KC + t_local, tap l = LP - 1 - t),
+// columns (2j, 2j+1) = (re, im) of neighbour j of the group; plane r holds (cr, ci), plane i
+// holds (-ci, cr).
 template <typename V>
 __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restrict__ off, const int* __restrict__ len,
-                              int k, int NJ, int KC, int NCK, int terms, __nv_bfloat16* __restrict__ out) {
+                              int k, int NJ, int KC, int NCK, int terms, bool tf32, void* __restrict__ out_v) {
   using R = typename real_of<V>::type;
   const int g = blockIdx.y;
   const int N = 2 * NJ;
@@ -99,24 +129,36 @@ __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restr
     }
     const R vr = (col & 1) ? ci : cr;
     const R vi = (col & 1) ? cr : -ci;
-    __nv_bfloat16 r0, r1, r2, i0, i1, i2;
-    split3<R>(vr, r0, r1, r2);
-    split3<R>(vi, i0, i1, i2);
-    __nv_bfloat16* oc = out + ((int64_t)g * NCK + c) * 2 * terms * per_plane_term;
-    const int64_t pos = (int64_t)(col / 8) * (KC / 8) * 64 + (tl / 8) * 64 + (col % 8) * 8 + (tl % 8);
-    const __nv_bfloat16 rr[3] = {r0, r1, r2}, ii[3] = {i0, i1, i2};
-    for (int s = 0; s < terms; ++s) {
-      oc[(0 * terms + s) * per_plane_term + pos] = rr[s];
-      oc[(1 * terms + s) * per_plane_term + pos] = ii[s];
+    const int64_t chunk = ((int64_t)g * NCK + c) * 2 * terms * per_plane_term;
+    if (tf32) {
+      float rr[2], ii[2];
+      split2_tf32<R>(vr, rr[0], rr[1]);
+      split2_tf32<R>(vi, ii[0], ii[1]);
+      float* oc = static_cast<float*>(out_v) + chunk;
+      const int64_t pos = (int64_t)(col / 8) * (KC / 4) * 32 + (tl / 4) * 32 + (col % 8) * 4 + (tl % 4);
+      for (int s = 0; s < terms; ++s) {
+        oc[(0 * terms + s) * per_plane_term + pos] = rr[s];
+        oc[(1 * terms + s) * per_plane_term + pos] = ii[s];
+      }
+    } else {
+      __nv_bfloat16 rr[3], ii[3];
+      split3<R>(vr, rr[0], rr[1], rr[2]);
+      split3<R>(vi, ii[0], ii[1], ii[2]);
+      __nv_bfloat16* oc = static_cast<__nv_bfloat16*>(out_v) + chunk;
+      const int64_t pos = (int64_t)(col / 8) * (KC / 8) * 64 + (tl / 8) * 64 + (col % 8) * 8 + (tl % 8);
+      for (int s = 0; s < terms; ++s) {
+        oc[(0 * terms + s) * per_plane_term + pos] = rr[s];
+        oc[(1 * terms + s) * per_plane_term + pos] = ii[s];
+      }
     }
   }
 }
 
-// z_ref split into BF16 planes once per call: plane (p, s) holds term s of the real (p = 0)
-// or imaginary (p = 1) part, element x of the circular sequence at index x + pad for
-// x in [-pad, n + tail); pad = 7 (mod 8) makes every Hankel row-block window 16-byte aligned.
-// The split runs in FP32 (complex128 inputs are rounded to FP32 first, well inside the
-// three-term resolution).
+// z_ref split into BF16 (or TF32) planes once per call: plane (p, s) holds term s of the
+// real (p = 0) or imaginary (p = 1) part, element x of the circular sequence at index x + pad
+// for x in [-pad, n + tail); pad = 7 (mod 8) makes every Hankel row-block window 16-byte
+// aligned.  The split runs in FP32 (complex128 inputs are rounded to FP32 first, well inside
+// the resolution of the split terms).
 static int64_t gemm_zpad(int64_t LP) { return ((LP + 8 + 7) / 8) * 8 + 7; }
 static int64_t gemm_zlen(int64_t n, int64_t LP) { return ((gemm_zpad(LP) + n + 160 + 7) / 8) * 8; }
 
@@ -132,6 +174,21 @@ __global__ void k_gemm_split_z(const V* __restrict__ z, int64_t n, int64_t pad, 
   for (int s = 0; s < terms; ++s) {
     planes[(int64_t)(0 * terms + s) * len + idx] = r[s];
     planes[(int64_t)(1 * terms + s) * len + idx] = i[s];
+  }
+}
+
+template <typename V>
+__global__ void k_gemm_split_z_tf32(const V* __restrict__ z, int64_t n, int64_t pad, int64_t len,
+                                    float* __restrict__ planes) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= len) return;
+  const V v = z[(idx - pad) & (n - 1)];
+  float r[2], i[2];
+  split2_tf32<float>((float)v.x, r[0], r[1]);
+  split2_tf32<float>((float)v.y, i[0], i[1]);
+  for (int s = 0; s < 2; ++s) {
+    planes[(int64_t)(0 * 2 + s) * len + idx] = r[s];
+    planes[(int64_t)(1 * 2 + s) * len + idx] = i[s];
   }
 }
 
@@ -175,9 +232,9 @@ __host__ __device__ constexpr int tile_col(int prec, int ta, int N) {
 // (K step, plane, A term) whose N spans every B term paired with that A term, and folds
 // the chunk's tiles into FP32 register sums (plain BF16 accumulates in tensor memory).
 template <typename V, int NJ, int PREC, bool WINMAX>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __nv_bfloat16* __restrict__ zp, int64_t zpad,
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict__ zp_v, int64_t zpad,
                                                           int64_t zlen, int64_t n,
-                                                          const __nv_bfloat16* __restrict__ Bg, int KC, int NCK,
+                                                          const void* __restrict__ Bg, int KC, int NCK,
                                                           int k, const int* __restrict__ lag0, int TM,
                                                           V* __restrict__ z_out, unsigned long long* __restrict__ keys,
                                                           int64_t W, int64_t nw, int tmem_cols,
@@ -186,6 +243,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __nv_bfloat16* _
   constexpr int N = 2 * NJ;                // columns per B term
   constexpr int TERMS = prec_terms(PREC);
   constexpr bool FOLD = PREC != RF_PREC_BF16;
+  constexpr bool TF = prec_tf32(PREC);
+  constexpr int EB = prec_ebytes(PREC);     // bytes per operand value
   static_assert(N % 16 == 0 && N * b_terms_for(PREC, 0) <= 256, "MMA width");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
@@ -193,16 +252,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __nv_bfloat16* _
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = blockIdx.y;
   const int LP = KC * NCK;
-  const int nH = 15 + KC / 8;                         // distinct Hankel core matrices per chunk
+  const int nH = hankel_cores(PREC, KC);              // distinct Hankel core matrices per chunk
   const int a_bytes = nH * 128;                       // per (plane, term)
-  const int b_bytes = N * KC * 2;                     // per (plane, term)
+  const int b_bytes = N * KC * EB;                    // per (plane, term)
   unsigned char* sA = smem;                           // [plane][term][nH][128 B]
-  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][N/8][KC/8][128 B]
+  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][N/8][KC/(16/EB)][128 B]
   const int64_t mask = n - 1;
-  const __nv_bfloat16* Bgrp = Bg + (int64_t)g * NCK * 2 * TERMS * N * KC;
+  const unsigned char* Bgrp = static_cast<const unsigned char*>(Bg) + (int64_t)g * NCK * 2 * TERMS * b_bytes;
 
   auto stage_b = [&](int c) {
-    const uint4* src = reinterpret_cast<const uint4*>(Bgrp + (int64_t)c * 2 * TERMS * N * KC);
+    const uint4* src = reinterpret_cast<const uint4*>(Bgrp + (int64_t)c * 2 * TERMS * b_bytes);
     uint4* dst = reinterpret_cast<uint4*>(sB);
     const int cnt = 2 * TERMS * b_bytes / 16;
     for (int e = tid; e < cnt; e += kGemmThreads) dst[e] = src[e];
@@ -240,46 +299,69 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __nv_bfloat16* _
       // b + c KC + 8d gives all eight rows by funnel shifts.  (One 16-byte row per thread
       // avoids the shared-memory bank conflicts of these stores but measured slower: five
       // scalar loads per row instead of two vector loads per eight rows.)
+      // (TF32: row a of H_d is z[b + c KC + 4d + a + e], e < 4, words a..a+3 of the aligned
+      // 12-word window at b + c KC + 4d.)
       const int64_t bc = b + (int64_t)c * KC + zpad;  // plane index of the chunk's first element
       for (int task = tid; task < 2 * TERMS * nH; task += kGemmThreads) {
         const int pt = task / nH, d = task - pt * nH;
-        const uint4* src = reinterpret_cast<const uint4*>(zp + (int64_t)pt * zlen + bc + 8 * d);
-        const uint4 lo = src[0], hi = src[1];
-        const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
         unsigned char* dst = sA + pt * a_bytes + d * 128;
+        if constexpr (TF) {
+          const uint4* src =
+              reinterpret_cast<const uint4*>(static_cast<const float*>(zp_v) + (int64_t)pt * zlen + bc + 4 * d);
+          const uint4 p0 = src[0], p1 = src[1], p2 = src[2];
+          const uint32_t w[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          uint32_t o[4];
+          for (int a = 0; a < 8; ++a)
+            *reinterpret_cast<uint4*>(dst + a * 16) = make_uint4(w[a], w[a + 1], w[a + 2], w[a + 3]);
+        } else {
+          const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(zp_v) +
+                                                            (int64_t)pt * zlen + bc + 8 * d);
+          const uint4 lo = src[0], hi = src[1];
+          const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) o[q] = __funnelshift_r(w[a / 2 + q], w[a / 2 + q + 1], (a & 1) * 16);
-          *reinterpret_cast<uint4*>(dst + a * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+          for (int a = 0; a < 8; ++a) {
+            uint32_t o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = __funnelshift_r(w[a / 2 + q], w[a / 2 + q + 1], (a & 1) * 16);
+            *reinterpret_cast<uint4*>(dst + a * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+          }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // K step ks adds ks * 256 bytes to each start address, i.e. ks * 16 to the
-        // descriptor's low field (addresses stay below 256 KB, so the field never carries)
+        // A K step (32 bytes of every row: K = 16 BF16 or 8 TF32 values) spans two core
+        // matrices along K, so step ks adds ks * 256 bytes to each start address, i.e. ks * 16
+        // to the descriptor's low field (addresses stay below 256 KB, so the field never
+        // carries).  Leading byte offset = next core matrix along K, stride byte offset = next
+        // 8-row block along M or N.
         uint64_t adesc[2 * TERMS], bdesc[2];
 #pragma unroll
-        for (int i = 0; i < 2 * TERMS; ++i) adesc[i] = smem_desc(smem_u32(sA + i * a_bytes), 128, 128);
+        for (int i = 0; i < 2 * TERMS; ++i) adesc[i] = smem_desc(smem_u32(sA + i * a_bytes), 128, TF ? 256 : 128);
 #pragma unroll
-        for (int pl = 0; pl < 2; ++pl) bdesc[pl] = smem_desc(smem_u32(sB + pl * TERMS * b_bytes), 128, KC * 16);
-        for (int ks = 0; ks < KC / 16; ++ks) {
+        for (int pl = 0; pl < 2; ++pl)
+          bdesc[pl] = smem_desc(smem_u32(sB + pl * TERMS * b_bytes), 128, KC * 8 * EB);
+        for (int ks = 0; ks < KC * EB / 32; ++ks) {
           const uint64_t koff = (uint64_t)(ks * 16);
 #pragma unroll
           for (int pl = 0; pl < 2; ++pl)
 #pragma unroll
             for (int ta = 0; ta < TERMS; ++ta) {
-              const uint32_t idesc = mma_idesc_bf16(N * b_terms_for(PREC, ta));
+              const uint32_t idesc = mma_idesc(N * b_terms_for(PREC, ta), TF ? 2u : 1u);
               const uint32_t d = tmem + (uint32_t)tile_col(PREC, ta, N);
               const bool first = (FOLD || c == 0) && ks == 0 && pl == 0;
               const uint32_t acc = first ? 0u : 1u;
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                  "l"(adesc[pl * TERMS + ta] + koff), "l"(bdesc[pl] + koff), "r"(idesc), "r"(acc));
+              if constexpr (TF)
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                    "l"(adesc[pl * TERMS + ta] + koff), "l"(bdesc[pl] + koff), "r"(idesc), "r"(acc));
+              else
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                    "l"(adesc[pl * TERMS + ta] + koff), "l"(bdesc[pl] + koff), "r"(idesc), "r"(acc));
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
@@ -387,9 +469,10 @@ __global__ void k_gemm_unpack(const unsigned long long* __restrict__ keys, int64
   arg[i] = (int)(0xffffffffu - (unsigned int)(kk & 0xffffffffull));
 }
 
-size_t gemm_smem_bytes(int terms, int NJ, int KC) {
-  const int nH = 15 + KC / 8;
-  return (size_t)2 * terms * nH * 128 + (size_t)2 * terms * (2 * NJ) * KC * 2 + 1024;
+size_t gemm_smem_bytes(int prec, int NJ, int KC) {
+  const int terms = prec_terms(prec);
+  return (size_t)2 * terms * hankel_cores(prec, KC) * 128 + (size_t)2 * terms * (2 * NJ) * KC * prec_ebytes(prec) +
+         1024;
 }
 
 // Tensor-memory columns: one column group of 2 NJ per product, rounded up to a power of two.
@@ -407,6 +490,7 @@ int gemm_nj_max(int prec) {
     case RF_PREC_BF16: return 128;
     case RF_PREC_BF16X3: return 48;
     case RF_PREC_BF16X6: return 40;
+    case RF_PREC_3XTF32: return 48;
     default: return 24;
   }
 }
@@ -421,7 +505,7 @@ void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, un
   // 512 tensor-memory columns of the SM (an allocation would otherwise wait for a release)
   const size_t smem_max = 227 * 1024;
   const int max_blocks = 512 / cols;
-  size_t smem = gemm_smem_bytes(prec_terms(PREC), NJ, KC);
+  size_t smem = gemm_smem_bytes(PREC, NJ, KC);
   smem = std::max(smem, smem_max / (size_t)(max_blocks + 1) + 1024);
   smem = std::min(smem, (size_t)220 * 1024);
   auto fn = k_gemm<V, NJ, PREC, WINMAX>;
@@ -435,15 +519,19 @@ void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, un
   int TM = 1;
   while (TM < 16 && (tiles / (TM * 2)) * groups >= 4LL * c->nsm) TM *= 2;
   dim3 grid((unsigned)((tiles + TM - 1) / TM), (unsigned)groups);
-  // z_ref split into BF16 planes, padded so that no Hankel window wraps
-  const int terms = prec_terms(PREC);
+  // z_ref split into BF16 (TF32) planes, padded so that no Hankel window wraps
   const int64_t LP = (int64_t)KC * NCK;
   const int64_t zpad = gemm_zpad(LP), zlen = gemm_zlen(c->n, LP);
-  c->scratch2.ensure(gemm_zplanes_bytes(c->n, LP, terms));
-  __nv_bfloat16* zp = c->scratch2.as<__nv_bfloat16>();
-  k_gemm_split_z<V><<<(unsigned)((zlen + 255) / 256), 256, 0, s>>>(z_ref, c->n, zpad, zlen, terms, zp);
+  c->scratch2.ensure(gemm_zplanes_bytes(c->n, LP, PREC));
+  void* zp = c->scratch2.as<unsigned char>();
+  if constexpr (prec_tf32(PREC))
+    k_gemm_split_z_tf32<V><<<(unsigned)((zlen + 255) / 256), 256, 0, s>>>(z_ref, c->n, zpad, zlen,
+                                                                         static_cast<float*>(zp));
+  else
+    k_gemm_split_z<V><<<(unsigned)((zlen + 255) / 256), 256, 0, s>>>(z_ref, c->n, zpad, zlen, prec_terms(PREC),
+                                                                    static_cast<__nv_bfloat16*>(zp));
   RF_LAUNCHED();
-  fn<<<grid, kGemmThreads, smem, s>>>(zp, zpad, zlen, c->n, kern->gemm_B.as<__nv_bfloat16>(), KC, NCK, kern->k,
+  fn<<<grid, kGemmThreads, smem, s>>>(zp, zpad, zlen, c->n, kern->gemm_B.as<unsigned char>(), KC, NCK, kern->k,
                                       kern->lag0_d.as<int>(), TM, z_out, keys, W, nw, cols, c->status.as<int>());
   RF_LAUNCHED();
 }
@@ -451,7 +539,10 @@ void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, un
 template <typename V, int PREC, bool WINMAX>
 void launch_gemm_nj(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, unsigned long long* keys, int64_t W,
                     int64_t nw, cudaStream_t s) {
-  constexpr int NJMAX = PREC == RF_PREC_BF16 ? 128 : PREC == RF_PREC_BF16X3 ? 48 : PREC == RF_PREC_BF16X6 ? 40 : 24;
+  constexpr int NJMAX = PREC == RF_PREC_BF16                                 ? 128
+                        : (PREC == RF_PREC_BF16X3 || PREC == RF_PREC_3XTF32) ? 48
+                        : PREC == RF_PREC_BF16X6                             ? 40
+                                                                             : 24;
   if (kern->gemm_NJ == 16) launch_gemm<V, 16, PREC, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s);
   else launch_gemm<V, NJMAX, PREC, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s);
 }
@@ -463,6 +554,7 @@ void launch_gemm_prec(rf_ctx* c, const rf_kernels* kern, int prec, const V* z_re
     case RF_PREC_BF16: launch_gemm_nj<V, RF_PREC_BF16, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
     case RF_PREC_BF16X3: launch_gemm_nj<V, RF_PREC_BF16X3, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
     case RF_PREC_BF16X6: launch_gemm_nj<V, RF_PREC_BF16X6, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
+    case RF_PREC_3XTF32: launch_gemm_nj<V, RF_PREC_3XTF32, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
     default: launch_gemm_nj<V, RF_PREC_BF16X9, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s); break;
   }
 }
@@ -489,41 +581,45 @@ void wait_selftest(rf_ctx* c, cudaStream_t s) {
   RF_LAUNCHED();
 }
 
-size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int terms) {
-  return sizeof(__nv_bfloat16) * (size_t)(2 * terms) * (size_t)gemm_zlen(n, LP) + 256;
+size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int prec) {
+  return (size_t)prec_ebytes(prec) * (size_t)(2 * prec_terms(prec)) * (size_t)gemm_zlen(n, LP) + 256;
 }
 
 int gemm_max_len() { return 1 << 16; }
 
 void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
   const int terms = prec_terms(prec);
-  // K chunks of 128 taps; groups of 16 neighbours when the set is small, else the widest
+  const bool tf32 = prec_tf32(prec);
+  // K chunks of 128 taps (64 for TF32 operands, twice the bytes per tap); groups of 16
+  // neighbours when the set is small, else the widest
   const int L16 = std::max(16, (kern->max_len + 15) / 16 * 16);
-  const int KC = std::min(128, L16);
-  const int NCK = (L16 + KC - 1) / KC;
   const int NJ = kern->k <= 16 ? 16 : gemm_nj_max(prec);
-  RF_REQUIRE(gemm_smem_bytes(terms, NJ, KC) <= 220 * 1024, "tensor-core direct form: chunk of %d taps does not fit",
+  int KC = std::min(128, L16);
+  while (KC > 16 && gemm_smem_bytes(prec, NJ, KC) > (size_t)160 * 1024) KC /= 2;
+  const int NCK = (L16 + KC - 1) / KC;
+  RF_REQUIRE(gemm_smem_bytes(prec, NJ, KC) <= 220 * 1024, "tensor-core direct form: chunk of %d taps does not fit",
              KC);
-  if (kern->gemm_ready && kern->gemm_terms == terms && kern->gemm_KC == KC && kern->gemm_NCK == NCK &&
-      kern->gemm_NJ == NJ)
+  if (kern->gemm_ready && kern->gemm_terms == terms && kern->gemm_tf32 == tf32 && kern->gemm_KC == KC &&
+      kern->gemm_NCK == NCK && kern->gemm_NJ == NJ)
     return;
   const int groups = std::max(1, (kern->k + NJ - 1) / NJ);
   const int LP = KC * NCK;
   const size_t elems = (size_t)groups * 2 * terms * (2 * NJ) * LP;
-  kern->gemm_B.ensure(sizeof(__nv_bfloat16) * std::max<size_t>(elems, 8));
+  kern->gemm_B.ensure((size_t)prec_ebytes(prec) * std::max<size_t>(elems, 8));
   dim3 grid((unsigned)std::max<int64_t>(1, (2 * NJ * LP + 255) / 256), (unsigned)groups);
   if (kern->dtype == RF_F64)
     k_gemm_prep_b<double2><<<grid, 256, 0, s>>>(kern->taps.as<double2>(), kern->off_d.as<int64_t>(),
-                                                kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms,
-                                                kern->gemm_B.as<__nv_bfloat16>());
+                                                kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms, tf32,
+                                                kern->gemm_B.as<unsigned char>());
   else
     k_gemm_prep_b<float2><<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(),
-                                               kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms,
-                                               kern->gemm_B.as<__nv_bfloat16>());
+                                               kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms, tf32,
+                                               kern->gemm_B.as<unsigned char>());
   RF_LAUNCHED();
   RF_CUDA(cudaStreamSynchronize(s));
   kern->gemm_ready = true;
   kern->gemm_terms = terms;
+  kern->gemm_tf32 = tf32;
   kern->gemm_KC = KC;
   kern->gemm_NCK = NCK;
   kern->gemm_NJ = NJ;

@@ -146,12 +146,13 @@ struct rf_kernels {
   rf::DevBuf os_spec;      // float2, sum_j P_j B_j values
   rf::DevBuf os_off_d;     // int64 [k]: element offset of kernel j's first partition spectrum
   rf::DevBuf os_parts_d;   // int32 [k]
-  // Tensor-core direct form: split-BF16 tap operands per group of gemm_NJ neighbours, taps
+  // Tensor-core direct form: split-BF16 (or TF32) tap operands per group of gemm_NJ neighbours, taps
   // padded to gemm_NCK chunks of gemm_KC (see reconstruct_gemm.cu).
   // Form chosen by rf_autotune (RF_ALGO_AUTO then follows it; 0 when not tuned).
   int tuned_algo = 0, tuned_prec = 0;
   bool gemm_ready = false;
   int gemm_terms = 0, gemm_KC = 0, gemm_NCK = 0, gemm_NJ = 0;
+  bool gemm_tf32 = false;
   rf::DevBuf gemm_B;
 };
 
@@ -219,8 +220,8 @@ void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
 // launches the bounded-wait health check (reconstruct_gemm.cu)
 void wait_selftest(rf_ctx* c, cudaStream_t s);
-// bytes of the BF16 planes of z_ref used by the tensor-core path (taps padded to LP)
-size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int terms);
+// bytes of the split planes of z_ref used by the tensor-core path at prec (taps padded to LP)
+size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int prec);
 void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,
                     int32_t* argmax_out, cudaStream_t s);
 void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,

@@ -681,8 +681,10 @@ def test_batched_step_captures_in_a_cuda_graph(torch):
 
 # Error bars of the split-BF16 products relative to max|z| (x = x0 + x1 + x2, u = 2^-9 the BF16
 # unit roundoff of each term): the dropped products are O(u) for BF16, O(u^2) for x3, and O(u^3)
-# for x6/x9, where the FP32 accumulation (about 1e-7 of the running sum) dominates.
-GEMM_TOL = {"bf16": 2e-2, "bf16x3": 2e-4, "bf16x6": 2e-6, "bf16x9": 2e-6}
+# for x6/x9, where the FP32 accumulation (about 1e-7 of the running sum) dominates.  3xTF32
+# (u = 2^-11 per TF32 term, two terms) drops x1 y1 and both split residuals, 3 u^2 = 7e-7 of
+# |x||y| per product at most.
+GEMM_TOL = {"bf16": 2e-2, "bf16x3": 2e-4, "bf16x6": 2e-6, "bf16x9": 2e-6, "3xtf32": 2e-6}
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
@@ -721,8 +723,9 @@ def test_reconstruct_gemm_edge_lengths(torch, dtype):
             Po, Ao = reconstruct.window_peaks(zo[j], 1000)
             assert np.abs(P[j] - Po).max() <= 4 * tol * Po.max()
             _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, 1000, 8 * tol * Po.max())
-    # each extra set of products improves the result
+    # each extra set of products improves the result; two TF32 terms resolve about 2^-22
     assert errs["bf16x3"] < errs["bf16"] / 10 and errs["bf16x6"] < errs["bf16x3"] / 10
+    assert errs["3xtf32"] < errs["bf16x3"] / 10
 
 
 def test_reconstruct_gemm_precision_form_workload(torch):
