@@ -542,23 +542,16 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_max = 2070.0
     if algo_used == "gemm":
-        # tensor-pipe work actually issued: per 128-output tile and group of NJ neighbours,
-        # LP taps x 2 planes x products, each 2 x 128 x (2 NJ) flops per tap (the chunk KC
-        # and group width NJ follow the library's choice for the precision)
-        terms = {"bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 3, "3xtf32": 2}[prec]
+        # tensor-pipe work actually issued, from the layout the library chose: per super-tile of
+        # S x 128 outputs and group of NJ neighbours, KC x NCK taps (LP + 128 (S - 1)) x 2 planes
+        # x products, each 2 x 128 x (S x 2 NJ) flops per tap
         nprod = {"bf16": 1, "bf16x3": 3, "bf16x6": 6, "bf16x9": 9, "3xtf32": 3}[prec]
-        ebytes = 4 if prec == "3xtf32" else 2
         mma_flops = 0.0
         for k in kerns:
-            L16 = max(16, -(-int(k.length.max()) // 16) * 16)
-            NJ = 16 if k.k <= 16 else {"bf16": 128, "bf16x3": 48, "bf16x6": 40, "bf16x9": 24, "3xtf32": 48}[prec]
-            KC = min(128, L16)
-            while KC > 16 and (2 * terms * ((30 + KC // 4) if ebytes == 4 else (15 + KC // 8)) * 128
-                               + 2 * terms * 2 * NJ * KC * ebytes + 1024) > 160 * 1024:
-                KC //= 2
-            LP = KC * (-(-L16 // KC))
+            lay = k.gemm_layout()
+            S, NJ = lay["shifts"], lay["nj"]
             groups = -(-k.k // NJ)
-            mma_flops += (n / 128) * groups * LP * 2 * nprod * (2 * 128 * 2 * NJ)
+            mma_flops += (-(-n // (128 * S))) * groups * (lay["kc"] * lay["nck"]) * 2 * nprod * (2 * 128 * S * 2 * NJ)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak_tflops = float(peaks.get("bf16_tflops", 1900.0))

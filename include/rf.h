@@ -226,6 +226,12 @@ rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t*
  * `dst`.  Async on stream. */
 rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream);
 
+/* Tensor-core layout a kernel set was last prepared for (by its last RF_ALGO_GEMM call): out[0]
+ * = rf_prec, out[1] = neighbours per group, out[2] = output tiles of 128 stacked along N,
+ * out[3] = taps per K chunk, out[4] = K chunks, out[5] = padded kernel length (all 0 when not
+ * prepared).  out is a host int32[6]. */
+rf_status rf_kernels_gemm_layout(const rf_kernels* kern, int32_t* out);
+
 /* Borrowed view of the build grid of each kernel (host int64[k]; n for imported kernels). */
 rf_status rf_kernels_grids(const rf_kernels* kern, const int64_t** grids);
 

@@ -31,6 +31,7 @@ EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
     "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_os_buckets", "rf_kernels_grids",
+    "rf_kernels_gemm_layout",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
     "rf_selftest_bounded_wait", "rf_autotune",
@@ -90,6 +91,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_kernels_copy_taps": (i32, [vp, vp, vp]),
         "rf_kernels_prepare": (i32, [vp, vp, i32, i32, vp]),
         "rf_kernels_os_layout": (i32, [vp, P(i32), P(i32)]),
+        "rf_kernels_gemm_layout": (i32, [vp, P(i32)]),
         "rf_kernels_prepare_buckets": (i32, [vp, vp, i32, P(i32), P(i32), P(i32), vp]),
         "rf_kernels_os_buckets": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
         "rf_kernels_free": (None, [vp]),
@@ -194,6 +196,17 @@ class Kernels:
         b, p = ctypes.c_int32(0), ctypes.c_int32(0)
         _check(_lib.rf_kernels_os_layout(self.handle, ctypes.byref(b), ctypes.byref(p)))
         return b.value, p.value
+
+    def gemm_layout(self):
+        """Tensor-core layout of the last RF_ALGO_GEMM call: dict of prec, neighbours per group
+        (nj), stacked output tiles (shifts), taps per K chunk (kc), chunks (nck) and padded
+        length (lp); None when not prepared."""
+        o = (ctypes.c_int32 * 6)()
+        _check(_lib.rf_kernels_gemm_layout(self.handle, o))
+        if o[1] == 0:
+            return None
+        pn = {v: k for k, v in PRECS.items()}
+        return {"prec": pn[o[0]], "nj": o[1], "shifts": o[2], "kc": o[3], "nck": o[4], "lp": o[5]}
 
     def free(self) -> None:
         if self.handle:

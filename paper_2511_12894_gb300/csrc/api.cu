@@ -345,6 +345,20 @@ rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* 
   });
 }
 
+rf_status rf_kernels_gemm_layout(const rf_kernels* kern, int32_t* out) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    RF_REQUIRE(out != nullptr, "out is NULL");
+    const bool r = kern->gemm_ready;
+    out[0] = r ? kern->gemm_prec : 0;
+    out[1] = r ? kern->gemm_NJ : 0;
+    out[2] = r ? kern->gemm_S : 0;
+    out[3] = r ? kern->gemm_KC : 0;
+    out[4] = r ? kern->gemm_NCK : 0;
+    out[5] = r ? kern->gemm_LP : 0;
+  });
+}
+
 rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream) {
   return guard([&] {
     RF_REQUIRE(kern != nullptr, "kern is NULL");

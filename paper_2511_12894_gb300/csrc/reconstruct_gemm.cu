@@ -101,27 +101,30 @@ __host__ __device__ constexpr int prec_terms(int prec) {
 }
 
 // Tap operands of one neighbour group, prepared once per kernel set, chunk by chunk:
-// [K chunk c][plane (r, i)][term][N/8 row blocks][KC/8 K blocks][8 rows][8 BF16] (TF32:
-// [KC/4 K blocks][8 rows][4 words]), taps in reverse (t = c KC + t_local, tap l = LP - 1 - t),
-// columns (2j, 2j+1) = (re, im) of neighbour j of the group; plane r holds (cr, ci), plane i
-// holds (-ci, cr).
+// [K chunk c][plane (r, i)][term][NC/8 row blocks][KC/8 K blocks][8 rows][8 BF16] (TF32:
+// [KC/4 K blocks][8 rows][4 words]) over the extended K range t in [0, NCK KC), NCK KC =
+// LP + 128 (S - 1).  Column s 2 NJ + 2j (+1) = re (im) of neighbour j of the group at output
+// shift s, holding tap l = LP - 1 - t + 128 s (zero outside the kernel); plane r holds
+// (cr, ci), plane i holds (-ci, cr).
 template <typename V>
 __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restrict__ off, const int* __restrict__ len,
-                              int k, int NJ, int KC, int NCK, int terms, bool tf32, void* __restrict__ out_v) {
+                              int k, int NJ, int S, int KC, int NCK, int LP, int terms, bool tf32,
+                              void* __restrict__ out_v) {
   using R = typename real_of<V>::type;
   const int g = blockIdx.y;
-  const int N = 2 * NJ;
-  const int LP = KC * NCK;
-  const int64_t per_plane_term = (int64_t)N * KC;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)N * LP;
+  const int NC = S * 2 * NJ;
+  const int LPX = KC * NCK;
+  const int64_t per_plane_term = (int64_t)NC * KC;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)NC * LPX;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(e / LP), t = (int)(e % LP);
+    const int col = (int)(e / LPX), t = (int)(e % LPX);
     const int c = t / KC, tl = t % KC;
-    const int j = g * NJ + col / 2;
+    const int sh = col / (2 * NJ);
+    const int j = g * NJ + (col % (2 * NJ)) / 2;
     R cr = 0, ci = 0;
     if (j < k) {
-      const int l = LP - 1 - t;
-      if (l < len[j]) {
+      const int l = LP - 1 - t + kGemmM * sh;
+      if (l >= 0 && l < len[j]) {
         const V v = taps[off[j] + l];
         cr = v.x;
         ci = v.y;
@@ -156,11 +159,11 @@ __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restr
 
 // z_ref split into BF16 (or TF32) planes once per call: plane (p, s) holds term s of the
 // real (p = 0) or imaginary (p = 1) part, element x of the circular sequence at index x + pad
-// for x in [-pad, n + tail); pad = 7 (mod 8) makes every Hankel row-block window 16-byte
-// aligned.  The split runs in FP32 (complex128 inputs are rounded to FP32 first, well inside
+// for x in [-pad, n + tail) (the tail covers the extended K range of up to 8 output shifts);
+// pad = 7 (mod 8) makes every Hankel row-block window 16-byte aligned.  The split runs in FP32 (complex128 inputs are rounded to FP32 first, well inside
 // the resolution of the split terms).
 static int64_t gemm_zpad(int64_t LP) { return ((LP + 8 + 7) / 8) * 8 + 7; }
-static int64_t gemm_zlen(int64_t n, int64_t LP) { return ((gemm_zpad(LP) + n + 160 + 7) / 8) * 8; }
+static int64_t gemm_zlen(int64_t n, int64_t LP) { return ((gemm_zpad(LP) + n + 1024 + 160 + 7) / 8) * 8; }
 
 template <typename V>
 __global__ void k_gemm_split_z(const V* __restrict__ z, int64_t n, int64_t pad, int64_t len, int terms,
@@ -219,56 +222,84 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar_addr, uint32_t phase, in
 __host__ __device__ constexpr int b_terms_for(int prec, int ta) {
   return prec == RF_PREC_BF16X9 ? 3 : prec_terms(prec) - ta;
 }
-// Tensor-memory column of the tile of A term ta (tiles follow each other, N columns per B term).
-__host__ __device__ constexpr int tile_col(int prec, int ta, int N) {
+// Tensor-memory column groups.  The products of one order ta + tb accumulate into one group
+// of NC columns (the leading product alone, then the first-order corrections, ...): the MMA of
+// A term ta covers B terms 0.., so it writes orders ta, ta + 1, ... and starts at group ta, and
+// the MMA of A term 0 reaches every order first, so it initialises them all.  bf16x9's orders
+// 3 and 4 are first reached by later A terms, so it keeps one group per product.
+__host__ __device__ constexpr bool prec_merged(int prec) { return prec != RF_PREC_BF16X9; }
+__host__ __device__ constexpr int prec_groups(int prec) {
+  return prec_merged(prec) ? prec_terms(prec) : prec_products(prec);
+}
+__host__ __device__ constexpr int tile_col(int prec, int ta, int NC) {
+  if (prec_merged(prec)) return ta * NC;
   int c = 0;
-  for (int t = 0; t < ta; ++t) c += N * b_terms_for(prec, t);
+  for (int t = 0; t < ta; ++t) c += NC * b_terms_for(prec, t);
   return c;
 }
+// Output shifts stacked along N for a group of NJ neighbours: the widest power of two S <= 8
+// whose MMA of A term 0 (S * 2 NJ columns per B term) stays within N = 256 and whose column
+// groups fit the 512 columns of tensor memory.
+__host__ __device__ constexpr int gemm_shifts_max(int prec, int NJ) {
+  int s = 8;
+  while (s > 1 && (s * 2 * NJ * b_terms_for(prec, 0) > 256 || s * 2 * NJ * prec_groups(prec) > 512)) s /= 2;
+  return s;
+}
 
-// One block: TM consecutive 128-output tiles of one group of NJ neighbours.  The taps are
-// consumed in NCK chunks of KC taps: per chunk the block stages the Hankel core matrices
-// and (when there is more than one chunk) the chunk's tap operands, issues one MMA per
-// (K step, plane, A term) whose N spans every B term paired with that A term, and folds
-// the chunk's tiles into FP32 register sums (plain BF16 accumulates in tensor memory).
-template <typename V, int NJ, int PREC, bool WINMAX>
+// One block: TM consecutive super-tiles of S x 128 outputs of one group of NJ neighbours.
+// Output shift s (tile rows i0 + 128 s + m) needs z[b + m + t'] at t' = t + 128 s, so all S
+// tiles share the Hankel operand of an extended K range (LP + 128 (S - 1) taps) and the tap
+// operand holds, per shift, the taps moved down by 128 s (zero outside the kernel): one MMA
+// serves S tiles, NC = S x 2 NJ columns per B term.  The taps are consumed in NCK chunks of KC:
+// per chunk the block stages the Hankel core matrices and (when there is more than one chunk)
+// the chunk's tap operands, issues one MMA per (K step, plane, A term) whose N spans every B
+// term paired with that A term, and folds the chunk's column groups into FP32 register sums
+// (plain BF16 accumulates in tensor memory).
+template <typename V, int NJ, int PREC, bool WINMAX, int S>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict__ zp_v, int64_t zpad,
                                                           int64_t zlen, int64_t n,
-                                                          const void* __restrict__ Bg, int KC, int NCK,
+                                                          const void* __restrict__ Bg, int KC, int NCK, int LP,
                                                           int k, const int* __restrict__ lag0, int TM,
                                                           V* __restrict__ z_out, unsigned long long* __restrict__ keys,
                                                           int64_t W, int64_t nw, int tmem_cols,
                                                           int* __restrict__ status) {
   using R = typename real_of<V>::type;
-  constexpr int N = 2 * NJ;                // columns per B term
+  constexpr int NC = S * 2 * NJ;           // columns per B term (all shifts)
   constexpr int TERMS = prec_terms(PREC);
   constexpr bool FOLD = PREC != RF_PREC_BF16;
+  constexpr bool MERGED = prec_merged(PREC);
   constexpr bool TF = prec_tf32(PREC);
   constexpr int EB = prec_ebytes(PREC);     // bytes per operand value
-  static_assert(N % 16 == 0 && N * b_terms_for(PREC, 0) <= 256, "MMA width");
+  static_assert(NC % 16 == 0 && NC * b_terms_for(PREC, 0) <= 256, "MMA width");
+  static_assert((2 * NJ) % 16 == 0, "a 16-column slice holds one shift");
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ __align__(8) unsigned long long mbar, mbar_b;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = blockIdx.y;
-  const int LP = KC * NCK;
   const int nH = hankel_cores(PREC, KC);              // distinct Hankel core matrices per chunk
   const int a_bytes = nH * 128;                       // per (plane, term)
-  const int b_bytes = N * KC * EB;                    // per (plane, term)
+  const int b_bytes = NC * KC * EB;                   // per (plane, term)
   unsigned char* sA = smem;                           // [plane][term][nH][128 B]
-  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][N/8][KC/(16/EB)][128 B]
+  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][NC/8][KC/(16/EB)][128 B]
   const int64_t mask = n - 1;
   const unsigned char* Bgrp = static_cast<const unsigned char*>(Bg) + (int64_t)g * NCK * 2 * TERMS * b_bytes;
 
-  auto stage_b = [&](int c) {
-    const uint4* src = reinterpret_cast<const uint4*>(Bgrp + (int64_t)c * 2 * TERMS * b_bytes);
-    uint4* dst = reinterpret_cast<uint4*>(sB);
-    const int cnt = 2 * TERMS * b_bytes / 16;
-    for (int e = tid; e < cnt; e += kGemmThreads) dst[e] = src[e];
+  // The chunk's tap operands (contiguous in global memory) arrive by one bulk copy, issued by
+  // thread 0 and completed on mbar_b, while the block stages the Hankel core matrices.
+  const uint32_t mbar_b_addr = smem_u32(&mbar_b);
+  const uint32_t b_chunk_bytes = (uint32_t)(2 * TERMS * b_bytes);
+  auto issue_b = [&](int c) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_b_addr), "r"(b_chunk_bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(sB)),
+        "l"(Bgrp + (int64_t)c * b_chunk_bytes), "r"(b_chunk_bytes), "r"(mbar_b_addr)
+        : "memory");
   };
-  if (NCK == 1) stage_b(0);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_b_addr));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -281,19 +312,25 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t mbar_addr = smem_u32(&mbar);
-  uint32_t phase = 0;
+  uint32_t phase = 0, phase_b = 0;
   bool ok = true;
   const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  const unsigned int Wu = (unsigned int)(W < n ? W : n), nwu = (unsigned int)nw;  // n <= 2^24
+  bool b_pending = NCK == 1;  // a single chunk is loaded once for every tile
+  if (b_pending && tid == 0) issue_b(0);
 
   for (int tile = 0; tile < TM && ok; ++tile) {
-    const int64_t i0 = ((int64_t)blockIdx.x * TM + tile) * kGemmM;
+    const int64_t i0 = ((int64_t)blockIdx.x * TM + tile) * (kGemmM * S);
     if (i0 >= n) break;
     const int64_t b = i0 - LP + 1;
-    float run[FOLD ? N : 1];
+    float run[FOLD ? NC : 1];
 #pragma unroll
-    for (int cidx = 0; cidx < (FOLD ? N : 1); ++cidx) run[cidx] = 0.f;
+    for (int cidx = 0; cidx < (FOLD ? NC : 1); ++cidx) run[cidx] = 0.f;
     for (int c = 0; c < NCK && ok; ++c) {
-      if (NCK > 1) stage_b(c);
+      if (NCK > 1) {
+        if (tid == 0) issue_b(c);
+        b_pending = true;
+      }
       // Hankel core matrices of the chunk: row a of H_d is z[b + c KC + 8d + a + e], e < 8.
       // One task = one (plane, term, d): the aligned 16-element window starting at
       // b + c KC + 8d gives all eight rows by funnel shifts.  (One 16-byte row per thread
@@ -328,7 +365,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
+      bool b_ok = true;
+      if (b_pending) {
+        if (tid == 0) b_ok = mbar_wait(mbar_b_addr, phase_b);
+        phase_b ^= 1u;
+        b_pending = false;
+      }
+      if (!__syncthreads_and(b_ok)) {
+        if (tid == 0) {
+          atomicExch(status, (int)RF_ETIMEOUT);
+          mbar_wait(mbar_b_addr, phase_b ^ 1u);  // one more bounded wait for the copy in flight
+        }
+        ok = false;
+        __syncthreads();
+        break;
+      }
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // A K step (32 bytes of every row: K = 16 BF16 or 8 TF32 values) spans two core
@@ -348,9 +399,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
           for (int pl = 0; pl < 2; ++pl)
 #pragma unroll
             for (int ta = 0; ta < TERMS; ++ta) {
-              const uint32_t idesc = mma_idesc(N * b_terms_for(PREC, ta), TF ? 2u : 1u);
-              const uint32_t d = tmem + (uint32_t)tile_col(PREC, ta, N);
-              const bool first = (FOLD || c == 0) && ks == 0 && pl == 0;
+              const uint32_t idesc = mma_idesc(NC * b_terms_for(PREC, ta), TF ? 2u : 1u);
+              const uint32_t d = tmem + (uint32_t)tile_col(PREC, ta, NC);
+              // the first MMA of a chunk (of the call, for plain BF16) overwrites its columns;
+              // merged groups are all first written by A term 0
+              const bool first = (FOLD || c == 0) && ks == 0 && pl == 0 && (!MERGED || ta == 0);
               const uint32_t acc = first ? 0u : 1u;
               if constexpr (TF)
                 asm volatile(
@@ -377,25 +430,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if constexpr (FOLD) {
-        // row sums of the chunk: the leading product (A term 0 x B term 0) plus the corrections
+        // row sums of the chunk: the leading product plus the corrections
+        constexpr int NG = prec_groups(PREC);
 #pragma unroll
-        for (int h = 0; h < N / 16; ++h) {
+        for (int h = 0; h < NC / 16; ++h) {
           float big[16], small[16];
 #pragma unroll
           for (int cc = 0; cc < 16; ++cc) big[cc] = small[cc] = 0.f;
 #pragma unroll
-          for (int ta = 0; ta < TERMS; ++ta)
+          for (int grp = 0; grp < NG; ++grp) {
+            uint32_t v[16];
+            tmem_ld16(taddr + (uint32_t)(grp * NC + 16 * h), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int tb = 0; tb < b_terms_for(PREC, ta); ++tb) {
-              uint32_t v[16];
-              tmem_ld16(taddr + (uint32_t)(tile_col(PREC, ta, N) + tb * N + 16 * h), v);
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-              for (int cc = 0; cc < 16; ++cc) {
-                if (ta == 0 && tb == 0) big[cc] += __uint_as_float(v[cc]);
-                else small[cc] += __uint_as_float(v[cc]);
-              }
+            for (int cc = 0; cc < 16; ++cc) {
+              if (grp == 0) big[cc] += __uint_as_float(v[cc]);
+              else small[cc] += __uint_as_float(v[cc]);
             }
+          }
 #pragma unroll
           for (int cc = 0; cc < 16; ++cc) run[16 * h + cc] += big[cc] + small[cc];
         }
@@ -405,9 +457,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
     }
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int64_t ip = i0 + warp * 32 + lane;  // i'
 #pragma unroll
-    for (int h = 0; h < N / 16; ++h) {
+    for (int h = 0; h < NC / 16; ++h) {
+      const int sh = (16 * h) / (2 * NJ);             // output shift of this column slice
+      if (i0 + (int64_t)kGemmM * sh >= n) break;      // uniform across the block
+      const int64_t ip = i0 + kGemmM * sh + warp * 32 + lane;  // i'
+      const int jb = ((16 * h) % (2 * NJ)) / 2;       // first neighbour of the slice
       float val[16];
       if constexpr (FOLD) {
 #pragma unroll
@@ -421,32 +476,34 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
       }
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const int j = g * NJ + 8 * h + jj;
+        const int j = g * NJ + jb + jj;
         if (j >= k) break;  // uniform across the block
         const float re = val[2 * jj], im = val[2 * jj + 1];
-        const int64_t i = (ip + lag0[j]) & mask;
+        const unsigned int i = (unsigned int)((ip + lag0[j]) & mask);
         if (!WINMAX) {
           z_out[(int64_t)j * n + i] = cmake<V>((R)re, (R)im);
         } else {
-          const unsigned long long key = gemm_key(re * re + im * im, (unsigned int)i);
+          // The warp's 32 outputs are consecutive modulo n: usually they fall in lane 0's window
+          // wA and the next one wB (window 0 after the wrap), decided by comparison; per window
+          // the largest |z|^2 (non-negative floats order as their bit patterns) and then the
+          // smallest index holding it come from two 32-bit warp reductions.
+          const float p = re * re + im * im;
+          const unsigned int pb = __float_as_uint(p);
           unsigned long long* kj = keys + (int64_t)j * nw;
-          const int64_t i_lane0 = __shfl_sync(0xffffffffu, i, 0);
-          const int64_t wA = i_lane0 / W;
-          const int64_t wB = (wA + 1 == nw) ? 0 : wA + 1;
-          const int64_t w = i / W;
-          const bool slow = !(w == wA || w == wB);
-          if (__any_sync(0xffffffffu, slow)) {
-            atomicMax(kj + w, key);
+          const unsigned int wA = __shfl_sync(0xffffffffu, i, 0) / Wu;
+          const unsigned int wB = (wA + 1 == nwu) ? 0u : wA + 1;
+          const bool inA = i - wA * Wu < Wu;
+          const bool inB = !inA && i - wB * Wu < Wu;
+          if (__any_sync(0xffffffffu, !(inA || inB))) {
+            atomicMax(kj + i / Wu, gemm_key(p, i));
           } else {
-            unsigned long long kA = (w == wA) ? key : 0ull, kB = (w == wB) ? key : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
-              kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
-            }
+            const unsigned int mA = __reduce_max_sync(0xffffffffu, inA ? pb : 0u);
+            const unsigned int mB = __reduce_max_sync(0xffffffffu, inB ? pb : 0u);
+            const unsigned int xA = __reduce_min_sync(0xffffffffu, (inA && pb == mA) ? i : 0xffffffffu);
+            const unsigned int xB = __reduce_min_sync(0xffffffffu, (inB && pb == mB) ? i : 0xffffffffu);
             if (lane == 0) {
-              if (kA) atomicMax(kj + wA, kA);
-              if (kB) atomicMax(kj + wB, kB);
+              if (xA != 0xffffffffu) atomicMax(kj + wA, gemm_key(__uint_as_float(mA), xA));
+              if (xB != 0xffffffffu) atomicMax(kj + wB, gemm_key(__uint_as_float(mB), xB));
             }
           }
         }
@@ -469,58 +526,55 @@ __global__ void k_gemm_unpack(const unsigned long long* __restrict__ keys, int64
   arg[i] = (int)(0xffffffffu - (unsigned int)(kk & 0xffffffffull));
 }
 
-size_t gemm_smem_bytes(int prec, int NJ, int KC) {
+size_t gemm_smem_bytes(int prec, int NJ, int S, int KC) {
   const int terms = prec_terms(prec);
-  return (size_t)2 * terms * hankel_cores(prec, KC) * 128 + (size_t)2 * terms * (2 * NJ) * KC * prec_ebytes(prec) +
-         1024;
+  return (size_t)2 * terms * hankel_cores(prec, KC) * 128 +
+         (size_t)2 * terms * (S * 2 * NJ) * KC * prec_ebytes(prec) + 1024;
 }
 
-// Tensor-memory columns: one column group of 2 NJ per product, rounded up to a power of two.
-int gemm_tmem_cols(int prec, int NJ) {
-  const int need = prec_products(prec) * 2 * NJ;
+// Tensor-memory columns: one group of S x 2 NJ columns per product order (per product for
+// bf16x9), rounded up to a power of two.
+int gemm_tmem_cols(int prec, int NJ, int S) {
+  const int need = prec_groups(prec) * S * 2 * NJ;
   int cols = 32;
   while (cols < need) cols *= 2;
   return cols;
 }
 
 // Neighbours per group: the widest MMA (all B terms of A term 0) must fit N <= 256, and the
-// tile columns of all products must fit the 512 of tensor memory.
-int gemm_nj_max(int prec) {
-  switch (prec) {
-    case RF_PREC_BF16: return 128;
-    case RF_PREC_BF16X3: return 48;
-    case RF_PREC_BF16X6: return 40;
-    case RF_PREC_3XTF32: return 48;
-    default: return 24;
-  }
+// column groups must fit the 512 of tensor memory.
+__host__ __device__ constexpr int gemm_nj_max(int prec) {
+  return prec == RF_PREC_BF16                                 ? 128
+         : (prec == RF_PREC_BF16X3 || prec == RF_PREC_3XTF32) ? 48
+         : prec == RF_PREC_BF16X6                             ? 40
+                                                              : 24;
 }
 
-template <typename V, int NJ, int PREC, bool WINMAX>
+template <typename V, int NJ, int PREC, bool WINMAX, int S>
 void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, unsigned long long* keys, int64_t W,
                  int64_t nw, cudaStream_t s) {
-  const int KC = kern->gemm_KC, NCK = kern->gemm_NCK;
-  const int cols = gemm_tmem_cols(PREC, NJ);
+  const int KC = kern->gemm_KC, NCK = kern->gemm_NCK, LP = kern->gemm_LP;
+  const int cols = gemm_tmem_cols(PREC, NJ, S);
   RF_REQUIRE(cols <= 512, "tensor-core form: %d tensor-memory columns needed", cols);
   // shared memory sized so that the blocks resident on one SM never ask for more than the
   // 512 tensor-memory columns of the SM (an allocation would otherwise wait for a release)
   const size_t smem_max = 227 * 1024;
   const int max_blocks = 512 / cols;
-  size_t smem = gemm_smem_bytes(PREC, NJ, KC);
+  size_t smem = gemm_smem_bytes(PREC, NJ, S, KC);
   smem = std::max(smem, smem_max / (size_t)(max_blocks + 1) + 1024);
   smem = std::min(smem, (size_t)220 * 1024);
-  auto fn = k_gemm<V, NJ, PREC, WINMAX>;
+  auto fn = k_gemm<V, NJ, PREC, WINMAX, S>;
   RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGemmThreads, smem));
   RF_REQUIRE(per_sm >= 1 && per_sm * cols <= 512,
              "tensor-core form: %d blocks per SM x %d columns exceed tensor memory", per_sm, cols);
-  const int64_t tiles = c->n / kGemmM;
+  const int64_t tiles = (c->n + kGemmM * S - 1) / (kGemmM * S);
   const int groups = (kern->k + NJ - 1) / NJ;
   int TM = 1;
   while (TM < 16 && (tiles / (TM * 2)) * groups >= 4LL * c->nsm) TM *= 2;
   dim3 grid((unsigned)((tiles + TM - 1) / TM), (unsigned)groups);
   // z_ref split into BF16 (TF32) planes, padded so that no Hankel window wraps
-  const int64_t LP = (int64_t)KC * NCK;
   const int64_t zpad = gemm_zpad(LP), zlen = gemm_zlen(c->n, LP);
   c->scratch2.ensure(gemm_zplanes_bytes(c->n, LP, PREC));
   void* zp = c->scratch2.as<unsigned char>();
@@ -531,20 +585,25 @@ void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, un
     k_gemm_split_z<V><<<(unsigned)((zlen + 255) / 256), 256, 0, s>>>(z_ref, c->n, zpad, zlen, prec_terms(PREC),
                                                                     static_cast<__nv_bfloat16*>(zp));
   RF_LAUNCHED();
-  fn<<<grid, kGemmThreads, smem, s>>>(zp, zpad, zlen, c->n, kern->gemm_B.as<unsigned char>(), KC, NCK, kern->k,
+  fn<<<grid, kGemmThreads, smem, s>>>(zp, zpad, zlen, c->n, kern->gemm_B.as<unsigned char>(), KC, NCK, LP, kern->k,
                                       kern->lag0_d.as<int>(), TM, z_out, keys, W, nw, cols, c->status.as<int>());
   RF_LAUNCHED();
 }
 
+// Layouts: 16-neighbour groups with the widest output-shift stack, or the widest groups
+// without shifts.
 template <typename V, int PREC, bool WINMAX>
 void launch_gemm_nj(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, unsigned long long* keys, int64_t W,
                     int64_t nw, cudaStream_t s) {
-  constexpr int NJMAX = PREC == RF_PREC_BF16                                 ? 128
-                        : (PREC == RF_PREC_BF16X3 || PREC == RF_PREC_3XTF32) ? 48
-                        : PREC == RF_PREC_BF16X6                             ? 40
-                                                                             : 24;
-  if (kern->gemm_NJ == 16) launch_gemm<V, 16, PREC, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s);
-  else launch_gemm<V, NJMAX, PREC, WINMAX>(c, kern, z_ref, z_out, keys, W, nw, s);
+  constexpr int NJMAX = gemm_nj_max(PREC);
+  constexpr int SMAX = gemm_shifts_max(PREC, 16);
+  if (kern->gemm_NJ == 16) {
+    RF_REQUIRE(kern->gemm_S == SMAX, "tensor-core form: unexpected shift count %d", kern->gemm_S);
+    launch_gemm<V, 16, PREC, WINMAX, SMAX>(c, kern, z_ref, z_out, keys, W, nw, s);
+  } else {
+    RF_REQUIRE(kern->gemm_S == 1 && kern->gemm_NJ == NJMAX, "tensor-core form: unexpected layout");
+    launch_gemm<V, NJMAX, PREC, WINMAX, 1>(c, kern, z_ref, z_out, keys, W, nw, s);
+  }
 }
 
 template <typename V, bool WINMAX>
@@ -590,39 +649,62 @@ int gemm_max_len() { return 1 << 16; }
 void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
   const int terms = prec_terms(prec);
   const bool tf32 = prec_tf32(prec);
-  // K chunks of 128 taps (64 for TF32 operands, twice the bytes per tap); groups of 16
-  // neighbours when the set is small, else the widest
+  // Layout: up to 16 neighbours with kernels longer than one 128-output tile take 16-wide
+  // groups with the widest output-shift stack S (MMAs per output scale as
+  // (LP + 128 (S - 1)) / S); otherwise the widest groups and no shifts.  K chunks of up to 128
+  // taps (a power of two, so that they divide the 128 (S - 1) extension), halved while the
+  // block's shared memory would keep a second block (as many as tensor memory admits) off
+  // the SM.
   const int L16 = std::max(16, (kern->max_len + 15) / 16 * 16);
-  const int NJ = kern->k <= 16 ? 16 : gemm_nj_max(prec);
-  int KC = std::min(128, L16);
-  while (KC > 16 && gemm_smem_bytes(prec, NJ, KC) > (size_t)160 * 1024) KC /= 2;
-  const int NCK = (L16 + KC - 1) / KC;
-  RF_REQUIRE(gemm_smem_bytes(prec, NJ, KC) <= 220 * 1024, "tensor-core direct form: chunk of %d taps does not fit",
-             KC);
+  int KC = 16;
+  while (KC < 128 && KC < L16) KC *= 2;
+  const bool stack = kern->k <= 16 && L16 > kGemmM;
+  const int NJ = stack ? 16 : gemm_nj_max(prec);
+  int S = 1;
+  if (stack) {
+    switch (prec) {
+      case RF_PREC_BF16: S = gemm_shifts_max(RF_PREC_BF16, 16); break;
+      case RF_PREC_BF16X3: S = gemm_shifts_max(RF_PREC_BF16X3, 16); break;
+      case RF_PREC_BF16X6: S = gemm_shifts_max(RF_PREC_BF16X6, 16); break;
+      case RF_PREC_3XTF32: S = gemm_shifts_max(RF_PREC_3XTF32, 16); break;
+      default: S = gemm_shifts_max(RF_PREC_BF16X9, 16); break;
+    }
+  }
+  const size_t smem_cap = (size_t)(gemm_tmem_cols(prec, NJ, S) <= 256 ? 110 : 160) * 1024;
+  while (KC > 16 && gemm_smem_bytes(prec, NJ, S, KC) > smem_cap) KC /= 2;
+  const int LP = KC * ((L16 + KC - 1) / KC);
+  const int NCK = (LP + kGemmM * (S - 1)) / KC;
+  RF_REQUIRE(gemm_smem_bytes(prec, NJ, S, KC) <= 220 * 1024,
+             "tensor-core direct form: chunk of %d taps does not fit", KC);
   if (kern->gemm_ready && kern->gemm_terms == terms && kern->gemm_tf32 == tf32 && kern->gemm_KC == KC &&
-      kern->gemm_NCK == NCK && kern->gemm_NJ == NJ)
+      kern->gemm_NCK == NCK && kern->gemm_NJ == NJ && kern->gemm_S == S && kern->gemm_LP == LP) {
+    kern->gemm_prec = prec;  // same operands (the split terms serve every precision of the count)
     return;
+  }
   const int groups = std::max(1, (kern->k + NJ - 1) / NJ);
-  const int LP = KC * NCK;
-  const size_t elems = (size_t)groups * 2 * terms * (2 * NJ) * LP;
+  const int NC = S * 2 * NJ;
+  const size_t elems = (size_t)groups * 2 * terms * NC * ((size_t)KC * NCK);
   kern->gemm_B.ensure((size_t)prec_ebytes(prec) * std::max<size_t>(elems, 8));
-  dim3 grid((unsigned)std::max<int64_t>(1, (2 * NJ * LP + 255) / 256), (unsigned)groups);
+  dim3 grid((unsigned)std::max<int64_t>(1, ((int64_t)NC * KC * NCK + 255) / 256), (unsigned)groups);
   if (kern->dtype == RF_F64)
     k_gemm_prep_b<double2><<<grid, 256, 0, s>>>(kern->taps.as<double2>(), kern->off_d.as<int64_t>(),
-                                                kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms, tf32,
+                                                kern->len_d.as<int>(), kern->k, NJ, S, KC, NCK, LP, terms, tf32,
                                                 kern->gemm_B.as<unsigned char>());
   else
     k_gemm_prep_b<float2><<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(),
-                                               kern->len_d.as<int>(), kern->k, NJ, KC, NCK, terms, tf32,
+                                               kern->len_d.as<int>(), kern->k, NJ, S, KC, NCK, LP, terms, tf32,
                                                kern->gemm_B.as<unsigned char>());
   RF_LAUNCHED();
   RF_CUDA(cudaStreamSynchronize(s));
   kern->gemm_ready = true;
+  kern->gemm_prec = prec;
   kern->gemm_terms = terms;
   kern->gemm_tf32 = tf32;
   kern->gemm_KC = KC;
   kern->gemm_NCK = NCK;
   kern->gemm_NJ = NJ;
+  kern->gemm_S = S;
+  kern->gemm_LP = LP;
 }
 
 void reconstruct_gemm(rf_ctx* c, const void* z_ref, rf_kernels* kern, int prec, void* z_out, int64_t W,

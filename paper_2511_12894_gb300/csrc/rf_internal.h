@@ -146,12 +146,13 @@ struct rf_kernels {
   rf::DevBuf os_spec;      // float2, sum_j P_j B_j values
   rf::DevBuf os_off_d;     // int64 [k]: element offset of kernel j's first partition spectrum
   rf::DevBuf os_parts_d;   // int32 [k]
-  // Tensor-core direct form: split-BF16 (or TF32) tap operands per group of gemm_NJ neighbours, taps
-  // padded to gemm_NCK chunks of gemm_KC (see reconstruct_gemm.cu).
+  // Tensor-core direct form: split-BF16 (or TF32) tap operands per group of gemm_NJ neighbours and
+  // gemm_S output shifts, taps padded to gemm_LP and extended to gemm_NCK chunks of gemm_KC
+  // (see reconstruct_gemm.cu).
   // Form chosen by rf_autotune (RF_ALGO_AUTO then follows it; 0 when not tuned).
   int tuned_algo = 0, tuned_prec = 0;
   bool gemm_ready = false;
-  int gemm_terms = 0, gemm_KC = 0, gemm_NCK = 0, gemm_NJ = 0;
+  int gemm_prec = 0, gemm_terms = 0, gemm_KC = 0, gemm_NCK = 0, gemm_NJ = 0, gemm_S = 1, gemm_LP = 0;
   bool gemm_tf32 = false;
   rf::DevBuf gemm_B;
 };

@@ -751,6 +751,67 @@ def test_reconstruct_gemm_precision_form_workload(torch):
     assert A[inj.template_index, inj.sample // cfg.window].item() == inj.sample
 
 
+# Output tiles stacked along N for sets of at most 16 neighbours: the widest stack whose MMA of
+# the leading A term fits N = 256 (S x 32 columns per B term) and whose product-order column
+# groups fit tensor memory (bf16x9 keeps one group per product, 9 x 32 x S <= 512).
+GEMM_SHIFTS = {"bf16": 8, "bf16x3": 4, "bf16x6": 2, "bf16x9": 1, "3xtf32": 4}
+
+
+@pytest.mark.parametrize("n", [512, 1 << 12])
+def test_reconstruct_gemm_stacked_tiles(torch, n):
+    """Few neighbours with kernels longer than a tile: the output-shift stack, including a
+    segment shorter than one stacked super-tile (n = 512 < 8 x 128), against the oracle."""
+    rng = np.random.default_rng(29)
+    lengths = [300, 129, 5, 257]
+    lags = [0, -n // 2 + 1, 17, n // 3]
+    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype="f32")
+    rf = _rf(cfg)
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    taps = [((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(L)).astype(np.complex64)
+            for L in lengths]
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    zt = torch.tensor(z, device="cuda")
+    zo = [reconstruct.reconstruct_direct(z.astype(np.complex128), lags[j], taps[j].astype(np.complex128))
+          for j in range(len(lengths))]
+    for prec, tol in GEMM_TOL.items():
+        out = rf.reconstruct(zt, kern, "gemm", prec=prec).cpu().numpy()
+        lay = kern.gemm_layout()
+        assert lay["prec"] == prec and lay["nj"] == 16 and lay["shifts"] == GEMM_SHIFTS[prec], lay
+        assert lay["kc"] * lay["nck"] == lay["lp"] + 128 * (lay["shifts"] - 1) and lay["lp"] >= 300
+        worst = max(_relerr(out[j], zo[j]) for j in range(len(lengths)))
+        assert worst < tol, (prec, worst)
+        P, A = rf.reconstruct_winmax(zt, kern, 100, "gemm", prec=prec)
+        P, A = P.cpu().numpy(), A.cpu().numpy()
+        for j in range(len(lengths)):
+            Po, Ao = reconstruct.window_peaks(zo[j], 100)
+            assert np.abs(P[j] - Po).max() <= 4 * tol * Po.max()
+            _argmax_ok(zo[j].real ** 2 + zo[j].imag ** 2, A[j], Ao, 100, 8 * tol * Po.max())
+
+
+def test_reconstruct_gemm_short_kernels_small_set(torch):
+    """At most 16 neighbours whose kernels fit one tile take the widest groups without stacked
+    tiles; results against the oracle."""
+    n = 1 << 12
+    rng = np.random.default_rng(31)
+    lengths = [1, 64, 128, 100, 7]
+    lags = [3, -9, 0, 200, -1000]
+    cfg = replace(workload.config(1, n_override=n, k_override=1), dtype="f32")
+    rf = _rf(cfg)
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    taps = [((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(L)).astype(np.complex64)
+            for L in lengths]
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    zt = torch.tensor(z, device="cuda")
+    zo = [reconstruct.reconstruct_direct(z.astype(np.complex128), lags[j], taps[j].astype(np.complex128))
+          for j in range(len(lengths))]
+    for prec, tol in GEMM_TOL.items():
+        out = rf.reconstruct(zt, kern, "gemm", prec=prec).cpu().numpy()
+        lay = kern.gemm_layout()
+        assert lay["shifts"] == 1 and lay["nj"] > 16, lay
+        worst = max(_relerr(out[j], zo[j]) for j in range(len(lengths)))
+        assert worst < tol, (prec, worst)
+
+
 def test_reconstruct_gemm_wide_groups(torch):
     """More neighbours than one 16-wide group: the widest tensor-core tiles (all split terms of
     a group side by side in N) against the oracle, with a ragged last group."""
