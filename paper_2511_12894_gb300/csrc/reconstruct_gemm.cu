@@ -29,7 +29,9 @@
 // an MMA spans K = 8, so the Hankel core matrix at row block r and K block q starts at
 // z[b + 8r + 4q], i.e. depends on d = 2r + q: consecutive d are the K neighbours and d + 2
 // the next row block.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <memory>
@@ -157,41 +159,69 @@ __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restr
   }
 }
 
-// z_ref split into BF16 (or TF32) planes once per call: plane (p, s) holds term s of the
-// real (p = 0) or imaginary (p = 1) part, element x of the circular sequence at index x + pad
-// for x in [-pad, n + tail) (the tail covers the extended K range of up to 8 output shifts);
-// pad = 7 (mod 8) makes every Hankel row-block window 16-byte aligned.  The split runs in FP32 (complex128 inputs are rounded to FP32 first, well inside
-// the resolution of the split terms).
+// z_ref split into BF16 (or TF32) terms once per call and stored as the Hankel core matrices the
+// MMAs read, for every start position: record [pt][d] (pt = plane r/i x term s) is the 8 x 16-byte
+// core matrix whose row a holds term s of elements x = R d + a + e - pad (e < R values per row;
+// R = 8 BF16 or 4 TF32) of the circular sequence, so a chunk's distinct core matrices are one
+// contiguous run of records per (plane, term) and one TMA box loads them all.  pad = 7 (mod 8)
+// makes every chunk start a whole record; the tail covers the extended K range of up to 8 output
+// shifts.  The split runs in FP32 (complex128 inputs are rounded to FP32 first, well inside the
+// resolution of the split terms).
 static int64_t gemm_zpad(int64_t LP) { return ((LP + 8 + 7) / 8) * 8 + 7; }
 static int64_t gemm_zlen(int64_t n, int64_t LP) { return ((gemm_zpad(LP) + n + 1024 + 160 + 7) / 8) * 8; }
+static int64_t gemm_zrecs(int64_t n, int64_t LP, bool tf32) { return gemm_zlen(n, LP) / (tf32 ? 4 : 8); }
+
+__device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&v)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w[i] = (uint32_t)__bfloat16_as_ushort(v[2 * i]) | ((uint32_t)__bfloat16_as_ushort(v[2 * i + 1]) << 16);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
 
 template <typename V>
-__global__ void k_gemm_split_z(const V* __restrict__ z, int64_t n, int64_t pad, int64_t len, int terms,
-                               __nv_bfloat16* __restrict__ planes) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= len) return;
-  const V v = z[(idx - pad) & (n - 1)];
-  __nv_bfloat16 r[3], i[3];
-  split3<float>((float)v.x, r[0], r[1], r[2]);
-  split3<float>((float)v.y, i[0], i[1], i[2]);
-  for (int s = 0; s < terms; ++s) {
-    planes[(int64_t)(0 * terms + s) * len + idx] = r[s];
-    planes[(int64_t)(1 * terms + s) * len + idx] = i[s];
+__global__ void k_gemm_split_z(const V* __restrict__ z, int64_t n, int64_t pad, int64_t recs, int terms,
+                               __nv_bfloat16* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (record d, row a)
+  if (t >= recs * 8) return;
+  const int64_t d = t >> 3;
+  const int a = (int)(t & 7);
+  __nv_bfloat16 r[3][8], im[3][8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const V v = z[(8 * d + a + e - pad) & (n - 1)];
+    split3<float>((float)v.x, r[0][e], r[1][e], r[2][e]);
+    split3<float>((float)v.y, im[0][e], im[1][e], im[2][e]);
+  }
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    if (s < terms) {
+      *reinterpret_cast<uint4*>(out + ((int64_t)(0 * terms + s) * recs + d) * 64 + a * 8) = pack8(r[s]);
+      *reinterpret_cast<uint4*>(out + ((int64_t)(1 * terms + s) * recs + d) * 64 + a * 8) = pack8(im[s]);
+    }
   }
 }
 
 template <typename V>
-__global__ void k_gemm_split_z_tf32(const V* __restrict__ z, int64_t n, int64_t pad, int64_t len,
-                                    float* __restrict__ planes) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= len) return;
-  const V v = z[(idx - pad) & (n - 1)];
-  float r[2], i[2];
-  split2_tf32<float>((float)v.x, r[0], r[1]);
-  split2_tf32<float>((float)v.y, i[0], i[1]);
+__global__ void k_gemm_split_z_tf32(const V* __restrict__ z, int64_t n, int64_t pad, int64_t recs,
+                                    float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (record d, row a)
+  if (t >= recs * 8) return;
+  const int64_t d = t >> 3;
+  const int a = (int)(t & 7);
+  float r[2][4], im[2][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const V v = z[(4 * d + a + e - pad) & (n - 1)];
+    split2_tf32<float>((float)v.x, r[0][e], r[1][e]);
+    split2_tf32<float>((float)v.y, im[0][e], im[1][e]);
+  }
+#pragma unroll
   for (int s = 0; s < 2; ++s) {
-    planes[(int64_t)(0 * 2 + s) * len + idx] = r[s];
-    planes[(int64_t)(1 * 2 + s) * len + idx] = i[s];
+    *reinterpret_cast<float4*>(out + ((int64_t)(0 * 2 + s) * recs + d) * 32 + a * 4) =
+        make_float4(r[s][0], r[s][1], r[s][2], r[s][3]);
+    *reinterpret_cast<float4*>(out + ((int64_t)(1 * 2 + s) * recs + d) * 32 + a * 4) =
+        make_float4(im[s][0], im[s][1], im[s][2], im[s][3]);
   }
 }
 
@@ -250,16 +280,17 @@ __host__ __device__ constexpr int gemm_shifts_max(int prec, int NJ) {
 // Output shift s (tile rows i0 + 128 s + m) needs z[b + m + t'] at t' = t + 128 s, so all S
 // tiles share the Hankel operand of an extended K range (LP + 128 (S - 1) taps) and the tap
 // operand holds, per shift, the taps moved down by 128 s (zero outside the kernel): one MMA
-// serves S tiles, NC = S x 2 NJ columns per B term.  The taps are consumed in NCK chunks of KC:
-// per chunk the block stages the Hankel core matrices and (when there is more than one chunk)
-// the chunk's tap operands, issues one MMA per (K step, plane, A term) whose N spans every B
-// term paired with that A term, and folds the chunk's column groups into FP32 register sums
-// (plain BF16 accumulates in tensor memory).
+// serves S tiles, NC = S x 2 NJ columns per B term.  The (tile, chunk) steps q of the block run
+// through two shared-memory stages: thread 0 loads step q + 1 (the chunk's Hankel core matrices
+// by one TMA box, its tap operands by one bulk copy, both completing on full[stage]) while the
+// MMAs of step q run; it issues one MMA per (K step, plane, A term) whose N spans every B term
+// paired with that A term; the block folds the chunk's column groups into FP32 register sums
+// (plain BF16 accumulates in tensor memory) and after the tile's last chunk writes the outputs
+// or their window peaks.
 template <typename V, int NJ, int PREC, bool WINMAX, int S>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict__ zp_v, int64_t zpad,
-                                                          int64_t zlen, int64_t n,
-                                                          const void* __restrict__ Bg, int KC, int NCK, int LP,
-                                                          int k, const int* __restrict__ lag0, int TM,
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant__ CUtensorMap zmap, int64_t zpad,
+                                                          int64_t n, const void* __restrict__ Bg, int KC, int NCK,
+                                                          int LP, int k, const int* __restrict__ lag0, int TM,
                                                           V* __restrict__ z_out, unsigned long long* __restrict__ keys,
                                                           int64_t W, int64_t nw, int tmem_cols,
                                                           int* __restrict__ status) {
@@ -270,36 +301,53 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
   constexpr bool MERGED = prec_merged(PREC);
   constexpr bool TF = prec_tf32(PREC);
   constexpr int EB = prec_ebytes(PREC);     // bytes per operand value
+  constexpr int RSTEP = TF ? 4 : 8;         // elements between consecutive core-matrix records
   static_assert(NC % 16 == 0 && NC * b_terms_for(PREC, 0) <= 256, "MMA width");
   static_assert((2 * NJ) % 16 == 0, "a 16-column slice holds one shift");
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long mbar, mbar_b;
+  __shared__ __align__(8) unsigned long long mbar, full[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = blockIdx.y;
   const int nH = hankel_cores(PREC, KC);              // distinct Hankel core matrices per chunk
   const int a_bytes = nH * 128;                       // per (plane, term)
   const int b_bytes = NC * KC * EB;                   // per (plane, term)
-  unsigned char* sA = smem;                           // [plane][term][nH][128 B]
-  unsigned char* sB = smem + 2 * TERMS * a_bytes;     // [plane][term][NC/8][KC/(16/EB)][128 B]
+  const uint32_t a_stage = (uint32_t)(2 * TERMS * a_bytes), b_stage = (uint32_t)(2 * TERMS * b_bytes);
+  // stage st: [plane][term][nH][128 B] Hankel cores, then [plane][term][NC/8][KC/(16/EB)][128 B] taps
+  auto stage_a = [&](int st) { return smem + st * (a_stage + b_stage); };
   const int64_t mask = n - 1;
-  const unsigned char* Bgrp = static_cast<const unsigned char*>(Bg) + (int64_t)g * NCK * 2 * TERMS * b_bytes;
+  const unsigned char* Bgrp = static_cast<const unsigned char*>(Bg) + (int64_t)g * NCK * b_stage;
+  const int64_t tiles = (n + kGemmM * S - 1) / (kGemmM * S);
+  const int64_t tile0 = (int64_t)blockIdx.x * TM;
+  const int my_tiles = (int)max((int64_t)0, min((int64_t)TM, tiles - tile0));
+  const int Q = my_tiles * NCK;                       // (tile, chunk) steps of this block
 
-  // The chunk's tap operands (contiguous in global memory) arrive by one bulk copy, issued by
-  // thread 0 and completed on mbar_b, while the block stages the Hankel core matrices.
-  const uint32_t mbar_b_addr = smem_u32(&mbar_b);
-  const uint32_t b_chunk_bytes = (uint32_t)(2 * TERMS * b_bytes);
-  auto issue_b = [&](int c) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_b_addr), "r"(b_chunk_bytes)
+  // thread 0: start the loads of step q into stage st
+  auto issue_loads = [&](int q, int st) {
+    const int tile = q / NCK, c = q - tile * NCK;
+    const int64_t i0 = (tile0 + tile) * (kGemmM * S);
+    const int64_t bc = i0 - LP + 1 + (int64_t)c * KC + zpad;  // first element of the chunk (a record start)
+    const uint32_t fb = smem_u32(&full[st]);
+    unsigned char* sa = stage_a(st);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(a_stage + b_stage)
                  : "memory");
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(sB)),
-        "l"(Bgrp + (int64_t)c * b_chunk_bytes), "r"(b_chunk_bytes), "r"(mbar_b_addr)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(sa)),
+        "l"(reinterpret_cast<uint64_t>(&zmap)), "r"(0), "r"((int)(bc / RSTEP)), "r"(0), "r"(fb)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sa + a_stage)),
+        "l"(Bgrp + (int64_t)c * b_stage), "r"(b_stage), "r"(fb)
         : "memory");
   };
+
   if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&zmap)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_b_addr));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[1])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -312,76 +360,31 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t mbar_addr = smem_u32(&mbar);
-  uint32_t phase = 0, phase_b = 0;
-  bool ok = true;
+  uint32_t phase = 0;
   const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
   const unsigned int Wu = (unsigned int)(W < n ? W : n), nwu = (unsigned int)nw;  // n <= 2^24
-  bool b_pending = NCK == 1;  // a single chunk is loaded once for every tile
-  if (b_pending && tid == 0) issue_b(0);
+  if (tid == 0 && Q > 0) issue_loads(0, 0);
+  float run[FOLD ? NC : 1];
 
-  for (int tile = 0; tile < TM && ok; ++tile) {
-    const int64_t i0 = ((int64_t)blockIdx.x * TM + tile) * (kGemmM * S);
-    if (i0 >= n) break;
-    const int64_t b = i0 - LP + 1;
-    float run[FOLD ? NC : 1];
+  for (int q = 0; q < Q; ++q) {
+    const int st = q & 1, tile = q / NCK, c = q - tile * NCK;
+    const int64_t i0 = (tile0 + tile) * (kGemmM * S);
+    if (c == 0) {
 #pragma unroll
-    for (int cidx = 0; cidx < (FOLD ? NC : 1); ++cidx) run[cidx] = 0.f;
-    for (int c = 0; c < NCK && ok; ++c) {
-      if (NCK > 1) {
-        if (tid == 0) issue_b(c);
-        b_pending = true;
+      for (int cidx = 0; cidx < (FOLD ? NC : 1); ++cidx) run[cidx] = 0.f;
+    }
+    bool lok = true, next = false;
+    if (tid == 0) {
+      // the other stage was last read by the MMAs of step q - 1, which have completed: its
+      // next loads start before this step's MMAs, a whole step ahead of their use
+      if (q + 1 < Q) {
+        issue_loads(q + 1, st ^ 1);
+        next = true;
       }
-      // Hankel core matrices of the chunk: row a of H_d is z[b + c KC + 8d + a + e], e < 8.
-      // One task = one (plane, term, d): the aligned 16-element window starting at
-      // b + c KC + 8d gives all eight rows by funnel shifts.  (One 16-byte row per thread
-      // avoids the shared-memory bank conflicts of these stores but measured slower: five
-      // scalar loads per row instead of two vector loads per eight rows.)
-      // (TF32: row a of H_d is z[b + c KC + 4d + a + e], e < 4, words a..a+3 of the aligned
-      // 12-word window at b + c KC + 4d.)
-      const int64_t bc = b + (int64_t)c * KC + zpad;  // plane index of the chunk's first element
-      for (int task = tid; task < 2 * TERMS * nH; task += kGemmThreads) {
-        const int pt = task / nH, d = task - pt * nH;
-        unsigned char* dst = sA + pt * a_bytes + d * 128;
-        if constexpr (TF) {
-          const uint4* src =
-              reinterpret_cast<const uint4*>(static_cast<const float*>(zp_v) + (int64_t)pt * zlen + bc + 4 * d);
-          const uint4 p0 = src[0], p1 = src[1], p2 = src[2];
-          const uint32_t w[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
-#pragma unroll
-          for (int a = 0; a < 8; ++a)
-            *reinterpret_cast<uint4*>(dst + a * 16) = make_uint4(w[a], w[a + 1], w[a + 2], w[a + 3]);
-        } else {
-          const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(zp_v) +
-                                                            (int64_t)pt * zlen + bc + 8 * d);
-          const uint4 lo = src[0], hi = src[1];
-          const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            uint32_t o[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = __funnelshift_r(w[a / 2 + q], w[a / 2 + q + 1], (a & 1) * 16);
-            *reinterpret_cast<uint4*>(dst + a * 16) = make_uint4(o[0], o[1], o[2], o[3]);
-          }
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bool b_ok = true;
-      if (b_pending) {
-        if (tid == 0) b_ok = mbar_wait(mbar_b_addr, phase_b);
-        phase_b ^= 1u;
-        b_pending = false;
-      }
-      if (!__syncthreads_and(b_ok)) {
-        if (tid == 0) {
-          atomicExch(status, (int)RF_ETIMEOUT);
-          mbar_wait(mbar_b_addr, phase_b ^ 1u);  // one more bounded wait for the copy in flight
-        }
-        ok = false;
-        __syncthreads();
-        break;
-      }
-      if (tid == 0) {
+      lok = mbar_wait(smem_u32(&full[st]), (uint32_t)((q >> 1) & 1));
+      if (lok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* sa = stage_a(st);
         // A K step (32 bytes of every row: K = 16 BF16 or 8 TF32 values) spans two core
         // matrices along K, so step ks adds ks * 256 bytes to each start address, i.e. ks * 16
         // to the descriptor's low field (addresses stay below 256 KB, so the field never
@@ -389,10 +392,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
         // 8-row block along M or N.
         uint64_t adesc[2 * TERMS], bdesc[2];
 #pragma unroll
-        for (int i = 0; i < 2 * TERMS; ++i) adesc[i] = smem_desc(smem_u32(sA + i * a_bytes), 128, TF ? 256 : 128);
+        for (int i = 0; i < 2 * TERMS; ++i) adesc[i] = smem_desc(smem_u32(sa + i * a_bytes), 128, TF ? 256 : 128);
 #pragma unroll
         for (int pl = 0; pl < 2; ++pl)
-          bdesc[pl] = smem_desc(smem_u32(sB + pl * TERMS * b_bytes), 128, KC * 8 * EB);
+          bdesc[pl] = smem_desc(smem_u32(sa + a_stage + pl * TERMS * b_bytes), 128, KC * 8 * EB);
         for (int ks = 0; ks < KC * EB / 32; ++ks) {
           const uint64_t koff = (uint64_t)(ks * 16);
 #pragma unroll
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
             for (int ta = 0; ta < TERMS; ++ta) {
               const uint32_t idesc = mma_idesc(NC * b_terms_for(PREC, ta), TF ? 2u : 1u);
               const uint32_t d = tmem + (uint32_t)tile_col(PREC, ta, NC);
-              // the first MMA of a chunk (of the call, for plain BF16) overwrites its columns;
+              // the first MMA of a chunk (of the tile, for plain BF16) overwrites its columns;
               // merged groups are all first written by A term 0
               const bool first = (FOLD || c == 0) && ks == 0 && pl == 0 && (!MERGED || ta == 0);
               const uint32_t acc = first ? 0u : 1u;
@@ -417,100 +420,134 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const void* __restrict
                     "l"(adesc[pl * TERMS + ta] + koff), "l"(bdesc[pl] + koff), "r"(idesc), "r"(acc));
             }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
-                     : "memory");
       }
-      const bool done = mbar_wait(mbar_addr, phase);
-      phase ^= 1u;
-      if (!__syncthreads_and(done)) {
-        if (tid == 0) atomicExch(status, (int)RF_ETIMEOUT);
-        ok = false;
-        mbar_wait(mbar_addr, phase ^ 1u);  // one more bounded wait before tensor memory is released
-        break;
+      // the commit arrives once every MMA issued so far has completed (at once when none was)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
+                   : "memory");
+    }
+    const bool done = mbar_wait(mbar_addr, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(done && lok)) {
+      if (tid == 0) {
+        atomicExch(status, (int)RF_ETIMEOUT);
+        // bounded waits for whatever is still in flight before shared and tensor memory go
+        if (!lok) mbar_wait(smem_u32(&full[st]), (uint32_t)((q >> 1) & 1));
+        if (next) mbar_wait(smem_u32(&full[st ^ 1]), (uint32_t)(((q + 1) >> 1) & 1));
+        if (!done) mbar_wait(mbar_addr, phase ^ 1u);
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if constexpr (FOLD) {
-        // row sums of the chunk: the leading product plus the corrections
-        constexpr int NG = prec_groups(PREC);
+      __syncthreads();
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if constexpr (FOLD) {
+      // row sums of the chunk: the leading product plus the corrections
+      constexpr int NG = prec_groups(PREC);
 #pragma unroll
-        for (int h = 0; h < NC / 16; ++h) {
-          float big[16], small[16];
+      for (int h = 0; h < NC / 16; ++h) {
+        float big[16], small[16];
 #pragma unroll
-          for (int cc = 0; cc < 16; ++cc) big[cc] = small[cc] = 0.f;
+        for (int g0 = 0; g0 < NG; g0 += 3) {  // up to three loads in flight per wait
+          uint32_t v[3][16];
 #pragma unroll
-          for (int grp = 0; grp < NG; ++grp) {
-            uint32_t v[16];
-            tmem_ld16(taddr + (uint32_t)(grp * NC + 16 * h), v);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int gg = 0; gg < 3; ++gg)
+            if (g0 + gg < NG) tmem_ld16(taddr + (uint32_t)((g0 + gg) * NC + 16 * h), v[gg]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int gg = 0; gg < 3; ++gg)
 #pragma unroll
             for (int cc = 0; cc < 16; ++cc) {
-              if (grp == 0) big[cc] += __uint_as_float(v[cc]);
-              else small[cc] += __uint_as_float(v[cc]);
+              if (g0 + gg == 0) {
+                big[cc] = __uint_as_float(v[gg][cc]);
+                small[cc] = 0.f;
+              } else if (g0 + gg < NG) {
+                small[cc] += __uint_as_float(v[gg][cc]);
+              }
             }
-          }
-#pragma unroll
-          for (int cc = 0; cc < 16; ++cc) run[16 * h + cc] += big[cc] + small[cc];
         }
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) run[16 * h + cc] += big[cc] + small[cc];
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // shared tiles and tensor memory are rewritten by the next chunk
     }
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (c == NCK - 1) {
 #pragma unroll
-    for (int h = 0; h < NC / 16; ++h) {
-      const int sh = (16 * h) / (2 * NJ);             // output shift of this column slice
-      if (i0 + (int64_t)kGemmM * sh >= n) break;      // uniform across the block
-      const int64_t ip = i0 + kGemmM * sh + warp * 32 + lane;  // i'
-      const int jb = ((16 * h) % (2 * NJ)) / 2;       // first neighbour of the slice
-      float val[16];
-      if constexpr (FOLD) {
+      for (int h = 0; h < NC / 16; ++h) {
+        const int sh = (16 * h) / (2 * NJ);             // output shift of this column slice
+        if (i0 + (int64_t)kGemmM * sh >= n) break;      // uniform across the block
+        const int64_t ip = i0 + kGemmM * sh + warp * 32 + lane;  // i'
+        const int jb = ((16 * h) % (2 * NJ)) / 2;       // first neighbour of the slice
+        float val[16];
+        if constexpr (FOLD) {
 #pragma unroll
-        for (int cc = 0; cc < 16; ++cc) val[cc] = run[16 * h + cc];
-      } else {
-        uint32_t v[16];
-        tmem_ld16(taddr + (uint32_t)(16 * h), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int cc = 0; cc < 16; ++cc) val[cc] = run[16 * h + cc];
+        } else {
+          uint32_t v[16];
+          tmem_ld16(taddr + (uint32_t)(16 * h), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int cc = 0; cc < 16; ++cc) val[cc] = __uint_as_float(v[cc]);
-      }
+          for (int cc = 0; cc < 16; ++cc) val[cc] = __uint_as_float(v[cc]);
+        }
+        const int nj = min(8, k - (g * NJ + jb));  // neighbours in this slice (uniform)
+        if (nj <= 0) continue;
+        if constexpr (!WINMAX) {
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int j = g * NJ + jb + jj;
-        if (j >= k) break;  // uniform across the block
-        const float re = val[2 * jj], im = val[2 * jj + 1];
-        const unsigned int i = (unsigned int)((ip + lag0[j]) & mask);
-        if (!WINMAX) {
-          z_out[(int64_t)j * n + i] = cmake<V>((R)re, (R)im);
+          for (int jj = 0; jj < 8; ++jj) {
+            if (jj >= nj) break;
+            const int j = g * NJ + jb + jj;
+            const unsigned int i = (unsigned int)((ip + lag0[j]) & mask);
+            z_out[(int64_t)j * n + i] = cmake<V>((R)val[2 * jj], (R)val[2 * jj + 1]);
+          }
         } else {
           // The warp's 32 outputs are consecutive modulo n: usually they fall in lane 0's window
           // wA and the next one wB (window 0 after the wrap), decided by comparison; per window
           // the largest |z|^2 (non-negative floats order as their bit patterns) and then the
-          // smallest index holding it come from two 32-bit warp reductions.
-          const float p = re * re + im * im;
-          const unsigned int pb = __float_as_uint(p);
-          unsigned long long* kj = keys + (int64_t)j * nw;
-          const unsigned int wA = __shfl_sync(0xffffffffu, i, 0) / Wu;
-          const unsigned int wB = (wA + 1 == nwu) ? 0u : wA + 1;
-          const bool inA = i - wA * Wu < Wu;
-          const bool inB = !inA && i - wB * Wu < Wu;
-          if (__any_sync(0xffffffffu, !(inA || inB))) {
-            atomicMax(kj + i / Wu, gemm_key(p, i));
+          // smallest index holding it come from two 32-bit warp reductions.  The slice's
+          // neighbours are independent chains, interleaved.
+          unsigned int iv[8], pb[8], wA[8], wB[8];
+          bool inA[8], inB[8], slow = false;
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = g * NJ + jb + min(jj, nj - 1);
+            iv[jj] = (unsigned int)((ip + lag0[j]) & mask);
+            pb[jj] = __float_as_uint(val[2 * jj] * val[2 * jj] + val[2 * jj + 1] * val[2 * jj + 1]);
+            wA[jj] = (unsigned int)((ip - lane + lag0[j]) & mask) / Wu;  // lane 0's window
+            wB[jj] = (wA[jj] + 1 == nwu) ? 0u : wA[jj] + 1;
+            inA[jj] = iv[jj] - wA[jj] * Wu < Wu;
+            inB[jj] = !inA[jj] && iv[jj] - wB[jj] * Wu < Wu;
+            if (jj < nj) slow |= !(inA[jj] || inB[jj]);
+          }
+          if (__any_sync(0xffffffffu, slow)) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+              if (jj < nj)
+                atomicMax(keys + (int64_t)(g * NJ + jb + jj) * nw + iv[jj] / Wu,
+                          gemm_key(__uint_as_float(pb[jj]), iv[jj]));
           } else {
-            const unsigned int mA = __reduce_max_sync(0xffffffffu, inA ? pb : 0u);
-            const unsigned int mB = __reduce_max_sync(0xffffffffu, inB ? pb : 0u);
-            const unsigned int xA = __reduce_min_sync(0xffffffffu, (inA && pb == mA) ? i : 0xffffffffu);
-            const unsigned int xB = __reduce_min_sync(0xffffffffu, (inB && pb == mB) ? i : 0xffffffffu);
+            unsigned int mA[8], mB[8], xA[8], xB[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              mA[jj] = __reduce_max_sync(0xffffffffu, inA[jj] ? pb[jj] : 0u);
+              mB[jj] = __reduce_max_sync(0xffffffffu, inB[jj] ? pb[jj] : 0u);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              xA[jj] = __reduce_min_sync(0xffffffffu, (inA[jj] && pb[jj] == mA[jj]) ? iv[jj] : 0xffffffffu);
+              xB[jj] = __reduce_min_sync(0xffffffffu, (inB[jj] && pb[jj] == mB[jj]) ? iv[jj] : 0xffffffffu);
+            }
             if (lane == 0) {
-              if (xA != 0xffffffffu) atomicMax(kj + wA, gemm_key(__uint_as_float(mA), xA));
-              if (xB != 0xffffffffu) atomicMax(kj + wB, gemm_key(__uint_as_float(mB), xB));
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                if (jj >= nj) break;
+                unsigned long long* kj = keys + (int64_t)(g * NJ + jb + jj) * nw;
+                if (xA[jj] != 0xffffffffu) atomicMax(kj + wA[jj], gemm_key(__uint_as_float(mA[jj]), xA[jj]));
+                if (xB[jj] != 0xffffffffu) atomicMax(kj + wB[jj], gemm_key(__uint_as_float(mB[jj]), xB[jj]));
+              }
             }
           }
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // tensor memory is rewritten by the next tile
+    __syncthreads();  // tensor memory is rewritten by the next step's MMAs
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -526,10 +563,36 @@ __global__ void k_gemm_unpack(const unsigned long long* __restrict__ keys, int64
   arg[i] = (int)(0xffffffffu - (unsigned int)(kk & 0xffffffffull));
 }
 
+// Two stages of (Hankel records, tap operands).
 size_t gemm_smem_bytes(int prec, int NJ, int S, int KC) {
   const int terms = prec_terms(prec);
-  return (size_t)2 * terms * hankel_cores(prec, KC) * 128 +
-         (size_t)2 * terms * (S * 2 * NJ) * KC * prec_ebytes(prec) + 1024;
+  return 2 * ((size_t)2 * terms * hankel_cores(prec, KC) * 128 +
+              (size_t)2 * terms * (S * 2 * NJ) * KC * prec_ebytes(prec)) +
+         1024;
+}
+
+// Tensor map over the core-matrix records: element type BF16 (or 32-bit words for TF32),
+// dims (values per record, records, planes x terms), no swizzle, zero fill outside.
+CUtensorMap gemm_tensor_map(void* base, bool tf32, int64_t recs, int planes, int box_recs) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q{};
+    void* fn = nullptr;
+    RF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    RF_REQUIRE(fn != nullptr && q == cudaDriverEntryPointSuccess, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint32_t per = tf32 ? 32 : 64;  // values per 128-byte record
+  CUtensorMap m;
+  const cuuint64_t dims[3] = {per, (cuuint64_t)recs, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {128, (cuuint64_t)recs * 128};
+  const cuuint32_t box[3] = {per, (cuuint32_t)box_recs, (cuuint32_t)planes};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(&m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base,
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  RF_REQUIRE(r == CUDA_SUCCESS, "tensor map for the Hankel records rejected (CUresult %d)", (int)r);
+  return m;
 }
 
 // Tensor-memory columns: one group of S x 2 NJ columns per product order (per product for
@@ -564,28 +627,38 @@ void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, un
   smem = std::max(smem, smem_max / (size_t)(max_blocks + 1) + 1024);
   smem = std::min(smem, (size_t)220 * 1024);
   auto fn = k_gemm<V, NJ, PREC, WINMAX, S>;
-  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGemmThreads, smem));
-  RF_REQUIRE(per_sm >= 1 && per_sm * cols <= 512,
-             "tensor-core form: %d blocks per SM x %d columns exceed tensor memory", per_sm, cols);
+  // the attribute and the occupancy check are made once per (device, shared-memory size)
+  static size_t done_smem[16] = {};
+  const int dv = c->device & 15;
+  if (done_smem[dv] != smem) {
+    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGemmThreads, smem));
+    RF_REQUIRE(per_sm >= 1 && per_sm * cols <= 512,
+               "tensor-core form: %d blocks per SM x %d columns exceed tensor memory", per_sm, cols);
+    done_smem[dv] = smem;
+  }
   const int64_t tiles = (c->n + kGemmM * S - 1) / (kGemmM * S);
   const int groups = (kern->k + NJ - 1) / NJ;
   int TM = 1;
   while (TM < 16 && (tiles / (TM * 2)) * groups >= 4LL * c->nsm) TM *= 2;
   dim3 grid((unsigned)((tiles + TM - 1) / TM), (unsigned)groups);
-  // z_ref split into BF16 (TF32) planes, padded so that no Hankel window wraps
-  const int64_t zpad = gemm_zpad(LP), zlen = gemm_zlen(c->n, LP);
+  // z_ref split into BF16 (TF32) core-matrix records, padded so that no Hankel window wraps
+  constexpr bool TF = prec_tf32(PREC);
+  const int64_t zpad = gemm_zpad(LP), recs = gemm_zrecs(c->n, LP, TF);
   c->scratch2.ensure(gemm_zplanes_bytes(c->n, LP, PREC));
   void* zp = c->scratch2.as<unsigned char>();
-  if constexpr (prec_tf32(PREC))
-    k_gemm_split_z_tf32<V><<<(unsigned)((zlen + 255) / 256), 256, 0, s>>>(z_ref, c->n, zpad, zlen,
-                                                                         static_cast<float*>(zp));
+  const unsigned split_blocks = (unsigned)((recs * 8 + 255) / 256);
+  if constexpr (TF)
+    k_gemm_split_z_tf32<V><<<split_blocks, 256, 0, s>>>(z_ref, c->n, zpad, recs, static_cast<float*>(zp));
   else
-    k_gemm_split_z<V><<<(unsigned)((zlen + 255) / 256), 256, 0, s>>>(z_ref, c->n, zpad, zlen, prec_terms(PREC),
-                                                                    static_cast<__nv_bfloat16*>(zp));
+    k_gemm_split_z<V><<<split_blocks, 256, 0, s>>>(z_ref, c->n, zpad, recs, prec_terms(PREC),
+                                                   static_cast<__nv_bfloat16*>(zp));
   RF_LAUNCHED();
-  fn<<<grid, kGemmThreads, smem, s>>>(zp, zpad, zlen, c->n, kern->gemm_B.as<unsigned char>(), KC, NCK, LP, kern->k,
+  // one TMA box = a chunk's nH records of every (plane, term): dims (record bytes / EB, records,
+  // planes x terms)
+  const CUtensorMap zmap = gemm_tensor_map(zp, TF, recs, 2 * prec_terms(PREC), hankel_cores(PREC, KC));
+  fn<<<grid, kGemmThreads, smem, s>>>(zmap, zpad, c->n, kern->gemm_B.as<unsigned char>(), KC, NCK, LP, kern->k,
                                       kern->lag0_d.as<int>(), TM, z_out, keys, W, nw, cols, c->status.as<int>());
   RF_LAUNCHED();
 }
@@ -641,7 +714,7 @@ void wait_selftest(rf_ctx* c, cudaStream_t s) {
 }
 
 size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int prec) {
-  return (size_t)prec_ebytes(prec) * (size_t)(2 * prec_terms(prec)) * (size_t)gemm_zlen(n, LP) + 256;
+  return (size_t)128 * (size_t)(2 * prec_terms(prec)) * (size_t)gemm_zrecs(n, LP, prec_tf32(prec)) + 256;
 }
 
 int gemm_max_len() { return 1 << 16; }
