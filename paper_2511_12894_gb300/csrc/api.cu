@@ -166,7 +166,7 @@ rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out) {
     // overlap-save segment spectra plus packed window keys for windows of >= 16 samples
     const size_t bytes = os_workspace_bytes(ctx, k_max, 16, 8);  // the largest partition ratio
     ctx->scratch.ensure(bytes);
-    // split planes of z_ref for the tensor-core path, for taps up to the segment length
+    // core-matrix records of z_ref for the tensor-core path, for taps up to the segment length
     const size_t planes = std::max(gemm_zplanes_bytes(ctx->n, ctx->n + 128, RF_PREC_BF16X9),
                                    gemm_zplanes_bytes(ctx->n, ctx->n + 128, RF_PREC_3XTF32));
     ctx->scratch2.ensure(planes);

@@ -9,19 +9,19 @@
 //   D[m][2j]   = sum_t zr A_t cr_j - zi A_t ci_j,    D[m][2j+1] = sum_t zr ci_j + zi cr_j,
 // i.e. D = A_r B_r + A_i B_i with B_r = [cr ci], B_i = [-ci cr] per neighbour.
 //
-// The Hankel operand is never expanded: in the no-swizzle K-major layout an 8x8 BF16 core
-// matrix (8 rows of 16 bytes) at row block r and K block q holds z[b + 8(r + q) + a + e]
-// (a, e < 8), which depends on r + q only.  Shared memory keeps the distinct core matrices
-// H_d, d = r + q, back to back, and the descriptor uses the same 128-byte stride for the M
-// and K directions.
+// The Hankel operand is never expanded in shared memory: in the no-swizzle K-major layout an
+// 8x8 BF16 core matrix (8 rows of 16 bytes) at row block r and K block q holds
+// z[b + 8(r + q) + a + e] (a, e < 8), which depends on r + q only.  Shared memory keeps the
+// distinct core matrices H_d, d = r + q, back to back, and the descriptor uses the same
+// 128-byte stride for the M and K directions.  Global memory holds every core matrix as a
+// 128-byte record per start position, so a chunk's H_d arrive by one TMA box.
 //
 // Split precision: x = x0 + x1 + x2 with x_k = bf16(x - x0 - ... - x_{k-1}); the products
 // kept are (0,0) for BF16, + (0,1),(1,0) for x3, + (0,2),(1,1),(2,0) for x6, + (1,2),(2,1),(2,2)
 // for x9.  The tensor core's FP32 accumulation loses a fraction of an ulp of the running
-// sum at every MMA, so every product of every K chunk (at most 256 taps) accumulates into
-// its own tensor-memory tile, and the block adds the tiles in FP32 registers (round to
-// nearest), corrections apart from the leading product.  Separate tiles also keep
-// consecutive MMAs independent, which the tensor pipe needs to overlap short (N = 32) MMAs.
+// sum at every MMA, so the products of every K chunk (at most 128 taps) accumulate in tensor
+// memory by order (ta + tb) and the block adds them into FP32 register sums (round to
+// nearest), corrections apart from the leading product.
 //
 // 3xTF32 runs the same tiles with kind::tf32 MMAs: x = x0 + x1, x0 = tf32(x) and
 // x1 = tf32(x - x0) (each TF32 term carries 11 significant bits, so x1 resolves x to about

@@ -221,7 +221,7 @@ void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
 // launches the bounded-wait health check (reconstruct_gemm.cu)
 void wait_selftest(rf_ctx* c, cudaStream_t s);
-// bytes of the split planes of z_ref used by the tensor-core path at prec (taps padded to LP)
+// bytes of the core-matrix records of z_ref used by the tensor-core path at prec (taps padded to LP)
 size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int prec);
 void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out, int64_t W, float* max_out,
                     int32_t* argmax_out, cudaStream_t s);
