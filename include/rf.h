@@ -124,8 +124,8 @@ void rf_destroy(rf_ctx* ctx);
 /* Largest workspace the context will use for `k_max` kernels (bytes), and reserve it now
  * (allocation happens here, never later in an rf_reconstruct* call of at most k_max kernels;
  * needed before capturing reconstruct calls in a CUDA graph).  Includes the tensor-core
- * form's Hankel core-matrix records of z_ref for kernels up to n taps (about 128 (2n + 1200)
- * bytes, the 3xTF32 layout being the largest). */
+ * form's Hankel core-matrix records of z_ref for its longest kernels (min(n, 65536) taps:
+ * about 128 (n + min(n, 65536) + 1300) bytes, the 3xTF32 layout being the largest). */
 rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out);
 
 /* Template spectrum h~(f_k) = B(f_k) exp(-i Psi(f_k)), k = 0..n/2, 0 at DC (App. A, Eq. A1).

@@ -167,8 +167,9 @@ rf_status rf_reserve(rf_ctx* ctx, int32_t k_max, int64_t* bytes_out) {
     const size_t bytes = os_workspace_bytes(ctx, k_max, 16, 8);  // the largest partition ratio
     ctx->scratch.ensure(bytes);
     // core-matrix records of z_ref for the tensor-core path, for taps up to the segment length
-    const size_t planes = std::max(gemm_zplanes_bytes(ctx->n, ctx->n + 128, RF_PREC_BF16X9),
-                                   gemm_zplanes_bytes(ctx->n, ctx->n + 128, RF_PREC_3XTF32));
+    const int64_t lp_max = std::min<int64_t>(ctx->n, gemm_max_len()) + 128;
+    const size_t planes = std::max(gemm_zplanes_bytes(ctx->n, lp_max, RF_PREC_BF16X9),
+                                   gemm_zplanes_bytes(ctx->n, lp_max, RF_PREC_3XTF32));
     ctx->scratch2.ensure(planes);
     ctx->reserved = bytes;
     if (bytes_out) *bytes_out = (int64_t)(bytes + planes);
