@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -88,7 +89,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"rf_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -653,6 +654,12 @@ def main():
             "build_s": build_s, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "plain_mf_cufft": baseline, "err_vs_full_mf": err,
             "scipy_oaconvolve": sb,
+            # what a search keeps per template between analyses (Sec. IV): the plain method a
+            # template spectrum of n/2 + 1 complex values per neighbour, the ratio filter the
+            # neighbour's truncated kernel (sum of the kernel lengths); the references' own
+            # filters are common to both
+            "storage": {"full_values": int(rows * (n // 2 + 1)), "ratio_kernel_values": int(L.sum()),
+                        "ratio": float(rows * (n // 2 + 1) / max(1, int(L.sum())))},
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
