@@ -21,6 +21,9 @@ Sec. II.B-II.D and App. A.
   circular arc [m0, m0 + L) that covers every above-threshold lag (sub-threshold
   lags inside it are kept); ties go to the arc whose start, mapped to
   (-n/2, n/2], is smallest.
+* Sec. II.D with App. A, analytic truncation (optional): the kept lags come from the
+  App. A expressions instead of the kernel's magnitudes (bounds.analytic_span); parity
+  pinned against the computed kernels' tails where the bounds are asymptotic.
 * Sec. II.D, build grid: the kernels may be built on a coarser frequency grid
   f_k = k fs / n_b (n_b a power of two <= n) as long as 1/df of that grid exceeds
   the kernel's duration; rho is then the n_b-point inverse transform (the same
@@ -38,6 +41,7 @@ from typing import List, Sequence, Tuple
 
 import numpy as np
 
+from . import bounds
 from . import fft as _fft
 from . import taylorf2
 from .mf import band_limited_inv_psd, freqs, sigma
@@ -67,6 +71,17 @@ def df_low_rule(ref, tgt, pn_order: int, f_low: float, df_low_max: float) -> flo
     return min(df_low_max, 0.5 * f_low, rule)
 
 
+def norm_ratio(ref, tgt, n: int, fs: float, f_low: float, f_high: float, pn_order: int,
+               inv_psd: np.ndarray) -> float:
+    """N_ref / N (Eq. 3) on the data grid of n samples."""
+    f = freqs(n, fs)
+    ipb = band_limited_inv_psd(inv_psd, n, fs, f_low, f_high)
+    df = fs / n
+    h_ref = taylorf2.template_fd(f, ref.m1, ref.m2, pn_order, ref.tc, ref.phic)
+    h_tgt = taylorf2.template_fd(f, tgt.m1, tgt.m2, pn_order, tgt.tc, tgt.phic)
+    return sigma(h_ref, ipb, df) / sigma(h_tgt, ipb, df)
+
+
 def kernel_spectrum(ref, tgt, n: int, fs: float, f_low: float, f_high: float, pn_order: int,
                     inv_psd: np.ndarray, df_low_max: float = 5.0, df_high: float = 53.0,
                     df_low: float = None, n_build: int = None) -> Tuple[np.ndarray, float]:
@@ -74,14 +89,9 @@ def kernel_spectrum(ref, tgt, n: int, fs: float, f_low: float, f_high: float, pn
     (n_b = n_build, default n); N_ref / N (Eq. 3) on the data grid of n samples.  Returns
     (K~, df_low)."""
     nb = n if n_build is None else n_build
-    f = freqs(n, fs)
     if df_low is None:
         df_low = df_low_rule(ref, tgt, pn_order, f_low, df_low_max)
-    ipb = band_limited_inv_psd(inv_psd, n, fs, f_low, f_high)
-    df = fs / n
-    h_ref = taylorf2.template_fd(f, ref.m1, ref.m2, pn_order, ref.tc, ref.phic)
-    h_tgt = taylorf2.template_fd(f, tgt.m1, tgt.m2, pn_order, tgt.tc, tgt.phic)
-    norm = sigma(h_ref, ipb, df) / sigma(h_tgt, ipb, df)            # N_ref / N
+    norm = norm_ratio(ref, tgt, n, fs, f_low, f_high, pn_order, inv_psd)   # N_ref / N
     fb = freqs(nb, fs)
     w = window(fb, f_low, f_high, df_low, df_high)
     sup = w > 0
@@ -172,11 +182,15 @@ class PackedKernels:
 
 def build_ratio_kernels(ref, targets: Sequence, n: int, fs: float, f_low: float, f_high: float,
                         pn_order: int, inv_psd: np.ndarray, thr: float, relative: bool = True,
-                        df_low_max: float = 5.0, df_high: float = 53.0, n_build: int = 0) -> PackedKernels:
+                        df_low_max: float = 5.0, df_high: float = 53.0, n_build: int = 0,
+                        analytic: bool = False) -> PackedKernels:
     """Kernel spectrum -> full kernel -> threshold truncation, per target.
 
     n_build: 0 builds on the data grid (n lags); a power of two builds every kernel on that
-    grid; -1 takes build_grid_rule per target.  Lags are signed on the build grid."""
+    grid; -1 takes build_grid_rule per target.  Lags are signed on the build grid.
+    analytic: the kept lags come from the App. A expressions (bounds.analytic_span) instead
+    of the kernel's own magnitudes; a relative threshold is then taken on the kernel's peak
+    of |r| = 2 fs |rho| / (N_ref / N), an absolute one is a threshold amplitude on |r| in 1/s."""
     lag0: List[int] = []
     length: List[int] = []
     taps: List[np.ndarray] = []
@@ -188,7 +202,17 @@ def build_ratio_kernels(ref, targets: Sequence, n: int, fs: float, f_low: float,
                                      build_grid_rule(ref, t, n, fs, f_low, f_high, pn_order, d, df_high))
         K, _ = kernel_spectrum(ref, t, n, fs, f_low, f_high, pn_order, inv_psd, df_low_max, df_high, d, nb)
         rho = kernel_full(K, nb)
-        m0, L, c = truncate(rho, thr, relative)
+        if analytic:
+            peak = float(np.abs(rho).max()) if nb else 0.0
+            amp = thr * 2.0 * fs * peak / norm_ratio(ref, t, n, fs, f_low, f_high, pn_order, inv_psd) \
+                if relative else thr
+            if amp <= 0.0:
+                m0, L, c = 0, 0, np.zeros(0, dtype=np.complex128)
+            else:
+                m0, L = bounds.analytic_span(ref, t, pn_order, f_low, f_high, d, df_high, fs, nb, amp)
+                c = rho[(m0 + np.arange(L)) % nb]
+        else:
+            m0, L, c = truncate(rho, thr, relative)
         lag0.append(m0)
         length.append(L)
         taps.append(c)

@@ -234,3 +234,46 @@ def test_coarse_build_grid_reproduces_the_data_grid_kernels():
     # longer kernels get grids at least as large
     order = np.argsort(fine.length)
     assert np.all(np.diff(coarse.grid[order]) >= 0)
+
+
+@pytest.mark.parametrize("cfg_id,js", [(1, [0, 7, 15]), (2, [0, 5, 200])])
+def test_analytic_span_follows_the_kernel(cfg_id, js):
+    """Analytic truncation (Sec. II.D with the App. A expressions): the kept lags contain the
+    stationary region between the window edges' times, outside them the kernel's |r| stays
+    within a small factor of the threshold amplitude (the Eqs. (A9)-(A10) bounds hold far from
+    the edges only), and the span is of the order of the numeric arc at the same threshold;
+    absolute thresholds (the paper's 1e-3 / s, and 1e-2 / s) and a small relative one, where
+    the tails reach well past the edges (the bounds are asymptotic: at a relative 1e-3 the
+    reach beyond a sharp high-frequency edge is under two taper widths and the near sidelobes
+    exceed it)."""
+    cfg = workload.config(cfg_id)
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    for rel, thr in [(True, 3e-5), (False, 1e-3), (False, 1e-2)]:
+        for j in js:
+            t = nb[j]
+            a = ratio.build_ratio_kernels(ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, thr, rel,
+                                          n_build=-1, analytic=True)
+            nbg = int(a.grid[0])
+            d = ratio.df_low_rule(ref, t, cfg.pn_order, cfg.f_low, cfg.df_low_max)
+            K, _ = ratio.kernel_spectrum(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, n_build=nbg)
+            rho = ratio.kernel_full(K, nbg)
+            norm = ratio.norm_ratio(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
+            r = 2.0 * cfg.fs * np.abs(rho) / norm                 # |r| envelope (1/s)
+            amp = thr * r.max() if rel else thr
+            m0, L = int(a.lag0[0]), int(a.length[0])
+            kept = np.zeros(nbg, bool)
+            kept[(m0 + np.arange(L)) % nbg] = True
+            # the stationary region -dt(f) for f in [f_low, f_high]
+            fe = np.array([cfg.f_low, cfg.f_high])
+            c = -bounds.delta_t(fe, ref, t, cfg.pn_order) * cfg.fs
+            stat = np.arange(int(np.ceil(c.min())), int(np.floor(c.max())) + 1)
+            assert kept[stat % nbg].all()
+            # outside: below a few times the threshold amplitude (the bounds are asymptotic;
+            # a span on the wrong side or without the tails leaves 1e3 and more)
+            assert r[~kept].max() < 4.0 * amp, (cfg_id, j, rel, thr, r[~kept].max() / amp)
+            # of the order of the numeric arc at the same threshold
+            _, Ln, _ = ratio.truncate(rho * (1.0 if rel else 2.0 * cfg.fs / norm), thr, rel)
+            assert 0.5 * Ln <= L <= 2.0 * Ln, (cfg_id, j, rel, thr, L, Ln)
+            # the taps are the kernel itself on the kept lags
+            np.testing.assert_array_equal(a.taps, rho[(m0 + np.arange(L)) % nbg])
