@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--prec", default=None, choices=["native", "bf16", "bf16x3", "bf16x6", "bf16x9", "3xtf32"],
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
+    ap.add_argument("--analytic", action="store_true",
+                    help="truncate the kernels with the App. A expressions instead of their magnitudes")
+    ap.add_argument("--absolute", action="store_true",
+                    help="absolute threshold (on |rho|; with --analytic a threshold amplitude on |r| in 1/s)")
     ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default)")
     ap.add_argument("--n-build", type=int, default=None,
                     help="kernel build grid: 0 the data grid, -1 per neighbour, or a power of two "
@@ -299,12 +303,12 @@ def ncu_traffic(kernel: str, layout: str = None):
         return None
 
 
-def workload_label(cfg, config: int, thr: float) -> str:
+def workload_label(cfg, config: int, thr: float, trunc: str = "rel") -> str:
     """The workload name both arms print in config.workload."""
     G = len(cfg.groups)
     rows = sum(len(nb) for _, nb in cfg.groups)
     return (f"cfg{config}: {cfg.name}; n=2^{int(math.log2(cfg.n))} fs={cfg.fs:g} f_low={cfg.f_low:g}; "
-            f"{G} ref + {rows} TaylorF2 nbrs; thr={thr:g} rel; W={cfg.window}")
+            f"{G} ref + {rows} TaylorF2 nbrs; thr={thr:g} {trunc}; W={cfg.window}")
 
 
 # --------------------------------------------------------------------------- main
@@ -377,7 +381,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     n_build = args.n_build if args.n_build is not None else (-1 if cfg.n > (1 << 20) else 0)
-    kerns = [rf.build_ratio_kernels(r, nb, ip, thr, n_build=n_build) for r, nb in cfg.groups]
+    kerns = [rf.build_ratio_kernels(r, nb, ip, thr, relative=not args.absolute, n_build=n_build,
+                                    analytic=args.analytic) for r, nb in cfg.groups]
     filt, sig = rf.reference_filters(ip, refs)
     tune, tune_s = None, 0.0
     if args.buckets:
@@ -643,7 +648,9 @@ def main():
             "scaling": "strong" if sharded else "weak", "vs_baseline": None,
             "dtype": "f32" if cfg.dtype == "f32" else "f64",
             "data": "synthetic",
-            "config": {"workload": workload_label(full_cfg, args.config, thr),
+            "config": {"workload": workload_label(full_cfg, args.config, thr,
+                                                  ("abs" if args.absolute else "rel") +
+                                                  (" analytic" if args.analytic else "")),
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
                        "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf, "n_build": n_build,

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RF_ABI_VERSION 3
+#define RF_ABI_VERSION 4
 
 typedef struct rf_ctx rf_ctx;
 typedef struct rf_kernels rf_kernels;
@@ -163,19 +163,33 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
 /* Ratio kernels of k neighbours of one reference (Sec. II.B-II.D).  Per neighbour j, in FP64:
  *   K~_k = (N_ref/N_j) W(f_k) conj(h~_j(f_k) / h~_ref(f_k))   (Eqs. 5, 7 and window Eq. 9)
  *   rho[m] = (1/n) sum_{k=0}^{n/2} K~_k exp(+2 pi i k m / n),  m = 0..n-1
- * then truncation: with a = max|rho|^2, the kept lags are those with |rho|^2 >= thr^2 a
- * (relative != 0) or |rho|^2 >= thr^2 (relative == 0); the kernel is the shortest circular
- * arc [m0, m0+L) covering them (ties: smallest m0 in (-n/2, n/2]).  Taps c[l] = rho[m0+l]
- * are stored packed (grid dtype) with int32 signed m0 and length L per neighbour.
+ * then truncation, chosen by the flags `relative` (RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC):
+ * numeric (default): with a = max|rho|^2, the kept lags are those with |rho|^2 >= thr^2 a
+ * (RF_TRUNC_RELATIVE) or |rho|^2 >= thr^2; the kernel is the shortest circular arc
+ * [m0, m0+L) covering them (ties: smallest m0 in (-n/2, n/2]).
+ * analytic (RF_TRUNC_ANALYTIC; Sec. II.D with the App. A expressions): a threshold amplitude
+ * A on |r| = 2 fs |rho| / (N_ref/N_j) (1/s), A = thr max|r| with RF_TRUNC_RELATIVE, else
+ * A = thr (the paper's threshold amplitude); for the four taper ends f_e = f_low - df_low,
+ * f_low, f_high, f_high + df_high (taper widths df_e = df_low, df_low, df_high, df_high), with
+ * c_e = -(Psi_j'(f_e) - Psi_ref'(f_e)) / (2 pi) and d_e = (R(f_e) / (4 pi df_e^2 A))^(1/3)
+ * (R = B_j / B_ref), the kept lag times run from min(c_e - d_e) to max(c_e + d_e): lags
+ * floor(min fs) .. ceil(max fs), at most the grid length, m0 signed in (-n/2, n/2].  The
+ * App. A bounds are asymptotic, so A should leave the reach well past the taper widths (the
+ * paper's absolute 1e-3 / s, or a relative threshold of 1e-4 or less).
+ * Taps c[l] = rho[m0+l] are stored packed (grid dtype) with int32 signed m0 and length L per
+ * neighbour.
  * Build grid (Sec. II.D: a kernel needs a frequency grid only as fine as its duration):
  * n_build = 0 builds on the data grid (n bins, the definition above); a power of two in
  * [16, n] builds every kernel on that grid (K~ at f_k = k fs / n_b, an n_b-point inverse
  * transform with the 1/n_b factor, lags signed in (-n_b/2, n_b/2]); -1 picks per neighbour the
  * smallest power of two of at least four times its lag extent (time offsets (Psi_j' -
  * Psi_ref')/(2 pi) at f_low - df_low and f_high + df_high, times fs, plus 4 fs / df_low),
- * capped at n.  N_ref / N_j stays on the data grid.  RF_EINVAL for other n_build.
+ * capped at n.  N_ref / N_j stays on the data grid.  RF_EINVAL for other n_build, for flags
+ * outside RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC, and for an analytic threshold of 0.
  * refs/nbrs: host; inv_psd: device double[n/2+1].  SYNCHRONISES `stream` (the lengths are
  * read back).  *out is freed with rf_kernels_free. */
+#define RF_TRUNC_RELATIVE 1
+#define RF_TRUNC_ANALYTIC 2
 rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_template* nbrs,
                                  int32_t k, const double* inv_psd, double threshold,
                                  int32_t relative, int64_t n_build, rf_kernels** out, rf_stream stream);

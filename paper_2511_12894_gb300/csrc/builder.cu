@@ -49,6 +49,42 @@ __global__ void k_grid_extent(Tf2 ref, const Tf2* __restrict__ tg, const double*
   out[j] = fmax(fabs(ta), fabs(tb)) * fs + 4.0 * fs / dfl[j];
 }
 
+// Analytic truncation (Sec. II.D with the App. A expressions), one thread per template: the
+// threshold amplitude A on |r| = 2 fs |rho| (N_ref / N_j = 1: one amplitude law) is thr times
+// the kernel's peak (relative) or thr; each taper end f_e reaches d_e = (R / (4 pi df_e^2 A))^(1/3)
+// on both sides of its lag time c_e = -dt(f_e); the kept lags run from floor(min(c_e - d_e) fs)
+// to ceil(max(c_e + d_e) fs), at most the grid.
+__global__ void k_analytic_span(Tf2 ref, const Tf2* __restrict__ tg, const double* __restrict__ dfl,
+                                const double* __restrict__ amax2, int count, double thr, int relative, int64_t nb,
+                                double fs, double f_low, double f_high, double df_high, int* __restrict__ m0_out,
+                                int* __restrict__ len_out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= count) return;
+  const double amp = relative ? thr * 2.0 * fs * sqrt(amax2[j]) : thr;
+  if (!(amp > 0.0)) {
+    m0_out[j] = 0;
+    len_out[j] = 0;
+    return;
+  }
+  const double fe[4] = {f_low - dfl[j], f_low, f_high, f_high + df_high};
+  const double dfe[4] = {dfl[j], dfl[j], df_high, df_high};
+  double lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const double c = -((tf2_dphase(tg[j], fe[e]) - tf2_dphase(ref, fe[e])) / kTwoPi);
+    const double R = tf2_amp(fe[e]) / tf2_amp(fe[e]);  // B_j / B_ref: one amplitude law
+    const double d = cbrt(R / (4.0 * kPi * dfe[e] * dfe[e] * amp));
+    lo = fmin(lo, c - d);
+    hi = fmax(hi, c + d);
+  }
+  const long long m_lo = (long long)floor(lo * fs), m_hi = (long long)ceil(hi * fs);
+  const long long L = min(m_hi - m_lo + 1, (long long)nb);
+  long long m0 = m_lo & (nb - 1);
+  if (m0 > nb / 2) m0 -= nb;
+  m0_out[j] = (int)m0;
+  len_out[j] = (int)L;
+}
+
 __global__ void __launch_bounds__(256) k_ref_phase(Tf2 ref, int64_t nbins, double df, double* __restrict__ psi) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nbins) return;
@@ -304,8 +340,14 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
     fft_c2c_f64(bufK, bufR, bufT, nb, cnt, +1, c->tw64.as<double2>(), n, s);
     k_row_max2<<<cnt, 1024, 0, s>>>(bufR, nb, d_amax);
     RF_LAUNCHED();
-    const int nt = (int)std::min<int64_t>(1024, nb);
-    k_arc<<<cnt, nt, 0, s>>>(bufR, nb, d_amax, thr, relative, d_m0, d_len);
+    if (relative & RF_TRUNC_ANALYTIC) {
+      k_analytic_span<<<(cnt + 63) / 64, 64, 0, s>>>(pr, d_tgs + q0, d_dfls + q0, d_amax, cnt, thr,
+                                                     relative & RF_TRUNC_RELATIVE, nb, c->g.fs, c->g.f_low,
+                                                     c->g.f_high, c->g.df_high, d_m0, d_len);
+    } else {
+      const int nt = (int)std::min<int64_t>(1024, nb);
+      k_arc<<<cnt, nt, 0, s>>>(bufR, nb, d_amax, thr, relative & RF_TRUNC_RELATIVE, d_m0, d_len);
+    }
     RF_LAUNCHED();
     RF_CUDA(cudaMemcpyAsync(hm0.data(), d_m0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
     RF_CUDA(cudaMemcpyAsync(hlen.data(), d_len, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));

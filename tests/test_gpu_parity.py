@@ -186,6 +186,48 @@ def test_build_ratio_kernels_coarse_grid(torch, n_build):
     assert _relerr(kern.taps().cpu().numpy(), pk.taps) < TOL["f64"]
 
 
+@pytest.mark.parametrize("n_build,rel,thr", [(0, True, 3e-5), (0, False, 1e-3), (-1, False, 1e-2), (-1, True, 1e-4)])
+def test_build_ratio_kernels_analytic(torch, n_build, rel, thr):
+    """Analytic truncation (Sec. II.D with the App. A expressions) against the oracle's same
+    definition: spans and signed lags exact, taps to FP64 rounding; on the data grid and on
+    per-neighbour build grids, with relative and absolute (1/s) thresholds."""
+    n = 1 << 16
+    cfg = workload.config(1, n_override=n, k_override=4)
+    ref = cfg.groups[0][0]
+    nb = list(cfg.groups[0][1]) + list(workload.duration_lattice(ref, cfg.f_low, 4, 0.2, 3.0,
+                                                                  np.random.default_rng(9), n_eta=1,
+                                                                  mrange=(1.0, 4.5)))
+    ip = workload.inv_psd(cfg)
+    rf = _rf(cfg)
+    kern = rf.build_ratio_kernels(ref, nb, torch.tensor(ip, device="cuda"), thr, relative=rel, n_build=n_build,
+                                  analytic=True)
+    pk = ratio.build_ratio_kernels(ref, nb, n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, thr, rel,
+                                   n_build=n_build, analytic=True)
+    assert np.array_equal(kern.grid, pk.grid)
+    assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
+    assert _relerr(kern.taps().cpu().numpy(), pk.taps) < TOL["f64"]
+    # the same threshold without the analytic flag truncates numerically (different spans)
+    num = rf.build_ratio_kernels(ref, nb, torch.tensor(ip, device="cuda"), thr if rel else thr / (2 * cfg.fs),
+                                 relative=rel, n_build=n_build)
+    assert not np.array_equal(num.length, kern.length)
+
+
+def test_build_rejects_unknown_truncation_flags(torch):
+    """Truncation flags outside RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC, and an analytic
+    threshold of 0, are rejected before any work."""
+    import ctypes
+    import paper_2511_12894_gb300 as P
+    cfg = workload.config(1, n_override=1 << 12, k_override=1)
+    ref, nb = cfg.groups[0]
+    rf = _rf(cfg)
+    ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
+    h = ctypes.c_void_p()
+    for flags, thr in [(4, 1e-3), (-1, 1e-3), (3, 0.0)]:
+        st = P._lib.rf_build_ratio_kernels(rf.handle, P._templates([ref]), P._templates(nb), len(nb),
+                                           ctypes.c_void_p(ip.data_ptr()), thr, flags, 0, ctypes.byref(h), None)
+        assert st == P.RF_EINVAL and not h.value
+
+
 def test_build_ratio_kernels_f32_long(torch):
     cfg = _small_f32_cfg(1 << 17, 6)
     ref = cfg.groups[0][0]
