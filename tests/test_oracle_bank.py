@@ -1,0 +1,70 @@
+"""Pins of the bank structuring (Sec. III.A): duration against the Newtonian chirp time,
+partition and limits, chirp-mass contiguity, medoid references by brute force."""
+import math
+
+import numpy as np
+import pytest
+
+import workload
+from oracle import bank
+
+
+def test_duration_is_the_newtonian_chirp_time_at_0pn():
+    """tau = -t(f_low) (Eq. A2) reduces to (5/256) (pi f)^(-8/3) Mc^(-5/3) at Newtonian order."""
+    for m1, m2 in [(1.4, 1.4), (2.9, 1.05), (2.2, 1.7)]:
+        t = workload.Template(m1, m2)
+        assert bank.duration(m1, m2, 20.0, 0) == pytest.approx(workload.newtonian_duration(t, 20.0), rel=1e-12)
+    # the PN corrections change a 1.4 + 1.4 inspiral from 20 Hz (about 158 s) by a few per cent
+    # (the positive 1PN term lengthens it)
+    t0, t7 = bank.duration(1.4, 1.4, 20.0, 0), bank.duration(1.4, 1.4, 20.0, 7)
+    assert t0 < t7 < 1.05 * t0
+
+
+@pytest.mark.parametrize("count,spread,size", [(3000, 10.0, 500), (3000, 2.0, 64), (40, 1e9, 7)])
+def test_sets_partition_the_bank_within_the_limits(count, spread, size):
+    b = workload.synthetic_bank(count, seed=3)
+    sets, refs, tau = bank.structure(b, 20.0, 7, spread, size)
+    allidx = np.sort(np.concatenate([np.array(s) for s in sets]))
+    assert np.array_equal(allidx, np.arange(count))
+    for s, r in zip(sets, refs):
+        assert len(s) <= size
+        assert len(s) == 1 or tau[s].max() - tau[s].min() <= spread
+        assert r in s
+        # medoid by brute force: no template of the set has a smaller sum of |d tau|
+        sums = np.abs(tau[s][:, None] - tau[s][None, :]).sum(axis=1)
+        assert sums[s.index(r)] <= sums.min() * (1 + 1e-9) + 1e-300
+        # ties go to the lowest bank index
+        tied = [i for i, v in zip(s, sums) if v <= sums.min() * (1 + 1e-9)]
+        assert r == min(tied)
+
+
+def test_chirp_mass_sets_are_contiguous_and_split_only_when_needed():
+    """Stage one cuts the chirp-mass order into runs; merging two neighbouring runs of one
+    split would exceed the duration limit for at least one of the splits made."""
+    b = workload.synthetic_bank(4000, seed=5)
+    spread = 10.0
+    sets, _, tau = bank.structure(b, 20.0, 7, spread, 10 ** 9)      # stage one only
+    mc = np.array([bank.chirp_mass(t.m1, t.m2) for t in b])
+    order = sorted(range(len(b)), key=lambda i: (mc[i], i))
+    flat = [i for s in sets for i in sorted(s, key=lambda i: (mc[i], i))]
+    assert flat == order                                               # contiguous runs, in order
+    # the coarsest split is needed: the whole bank's spread exceeds the limit
+    assert tau.max() - tau.min() > spread and len(sets) > 1
+    # sizes follow halving: every run is floor or ceil of n / 2^depth for some depth
+    n = len(b)
+    ok = {n}
+    frontier = [n]
+    for _ in range(20):
+        frontier = sorted({x for f in frontier for x in (f // 2, f - f // 2)})
+        ok.update(frontier)
+    assert all(len(s) in ok for s in sets)
+
+
+def test_references_are_the_duration_medians():
+    """In one dimension the minimiser of sum |tau_i - tau_j| is a median of the set."""
+    b = workload.synthetic_bank(1500, seed=7)
+    sets, refs, tau = bank.structure(b, 20.0, 7, 10.0, 500)
+    for s, r in zip(sets, refs):
+        d = np.sort(tau[s])
+        lo, hi = d[(len(s) - 1) // 2], d[len(s) // 2]
+        assert lo - 1e-9 <= tau[r] <= hi + 1e-9

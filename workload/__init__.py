@@ -295,3 +295,23 @@ def config(i: int, n_override: Optional[int] = None, k_override: Optional[int] =
                      noise_f_min=3.0)
         return replace(cfg, injections=_injections(5, groups, 16, (8.0, 30.0), n, ri, n // 64))
     raise ValueError(f"unknown config {i}")
+
+
+def synthetic_bank(count: int, mrange=(1.0, 3.0), seed: int = 0) -> Tuple[Template, ...]:
+    """A seeded non-spinning bank standing in for the paper's stochastic 1-3 M_sun bank
+    (Sec. III.A, about 5.1e4 templates): log-uniform chirp mass over the range the component
+    masses allow and uniform eta in [0.2, 0.25], keeping draws whose masses fall in mrange."""
+    rng = np.random.default_rng(seed)
+    lo, hi = mrange
+    mc_lo = (lo * lo) ** 0.6 / (2 * lo) ** 0.2
+    mc_hi = (hi * hi) ** 0.6 / (2 * hi) ** 0.2
+    out: List[Template] = []
+    while len(out) < count:
+        mc = float(np.exp(rng.uniform(np.log(mc_lo), np.log(mc_hi))))
+        eta = float(rng.uniform(0.2, 0.25))
+        m = mc / eta ** 0.6
+        d = float(np.sqrt(max(0.0, 1.0 - 4.0 * eta)))
+        m1, m2 = 0.5 * m * (1.0 + d), 0.5 * m * (1.0 - d)
+        if lo <= m2 and m1 <= hi:
+            out.append(Template(m1, m2))
+    return tuple(out)
