@@ -251,6 +251,23 @@ rf_status rf_kernels_gemm_layout(const rf_kernels* kern, int32_t* out);
 /* Borrowed view of the build grid of each kernel (host int64[k]; n for imported kernels). */
 rf_status rf_kernels_grids(const rf_kernels* kern, const int64_t** grids);
 
+/* Template-bank structuring (Sec. III.A), on the host: no context and no device work.
+ * Durations tau = -t(f_low) of the stationary-phase templates (t(f) = Psi'(f) / (2 pi) with
+ * t_c = 0, Eq. A2, at pn_order).  The bank in chirp-mass order (mc = (m1 m2)^(3/5) /
+ * (m1 + m2)^(1/5), ties in bank order) is halved (first half = floor of half) until every
+ * set's max tau - min tau <= max_spread (s); each set in symmetric-mass-ratio order (ties in
+ * bank order) is halved until it holds at most max_size templates; each set's reference is
+ * the template minimising sum_j |tau_i - tau_j| (sums within 1e-9 relative tie; the lowest
+ * bank index wins).  Sets are numbered depth first, first half first.
+ * bank: host rf_template[count]; outputs (host, caller-owned): set_of[count] (set of each
+ * template), ref_of_set[count] (bank index of each set's reference, the first *n_sets
+ * entries written), *n_sets, and duration_out[count] (tau, s; may be NULL).  RF_EINVAL for
+ * NULL pointers (count > 0), count < 0, f_low <= 0, pn_order outside 0..7, max_spread <= 0 or
+ * not finite, max_size < 1. */
+rf_status rf_bank_structure(const rf_template* bank, int32_t count, double f_low, int32_t pn_order,
+                            double max_spread, int32_t max_size, int32_t* set_of, int32_t* ref_of_set,
+                            int32_t* n_sets, double* duration_out);
+
 /* Release a kernel set.  NULL is a no-op. */
 void rf_kernels_free(rf_kernels* kern);
 

@@ -33,7 +33,7 @@ EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
     "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_os_buckets", "rf_kernels_grids",
-    "rf_kernels_gemm_layout",
+    "rf_kernels_gemm_layout", "rf_bank_structure",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
     "rf_selftest_bounded_wait", "rf_autotune",
@@ -94,6 +94,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_kernels_prepare": (i32, [vp, vp, i32, i32, vp]),
         "rf_kernels_os_layout": (i32, [vp, P(i32), P(i32)]),
         "rf_kernels_gemm_layout": (i32, [vp, P(i32)]),
+        "rf_bank_structure": (i32, [vp, i32, dbl, i32, dbl, i32, P(i32), P(i32), P(i32), P(dbl)]),
         "rf_kernels_prepare_buckets": (i32, [vp, vp, i32, P(i32), P(i32), P(i32), vp]),
         "rf_kernels_os_buckets": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
         "rf_kernels_free": (None, [vp]),
@@ -125,6 +126,26 @@ def _check(status: int) -> None:
     if status != RF_OK:
         msg = _lib.rf_last_error().decode(errors="replace") if _lib else ""
         raise RFError(status, msg)
+
+
+def bank_structure(bank: Sequence, f_low: float, pn_order: int = 7, max_spread: float = 10.0,
+                   max_size: int = 500):
+    """Template-bank structuring (Sec. III.A) by the library, on the host: (sets, refs,
+    durations) with sets lists of bank indices (depth first), refs the bank index of each
+    set's reference and durations tau = -t(f_low) in seconds."""
+    import numpy as np
+    lib = load_library()
+    n = len(bank)
+    set_of = (ctypes.c_int32 * max(1, n))()
+    refs = (ctypes.c_int32 * max(1, n))()
+    ns = ctypes.c_int32(0)
+    tau = (ctypes.c_double * max(1, n))()
+    _check(lib.rf_bank_structure(_templates(bank), n, float(f_low), int(pn_order), float(max_spread), int(max_size),
+                                 set_of, refs, ctypes.byref(ns), tau))
+    sets = [[] for _ in range(ns.value)]
+    for i in range(n):
+        sets[set_of[i]].append(i)
+    return sets, [refs[g] for g in range(ns.value)], np.array(tau[:n])
 
 
 def _templates(ts: Sequence) -> ctypes.Array:

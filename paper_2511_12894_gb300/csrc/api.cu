@@ -349,6 +349,25 @@ rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* 
   });
 }
 
+rf_status rf_bank_structure(const rf_template* bank, int32_t count, double f_low, int32_t pn_order,
+                            double max_spread, int32_t max_size, int32_t* set_of, int32_t* ref_of_set,
+                            int32_t* n_sets, double* duration_out) {
+  return guard([&] {
+    RF_REQUIRE(n_sets != nullptr, "n_sets is NULL");
+    RF_REQUIRE(count >= 0, "count must be >= 0");
+    RF_REQUIRE(std::isfinite(f_low) && f_low > 0, "f_low must be positive");
+    RF_REQUIRE(pn_order >= 0 && pn_order <= 7, "pn_order must be in 0..7");
+    RF_REQUIRE(std::isfinite(max_spread) && max_spread > 0, "max_spread must be positive");
+    RF_REQUIRE(max_size >= 1, "max_size must be >= 1");
+    if (count > 0) {
+      RF_REQUIRE(bank != nullptr && set_of != nullptr && ref_of_set != nullptr, "bank or outputs NULL");
+      for (int i = 0; i < count; ++i) check_template(bank[i], "bank[i]");
+    }
+    bank_structure_impl(bank, count, f_low, pn_order, max_spread, max_size, set_of, ref_of_set, n_sets,
+                        duration_out);
+  });
+}
+
 rf_status rf_kernels_gemm_layout(const rf_kernels* kern, int32_t* out) {
   return guard([&] {
     RF_REQUIRE(kern != nullptr, "kern is NULL");

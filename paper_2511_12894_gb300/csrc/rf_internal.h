@@ -78,6 +78,10 @@ struct Tf2 {
   double a6log;    // coefficient of v ln(4 v)
 };
 Tf2 make_tf2(const rf_template& t, int pn_order);
+// template-bank structuring on the host (bank.cu)
+void bank_structure_impl(const rf_template* bank, int32_t count, double f_low, int pn_order, double max_spread,
+                         int32_t max_size, int32_t* set_of, int32_t* ref_of_set, int32_t* n_sets,
+                         double* duration_out);
 
 }  // namespace rf
 

@@ -32,7 +32,7 @@ __device__ __forceinline__ double tf2_phase(const Tf2& p, double f) {
 }
 
 // g'(v) and g''(v)
-__device__ __forceinline__ void tf2_series_d(const Tf2& p, double v, double& g1, double& g2) {
+__host__ __device__ __forceinline__ void tf2_series_d(const Tf2& p, double v, double& g1, double& g2) {
   g1 = 0.0;
   g2 = 0.0;
 #pragma unroll
@@ -52,7 +52,7 @@ __device__ __forceinline__ void tf2_series_d(const Tf2& p, double v, double& g1,
 }
 
 // Psi'(f) = 2 pi tc + 3/(128 eta) g'(v) dv/df = 2 pi t(f) (Eq. A2)
-__device__ __forceinline__ double tf2_dphase(const Tf2& p, double f) {
+__host__ __device__ __forceinline__ double tf2_dphase(const Tf2& p, double f) {
   const double v = cbrt(kPi * p.M * f);
   double g1, g2;
   tf2_series_d(p, v, g1, g2);
