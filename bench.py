@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--prec", default=None, choices=["native", "bf16", "bf16x3", "bf16x6", "bf16x9", "3xtf32"],
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
     ap.add_argument("--threshold", type=float, default=None)
+    ap.add_argument("--bank", type=int, default=0,
+                    help="reference groups from a structured synthetic bank of this many 1-3 Msun templates "
+                         "(Sec. III.A: 10 s duration spread, at most 500 per set) on the batched workload's grid")
     ap.add_argument("--analytic", action="store_true",
                     help="truncate the kernels with the App. A expressions instead of their magnitudes")
     ap.add_argument("--absolute", action="store_true",
@@ -303,6 +306,19 @@ def ncu_traffic(kernel: str, layout: str = None):
         return None
 
 
+def load_workload(args):
+    """The configuration to run: one of the five workloads, or (--bank N) the batched
+    workload's grid with the sets of a structured synthetic bank as its reference groups."""
+    if not args.bank:
+        return workload.config(args.config, k_override=args.kernels)
+    from paper_2511_12894_gb300 import bank_structure
+    base = workload.config(4)
+    b = workload.synthetic_bank(args.bank, seed=2025)
+    sets, refs, _ = bank_structure(b, base.f_low, base.pn_order, 10.0, 500)
+    groups = [(b[r], tuple(b[i] for i in s if i != r)) for s, r in zip(sets, refs)]
+    return workload.with_groups(base, groups, f"structured-bank-{args.bank}")
+
+
 def workload_label(cfg, config: int, thr: float, trunc: str = "rel") -> str:
     """The workload name both arms print in config.workload."""
     G = len(cfg.groups)
@@ -351,7 +367,7 @@ def main():
     from paper_2511_12894_gb300 import RatioFilter, build, launch_count
     build.build()
 
-    cfg = workload.config(args.config, k_override=args.kernels)
+    cfg = load_workload(args)
     # multi-reference workloads are sharded by whole groups across ranks (no data-path
     # collective; every rank builds the same strain from the same seed); a single-group
     # workload runs as one replica per rank
@@ -367,7 +383,7 @@ def main():
         from dataclasses import replace as _replace
         cfg = _replace(cfg, groups=tuple(all_groups[g] for g in mine))
     units_total = sum(1 + len(nb) for _, nb in all_groups) * cfg.n
-    full_cfg = workload.config(args.config, k_override=args.kernels)   # the whole workload, for its label
+    full_cfg = load_workload(args)   # the whole workload, for its label
     # relative truncation threshold: the largest of 1e-3, 1e-4, 3e-5 whose window peaks stay
     # within 1e-4 of the loudest SNR against full matched filtering on this workload
     thr = args.threshold if args.threshold is not None else GATE_THRESHOLD
@@ -648,7 +664,7 @@ def main():
             "scaling": "strong" if sharded else "weak", "vs_baseline": None,
             "dtype": "f32" if cfg.dtype == "f32" else "f64",
             "data": "synthetic",
-            "config": {"workload": workload_label(full_cfg, args.config, thr,
+            "config": {"workload": workload_label(full_cfg, full_cfg.index, thr,
                                                   ("abs" if args.absolute else "rel") +
                                                   (" analytic" if args.analytic else "")),
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),

@@ -315,3 +315,12 @@ def synthetic_bank(count: int, mrange=(1.0, 3.0), seed: int = 0) -> Tuple[Templa
         if lo <= m2 and m1 <= hi:
             out.append(Template(m1, m2))
     return tuple(out)
+
+
+def with_groups(cfg: Config, groups, name: str, seed_index: int = 6) -> Config:
+    """``cfg`` with other reference groups (for instance the sets of a structured bank) and
+    injections regenerated for them (16 at SNR 8-20, seeded)."""
+    ri = np.random.default_rng(seed(seed_index, 2))
+    groups = tuple(groups)
+    cfg = replace(cfg, name=name, groups=groups)
+    return replace(cfg, injections=_injections(cfg.index, groups, 16, (8.0, 20.0), cfg.n, ri, cfg.n // 64))
