@@ -59,6 +59,8 @@ def parse():
                          "(Sec. III.A: 10 s duration spread, at most 500 per set) on the batched workload's grid")
     ap.add_argument("--analytic", action="store_true",
                     help="truncate the kernels with the App. A expressions instead of their magnitudes")
+    ap.add_argument("--real", action="store_true",
+                    help="the paper's real-kernel form (taps 2 Re rho) instead of the complex one-sided kernel")
     ap.add_argument("--absolute", action="store_true",
                     help="absolute threshold (on |rho|; with --analytic a threshold amplitude on |r| in 1/s)")
     ap.add_argument("--block", type=int, default=0, help="overlap-save block size (0: library default)")
@@ -398,7 +400,7 @@ def main():
     t0 = time.perf_counter()
     n_build = args.n_build if args.n_build is not None else (-1 if cfg.n > (1 << 20) else 0)
     kerns = [rf.build_ratio_kernels(r, nb, ip, thr, relative=not args.absolute, n_build=n_build,
-                                    analytic=args.analytic) for r, nb in cfg.groups]
+                                    analytic=args.analytic, real=args.real) for r, nb in cfg.groups]
     filt, sig = rf.reference_filters(ip, refs)
     tune, tune_s = None, 0.0
     if args.buckets:
@@ -666,7 +668,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_label(full_cfg, full_cfg.index, thr,
                                                   ("abs" if args.absolute else "rel") +
-                                                  (" analytic" if args.analytic else "")),
+                                                  (" analytic" if args.analytic else "") +
+                                                  (" real-kernel" if args.real else "")),
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
                        "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf, "n_build": n_build,

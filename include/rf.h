@@ -176,6 +176,10 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
  * floor(min fs) .. ceil(max fs), at most the grid length, m0 signed in (-n/2, n/2].  The
  * App. A bounds are asymptotic, so A should leave the reach well past the taper widths (the
  * paper's absolute 1e-3 / s, or a relative threshold of 1e-4 or less).
+ * RF_KERNEL_REAL: the paper's real-kernel form (Eq. 8 with r(t) = 2 Re of the App. A integrand):
+ * rho is replaced by 2 Re rho (imaginary parts zero) before truncation, which then acts on
+ * |2 Re rho| (analytic: |r| = fs |2 Re rho| / (N_ref/N_j)).  z_ref has no negative-frequency
+ * content, so untruncated the result equals the complex kernel's; truncated, the two differ.
  * Taps c[l] = rho[m0+l] are stored packed (grid dtype) with int32 signed m0 and length L per
  * neighbour.
  * Build grid (Sec. II.D: a kernel needs a frequency grid only as fine as its duration):
@@ -185,11 +189,13 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
  * smallest power of two of at least four times its lag extent (time offsets (Psi_j' -
  * Psi_ref')/(2 pi) at f_low - df_low and f_high + df_high, times fs, plus 4 fs / df_low),
  * capped at n.  N_ref / N_j stays on the data grid.  RF_EINVAL for other n_build, for flags
- * outside RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC, and for an analytic threshold of 0.
+ * outside RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC | RF_KERNEL_REAL, and for an analytic threshold
+ * of 0.
  * refs/nbrs: host; inv_psd: device double[n/2+1].  SYNCHRONISES `stream` (the lengths are
  * read back).  *out is freed with rf_kernels_free. */
 #define RF_TRUNC_RELATIVE 1
 #define RF_TRUNC_ANALYTIC 2
+#define RF_KERNEL_REAL 4
 rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_template* nbrs,
                                  int32_t k, const double* inv_psd, double threshold,
                                  int32_t relative, int64_t n_build, rf_kernels** out, rf_stream stream);

@@ -24,6 +24,10 @@ Sec. II.B-II.D and App. A.
 * Sec. II.D with App. A, analytic truncation (optional): the kept lags come from the
   App. A expressions instead of the kernel's magnitudes (bounds.analytic_span); parity
   pinned against the computed kernels' tails where the bounds are asymptotic.
+* Real-kernel form (optional; the paper's own, Eq. 8 with r(t) = 2 Re of the Eq. (A5)
+  integrand of App. A): taps 2 Re rho[m], truncated on |2 Re rho|.  z_ref has no negative-
+  frequency content, so before truncation the conjugate half of 2 Re rho multiplies zeros and
+  the result equals the complex kernel's; after truncation the two differ.
 * Sec. II.D, build grid: the kernels may be built on a coarser frequency grid
   f_k = k fs / n_b (n_b a power of two <= n) as long as 1/df of that grid exceeds
   the kernel's duration; rho is then the n_b-point inverse transform (the same
@@ -183,14 +187,16 @@ class PackedKernels:
 def build_ratio_kernels(ref, targets: Sequence, n: int, fs: float, f_low: float, f_high: float,
                         pn_order: int, inv_psd: np.ndarray, thr: float, relative: bool = True,
                         df_low_max: float = 5.0, df_high: float = 53.0, n_build: int = 0,
-                        analytic: bool = False) -> PackedKernels:
+                        analytic: bool = False, real: bool = False) -> PackedKernels:
     """Kernel spectrum -> full kernel -> threshold truncation, per target.
 
     n_build: 0 builds on the data grid (n lags); a power of two builds every kernel on that
     grid; -1 takes build_grid_rule per target.  Lags are signed on the build grid.
     analytic: the kept lags come from the App. A expressions (bounds.analytic_span) instead
     of the kernel's own magnitudes; a relative threshold is then taken on the kernel's peak
-    of |r| = 2 fs |rho| / (N_ref / N), an absolute one is a threshold amplitude on |r| in 1/s."""
+    of |r| = 2 fs |rho| / (N_ref / N), an absolute one is a threshold amplitude on |r| in 1/s.
+    real: the real-kernel form, taps 2 Re rho (imaginary parts zero), truncated on their
+    magnitude (numeric) or on the same analytic span."""
     lag0: List[int] = []
     length: List[int] = []
     taps: List[np.ndarray] = []
@@ -202,10 +208,13 @@ def build_ratio_kernels(ref, targets: Sequence, n: int, fs: float, f_low: float,
                                      build_grid_rule(ref, t, n, fs, f_low, f_high, pn_order, d, df_high))
         K, _ = kernel_spectrum(ref, t, n, fs, f_low, f_high, pn_order, inv_psd, df_low_max, df_high, d, nb)
         rho = kernel_full(K, nb)
+        if real:
+            rho = (2.0 * rho.real).astype(np.complex128)
         if analytic:
+            # |r| = 2 fs |rho| / (N_ref / N) for the complex kernel, fs |2 Re rho| / (N_ref / N) real
             peak = float(np.abs(rho).max()) if nb else 0.0
-            amp = thr * 2.0 * fs * peak / norm_ratio(ref, t, n, fs, f_low, f_high, pn_order, inv_psd) \
-                if relative else thr
+            amp = thr * (1.0 if real else 2.0) * fs * peak / \
+                norm_ratio(ref, t, n, fs, f_low, f_high, pn_order, inv_psd) if relative else thr
             if amp <= 0.0:
                 m0, L, c = 0, 0, np.zeros(0, dtype=np.complex128)
             else:

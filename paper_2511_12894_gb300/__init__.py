@@ -27,6 +27,7 @@ RF_F64, RF_F32 = 0, 1
 ALGOS = {"auto": 0, "direct": 1, "os": 2, "gemm": 3}
 RF_TRUNC_RELATIVE = 1
 RF_TRUNC_ANALYTIC = 2
+RF_KERNEL_REAL = 4
 PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4, "3xtf32": 5}
 
 EXPORTED = (
@@ -346,16 +347,18 @@ class RatioFilter:
                        arr(dl, kk, np.float64), arr(gp, kk, np.int64))
 
     def build_ratio_kernels(self, ref, nbrs: Sequence, inv_psd, threshold: float = 1e-3, relative: bool = True,
-                            stream=None, n_build: int = 0, analytic: bool = False) -> Kernels:
+                            stream=None, n_build: int = 0, analytic: bool = False, real: bool = False) -> Kernels:
         """Truncated ratio kernels of ``nbrs`` against ``ref`` (Sec. II.B-II.D); synchronises.
 
         n_build: 0 on the data grid, a power of two for that build grid, -1 per neighbour.
         analytic: kept lags from the App. A expressions (threshold amplitude on |r| in 1/s, or
-        relative to the kernel's peak) instead of the kernel's own magnitudes."""
+        relative to the kernel's peak) instead of the kernel's own magnitudes.
+        real: the paper's real-kernel form, taps 2 Re rho."""
         import torch
         ip = _dev(inv_psd, torch.float64, "inv_psd")
         h = ctypes.c_void_p()
-        flags = (RF_TRUNC_RELATIVE if relative else 0) | (RF_TRUNC_ANALYTIC if analytic else 0)
+        flags = (RF_TRUNC_RELATIVE if relative else 0) | (RF_TRUNC_ANALYTIC if analytic else 0) | \
+            (RF_KERNEL_REAL if real else 0)
         _check(_lib.rf_build_ratio_kernels(self.handle, _templates([ref]), _templates(nbrs), len(nbrs),
                                            ctypes.c_void_p(ip.data_ptr()), float(threshold), flags,
                                            int(n_build), ctypes.byref(h), _stream(stream)))

@@ -241,8 +241,8 @@ rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_t
     for (int j = 0; j < k; ++j) check_template(nbrs[j], "nbrs[j]");
     check_dev(inv_psd, "inv_psd");
     RF_REQUIRE(std::isfinite(threshold) && threshold >= 0, "threshold must be finite and >= 0");
-    RF_REQUIRE(relative >= 0 && relative <= (RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC),
-               "relative=%d: truncation flags are RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC", relative);
+    RF_REQUIRE(relative >= 0 && relative <= (RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC | RF_KERNEL_REAL),
+               "relative=%d: flags are RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC | RF_KERNEL_REAL", relative);
     RF_REQUIRE(!(relative & RF_TRUNC_ANALYTIC) || threshold > 0, "analytic truncation needs threshold > 0");
     RF_REQUIRE(n_build == 0 || n_build == -1 ||
                    (n_build >= 16 && n_build <= ctx->n && (n_build & (n_build - 1)) == 0),

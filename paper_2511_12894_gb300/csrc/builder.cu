@@ -54,13 +54,14 @@ __global__ void k_grid_extent(Tf2 ref, const Tf2* __restrict__ tg, const double*
 // the kernel's peak (relative) or thr; each taper end f_e reaches d_e = (R / (4 pi df_e^2 A))^(1/3)
 // on both sides of its lag time c_e = -dt(f_e); the kept lags run from floor(min(c_e - d_e) fs)
 // to ceil(max(c_e + d_e) fs), at most the grid.
+// (rfac: |r| = rfac fs |rho|, 2 for the complex kernel, 1 for the real form's taps 2 Re rho.)
 __global__ void k_analytic_span(Tf2 ref, const Tf2* __restrict__ tg, const double* __restrict__ dfl,
-                                const double* __restrict__ amax2, int count, double thr, int relative, int64_t nb,
-                                double fs, double f_low, double f_high, double df_high, int* __restrict__ m0_out,
-                                int* __restrict__ len_out) {
+                                const double* __restrict__ amax2, int count, double thr, int relative, double rfac,
+                                int64_t nb, double fs, double f_low, double f_high, double df_high,
+                                int* __restrict__ m0_out, int* __restrict__ len_out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= count) return;
-  const double amp = relative ? thr * 2.0 * fs * sqrt(amax2[j]) : thr;
+  const double amp = relative ? thr * rfac * fs * sqrt(amax2[j]) : thr;
   if (!(amp > 0.0)) {
     m0_out[j] = 0;
     len_out[j] = 0;
@@ -83,6 +84,12 @@ __global__ void k_analytic_span(Tf2 ref, const Tf2* __restrict__ tg, const doubl
   if (m0 > nb / 2) m0 -= nb;
   m0_out[j] = (int)m0;
   len_out[j] = (int)L;
+}
+
+// Real-kernel form: rho -> 2 Re rho in place (imaginary parts zero).
+__global__ void k_real_form(double2* __restrict__ rho, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    rho[i] = make_double2(2.0 * rho[i].x, 0.0);
 }
 
 __global__ void __launch_bounds__(256) k_ref_phase(Tf2 ref, int64_t nbins, double df, double* __restrict__ psi) {
@@ -338,12 +345,17 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
                                          c->g.f_high, c->g.df_high, bufK);
     RF_LAUNCHED();
     fft_c2c_f64(bufK, bufR, bufT, nb, cnt, +1, c->tw64.as<double2>(), n, s);
+    if (relative & RF_KERNEL_REAL) {
+      k_real_form<<<(unsigned)std::min<int64_t>(4096, (cnt * nb + 255) / 256), 256, 0, s>>>(bufR, cnt * nb);
+      RF_LAUNCHED();
+    }
     k_row_max2<<<cnt, 1024, 0, s>>>(bufR, nb, d_amax);
     RF_LAUNCHED();
     if (relative & RF_TRUNC_ANALYTIC) {
       k_analytic_span<<<(cnt + 63) / 64, 64, 0, s>>>(pr, d_tgs + q0, d_dfls + q0, d_amax, cnt, thr,
-                                                     relative & RF_TRUNC_RELATIVE, nb, c->g.fs, c->g.f_low,
-                                                     c->g.f_high, c->g.df_high, d_m0, d_len);
+                                                     relative & RF_TRUNC_RELATIVE,
+                                                     (relative & RF_KERNEL_REAL) ? 1.0 : 2.0, nb, c->g.fs,
+                                                     c->g.f_low, c->g.f_high, c->g.df_high, d_m0, d_len);
     } else {
       const int nt = (int)std::min<int64_t>(1024, nb);
       k_arc<<<cnt, nt, 0, s>>>(bufR, nb, d_amax, thr, relative & RF_TRUNC_RELATIVE, d_m0, d_len);

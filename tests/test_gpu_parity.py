@@ -212,6 +212,24 @@ def test_build_ratio_kernels_analytic(torch, n_build, rel, thr):
     assert not np.array_equal(num.length, kern.length)
 
 
+@pytest.mark.parametrize("analytic,rel,thr", [(False, True, 1e-3), (True, False, 1e-2)])
+def test_build_ratio_kernels_real_form(torch, analytic, rel, thr):
+    """The paper's real-kernel form (taps 2 Re rho) against the oracle's same definition,
+    numeric and analytic truncation: spans exact, taps to FP64 rounding, imaginary parts 0."""
+    n = 1 << 16
+    cfg = workload.config(1, n_override=n, k_override=6)
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    rf = _rf(cfg)
+    kern = rf.build_ratio_kernels(ref, nb, torch.tensor(ip, device="cuda"), thr, relative=rel, analytic=analytic,
+                                  real=True)
+    pk = ratio.build_ratio_kernels(ref, nb, n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, thr, rel,
+                                   analytic=analytic, real=True)
+    assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
+    taps = kern.taps().cpu().numpy()
+    assert _relerr(taps, pk.taps) < TOL["f64"] and np.all(taps.imag == 0)
+
+
 def test_build_rejects_unknown_truncation_flags(torch):
     """Truncation flags outside RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC, and an analytic
     threshold of 0, are rejected before any work."""
@@ -222,7 +240,7 @@ def test_build_rejects_unknown_truncation_flags(torch):
     rf = _rf(cfg)
     ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
     h = ctypes.c_void_p()
-    for flags, thr in [(4, 1e-3), (-1, 1e-3), (3, 0.0)]:
+    for flags, thr in [(8, 1e-3), (-1, 1e-3), (3, 0.0)]:
         st = P._lib.rf_build_ratio_kernels(rf.handle, P._templates([ref]), P._templates(nb), len(nb),
                                            ctypes.c_void_p(ip.data_ptr()), thr, flags, 0, ctypes.byref(h), None)
         assert st == P.RF_EINVAL and not h.value

@@ -277,3 +277,26 @@ def test_analytic_span_follows_the_kernel(cfg_id, js):
             assert 0.5 * Ln <= L <= 2.0 * Ln, (cfg_id, j, rel, thr, L, Ln)
             # the taps are the kernel itself on the kept lags
             np.testing.assert_array_equal(a.taps, rho[(m0 + np.arange(L)) % nbg])
+
+
+def test_real_kernel_form_equals_the_complex_one_before_truncation():
+    """The paper's real kernel 2 Re rho against the complex one-sided rho (Eq. 8): z_ref has
+    no negative-frequency content, so untruncated they give the same series to rounding;
+    truncated at the same threshold they differ, by less than the truncation error itself."""
+    cfg = workload.config(1, n_override=1 << 13, k_override=3)
+    ref, nb = cfg.groups[0]
+    ip = workload.inv_psd(cfg)
+    x = data.strain(cfg)
+    z, _ = mf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
+    for t in nb:
+        zc = reconstruct.reconstruct_direct(z, *ratio.build_ratio_kernels(
+            ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 0.0).kernel(0))
+        zr = reconstruct.reconstruct_direct(z, *ratio.build_ratio_kernels(
+            ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 0.0, real=True).kernel(0))
+        assert np.abs(zr - zc).max() <= 1e-12 * np.abs(zc).max()
+        zt = reconstruct.reconstruct_direct(z, *ratio.build_ratio_kernels(
+            ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 1e-3, real=True).kernel(0))
+        zct = reconstruct.reconstruct_direct(z, *ratio.build_ratio_kernels(
+            ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 1e-3).kernel(0))
+        e_real, e_cplx = np.abs(zt - zc).max(), np.abs(zct - zc).max()
+        assert 0 < e_real < 20 * max(e_cplx, 1e-12 * np.abs(zc).max())
