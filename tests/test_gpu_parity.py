@@ -696,6 +696,31 @@ def test_reconstruct_batched_other_forms_match_per_group(torch, algo, prec):
     assert row == P.shape[0]
 
 
+@pytest.mark.parametrize("algo,prec", [("os", "native"), ("direct", "native"), ("gemm", "bf16x6")])
+def test_reconstruct_batched_with_an_empty_group(torch, algo, prec):
+    """A reference without dependents (a one-template set of a structured bank) between two
+    groups: no rows of its own, the other groups' rows as in their own calls."""
+    cfg = _batch_cfg()
+    groups = (cfg.groups[0], (cfg.groups[1][0], ()), cfg.groups[2])
+    cfg = replace(cfg, groups=groups, injections=())
+    ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
+    x = torch.tensor(data.strain(cfg), dtype=torch.float32, device="cuda")
+    rf = _rf(cfg)
+    refs = [g[0] for g in cfg.groups]
+    z, _ = rf.mf_reference(x, ip, refs)
+    kerns = [rf.build_ratio_kernels(r, nb, ip, cfg.threshold) for r, nb in cfg.groups]
+    assert kerns[1].k == 0
+    W = cfg.window
+    P, A = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W, algo, prec=prec)
+    assert P.shape[0] == kerns[0].k + kerns[2].k
+    row = 0
+    for g, k in enumerate(kerns):
+        if k.k:
+            Pg, Ag = rf.reconstruct_winmax(z[g], k, W, algo, prec=prec)
+            assert torch.equal(P[row:row + k.k], Pg) and torch.equal(A[row:row + k.k], Ag)
+        row += k.k
+
+
 def test_batched_step_captures_in_a_cuda_graph(torch):
     """After a warm-up call, the whole online step (matched filter of every reference,
     reference peaks, batched reconstruction) replays from a CUDA graph with the same result."""
