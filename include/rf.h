@@ -173,7 +173,8 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
  * f_low, f_high, f_high + df_high (taper widths df_e = df_low, df_low, df_high, df_high), with
  * c_e = -(Psi_j'(f_e) - Psi_ref'(f_e)) / (2 pi) and d_e = (R(f_e) / (4 pi df_e^2 A))^(1/3)
  * (R = B_j / B_ref), the kept lag times run from min(c_e - d_e) to max(c_e + d_e): lags
- * floor(min fs) .. ceil(max fs), at most the grid length, m0 signed in (-n/2, n/2].  The
+ * floor(min fs) .. ceil(max fs), m0 signed in (-n/2, n/2] (a span as long as the grid keeps the
+ * whole grid from lag 0).  The
  * App. A bounds are asymptotic, so A should leave the reach well past the taper widths (the
  * paper's absolute 1e-3 / s, or a relative threshold of 1e-4 or less).
  * RF_KERNEL_REAL: the paper's real-kernel form (Eq. 8 with r(t) = 2 Re of the App. A integrand):

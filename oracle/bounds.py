@@ -24,7 +24,8 @@ c_e = -dt(f_e) on the kernel's axis and d_e = (R(f_e) / (4 pi df_e^2 A))^(1/3): 
 from the smallest c_e - d_e to the largest c_e + d_e, which contains the stationary region
 (dt monotonic).  A relative threshold takes A = thr max|r|, with |r| = 2 |q| = 2 fs |rho| /
 (N_ref / N) the kernel's own peak; an absolute one takes A = thr in 1/s (the paper's threshold
-amplitude).  Lags: floor and ceil of the end times times fs; the span is capped at the grid.
+amplitude).  Lags: floor and ceil of the end times times fs; a span as long as the grid keeps
+the whole grid from lag 0.
 """
 from __future__ import annotations
 
@@ -85,8 +86,9 @@ def analytic_span(ref, tgt, pn_order, f_low, f_high, df_low, df_high, fs, nb, am
     c_e = -t_e
     lo = float(np.min(c_e - d_e))
     hi = float(np.max(c_e + d_e))
+    if not (math.ceil(hi * fs) - math.floor(lo * fs) + 1.0 < nb):   # the whole grid, from lag 0
+        return 0, int(nb)
     m_lo = math.floor(lo * fs)
     m_hi = math.ceil(hi * fs)
-    L = min(m_hi - m_lo + 1, nb)
     m0 = m_lo % nb
-    return (m0 if m0 <= nb // 2 else m0 - nb), int(L)
+    return (m0 if m0 <= nb // 2 else m0 - nb), int(m_hi - m_lo + 1)

@@ -78,12 +78,19 @@ __global__ void k_analytic_span(Tf2 ref, const Tf2* __restrict__ tg, const doubl
     lo = fmin(lo, c - d);
     hi = fmax(hi, c + d);
   }
-  const long long m_lo = (long long)floor(lo * fs), m_hi = (long long)ceil(hi * fs);
-  const long long L = min(m_hi - m_lo + 1, (long long)nb);
+  // a span as long as the grid (a tiny amplitude, or a taper of width 0) keeps the whole
+  // grid from lag 0; decided in double, before any integer conversion
+  const double flo = floor(lo * fs), fhi = ceil(hi * fs);
+  if (!(fhi - flo + 1.0 < (double)nb)) {
+    m0_out[j] = 0;
+    len_out[j] = (int)nb;
+    return;
+  }
+  const long long m_lo = (long long)flo, m_hi = (long long)fhi;
   long long m0 = m_lo & (nb - 1);
   if (m0 > nb / 2) m0 -= nb;
   m0_out[j] = (int)m0;
-  len_out[j] = (int)L;
+  len_out[j] = (int)(m_hi - m_lo + 1);
 }
 
 // Real-kernel form: rho -> 2 Re rho in place (imaginary parts zero).

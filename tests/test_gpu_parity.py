@@ -186,11 +186,13 @@ def test_build_ratio_kernels_coarse_grid(torch, n_build):
     assert _relerr(kern.taps().cpu().numpy(), pk.taps) < TOL["f64"]
 
 
-@pytest.mark.parametrize("n_build,rel,thr", [(0, True, 3e-5), (0, False, 1e-3), (-1, False, 1e-2), (-1, True, 1e-4)])
+@pytest.mark.parametrize("n_build,rel,thr", [(0, True, 3e-5), (0, False, 1e-3), (-1, False, 1e-2), (-1, True, 1e-4),
+                                             (-1, False, 1e-30)])
 def test_build_ratio_kernels_analytic(torch, n_build, rel, thr):
     """Analytic truncation (Sec. II.D with the App. A expressions) against the oracle's same
     definition: spans and signed lags exact, taps to FP64 rounding; on the data grid and on
-    per-neighbour build grids, with relative and absolute (1/s) thresholds."""
+    per-neighbour build grids, with relative and absolute (1/s) thresholds; a vanishing
+    amplitude keeps each whole grid."""
     n = 1 << 16
     cfg = workload.config(1, n_override=n, k_override=4)
     ref = cfg.groups[0][0]
@@ -206,6 +208,9 @@ def test_build_ratio_kernels_analytic(torch, n_build, rel, thr):
     assert np.array_equal(kern.grid, pk.grid)
     assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
     assert _relerr(kern.taps().cpu().numpy(), pk.taps) < TOL["f64"]
+    if thr < 1e-20:
+        assert np.array_equal(kern.length, kern.grid) and not kern.lag0.any()
+        return
     # the same threshold without the analytic flag truncates numerically (different spans)
     num = rf.build_ratio_kernels(ref, nb, torch.tensor(ip, device="cuda"), thr if rel else thr / (2 * cfg.fs),
                                  relative=rel, n_build=n_build)
