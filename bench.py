@@ -59,6 +59,9 @@ def parse():
                          "(Sec. III.A: 10 s duration spread, at most 500 per set) on the batched workload's grid")
     ap.add_argument("--analytic", action="store_true",
                     help="truncate the kernels with the App. A expressions instead of their magnitudes")
+    ap.add_argument("--stream", type=int, default=0,
+                    help="also stream this many segment hops of data through rf_stream_winmax (guard from the "
+                         "longest template and kernel extent) and report its rate under 'stream'")
     ap.add_argument("--real", action="store_true",
                     help="the paper's real-kernel form (taps 2 Re rho) instead of the complex one-sided kernel")
     ap.add_argument("--absolute", action="store_true",
@@ -306,6 +309,30 @@ def ncu_traffic(kernel: str, layout: str = None):
         return rec["traffic_bytes_per_launch"] if m.hexdigest() == rec["sha256"] else None
     except Exception:
         return None
+
+
+def stream_rate(rf, cfg, x, filt, kerns, W: int, hops: int) -> dict:
+    """Data longer than one segment through rf_stream_winmax: guard = the longest template's
+    duration from f_low plus the largest kernel lag extent, in whole windows; the strain is the
+    segment's host copy repeated over `hops` segment hops (a rate measurement, host buffers in
+    and out, the per-segment copies included)."""
+    tau = max(workload.newtonian_duration(t, cfg.f_low) for r, nb in cfg.groups for t in (r,) + tuple(nb))
+    ext = max(int(np.max(np.maximum(np.abs(k.lag0), np.abs(k.lag0 + k.length)))) for k in kerns if k.k)
+    guard = int(math.ceil((1.05 * tau * cfg.fs + ext) / W)) * W
+    if 2 * guard >= cfg.n:
+        return {"unavailable": f"guard {guard} samples does not fit a segment of {cfg.n}"}
+    hop = cfg.n - 2 * guard
+    total = hops * hop // W * W
+    xh = np.resize(x.detach().cpu().numpy(), total)
+    rf.stream_winmax(xh[: cfg.n], filt, kerns, W, guard)          # warm-up: staging buffers, plans
+    t0 = time.perf_counter()
+    rf.stream_winmax(xh, filt, kerns, W, guard)
+    sec = time.perf_counter() - t0
+    rows = sum(k.k for k in kerns)
+    return {"value": (len(kerns) + rows) * total / sec, "unit": "template*samples/s", "seconds": sec,
+            "data_s": total / cfg.fs, "segments": -(-total // hop), "guard_s": guard / cfg.fs,
+            "hop_s": hop / cfg.fs, "what": "host strain -> per-segment matched filter, reference peaks and "
+                                          "batched reconstruction -> host window peaks of the stream"}
 
 
 def load_workload(args):
@@ -659,6 +686,10 @@ def main():
             except ImportError as e:   # scipy absent on the host
                 sb = {"unavailable": str(e)}
 
+    st = None
+    if rank == 0 and args.stream > 0:
+        st = stream_rate(rf, cfg, x, filt, kerns, W, args.stream)
+
     if rank == 0:
         line = {
             "metric": "template*samples/s", "value": value, "unit": "template*samples/s", "n_gpus": world,
@@ -680,6 +711,7 @@ def main():
             "build_s": build_s, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "plain_mf_cufft": baseline, "err_vs_full_mf": err,
             "scipy_oaconvolve": sb,
+            "stream": st,
             # what a search keeps per template between analyses (Sec. IV): the plain method a
             # template spectrum of n/2 + 1 complex values per neighbour, the ratio filter the
             # neighbour's truncated kernel (sum of the kernel lengths); the references' own

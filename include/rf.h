@@ -258,6 +258,25 @@ rf_status rf_kernels_gemm_layout(const rf_kernels* kern, int32_t* out);
 /* Borrowed view of the build grid of each kernel (host int64[k]; n for imported kernels). */
 rf_status rf_kernels_grids(const rf_kernels* kern, const int64_t** grids);
 
+/* Streaming over data longer than one segment.  With guard = guard_samples, segments of the
+ * context's n samples start at s_q = q hop - guard, hop = n - 2 guard (data outside [0, total)
+ * taken as zero), so their
+ * interiors [s_q + guard, s_q + n - guard) tile the stream; per segment the stored-filter
+ * matched filter of the G references (rf_mf_filtered with filt), their window peaks
+ * (rf_winmax) and the batched reconstruction of the neighbours (rf_reconstruct_batched,
+ * RF_ALGO_AUTO) run on `stream`, and every window of W samples is taken from the segment whose
+ * interior holds it.  A segment's circular wrap reaches only its first and last guard samples
+ * when guard covers the longest template (its duration from f_low) plus the kernels' lag
+ * extents.  x_host: host real[total] (grid dtype); filt: device complex[G][n/2+1] from
+ * rf_reference_filters; ks: the G kernel sets.  Outputs (host, caller-owned, nwt = total / W
+ * windows; samples past nwt W are not reported): ref_max/ref_arg [G][nwt], nbr_max/nbr_arg
+ * [sum k][nwt] (rows as in rf_reconstruct_batched), argmax as int64 stream sample indices.
+ * W must divide n and guard, 0 <= 2 guard < n, total >= W.  Allocates device and pinned
+ * staging buffers for the call; synchronises `stream` once per segment. */
+rf_status rf_stream_winmax(rf_ctx* ctx, const void* x_host, int64_t total, int32_t G, const void* filt,
+                           rf_kernels* const* ks, int64_t W, int64_t guard_samples, float* ref_max,
+                           int64_t* ref_arg, float* nbr_max, int64_t* nbr_arg, rf_stream stream);
+
 /* Template-bank structuring (Sec. III.A), on the host: no context and no device work.
  * Durations tau = -t(f_low) of the stationary-phase templates (t(f) = Psi'(f) / (2 pi) with
  * t_c = 0, Eq. A2, at pn_order).  The bank in chirp-mass order (mc = (m1 m2)^(3/5) /

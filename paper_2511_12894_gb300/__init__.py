@@ -34,7 +34,7 @@ EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
     "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
     "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_os_buckets", "rf_kernels_grids",
-    "rf_kernels_gemm_layout", "rf_bank_structure",
+    "rf_kernels_gemm_layout", "rf_bank_structure", "rf_stream_winmax",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
     "rf_selftest_bounded_wait", "rf_autotune",
@@ -96,6 +96,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_kernels_os_layout": (i32, [vp, P(i32), P(i32)]),
         "rf_kernels_gemm_layout": (i32, [vp, P(i32)]),
         "rf_bank_structure": (i32, [vp, i32, dbl, i32, dbl, i32, P(i32), P(i32), P(i32), P(dbl)]),
+        "rf_stream_winmax": (i32, [vp, vp, i64, i32, vp, vp, i64, i64, vp, vp, vp, vp, vp]),
         "rf_kernels_prepare_buckets": (i32, [vp, vp, i32, P(i32), P(i32), P(i32), vp]),
         "rf_kernels_os_buckets": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
         "rf_kernels_free": (None, [vp]),
@@ -444,6 +445,26 @@ class RatioFilter:
                                            ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()),
                                            _stream(stream)))
         return mo, ao
+
+    def stream_winmax(self, x, filt, kerns: Sequence[Kernels], W: int, guard: int, stream=None):
+        """Window peaks over a host strain longer than one segment (segments overlapping by
+        2 guard samples, each window from the segment whose interior holds it).  x: host
+        real array (grid dtype); filt: the references' stored filters (reference_filters).
+        Returns numpy (ref_max [G, nwt], ref_arg int64, nbr_max [sum k, nwt], nbr_arg int64)."""
+        import numpy as np
+        x = np.ascontiguousarray(x, dtype=np.float64 if self.dtype == "f64" else np.float32)
+        G = len(kerns)
+        fl = _dev(filt, self.cdtype, "filt")
+        nwt = x.size // int(W)
+        rows = sum(k.k for k in kerns)
+        rm, ra = np.zeros((G, nwt), np.float32), np.zeros((G, nwt), np.int64)
+        nm, na = np.zeros((max(rows, 1), nwt), np.float32), np.zeros((max(rows, 1), nwt), np.int64)
+        kp = (ctypes.c_void_p * G)(*[k.handle.value if isinstance(k.handle, ctypes.c_void_p) else k.handle
+                                     for k in kerns])
+        p = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _check(_lib.rf_stream_winmax(self.handle, p(x), x.size, G, ctypes.c_void_p(fl.data_ptr()), kp, int(W),
+                                     int(guard), p(rm), p(ra), p(nm), p(na), _stream(stream)))
+        return rm, ra, nm[:rows], na[:rows]
 
     def winmax(self, z, W: int, max_out=None, arg_out=None, stream=None):
         """Window peaks of series already in memory, z[count, n]."""

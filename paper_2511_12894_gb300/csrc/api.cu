@@ -349,6 +349,34 @@ rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* 
   });
 }
 
+rf_status rf_stream_winmax(rf_ctx* ctx, const void* x_host, int64_t total, int32_t G, const void* filt,
+                           rf_kernels* const* ks, int64_t W, int64_t guard_samples, float* ref_max, int64_t* ref_arg,
+                           float* nbr_max, int64_t* nbr_arg, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(G >= 1 && ks != nullptr, "G must be >= 1 and ks non-NULL");
+    RF_REQUIRE(W >= 1 && ctx->n % W == 0, "W=%lld must divide n", (long long)W);
+    RF_REQUIRE(guard_samples >= 0 && guard_samples % W == 0 && 2 * guard_samples < ctx->n,
+               "guard_samples=%lld: a multiple of W below n/2", (long long)guard_samples);
+    RF_REQUIRE(total >= W, "total=%lld: at least one window", (long long)total);
+    check_host(x_host, "x_host");
+    check_dev(filt, "filt");
+    check_host(ref_max, "ref_max");
+    check_host(ref_arg, "ref_arg");
+    int64_t rows = 0;
+    for (int g = 0; g < G; ++g) {
+      RF_REQUIRE(ks[g] != nullptr, "ks[%d] is NULL", g);
+      rows += ks[g]->k;
+    }
+    if (rows) {
+      check_host(nbr_max, "nbr_max");
+      check_host(nbr_arg, "nbr_arg");
+    }
+    stream_winmax_impl(ctx, x_host, total, G, filt, ks, W, guard_samples, ref_max, ref_arg, nbr_max, nbr_arg,
+                       (cudaStream_t)stream);
+  });
+}
+
 rf_status rf_bank_structure(const rf_template* bank, int32_t count, double f_low, int32_t pn_order,
                             double max_spread, int32_t max_size, int32_t* set_of, int32_t* ref_of_set,
                             int32_t* n_sets, double* duration_out) {

@@ -78,6 +78,10 @@ struct Tf2 {
   double a6log;    // coefficient of v ln(4 v)
 };
 Tf2 make_tf2(const rf_template& t, int pn_order);
+// streaming over data longer than one segment (stream.cu)
+void stream_winmax_impl(rf_ctx* c, const void* x_host, int64_t total, int32_t G, const void* filt,
+                        rf_kernels* const* ks, int64_t W, int64_t guard, float* ref_max, int64_t* ref_arg,
+                        float* nbr_max, int64_t* nbr_arg, cudaStream_t s);
 // template-bank structuring on the host (bank.cu)
 void bank_structure_impl(const rf_template* bank, int32_t count, double f_low, int pn_order, double max_spread,
                          int32_t max_size, int32_t* set_of, int32_t* ref_of_set, int32_t* n_sets,

@@ -78,6 +78,7 @@ def test_null_context_and_handles_are_rejected_by_every_entry_point(lib):
     assert lib.rf_kernels_os_layout(None, None, None) == RF_EINVAL
     assert lib.rf_kernels_gemm_layout(None, None) == RF_EINVAL
     assert lib.rf_bank_structure(None, 4, 20.0, 7, 10.0, 500, None, None, None, None) == RF_EINVAL
+    assert lib.rf_stream_winmax(None, None, 0, 0, None, None, 0, 0, None, None, None, None, None) == RF_EINVAL
     assert lib.rf_kernels_os_buckets(None, 1, None, None, None, None) == RF_EINVAL
     assert lib.rf_reconstruct(None, None, None, 0, 0, None, None) == RF_EINVAL
     assert lib.rf_reconstruct_winmax(None, None, None, 0, 0, 16, None, None, None) == RF_EINVAL

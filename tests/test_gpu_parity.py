@@ -726,6 +726,49 @@ def test_reconstruct_batched_with_an_empty_group(torch, algo, prec):
         row += k.k
 
 
+def test_stream_winmax_equals_the_segment_calls(torch):
+    """Streaming over a strain 2.5 segment hops long: every window equals the one the
+    segment whose interior holds it gives through the per-segment calls (stored-filter matched
+    filter, reference peaks, batched reconstruction), argmax shifted to stream indices; the
+    stream's first window comes from a segment starting guard samples before the data."""
+    cfg = _batch_cfg()
+    n, W = cfg.n, 2048
+    guard = 2 * W
+    hop = n - 2 * guard
+    total = 5 * hop // 2 // W * W
+    rng = np.random.default_rng(51)
+    x = rng.standard_normal(total).astype(np.float32)
+    ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
+    rf = _rf(cfg)
+    refs = [g[0] for g in cfg.groups]
+    filt, _ = rf.reference_filters(ip, refs)
+    kerns = [rf.build_ratio_kernels(r, nb, ip, cfg.threshold) for r, nb in cfg.groups]
+    rm, ra, nm, na = rf.stream_winmax(x, filt, kerns, W, guard)
+    nwt = total // W
+    assert rm.shape == (len(refs), nwt) and nm.shape == (sum(k.k for k in kerns), nwt)
+    seen = np.zeros(nwt, bool)
+    q = 0
+    while q * hop < nwt * W:
+        s0 = q * hop - guard
+        seg = np.zeros(n, np.float32)
+        a, b = max(0, s0), min(total, s0 + n)
+        seg[a - s0:b - s0] = x[a:b]
+        z = rf.mf_filtered(torch.tensor(seg, device="cuda"), filt)
+        Pr, Ar = rf.winmax(z, W)
+        Pn, An = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W)
+        for wl in range(guard // W, (n - guard) // W):
+            w = (s0 + wl * W) // W
+            if 0 <= w < nwt:
+                assert not seen[w]
+                seen[w] = True
+                assert np.array_equal(rm[:, w], Pr[:, wl].cpu().numpy())
+                assert np.array_equal(ra[:, w], s0 + Ar[:, wl].cpu().numpy().astype(np.int64))
+                assert np.array_equal(nm[:, w], Pn[:, wl].cpu().numpy())
+                assert np.array_equal(na[:, w], s0 + An[:, wl].cpu().numpy().astype(np.int64))
+        q += 1
+    assert seen.all() and q == 3
+
+
 def test_batched_step_captures_in_a_cuda_graph(torch):
     """After a warm-up call, the whole online step (matched filter of every reference,
     reference peaks, batched reconstruction) replays from a CUDA graph with the same result."""
