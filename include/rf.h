@@ -271,8 +271,10 @@ rf_status rf_kernels_grids(const rf_kernels* kern, const int64_t** grids);
  * rf_reference_filters; ks: the G kernel sets.  Outputs (host, caller-owned, nwt = total / W
  * windows; samples past nwt W are not reported): ref_max/ref_arg [G][nwt], nbr_max/nbr_arg
  * [sum k][nwt] (rows as in rf_reconstruct_batched), argmax as int64 stream sample indices.
- * W must divide n and guard, 0 <= 2 guard < n, total >= W.  Allocates device and pinned
- * staging buffers for the call; synchronises `stream` once per segment. */
+ * W must divide n and guard, 0 <= 2 guard < n, total >= W.  The context keeps its device and
+ * pinned staging buffers between calls (grown on first use); the next segment's upload and the
+ * previous segment's host scatter overlap the current segment's work; returns when the stream
+ * is done. */
 rf_status rf_stream_winmax(rf_ctx* ctx, const void* x_host, int64_t total, int32_t G, const void* filt,
                            rf_kernels* const* ks, int64_t W, int64_t guard_samples, float* ref_max,
                            int64_t* ref_arg, float* nbr_max, int64_t* nbr_arg, rf_stream stream);

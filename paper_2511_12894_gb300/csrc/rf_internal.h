@@ -65,6 +65,26 @@ struct DevBuf {
   T* as() const { return static_cast<T*>(p); }
 };
 
+// Pinned host memory, grown on demand (contents are not kept).
+struct PinBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  PinBuf() = default;
+  PinBuf(const PinBuf&) = delete;
+  PinBuf& operator=(const PinBuf&) = delete;
+  ~PinBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  void ensure(size_t b) {
+    if (b <= bytes) return;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    RF_CUDA(cudaMallocHost(&p, b));
+    bytes = b;
+  }
+};
+
 // ---------------------------------------------------------------- template model
 // TaylorF2 coefficients of one template (App. A, Eq. A1), prepared on the host
 // from the published post-Newtonian series and evaluated on the device in FP64.
@@ -118,6 +138,10 @@ struct rf_ctx {
   std::vector<int64_t> batch_lay_off;  // work items of layout bucket b: [off[b], off[b+1])
   int64_t batch_rows = 0, batch_nw = 0;
   rf::DevBuf batch_items, batch_zptr, batch_zs, batch_keys;
+  // Streaming (rf_stream_winmax): two device strain buffers, the references' series, the window
+  // peaks, and one pinned host block for the strain staging and the peaks; kept between calls.
+  rf::DevBuf st_x[2], st_z, st_pm, st_pa;
+  rf::PinBuf st_pin;
 };
 
 // One overlap-save layout bucket of a kernel set: the neighbours whose lengths fall in
