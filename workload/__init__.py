@@ -323,4 +323,9 @@ def with_groups(cfg: Config, groups, name: str, seed_index: int = 6) -> Config:
     ri = np.random.default_rng(seed(seed_index, 2))
     groups = tuple(groups)
     cfg = replace(cfg, name=name, groups=groups)
-    return replace(cfg, injections=_injections(cfg.index, groups, 16, (8.0, 20.0), cfg.n, ri, cfg.n // 64))
+    # injections go to groups with dependents (a one-template set has none)
+    live = [g for g, (_, nb) in enumerate(groups) if len(nb)]
+    if not live:
+        return replace(cfg, injections=())
+    inj = _injections(cfg.index, tuple(groups[g] for g in live), 16, (8.0, 20.0), cfg.n, ri, cfg.n // 64)
+    return replace(cfg, injections=tuple(replace(i, group=live[i.group]) for i in inj))
