@@ -22,10 +22,14 @@ Modules (paper passages they follow):
                      per-window peak (Sec. IV).
 * ``data``        -- strain with injections (Sec. III.B) from the seeded draws
                      of the ``workload`` module.
-* ``bounds``      -- App. A envelope and tail bounds (Eqs. A9-A11).
+* ``bounds``      -- App. A envelope and tail bounds (Eqs. A9-A11) and the
+                     analytic kernel spans they give.
+* ``bank``        -- structuring of a bank into reference sets: chirp-mass and
+                     symmetric-mass-ratio bisection, duration-medoid reference
+                     (Sec. III.A).
 
 Every function states which passage it follows.  Parity of the paper's printed
 example SNRs (Sec. IV, 5.769 and 8.903) is unpinned: the noise realisation and
 PSD file behind them are not published.
 """
-from . import fft, taylorf2, mf, ratio, reconstruct, data, bounds  # noqa: F401
+from . import fft, taylorf2, mf, ratio, reconstruct, data, bounds, bank  # noqa: F401
