@@ -38,6 +38,42 @@ def test_window_closed_form():
     assert np.all(np.diff(ratio.window(g, f_low, f_high, dl, dh)) <= 1e-15)
 
 
+@pytest.mark.parametrize("side", ["low", "high"])
+def test_window_tapers_are_raised_cosines(side):
+    """Eq. (9)'s tapers are raised cosines: flat at both ends of the taper (a linear ramp is
+    not), steepest at the midpoint with slope pi / (2 df), and point-symmetric about it."""
+    f_low, f_high, dl, dh = 40.0, 459.0, 3.0, 53.0
+    a, d = (f_low - dl, dl) if side == "low" else (f_high, dh)
+    w = lambda f: ratio.window(np.asarray(f, dtype=np.float64), f_low, f_high, dl, dh)
+    h = 1e-5 * d
+    slope = lambda f: (w(f + h) - w(f - h)) / (2 * h)
+    for end in (a + 1e-4 * d, a + d - 1e-4 * d):
+        assert abs(slope(end)) < 1e-3 / d
+    x = np.linspace(a + 0.01 * d, a + 0.99 * d, 999)
+    s = np.abs(slope(x))
+    assert abs(s.max() - math.pi / (2 * d)) < 1e-6 / d
+    assert abs(x[np.argmax(s)] - (a + d / 2)) < 2e-3 * d
+    u = np.linspace(0.0, d, 37)
+    assert np.allclose(w(a + u) + w(a + d - u), 1.0, rtol=0, atol=1e-14)
+
+
+def test_df_low_rule_newtonian_closed_form():
+    """Eq. (10) at Newtonian order: t(f) = -(5/256) Mc^(-5/3) (pi f)^(-8/3), so
+    |dt'(f_low)| = (8/3)(5/256) pi^(-8/3) f_low^(-11/3) |Mc_t^(-5/3) - Mc_ref^(-5/3)|; the
+    5 Hz cap and the f_low/2 guard bound it, and equal templates take the cap."""
+    ref = Template(1.6, 1.5)
+    for tgt, f_low in [(Template(1.62, 1.5), 20.0), (Template(1.4, 1.35), 30.0), (Template(2.0, 1.2), 40.0)]:
+        mc = lambda t: (t.m1 * t.m2) ** 0.6 / (t.m1 + t.m2) ** 0.2 * workload.MSUN_S
+        dtp = 8.0 / 3.0 * 5.0 / 256.0 * math.pi ** (-8.0 / 3.0) * f_low ** (-11.0 / 3.0) * \
+            abs(mc(tgt) ** (-5.0 / 3.0) - mc(ref) ** (-5.0 / 3.0))
+        want = 1.0 / math.sqrt(dtp)
+        got = ratio.df_low_rule(ref, tgt, 0, f_low, df_low_max=1e9)
+        assert abs(got / min(want, 0.5 * f_low) - 1.0) < 1e-12
+        assert ratio.df_low_rule(ref, tgt, 0, f_low, df_low_max=0.1) == 0.1
+    assert ratio.df_low_rule(ref, ref, 7, 20.0, df_low_max=5.0) == 5.0
+    assert ratio.df_low_rule(ref, ref, 7, 4.0, df_low_max=5.0) == 2.0
+
+
 def test_untruncated_identity_reproduces_full_matched_filter():
     """Eqs. (7)-(8): with the whole circular kernel, reconstruction equals direct MF."""
     cfg, ip, x, ref, nb, z_ref = _setup()
