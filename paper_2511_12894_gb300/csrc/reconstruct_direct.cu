@@ -186,10 +186,13 @@ void launch_direct(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, 
   }
   const int64_t nblk = (n + range - 1) / range;
   const size_t smem = sizeof(V) * (PAD + LC) + sizeof(R) * TILE + sizeof(Best<R>) * (size_t)(wpc + 2) + 16;
-  RF_REQUIRE(smem <= 200 * 1024, "direct reconstruct: window of %lld samples needs too much shared memory",
+  constexpr size_t smem_cap = 200 * 1024;
+  RF_REQUIRE(smem <= smem_cap, "direct reconstruct: window of %lld samples needs too much shared memory",
              (long long)W);
   auto kfn = k_direct<V, E, NT, LC, WINMAX>;
-  RF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // a process-wide attribute of the function: set to the cap that bounds every launch, so that a
+  // context on another host thread never lowers it under this launch
+  RF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
   int64_t done = 0;
   while (done < kern->k) {
     const int cnt = (int)std::min<int64_t>(65535, kern->k - done);

@@ -34,6 +34,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <memory>
 
 #include "cplx.cuh"
@@ -625,18 +626,21 @@ void launch_gemm(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, un
   const int max_blocks = 512 / cols;
   size_t smem = gemm_smem_bytes(PREC, NJ, S, KC);
   smem = std::max(smem, smem_max / (size_t)(max_blocks + 1) + 1024);
-  smem = std::min(smem, (size_t)220 * 1024);
+  constexpr size_t smem_cap = 220 * 1024;
+  smem = std::min(smem, smem_cap);
   auto fn = k_gemm<V, NJ, PREC, WINMAX, S>;
-  // the attribute and the occupancy check are made once per (device, shared-memory size)
-  static size_t done_smem[16] = {};
+  // The dynamic shared-memory limit is a process-wide attribute of the function, so it is set to
+  // the cap that bounds every launch: a context on another host thread never lowers it under a
+  // launch of this one.  The tensor-memory occupancy check runs once per (device, size).
+  static std::atomic<size_t> checked[16];
   const int dv = c->device & 15;
-  if (done_smem[dv] != smem) {
-    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (checked[dv].load(std::memory_order_acquire) != smem) {
+    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
     int per_sm = 0;
     RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGemmThreads, smem));
     RF_REQUIRE(per_sm >= 1 && per_sm * cols <= 512,
                "tensor-core form: %d blocks per SM x %d columns exceed tensor memory", per_sm, cols);
-    done_smem[dv] = smem;
+    checked[dv].store(smem, std::memory_order_release);
   }
   const int64_t tiles = (c->n + kGemmM * S - 1) / (kGemmM * S);
   const int groups = (kern->k + NJ - 1) / NJ;
