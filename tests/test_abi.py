@@ -89,3 +89,32 @@ def test_null_context_and_handles_are_rejected_by_every_entry_point(lib):
     assert lib.rf_device_status(None) == RF_EINVAL
     assert lib.rf_selftest_bounded_wait(None, None) == RF_EINVAL
     assert b"NULL" in lib.rf_last_error() or len(lib.rf_last_error()) > 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No silent fallback: without the built library the binding raises instead of computing."""
+    import paper_2511_12894_gb300 as p
+    monkeypatch.setattr(p, "_lib", None)
+    with pytest.raises(RuntimeError, match="not found"):
+        p.load_library(str(tmp_path / "librf.so"))
+
+
+def test_context_requires_a_cuda_device(lib, monkeypatch):
+    """There is no CPU path: a context on a machine without a CUDA device raises."""
+    import torch
+    import paper_2511_12894_gb300 as p
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        p.RatioFilter(1 << 12, 1024.0, 40.0, 459.0, 7)
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: importing the package (and its sharding helper) loads
+    no module of it."""
+    import subprocess
+    import sys
+    code = ("import sys; import paper_2511_12894_gb300, paper_2511_12894_gb300.shard; "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "assert not bad, bad")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
