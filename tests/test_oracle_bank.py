@@ -68,3 +68,24 @@ def test_references_are_the_duration_medians():
         d = np.sort(tau[s])
         lo, hi = d[(len(s) - 1) // 2], d[len(s) // 2]
         assert lo - 1e-9 <= tau[r] <= hi + 1e-9
+
+
+def test_hand_worked_bisection_of_three_templates():
+    """Sec. III.A by hand: three equal-mass templates whose Newtonian durations at 20 Hz are
+    111, 100 and 104 s (bank order).  In chirp-mass order (111, 104, 100 s) the spread of 11 s
+    exceeds 10 s, so the set is halved with the floor of half first: {111 s} and {104, 100 s}
+    (spread 4 s).  The second set's two durations tie on the summed difference, and the lower
+    bank index is its reference."""
+    f = 20.0
+    taus = [111.0, 100.0, 104.0]
+
+    def equal_mass(tau):
+        mc = (tau * 256.0 / 5.0 * (math.pi * f) ** (8.0 / 3.0)) ** (-3.0 / 5.0) / workload.MSUN_S
+        m = mc * 2.0 ** 0.2
+        return workload.Template(m, m)
+
+    bnk = [equal_mass(t) for t in taus]
+    sets, refs, tau = bank.structure(bnk, f, 0, max_spread=10.0, max_size=500)
+    np.testing.assert_allclose(tau, taus, rtol=1e-12)
+    assert sets == [[0], [1, 2]]
+    assert refs == [0, 1]

@@ -92,3 +92,15 @@ def test_snr_at_equals_the_series_at_those_samples():
     idx = np.array([0, 1, 17, n // 2, n - 1, 2049])
     zs = mf.snr_at(xf, h, ipb, n, fs, idx)
     assert np.abs(zs - z[idx]).max() <= 1e-10 * np.abs(z).max()
+
+
+def test_band_includes_both_edge_bins():
+    """Eq. (4): 1/S is zero outside the closed band [f_low, f_high]; when both edges fall on
+    grid bins, those bins are kept and their outer neighbours are not."""
+    n, fs = 1 << 12, 1024.0
+    df = fs / n
+    f_low, f_high = 160 * df, 1800 * df
+    ipb = mf.band_limited_inv_psd(np.ones(n // 2 + 1), n, fs, f_low, f_high)
+    assert ipb[160] == 1.0 and ipb[1800] == 1.0
+    assert ipb[159] == 0.0 and ipb[1801] == 0.0
+    assert np.count_nonzero(ipb) == 1800 - 160 + 1

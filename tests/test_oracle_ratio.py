@@ -336,3 +336,34 @@ def test_real_kernel_form_equals_the_complex_one_before_truncation():
             ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, 1e-3).kernel(0))
         e_real, e_cplx = np.abs(zt - zc).max(), np.abs(zct - zc).max()
         assert 0 < e_real < 20 * max(e_cplx, 1e-12 * np.abs(zc).max())
+
+
+def test_analytic_span_is_tight_to_the_kernel_tails():
+    """The App. A tail bounds (Eqs. A9-A10) are the tails' leading-order envelope, not a loose
+    bound.  The raised-cosine taper's second derivative jumps by pi^2 / (2 df^2) at each of its
+    two ends; three integrations by parts give |q| ~ 1 / (16 pi df^2 |t - c|^3) per end, and the
+    two ends together with |r| = 2 |q| give R / (4 pi df^2 |t - c|^3).  So the analytic span
+    (where that bound meets the threshold amplitude) slightly exceeds the numeric arc of the
+    kernel at the same amplitude.  A bound constant off by 2, or a relative amplitude taken on
+    |rho| instead of |r| = 2 fs |rho| / (N_ref / N), moves the span by 2^(1/3)."""
+    groups = {"relative": [], "absolute": []}
+    for cfg_id, js in [(1, [0, 7, 15]), (2, [0, 5, 100, 200, 255])]:
+        cfg = workload.config(cfg_id)
+        ref, nb = cfg.groups[0]
+        ip = workload.inv_psd(cfg)
+        for rel, thr in [(True, 3e-5), (True, 1e-4), (False, 1e-3), (False, 1e-2)]:
+            for j in js:
+                t = nb[j]
+                a = ratio.build_ratio_kernels(ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, thr,
+                                              rel, n_build=-1, analytic=True)
+                nbg = int(a.grid[0])
+                K, _ = ratio.kernel_spectrum(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip,
+                                             n_build=nbg)
+                rho = ratio.kernel_full(K, nbg)
+                norm = ratio.norm_ratio(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
+                _, Ln, _ = ratio.truncate(rho * (1.0 if rel else 2.0 * cfg.fs / norm), thr, rel)
+                q = int(a.length[0]) / Ln
+                assert 0.95 <= q <= 1.4, (cfg_id, j, rel, thr, q)
+                groups["relative" if rel else "absolute"].append(q)
+    for name, qs in groups.items():
+        assert 1.0 <= float(np.median(qs)) <= 1.25, (name, sorted(qs))
