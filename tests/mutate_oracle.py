@@ -61,6 +61,27 @@ M = [
  ("bank.py", "if best < 0 or s < best_sum - 1e-9 * best_sum:", "if best < 0 or s > best_sum + 1e-9 * best_sum:", "reference maximises"),
  ("bank.py", "elif abs(s - best_sum) <= 1e-9 * best_sum and i < best:", "elif abs(s - best_sum) <= 1e-9 * best_sum and i > best:", "reference tie to highest index"),
  ("bank.py", "order = sorted(range(n), key=lambda i: (mc[i], i))", "order = sorted(range(n), key=lambda i: (eta[i], i))", "first bisection by eta"),
+ ("fft.py", "rev |= ((idx >> b) & 1) << (bits - 1 - b)", "rev |= ((idx >> b) & 1) << b", "no bit reversal"),
+ ("fft.py", "w = np.exp(sign * 2j * np.pi * m / size)", "w = np.exp(sign * 2j * np.pi * m / n)", "twiddles of the whole length"),
+ ("fft.py", "a[..., half:] = top - bot", "a[..., half:] = bot - top", "butterfly difference reversed"),
+ ("fft.py", "return _transform(x, -1.0)", "return _transform(x, +1.0)", "forward transform sign"),
+ ("taylorf2.py", "return (math.pi * M / (128.0 * eta)) * (g2 / v ** 2 - 2.0 * g1 / v ** 3) * dv_df",
+  "return (math.pi * M / (128.0 * eta)) * (g2 / v ** 2 - g1 / v ** 3) * dv_df", "Psi'' product rule"),
+ ("taylorf2.py", "g1 += a6log * (np.log(4.0 * v) + 1.0)", "g1 += a6log * np.log(4.0 * v)", "log-term derivative"),
+ ("ratio.py", "return m if m <= n // 2 else m - n", "return m if m < n // 2 else m - n", "signed lag at n/2"),
+ ("bounds.py", "out[ok] = dt_s / np.sqrt(np.abs(delta_t_prime(fstar[ok], ref, tgt, pn_order)))",
+  "out[ok] = 2.0 * dt_s / np.sqrt(np.abs(delta_t_prime(fstar[ok], ref, tgt, pn_order)))", "stationary envelope factor"),
+ ("bounds.py", "fe = np.array([f_low - df_low, f_low, f_high, f_high + df_high])",
+  "fe = np.array([f_low, f_low, f_high, f_high])", "span from the band edges only"),
+ ("bounds.py", "return dt_s / (4.0 * math.pi * df_high ** 2 * np.abs(np.asarray(lags_s) + d1) ** 3)",
+  "return dt_s / (4.0 * math.pi * df_high ** 2 * np.abs(np.asarray(lags_s) - d1) ** 3)", "high tail centre sign"),
+ ("bounds.py", "m_hi = math.ceil(hi * fs)", "m_hi = math.floor(hi * fs)", "span end rounded inwards"),
+ ("bank.py", "return (m1 * m2) ** 0.6 / (m1 + m2) ** 0.2", "return (m1 * m2) ** 0.6 / (m1 + m2) ** 0.4", "chirp mass exponent"),
+ ("bank.py", "return m1 * m2 / ((m1 + m2) * (m1 + m2))", "return m1 * m2 / (m1 + m2)", "eta in the second bisection"),
+ ("reconstruct.py", "mag2 = (z.real.astype(np.float64) ** 2 + z.imag.astype(np.float64) ** 2)",
+  "mag2 = np.abs(z.real.astype(np.float64)) + np.abs(z.imag.astype(np.float64))", "peak of |Re| + |Im|"),
+ ("data.py", "h = template(n, fs, t.m1, t.m2, cfg.pn_order, tc=inj.sample / fs)",
+  "h = template(n, fs, t.m1, t.m2, cfg.pn_order, tc=(inj.sample + 1) / fs)", "injection one sample late"),
 ]
 
 # constant phase offsets of every template: |z|, t(f) and the ratio identity are unchanged

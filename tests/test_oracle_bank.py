@@ -89,3 +89,13 @@ def test_hand_worked_bisection_of_three_templates():
     np.testing.assert_allclose(tau, taus, rtol=1e-12)
     assert sets == [[0], [1, 2]]
     assert refs == [0, 1]
+
+
+def test_chirp_mass_and_symmetric_mass_ratio_closed_forms():
+    """The bisection keys: equal masses m give Mc = m 2^(-1/5) (1.4 + 1.4 Msun: 1.2188 Msun)
+    and eta = 1/4; masses 3 and 1 give Mc = 3^(3/5) / 4^(1/5) and eta = 3/16."""
+    assert bank.chirp_mass(1.4, 1.4) == pytest.approx(1.4 * 2.0 ** -0.2, rel=1e-14)
+    assert round(bank.chirp_mass(1.4, 1.4), 4) == 1.2188
+    assert bank.sym_mass_ratio(1.7, 1.7) == pytest.approx(0.25, rel=1e-15)
+    assert bank.chirp_mass(3.0, 1.0) == pytest.approx(3.0 ** 0.6 / 4.0 ** 0.2, rel=1e-14)
+    assert bank.sym_mass_ratio(3.0, 1.0) == pytest.approx(3.0 / 16.0, rel=1e-15)

@@ -150,10 +150,20 @@ def test_kernel_envelope_follows_stationary_phase():
     assert np.sum(np.abs(rho[sup % n]) ** 2) / np.sum(np.abs(rho) ** 2) > 0.99
 
 
-def test_kernel_tails_below_appendix_bounds_and_window_shortens_them():
+def _wide_pair():
+    """1.4 + 1.4 against 2 + 2 Msun: a 72 s duration difference and a high-frequency time
+    offset of 17 ms (17 lags), so the high tail's centre is resolved."""
+    n, fs = 1 << 17, 1024.0
+    return n, fs, 20.0, fs / 2 - 53.0, Template(1.4, 1.4), Template(2.0, 2.0)
+
+
+@pytest.mark.parametrize("pair", [_long_pair, _wide_pair])
+def test_kernel_tails_below_appendix_bounds_and_window_shortens_them(pair):
     """Eqs. (A9)-(A10): tails beyond the support decay below the bounds (x2 slack
-    for the one-sided vs 2 Re form); without the window (df = 0) they are longer (Fig. 2)."""
-    n, fs, fl, fh, ref, tgt = _long_pair()
+    for the one-sided vs 2 Re form), and reach them within a small factor: the bounds
+    are the tails' leading-order envelope (three integrations by parts over the
+    raised-cosine taper).  Without the window (df = 0) the tails are longer (Fig. 2)."""
+    n, fs, fl, fh, ref, tgt = pair()
     ip = np.ones(n // 2 + 1)
     K, dfl = ratio.kernel_spectrum(ref, tgt, n, fs, fl, fh, 7, ip)
     rho = ratio.kernel_full(K, n)
@@ -165,10 +175,12 @@ def test_kernel_tails_below_appendix_bounds_and_window_shortens_them():
     b_lo = bounds.low_tail_bound(t_lo, ref, tgt, 7, fl, dfl, 1 / fs)
     got_lo = np.abs(rho[np.round(t_lo * fs).astype(int) % n])
     assert np.all(got_lo <= 2.0 * b_lo + 1e-12)
+    assert np.max(got_lo / b_lo) > 0.4
     t_hi = -d_hi - sgn * np.linspace(2.0 / 53.0, 10.0 / 53.0, 50)
     b_hi = bounds.high_tail_bound(t_hi, ref, tgt, 7, fh, 53.0, 1 / fs)
     got_hi = np.abs(rho[np.round(t_hi * fs).astype(int) % n])
     assert np.all(got_hi <= 2.0 * b_hi + 1e-12)
+    assert np.max(got_hi / b_hi) > 0.4
     # the unwindowed kernel has a longer tail at the same lags
     K0, _ = ratio.kernel_spectrum(ref, tgt, n, fs, fl, fh, 7, ip, df_low=0.0, df_high=0.0)
     rho0 = ratio.kernel_full(K0, n)
@@ -367,3 +379,30 @@ def test_analytic_span_is_tight_to_the_kernel_tails():
                 groups["relative" if rel else "absolute"].append(q)
     for name, qs in groups.items():
         assert 1.0 <= float(np.median(qs)) <= 1.25, (name, sorted(qs))
+
+
+def test_analytic_span_covers_the_level_set_of_the_bounds():
+    """The analytic span by brute force (Sec. II.D with Eqs. A9-A10).  On a fine time grid, the
+    lag times where the bound of one of the four taper ends, R / (4 pi df_e^2 |t - c_e|^3) with
+    c_e = -dt(f_e) and R = 1 for this family, reaches the amplitude, together with the region
+    between the ends, form one interval.  The span covers it, rounded out to whole lags: at
+    most one lag more on each side."""
+    cfg = workload.config(2)
+    ref, nb = cfg.groups[0]
+    fs, n = cfg.fs, cfg.n
+    h = 0.02 / fs                                   # brute-force time step: a fiftieth of a lag
+    for j in (0, 100, 255):
+        t = nb[j]
+        d = ratio.df_low_rule(ref, t, cfg.pn_order, cfg.f_low, cfg.df_low_max)
+        fe = np.array([cfg.f_low - d, cfg.f_low, cfg.f_high, cfg.f_high + cfg.df_high])
+        dfe = np.array([d, d, cfg.df_high, cfg.df_high])
+        c = -bounds.delta_t(fe, ref, t, cfg.pn_order)
+        for amp in (1e-3, 1e-2, 0.3):
+            m0, L = bounds.analytic_span(ref, t, cfg.pn_order, cfg.f_low, cfg.f_high, d, cfg.df_high, fs, n, amp)
+            reach = (1.0 / (4.0 * math.pi * dfe.min() ** 2 * amp)) ** (1.0 / 3.0) + 1.0
+            tt = np.arange(c.min() - reach, c.max() + reach, h)
+            b = np.max(1.0 / (4.0 * math.pi * dfe[:, None] ** 2 * np.abs(tt[None, :] - c[:, None]) ** 3), axis=0)
+            inside = (b >= amp) | ((tt >= c.min()) & (tt <= c.max()))
+            lo, hi = tt[inside].min() * fs, tt[inside].max() * fs     # in lags
+            assert m0 <= lo + h * fs and m0 + L - 1 >= hi - h * fs, (j, amp, m0, L, lo, hi)
+            assert m0 > lo - 1.0 - h * fs and m0 + L - 1 < hi + 1.0 + h * fs, (j, amp, m0, L, lo, hi)
