@@ -163,17 +163,43 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dev(t, dtype, name):
-    """Contiguous, 16-byte-aligned CUDA tensor of the given dtype (copied only if needed)."""
+def _need(t, count: int, name: str):
+    """Raise unless ``t`` holds at least ``count`` elements: the library reads or writes that
+    many through a raw pointer and cannot check the buffer's size itself."""
+    if t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} elements; the call needs {count}")
+    return t
+
+
+def _dev(t, dtype, name, count: int = 0):
+    """Contiguous, 16-byte-aligned CUDA tensor of the given dtype with at least ``count``
+    elements (copied only if its layout needs it)."""
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch tensor")
+    _need(t, count, name)
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
     if not t.is_contiguous() or t.data_ptr() % 16:
         t = t.contiguous().clone()
+    return t
+
+
+def _out(t, dtype, count: int, name: str):
+    """A caller's output tensor, written in place (so never copied): CUDA, of the given dtype,
+    contiguous, 16-byte aligned and holding at least ``count`` elements."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    _need(t, count, name)
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.data_ptr() % 16:
+        raise ValueError(f"{name} must be contiguous and 16-byte aligned (it is written in place)")
     return t
 
 
@@ -288,8 +314,9 @@ class RatioFilter:
 
     def template_fd(self, tmpl, out=None, stream=None):
         import torch
-        out = out if out is not None else torch.empty(self.n // 2 + 1, dtype=self.cdtype, device="cuda")
-        out = _dev(out, self.cdtype, "out")
+        nf = self.n // 2 + 1
+        out = _out(out, self.cdtype, nf, "out") if out is not None else \
+            torch.empty(nf, dtype=self.cdtype, device="cuda")
         t = _templates([tmpl])
         _check(_lib.rf_template_fd(self.handle, t, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
@@ -297,11 +324,13 @@ class RatioFilter:
     def mf_reference(self, x, inv_psd, refs: Sequence, z_out=None, sigma_out=None, stream=None):
         """z_ref[nref, n] (complex) and N[nref] (float64) of each reference (Sec. II.A)."""
         import torch
-        x = _dev(x, self.rdtype, "x")
-        ip = _dev(inv_psd, torch.float64, "inv_psd")
+        x = _dev(x, self.rdtype, "x", self.n)
+        ip = _dev(inv_psd, torch.float64, "inv_psd", self.n // 2 + 1)
         nref = len(refs)
-        z = z_out if z_out is not None else torch.empty((nref, self.n), dtype=self.cdtype, device="cuda")
-        sg = sigma_out if sigma_out is not None else torch.empty(nref, dtype=torch.float64, device="cuda")
+        z = _out(z_out, self.cdtype, nref * self.n, "z_out") if z_out is not None else \
+            torch.empty((nref, self.n), dtype=self.cdtype, device="cuda")
+        sg = _out(sigma_out, torch.float64, nref, "sigma_out") if sigma_out is not None else \
+            torch.empty(nref, dtype=torch.float64, device="cuda")
         _check(_lib.rf_mf_reference(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(ip.data_ptr()),
                                     nref, _templates(refs), ctypes.c_void_p(z.data_ptr()),
                                     ctypes.c_void_p(sg.data_ptr()), _stream(stream)))
@@ -310,11 +339,13 @@ class RatioFilter:
     def reference_filters(self, inv_psd, refs: Sequence, filt_out=None, sigma_out=None, stream=None):
         """Stored filters [nref, n/2+1] (complex) and N[nref] of each reference (Sec. II.A)."""
         import torch
-        ip = _dev(inv_psd, torch.float64, "inv_psd")
+        nf = self.n // 2 + 1
+        ip = _dev(inv_psd, torch.float64, "inv_psd", nf)
         nref = len(refs)
-        f = filt_out if filt_out is not None else torch.empty((nref, self.n // 2 + 1), dtype=self.cdtype,
-                                                               device="cuda")
-        sg = sigma_out if sigma_out is not None else torch.empty(nref, dtype=torch.float64, device="cuda")
+        f = _out(filt_out, self.cdtype, nref * nf, "filt_out") if filt_out is not None else \
+            torch.empty((nref, nf), dtype=self.cdtype, device="cuda")
+        sg = _out(sigma_out, torch.float64, nref, "sigma_out") if sigma_out is not None else \
+            torch.empty(nref, dtype=torch.float64, device="cuda")
         _check(_lib.rf_reference_filters(self.handle, ctypes.c_void_p(ip.data_ptr()), nref, _templates(refs),
                                          ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(sg.data_ptr()),
                                          _stream(stream)))
@@ -323,11 +354,12 @@ class RatioFilter:
     def mf_filtered(self, x, filt, z_out=None, stream=None):
         """z_ref[nref, n] from stored filters ``filt`` [nref, n/2+1]."""
         import torch
-        x = _dev(x, self.rdtype, "x")
-        filt = _dev(filt, self.cdtype, "filt")
+        x = _dev(x, self.rdtype, "x", self.n)
+        filt = _dev(filt, self.cdtype, "filt", self.n // 2 + 1)
         f2 = filt.reshape(-1, self.n // 2 + 1)
         nref = f2.shape[0]
-        z = z_out if z_out is not None else torch.empty((nref, self.n), dtype=self.cdtype, device="cuda")
+        z = _out(z_out, self.cdtype, nref * self.n, "z_out") if z_out is not None else \
+            torch.empty((nref, self.n), dtype=self.cdtype, device="cuda")
         _check(_lib.rf_mf_filtered(self.handle, ctypes.c_void_p(x.data_ptr()), nref, ctypes.c_void_p(f2.data_ptr()),
                                    ctypes.c_void_p(z.data_ptr()), _stream(stream)))
         return z
@@ -356,7 +388,7 @@ class RatioFilter:
         relative to the kernel's peak) instead of the kernel's own magnitudes.
         real: the paper's real-kernel form, taps 2 Re rho."""
         import torch
-        ip = _dev(inv_psd, torch.float64, "inv_psd")
+        ip = _dev(inv_psd, torch.float64, "inv_psd", self.n // 2 + 1)
         h = ctypes.c_void_p()
         flags = (RF_TRUNC_RELATIVE if relative else 0) | (RF_TRUNC_ANALYTIC if analytic else 0) | \
             (RF_KERNEL_REAL if real else 0)
@@ -379,8 +411,9 @@ class RatioFilter:
     def reconstruct(self, z_ref, kern: Kernels, algo: str = "auto", out=None, stream=None, prec: str = "native"):
         """Neighbour SNR series [k, n] (Eq. 8)."""
         import torch
-        z_ref = _dev(z_ref, self.cdtype, "z_ref")
-        out = out if out is not None else torch.empty((kern.k, self.n), dtype=self.cdtype, device="cuda")
+        z_ref = _dev(z_ref, self.cdtype, "z_ref", self.n)
+        out = _out(out, self.cdtype, kern.k * self.n, "out") if out is not None else \
+            torch.empty((kern.k, self.n), dtype=self.cdtype, device="cuda")
         _check(_lib.rf_reconstruct(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo],
                                    PRECS[prec], ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
@@ -395,7 +428,7 @@ class RatioFilter:
 
         Returns the timed candidates, the winner first: dicts with algo, block, part, prec, ms."""
         G = len(z_refs)
-        zs = [_dev(z, self.cdtype, "z_refs[g]") for z in z_refs]
+        zs = [_dev(z, self.cdtype, "z_refs[g]", self.n) for z in z_refs]
         zp = (ctypes.c_void_p * G)(*[z.data_ptr() for z in zs])
         kp = (ctypes.c_void_p * G)(*[k.handle.value if isinstance(k.handle, ctypes.c_void_p) else k.handle
                                      for k in kerns])
@@ -416,10 +449,12 @@ class RatioFilter:
                            stream=None, prec: str = "native"):
         """Per-window max|z|^2 [k, nw] (float32) and its first index (int32)."""
         import torch
-        z_ref = _dev(z_ref, self.cdtype, "z_ref")
+        z_ref = _dev(z_ref, self.cdtype, "z_ref", self.n)
         nw = -(-self.n // int(W))
-        mo = max_out if max_out is not None else torch.empty((kern.k, nw), dtype=torch.float32, device="cuda")
-        ao = arg_out if arg_out is not None else torch.empty((kern.k, nw), dtype=torch.int32, device="cuda")
+        mo = _out(max_out, torch.float32, kern.k * nw, "max_out") if max_out is not None else \
+            torch.empty((kern.k, nw), dtype=torch.float32, device="cuda")
+        ao = _out(arg_out, torch.int32, kern.k * nw, "arg_out") if arg_out is not None else \
+            torch.empty((kern.k, nw), dtype=torch.int32, device="cuda")
         _check(_lib.rf_reconstruct_winmax(self.handle, ctypes.c_void_p(z_ref.data_ptr()), kern.handle, ALGOS[algo],
                                           PRECS[prec], int(W), ctypes.c_void_p(mo.data_ptr()),
                                           ctypes.c_void_p(ao.data_ptr()), _stream(stream)))
@@ -433,11 +468,13 @@ class RatioFilter:
         sets.  Returns ([sum k, nw] float32 peaks, int32 first indices), groups in order."""
         import torch
         G = len(z_refs)
-        zs = [_dev(z, self.cdtype, "z_refs[g]") for z in z_refs]
+        zs = [_dev(z, self.cdtype, "z_refs[g]", self.n) for z in z_refs]
         rows = sum(k.k for k in kerns)
         nw = -(-self.n // int(W))
-        mo = max_out if max_out is not None else torch.empty((rows, nw), dtype=torch.float32, device="cuda")
-        ao = arg_out if arg_out is not None else torch.empty((rows, nw), dtype=torch.int32, device="cuda")
+        mo = _out(max_out, torch.float32, rows * nw, "max_out") if max_out is not None else \
+            torch.empty((rows, nw), dtype=torch.float32, device="cuda")
+        ao = _out(arg_out, torch.int32, rows * nw, "arg_out") if arg_out is not None else \
+            torch.empty((rows, nw), dtype=torch.int32, device="cuda")
         zp = (ctypes.c_void_p * G)(*[z.data_ptr() for z in zs])
         kp = (ctypes.c_void_p * G)(*[k.handle.value if isinstance(k.handle, ctypes.c_void_p) else k.handle
                                      for k in kerns])
@@ -454,7 +491,7 @@ class RatioFilter:
         import numpy as np
         x = np.ascontiguousarray(x, dtype=np.float64 if self.dtype == "f64" else np.float32)
         G = len(kerns)
-        fl = _dev(filt, self.cdtype, "filt")
+        fl = _dev(filt, self.cdtype, "filt", G * (self.n // 2 + 1))
         nwt = x.size // int(W)
         rows = sum(k.k for k in kerns)
         rm, ra = np.zeros((G, nwt), np.float32), np.zeros((G, nwt), np.int64)
@@ -469,11 +506,14 @@ class RatioFilter:
     def winmax(self, z, W: int, max_out=None, arg_out=None, stream=None):
         """Window peaks of series already in memory, z[count, n]."""
         import torch
-        z = _dev(z, self.cdtype, "z")
+        z = _dev(z, self.cdtype, "z", self.n)
         z2 = z.reshape(-1, self.n)
         nw = -(-self.n // int(W))
-        mo = max_out if max_out is not None else torch.empty((z2.shape[0], nw), dtype=torch.float32, device="cuda")
-        ao = arg_out if arg_out is not None else torch.empty((z2.shape[0], nw), dtype=torch.int32, device="cuda")
+        cnt = z2.shape[0] * nw
+        mo = _out(max_out, torch.float32, cnt, "max_out") if max_out is not None else \
+            torch.empty((z2.shape[0], nw), dtype=torch.float32, device="cuda")
+        ao = _out(arg_out, torch.int32, cnt, "arg_out") if arg_out is not None else \
+            torch.empty((z2.shape[0], nw), dtype=torch.int32, device="cuda")
         _check(_lib.rf_winmax(self.handle, ctypes.c_void_p(z2.data_ptr()), z2.shape[0], int(W),
                               ctypes.c_void_p(mo.data_ptr()), ctypes.c_void_p(ao.data_ptr()), _stream(stream)))
         return mo, ao
@@ -490,10 +530,11 @@ def mf_reference_noalloc(grid: rf_grid, x, inv_psd, ref, z_out, sigma_out=None, 
     lib = load_library()
     cd = torch.complex128 if grid.dtype == RF_F64 else torch.complex64
     rd = torch.float64 if grid.dtype == RF_F64 else torch.float32
-    x = _dev(x, rd, "x")
-    ip = _dev(inv_psd, torch.float64, "inv_psd")
-    if z_out.dtype != cd or not z_out.is_cuda or not z_out.is_contiguous():
-        raise TypeError("z_out must be a contiguous CUDA tensor of the grid's complex dtype")
+    x = _dev(x, rd, "x", grid.n)
+    ip = _dev(inv_psd, torch.float64, "inv_psd", grid.n // 2 + 1)
+    z_out = _out(z_out, cd, grid.n, "z_out")
+    if sigma_out is not None:
+        sigma_out = _out(sigma_out, torch.float64, 1, "sigma_out")
     sp = ctypes.c_void_p(sigma_out.data_ptr()) if sigma_out is not None else None
     _check(lib.rf_mf_reference_noalloc(ctypes.byref(grid), ctypes.c_void_p(x.data_ptr()),
                                        ctypes.c_void_p(ip.data_ptr()), _templates([ref]),

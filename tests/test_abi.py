@@ -118,3 +118,22 @@ def test_product_package_never_imports_the_oracle():
             "assert not bad, bad")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
+
+
+def test_binding_rejects_short_buffers_before_any_launch():
+    """The library reads and writes through raw pointers and cannot see a buffer's size, so the
+    binding checks every tensor against the element count the call touches (before it checks
+    anything that needs a GPU)."""
+    import torch
+    import paper_2511_12894_gb300 as p
+    with pytest.raises(ValueError, match="holds 100 elements; the call needs 4096"):
+        p._dev(torch.zeros(100, dtype=torch.float32), torch.float32, "x", 4096)
+    with pytest.raises(ValueError, match="z_out holds 8 elements; the call needs 16"):
+        p._out(torch.zeros(8, dtype=torch.complex64), torch.complex64, 16, "z_out")
+    # large enough: the next check (a CUDA device) is reached
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        p._dev(torch.zeros(4096, dtype=torch.float32), torch.float32, "x", 4096)
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        p._out(torch.zeros(16, dtype=torch.complex64), torch.complex64, 16, "z_out")
+    with pytest.raises(TypeError, match="must be a torch tensor"):
+        p._out([0.0] * 16, torch.complex64, 16, "z_out")
