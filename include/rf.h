@@ -34,7 +34,13 @@
  *   enqueued and rf_last_error() (per host thread) describes why.  Arguments
  *   are validated on the host before any launch; no call aborts the process.
  *   RF_ECUDA reports a CUDA runtime error (message included).
- * Threads.  One rf_ctx must not be used by two host threads at once.
+ * Threads.  One rf_ctx must not be used by two host threads at once; different
+ *   contexts may be used from different host threads concurrently (the library's
+ *   process-wide state is a launch counter and per-function launch attributes set
+ *   to constant bounds).  rf_mf_reference_noalloc is the exception: its static
+ *   workspace is shared by every caller.
+ * Sizes.  Device buffers are plain pointers: the caller provides at least the
+ *   element counts each call states; the library cannot check a buffer's extent.
  */
 #ifndef RF_H
 #define RF_H
