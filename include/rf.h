@@ -36,9 +36,10 @@
  *   RF_ECUDA reports a CUDA runtime error (message included).
  * Threads.  One rf_ctx must not be used by two host threads at once; different
  *   contexts may be used from different host threads concurrently (the library's
- *   process-wide state is a launch counter and per-function launch attributes set
- *   to constant bounds).  rf_mf_reference_noalloc is the exception: its static
- *   workspace is shared by every caller.
+ *   process-wide state is counters, a driver entry point looked up once, and
+ *   per-function launch attributes set to constant bounds).
+ *   rf_mf_reference_noalloc is the exception: its static workspace is shared by
+ *   every caller.
  * Sizes.  Device buffers are plain pointers: the caller provides at least the
  *   element counts each call states; the library cannot check a buffer's extent.
  */

@@ -575,14 +575,15 @@ size_t gemm_smem_bytes(int prec, int NJ, int S, int KC) {
 // Tensor map over the core-matrix records: element type BF16 (or 32-bit words for TF32),
 // dims (values per record, records, planes x terms), no swizzle, zero fill outside.
 CUtensorMap gemm_tensor_map(void* base, bool tf32, int64_t recs, int planes, int box_recs) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once per process; the initialisation of a function-local static is thread-safe
+  // and is retried on the next call if it throws
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     cudaDriverEntryPointQueryResult q{};
     void* fn = nullptr;
     RF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
     RF_REQUIRE(fn != nullptr && q == cudaDriverEntryPointSuccess, "cuTensorMapEncodeTiled is not available");
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
   const cuuint32_t per = tf32 ? 32 : 64;  // values per 128-byte record
   CUtensorMap m;
   const cuuint64_t dims[3] = {per, (cuuint64_t)recs, (cuuint64_t)planes};
