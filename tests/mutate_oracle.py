@@ -82,6 +82,9 @@ M = [
   "mag2 = np.abs(z.real.astype(np.float64)) + np.abs(z.imag.astype(np.float64))", "peak of |Re| + |Im|"),
  ("data.py", "h = template(n, fs, t.m1, t.m2, cfg.pn_order, tc=inj.sample / fs)",
   "h = template(n, fs, t.m1, t.m2, cfg.pn_order, tc=(inj.sample + 1) / fs)", "injection one sample late"),
+ ("bank.py", "lambda s: float(tau[s].max() - tau[s].min()) <= max_spread", "lambda s: float(tau[s].max() - tau[s].min()) < max_spread", "spread limit strict"),
+ ("bank.py", "lambda x: len(x) <= max_size", "lambda x: len(x) < max_size", "size limit strict"),
+ ("bank.py", "key=lambda i: (mc[i], i)", "key=lambda i: (mc[i], -i)", "chirp-mass ties in reverse bank order"),
 ]
 
 # constant phase offsets of every template: |z|, t(f) and the ratio identity are unchanged

@@ -99,3 +99,32 @@ def test_chirp_mass_and_symmetric_mass_ratio_closed_forms():
     assert bank.sym_mass_ratio(1.7, 1.7) == pytest.approx(0.25, rel=1e-15)
     assert bank.chirp_mass(3.0, 1.0) == pytest.approx(3.0 ** 0.6 / 4.0 ** 0.2, rel=1e-14)
     assert bank.sym_mass_ratio(3.0, 1.0) == pytest.approx(3.0 / 16.0, rel=1e-15)
+
+
+def test_spread_limit_is_inclusive():
+    """Sec. III.A halves until the duration spread is equal to or less than the limit: a set
+    whose spread equals the limit (the same double) stays whole, one ulp less splits it."""
+    bnk = [workload.Template(1.4, 1.4), workload.Template(1.5, 1.45), workload.Template(1.6, 1.5)]
+    _, _, tau = bank.structure(bnk, 20.0, 7, 1e9, 500)
+    spread = float(tau.max() - tau.min())
+    assert spread > 1.0
+    assert sorted(map(sorted, bank.structure(bnk, 20.0, 7, spread, 500)[0])) == [[0, 1, 2]]
+    assert len(bank.structure(bnk, 20.0, 7, float(np.nextafter(spread, 0.0)), 500)[0]) > 1
+
+
+def test_size_limit_is_inclusive():
+    """Sets hold no more than the size limit: eight equal templates stay one set at a limit of
+    eight and split into halves at seven."""
+    t = workload.Template(1.4, 1.3)
+    assert bank.structure([t] * 8, 20.0, 7, 10.0, 8)[0] == [list(range(8))]
+    assert bank.structure([t] * 8, 20.0, 7, 10.0, 7)[0] == [[0, 1, 2, 3], [4, 5, 6, 7]]
+
+
+def test_equal_chirp_masses_keep_bank_order():
+    """By hand: two copies of a 1.4 + 1.4 template (indices 0, 1) and a 2 + 2 one, whose
+    durations at 20 Hz differ by far more than 10 s.  In chirp-mass order, equal keys in bank
+    order, the halving gives {0} and {1, 2}, then {1} and {2}."""
+    x, y = workload.Template(1.4, 1.4), workload.Template(2.0, 2.0)
+    sets, refs, tau = bank.structure([x, x, y], 20.0, 7, 10.0, 500)
+    assert tau[0] - tau[2] > 10.0
+    assert sets == [[0], [1], [2]] and refs == [0, 1, 2]
