@@ -85,6 +85,7 @@ M = [
  ("bank.py", "lambda s: float(tau[s].max() - tau[s].min()) <= max_spread", "lambda s: float(tau[s].max() - tau[s].min()) < max_spread", "spread limit strict"),
  ("bank.py", "lambda x: len(x) <= max_size", "lambda x: len(x) < max_size", "size limit strict"),
  ("bank.py", "key=lambda i: (mc[i], i)", "key=lambda i: (mc[i], -i)", "chirp-mass ties in reverse bank order"),
+ ("ratio.py", "amp = thr * (1.0 if real else 2.0) * fs * peak", "amp = thr * 2.0 * fs * peak", "real-form analytic amplitude factor"),
 ]
 
 # constant phase offsets of every template: |z|, t(f) and the ratio identity are unchanged

@@ -357,28 +357,33 @@ def test_analytic_span_is_tight_to_the_kernel_tails():
     two ends together with |r| = 2 |q| give R / (4 pi df^2 |t - c|^3).  So the analytic span
     (where that bound meets the threshold amplitude) slightly exceeds the numeric arc of the
     kernel at the same amplitude.  A bound constant off by 2, or a relative amplitude taken on
-    |rho| instead of |r| = 2 fs |rho| / (N_ref / N), moves the span by 2^(1/3)."""
-    groups = {"relative": [], "absolute": []}
-    for cfg_id, js in [(1, [0, 7, 15]), (2, [0, 5, 100, 200, 255])]:
-        cfg = workload.config(cfg_id)
-        ref, nb = cfg.groups[0]
-        ip = workload.inv_psd(cfg)
-        for rel, thr in [(True, 3e-5), (True, 1e-4), (False, 1e-3), (False, 1e-2)]:
-            for j in js:
-                t = nb[j]
-                a = ratio.build_ratio_kernels(ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, thr,
-                                              rel, n_build=-1, analytic=True)
-                nbg = int(a.grid[0])
-                K, _ = ratio.kernel_spectrum(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip,
-                                             n_build=nbg)
-                rho = ratio.kernel_full(K, nbg)
-                norm = ratio.norm_ratio(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
-                _, Ln, _ = ratio.truncate(rho * (1.0 if rel else 2.0 * cfg.fs / norm), thr, rel)
-                q = int(a.length[0]) / Ln
-                assert 0.95 <= q <= 1.4, (cfg_id, j, rel, thr, q)
-                groups["relative" if rel else "absolute"].append(q)
-    for name, qs in groups.items():
-        assert 1.0 <= float(np.median(qs)) <= 1.25, (name, sorted(qs))
+    |rho| instead of |r| = 2 fs |rho| / (N_ref / N) (complex form) or |r| = fs |2 Re rho| /
+    (N_ref / N) (real form), moves the span by 2^(1/3)."""
+    for real in (False, True):
+        groups = {"relative": [], "absolute": []}
+        for cfg_id, js in [(1, [0, 7, 15]), (2, [0, 5, 100, 200, 255])]:
+            cfg = workload.config(cfg_id)
+            ref, nb = cfg.groups[0]
+            ip = workload.inv_psd(cfg)
+            for rel, thr in [(True, 3e-5), (True, 1e-4), (False, 1e-3), (False, 1e-2)]:
+                for j in js:
+                    t = nb[j]
+                    a = ratio.build_ratio_kernels(ref, [t], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip,
+                                                  thr, rel, n_build=-1, analytic=True, real=real)
+                    nbg = int(a.grid[0])
+                    K, _ = ratio.kernel_spectrum(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip,
+                                                 n_build=nbg)
+                    rho = ratio.kernel_full(K, nbg)
+                    norm = ratio.norm_ratio(ref, t, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip)
+                    # |r| in 1/s, from the taps of either form
+                    taps, scale = ((2.0 * rho.real).astype(complex), cfg.fs / norm) if real else \
+                        (rho, 2.0 * cfg.fs / norm)
+                    _, Ln, _ = ratio.truncate(taps * (1.0 if rel else scale), thr, rel)
+                    q = int(a.length[0]) / Ln
+                    assert 0.95 <= q <= 1.4, (real, cfg_id, j, rel, thr, q)
+                    groups["relative" if rel else "absolute"].append(q)
+        for name, qs in groups.items():
+            assert 1.0 <= float(np.median(qs)) <= 1.25, (real, name, sorted(qs))
 
 
 def test_analytic_span_covers_the_level_set_of_the_bounds():
