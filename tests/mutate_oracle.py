@@ -86,6 +86,9 @@ M = [
  ("bank.py", "lambda x: len(x) <= max_size", "lambda x: len(x) < max_size", "size limit strict"),
  ("bank.py", "key=lambda i: (mc[i], i)", "key=lambda i: (mc[i], -i)", "chirp-mass ties in reverse bank order"),
  ("ratio.py", "amp = thr * (1.0 if real else 2.0) * fs * peak", "amp = thr * 2.0 * fs * peak", "real-form analytic amplitude factor"),
+ ("ratio.py", "extent = float(np.abs(d).max()) * fs + 4.0 * fs / df_low", "extent = float(np.abs(d).max()) * fs", "build grid without the taper spread"),
+ ("taylorf2.py", "g2 += ak * p * (p - 1) * v ** (p - 2)", "g2 += ak * p * p * v ** (p - 2)", "second derivative of a power"),
+ ("ratio.py", "cut2 = thr * thr * (amax2 if relative else 1.0)", "cut2 = thr * thr * (1.0 if relative else amax2)", "relative and absolute swapped"),
 ]
 
 # constant phase offsets of every template: |z|, t(f) and the ratio identity are unchanged
