@@ -248,7 +248,8 @@ rf_status rf_kernels_prepare_buckets(rf_ctx* ctx, rf_kernels* kern, int32_t nb, 
                                      const int32_t* blocks, const int32_t* parts, rf_stream stream);
 
 /* The bucket layout of a prepared kernel set: up to max_nb buckets into the host arrays cuts,
- * blocks, parts (any may be NULL) and their number into *nb (0 when not prepared). */
+ * blocks, parts and their number, at most max_nb, into *nb (0 when not prepared); any of the
+ * four may be NULL.  RF_EINVAL if kern is NULL or max_nb < 0. */
 rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t* cuts, int32_t* blocks,
                                 int32_t* parts, int32_t* nb);
 
@@ -259,7 +260,7 @@ rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stre
 /* Tensor-core layout a kernel set was last prepared for (by its last RF_ALGO_GEMM call): out[0]
  * = rf_prec, out[1] = neighbours per group, out[2] = output tiles of 128 stacked along N,
  * out[3] = taps per K chunk, out[4] = K chunks, out[5] = padded kernel length (all 0 when not
- * prepared).  out is a host int32[6]. */
+ * prepared).  out is a host int32[6].  RF_EINVAL if kern or out is NULL. */
 rf_status rf_kernels_gemm_layout(const rf_kernels* kern, int32_t* out);
 
 /* Borrowed view of the build grid of each kernel (host int64[k]; n for imported kernels). */
