@@ -190,13 +190,17 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
  * content, so untruncated the result equals the complex kernel's; truncated, the two differ.
  * Taps c[l] = rho[m0+l] are stored packed (grid dtype) with int32 signed m0 and length L per
  * neighbour.
+ * Normalisation: the templates are the stationary-phase family A f^-7/6 e^{-i Psi} on one band,
+ * so N_j / N_ref = A_j / A_ref and the factor (N_ref/N_j) |h~_j / h~_ref| is exactly 1 for any
+ * amplitude scales: K~ = W e^{+i (Psi_j - Psi_ref)}, and inv_psd (validated like every
+ * argument) does not change the taps.
  * Build grid (Sec. II.D: a kernel needs a frequency grid only as fine as its duration):
  * n_build = 0 builds on the data grid (n bins, the definition above); a power of two in
  * [16, n] builds every kernel on that grid (K~ at f_k = k fs / n_b, an n_b-point inverse
  * transform with the 1/n_b factor, lags signed in (-n_b/2, n_b/2]); -1 picks per neighbour the
  * smallest power of two of at least four times its lag extent (time offsets (Psi_j' -
  * Psi_ref')/(2 pi) at f_low - df_low and f_high + df_high, times fs, plus 4 fs / df_low),
- * capped at n.  N_ref / N_j stays on the data grid.  RF_EINVAL for other n_build, for flags
+ * capped at n.  RF_EINVAL for other n_build, for flags
  * outside RF_TRUNC_RELATIVE | RF_TRUNC_ANALYTIC | RF_KERNEL_REAL, and for an analytic threshold
  * of 0.
  * refs/nbrs: host; inv_psd: device double[n/2+1].  SYNCHRONISES `stream` (the lengths are
@@ -403,9 +407,14 @@ rf_status rf_winmax(rf_ctx* ctx, const void* z, int32_t count, int64_t W, float*
  * segment: grid->n must be a power of two in [2^8, 2^16]; larger n returns RF_EINVAL
  * with a message and launches nothing.
  *
- * The first call made with a given device current looks up the workspace's device
- * address (cudaGetSymbolAddress) and remembers it; make that first call before any
- * stream capture on that device.  All calls share the one workspace and it keeps the
+ * The array has its own device address in every CUDA context that loads the
+ * library: the runtime's primary context of each device, and any context a host
+ * application created itself with the driver API and made current.  The first call
+ * made in a context looks up that context's address (cudaGetSymbolAddress) and
+ * remembers it under the context's process-unique ID (cuCtxGetId), so a later context
+ * never receives an earlier one's address, even after cudaDeviceReset; make that first
+ * call in each context before any stream capture.  A thread with no current context
+ * uses the primary context of its current device.  All calls share the one workspace and it keeps the
  * last call's contents; every call rewrites each part it reads, so results never
  * depend on an earlier call.  Calls whose work overlaps on the GPU (different
  * streams, or different host threads) race on the workspace and corrupt each other:

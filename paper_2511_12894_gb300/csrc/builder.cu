@@ -107,9 +107,7 @@ __global__ void __launch_bounds__(256) k_ref_phase(Tf2 ref, int64_t nbins, doubl
 
 // One row per template (grid.y): K~ over the full length-n buffer.
 __global__ void __launch_bounds__(256) k_kernel_spectrum(const Tf2* __restrict__ tg, const double* __restrict__ dfl,
-                                                         const double* __restrict__ psi_ref,
-                                                         const double* __restrict__ sig2_ref,
-                                                         const double* __restrict__ sig2_tgt, int64_t n, double df,
+                                                         const double* __restrict__ psi_ref, int64_t n, double df,
                                                          double f_low, double f_high, double df_high,
                                                          double2* __restrict__ K) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,11 +119,13 @@ __global__ void __launch_bounds__(256) k_kernel_spectrum(const Tf2* __restrict__
     const double w = window_w(f, f_low, f_high, dfl[j], df_high);
     if (w > 0.0) {
       const double dpsi = tf2_phase(tg[j], f) - psi_ref[k];
-      const double norm = sqrt(sig2_ref[0] / sig2_tgt[0]);  // N_ref / N_j
-      const double R = tf2_amp(f) / tf2_amp(f);            // B_j / B_ref
+      // K~ = (N_ref / N_j) W conj(h~_j / h~_ref) (Eq. 5 normalised as in Eq. 3).  Every
+      // template of the stationary-phase family has the amplitude law A f^-7/6 on the same
+      // band, so h~_j / h~_ref = (A_j / A_ref) e^{-i dPsi} and N_j / N_ref = A_j / A_ref: the
+      // two amplitude factors cancel exactly for any scales A, and |K~| = W.
       double s, c;
       sincos(dpsi, &s, &c);
-      const double a = norm * R * w / (double)n;
+      const double a = w / (double)n;
       out = make_double2(a * c, a * s);
     }
   }
@@ -254,7 +254,7 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
     return owner.release();
   }
 
-  // device scratch: [Tf2 k][dfl k][extent k][Tf2 k, grid order][dfl k, grid order][psi_ref][sig2]
+  // device scratch: [Tf2 k][dfl k][extent k][Tf2 k, grid order][dfl k, grid order][psi_ref]
   // [amax2][m0][len]
   const int64_t nbins = n / 2 + 1;
   const int64_t kmax_chunk = std::min<int64_t>(k, 4096);
@@ -274,7 +274,6 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
   Tf2* d_tgs = reinterpret_cast<Tf2*>(carve(sizeof(Tf2) * k));
   double* d_dfls = reinterpret_cast<double*>(carve(sizeof(double) * k));
   double* d_psi = reinterpret_cast<double*>(carve(sizeof(double) * nbins));
-  double* d_sig2 = reinterpret_cast<double*>(carve(sizeof(double) * 2));
   double* d_amax = reinterpret_cast<double*>(carve(sizeof(double) * kmax_chunk));
   int* d_m0 = reinterpret_cast<int*>(carve(sizeof(int) * kmax_chunk));
   int* d_len = reinterpret_cast<int*>(carve(sizeof(int) * kmax_chunk));
@@ -319,8 +318,6 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
     RF_CUDA(cudaMemcpyAsync(d_dfls, dfls.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
     RF_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
   }
-  // N_ref^2 and N_j^2 (Eq. 3) on the data grid: one FP64 sum serves both (same amplitude law)
-  sigma2_impl(c, inv_psd, 1, d_sig2, s);
 
   // per kernel: its taps in a part buffer (one per chunk) and its place there
   std::vector<std::unique_ptr<DevBuf>> parts;
@@ -348,7 +345,7 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
     double2* bufR = bufK + cnt * nb;
     double2* bufT = bufR + cnt * nb;
     dim3 g1((unsigned)((nb + 255) / 256), (unsigned)cnt);
-    k_kernel_spectrum<<<g1, 256, 0, s>>>(d_tgs + q0, d_dfls + q0, d_psi, d_sig2, d_sig2, nb, dfb, c->g.f_low,
+    k_kernel_spectrum<<<g1, 256, 0, s>>>(d_tgs + q0, d_dfls + q0, d_psi, nb, dfb, c->g.f_low,
                                          c->g.f_high, c->g.df_high, bufK);
     RF_LAUNCHED();
     fft_c2c_f64(bufK, bufR, bufT, nb, cnt, +1, c->tw64.as<double2>(), n, s);

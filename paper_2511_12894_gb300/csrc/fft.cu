@@ -10,6 +10,7 @@
 // which leaves the transform in natural order after the last pass (Stockham
 // autosort).  Consecutive threads take consecutive j, so every load and (for
 // Ns >= 32) every store of a warp is one contiguous run.
+#include <array>
 #include <cmath>
 
 #include "cplx.cuh"
@@ -89,13 +90,15 @@ void fft_c2c(const V* in, V* out, V* tmp, int64_t n, int batch, int sign, const 
   RF_REQUIRE(in != out && in != tmp && out != tmp, "fft: buffers must be distinct");
   int bits = 0;
   while ((int64_t(1) << bits) < n) ++bits;
-  std::vector<int> radix;
+  // pass radices in a fixed array (no host allocation per call): n < 2^40 needs at most 10
+  std::array<int, 10> radix{};
+  int P = 0;
+  RF_REQUIRE(bits < 40, "fft: n=%lld is too large", (long long)n);
   while (bits >= 4) {
-    radix.push_back(16);
+    radix[P++] = 16;
     bits -= 4;
   }
-  if (bits) radix.push_back(1 << bits);
-  const int P = (int)radix.size();
+  if (bits) radix[P++] = 1 << bits;
   const int64_t tw_stride = table_n / n;
   const V* src = in;
   int64_t Ns = 1;

@@ -3,6 +3,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "cplx.cuh"
 #include "rf_internal.h"
 #include "tf2.cuh"
@@ -289,10 +291,19 @@ constexpr int64_t kNoAllocMaxN = int64_t(1) << 16;
 constexpr size_t kNoAllocSlot = (size_t)kNoAllocMaxN * sizeof(double2);  // one complex128 row of kNoAllocMaxN
 constexpr size_t kNoAllocRed = 8192;                                      // FP64 partial sums + sigma^2
 constexpr size_t kNoAllocBytes = 4 * kNoAllocSlot + kNoAllocRed;
-constexpr int kNoAllocMaxDevices = 64;
-
+// The array has its own device address in every CUDA context that loads the module (the
+// runtime's primary context of each device, or a context a host application created with
+// the driver API), so the addresses are remembered per context, keyed by the context's
+// process-unique ID (a handle value can be reused by a later context; the ID is not).
+constexpr int kNoAllocCacheSlots = 64;
+struct NoAllocSlot {
+  unsigned long long ctx_id;
+  void* addr;
+};
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+NoAllocSlot g_noalloc_cache[kNoAllocCacheSlots] = {};
+int g_noalloc_used = 0;
+int g_noalloc_next = 0;
 
 // exp(-2 pi i m / n), m < n, into the workspace (rebuilt on every call).
 template <typename V>
@@ -316,25 +327,83 @@ static __device__ __align__(256) unsigned char rf_noalloc_scratch[rf::kNoAllocBy
 namespace rf {
 namespace {
 
-// Device address of rf_noalloc_scratch on the current device, looked up on the first
-// call made with that device current and remembered.
-unsigned char* noalloc_scratch_address() {
-  int dev = -1;
-  RF_CUDA(cudaGetDevice(&dev));
-  RF_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, "device ordinal %d is beyond %d", dev, kNoAllocMaxDevices);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, rf_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      (void)cudaGetLastError();
-      set_error("cudaGetSymbolAddress of the static workspace failed on device %d: %s", dev,
-                cudaGetErrorString(e));
-      throw Fail{RF_ECUDA};
-    }
-    g_noalloc_addr[dev] = p;
+// Driver entry points for the current context and its ID, looked up once through the
+// runtime (no link against the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+struct CtxFns {
+  CtxGetCurrentFn get_current;
+  CtxGetIdFn get_id;
+};
+
+const CtxFns& ctx_fns() {
+  static const CtxFns fns = [] {
+    CtxFns f{nullptr, nullptr};
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa{}, qb{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 4000, cudaEnableDefault, &qa) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess)
+      f.get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess)
+      f.get_id = reinterpret_cast<CtxGetIdFn>(b);
+    (void)cudaGetLastError();
+    return f;
+  }();
+  return fns;
+}
+
+// Process-unique ID of the calling thread's current context, or 0 when none is current.
+unsigned long long current_context_id() {
+  const CtxFns& f = ctx_fns();
+  RF_REQUIRE(f.get_current != nullptr && f.get_id != nullptr,
+             "the driver does not provide cuCtxGetCurrent / cuCtxGetId");
+  CUcontext ctx = nullptr;
+  if (f.get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+  unsigned long long id = 0;
+  RF_REQUIRE(f.get_id(ctx, &id) == CUDA_SUCCESS, "cuCtxGetId failed on the current context");
+  return id;
+}
+
+void* lookup_scratch_symbol() {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, rf_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    (void)cudaGetLastError();
+    set_error("cudaGetSymbolAddress of the static workspace failed: %s", cudaGetErrorString(e));
+    throw Fail{RF_ECUDA};
   }
-  return static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return p;
+}
+
+// Device address of rf_noalloc_scratch in the calling thread's current context.  The
+// set-up (cudaGetSymbolAddress) runs on the first call made in a context and its result is
+// remembered for that context; a thread with no current context gets the runtime's
+// primary context of its current device, which that first runtime call binds.
+unsigned char* noalloc_scratch_address() {
+  unsigned long long id = current_context_id();
+  void* fresh = nullptr;
+  if (id == 0) {
+    fresh = lookup_scratch_symbol();  // binds the primary context
+    id = current_context_id();
+    RF_REQUIRE(id != 0, "no CUDA context is current after the workspace lookup");
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  for (int i = 0; i < g_noalloc_used; ++i)
+    if (g_noalloc_cache[i].ctx_id == id) return static_cast<unsigned char*>(g_noalloc_cache[i].addr);
+  if (!fresh) fresh = lookup_scratch_symbol();
+  // remember it; with every slot taken, the oldest entry makes room
+  int slot;
+  if (g_noalloc_used < kNoAllocCacheSlots) {
+    slot = g_noalloc_used++;
+  } else {
+    slot = g_noalloc_next;
+    g_noalloc_next = (g_noalloc_next + 1) % kNoAllocCacheSlots;
+  }
+  g_noalloc_cache[slot] = NoAllocSlot{id, fresh};
+  return static_cast<unsigned char*>(fresh);
 }
 
 void noalloc_check_dev(const void* p, const char* name, bool allow_null) {

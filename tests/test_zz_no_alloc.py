@@ -5,7 +5,8 @@ device memory, a low-latency loop that must not synchronise on an allocation).  
 them the library offers one entry point that works from a static device workspace
 and allocates nothing.  These tests call it through the C ABI and check it against
 the regular rf_mf_reference on the same inputs, twice in a row (the workspace keeps
-the previous call's contents, which must not leak into the next result).
+the previous call's contents, which must not leak into the next result), and once
+against the FP64 oracle's matched filter.
 
 The file sorts last so that a run stopping at the first failure has already run
 every other test.
@@ -75,6 +76,35 @@ def test_noalloc_matches_regular_matched_filter_twice(torch, cfg_index, n):
         assert np.abs(a - b).max() <= TOL[cfg.dtype] * np.abs(b).max()
         assert abs(sig.item() / sig_e.item() - 1) < 1e-14
     rf.close()
+
+
+@pytest.mark.parametrize("cfg_index", [1, 2])
+def test_noalloc_matches_the_oracle(torch, cfg_index):
+    """Its own twiddles (computed on the device, unlike the context's host tables) and its
+    workspace layout, against the FP64 oracle's direct matched filter (Eqs. 2-3)."""
+    from oracle import mf as omf
+    from paper_2511_12894_gb300 import load_library
+    lib = load_library()
+    cfg = workload.config(cfg_index, n_override=1 << 12, k_override=2)
+    ref = cfg.groups[0][0]
+    rdt = torch.float64 if cfg.dtype == "f64" else torch.float32
+    cdt = torch.complex128 if cfg.dtype == "f64" else torch.complex64
+    xh = data.strain(cfg)
+    iph = workload.inv_psd(cfg)
+    x = torch.tensor(xh, dtype=rdt, device="cuda")
+    ip = torch.tensor(iph, device="cuda")
+    z = torch.empty(cfg.n, dtype=cdt, device="cuda")
+    sig = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = lib.rf_mf_reference_noalloc(ctypes.byref(_grid(cfg)), ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(ip.data_ptr()), _templates([ref]), ctypes.c_void_p(z.data_ptr()),
+                                     ctypes.c_void_p(sig.data_ptr()),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.rf_last_error()
+    torch.cuda.synchronize()
+    zo, so = omf.matched_filter(np.asarray(xh, dtype=np.float64), iph, cfg.n, cfg.fs, cfg.f_low, cfg.f_high,
+                                ref.m1, ref.m2, cfg.pn_order)
+    assert np.abs(z.cpu().numpy() - zo).max() <= TOL[cfg.dtype] * np.abs(zo).max()
+    assert abs(sig.item() / so - 1) < 1e-12
 
 
 def test_noalloc_rejects_oversized_segment(torch):
