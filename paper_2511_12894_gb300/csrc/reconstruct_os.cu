@@ -261,8 +261,11 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restri
 // Batched form: neighbours of several references in one persistent launch.  Each item
 // describes one neighbour (its partition spectra, partitions, first lag, the segment
 // spectra of its reference and its output row); work units are (item, chunk of SC
-// output blocks), claimed in order from an atomic counter, so the units of one
-// reference run together and its segment spectra stay in L2.
+// output blocks), claimed in the order of `order` (unit code item * nchunk + chunk) from
+// an atomic counter.  The host orders them by reference, then by tiles of output chunks x
+// neighbours, so the segment spectra a tile reads and its neighbours' partition spectra stay
+// in L2 while the tile's units run (a 2^23-sample reference has 134-268 MB of segment
+// spectra, more than L2 holds).
 struct OsItem {
   const float2* C;
   const float2* Zs;
@@ -272,7 +275,8 @@ struct OsItem {
 };
 
 template <int B, int Q>
-__global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* __restrict__ items, int64_t units,
+__global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* __restrict__ items,
+                                                                 const long long* __restrict__ order, int64_t units,
                                                                  int nchunk, const float2* __restrict__ tw, int64_t n,
                                                                  int NQ, int NB, int SC,
                                                                  unsigned long long* __restrict__ keys,
@@ -286,8 +290,9 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* 
     const long long u = s_unit;
     __syncthreads();
     if (u >= units) break;
-    const OsItem it = items[u / nchunk];
-    const int s0 = (int)(u % nchunk) * SC;
+    const long long code = order[u];
+    const OsItem it = items[code / nchunk];
+    const int s0 = (int)(code % nchunk) * SC;
     const int s1 = min(NB, s0 + SC);
     os_blocks<B, Q, true>(it.Zs, it.C, it.P, it.lag0, tw, n, NQ, s0, s1, nullptr, keys + it.row * nw, W, nw, fastwin,
                           sm);
@@ -965,17 +970,52 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     c->batch_zs.ensure(zs_need);
     const float2* zs_all = c->batch_zs.as<float2>();
     c->batch_lay_off.assign(nb + 1, 0);
+    c->batch_unit_off.assign(nb + 1, 0);
+    c->batch_sc.assign(nb, 1);
+    std::vector<long long> order;
     for (int b = 0; b < nb; ++b) {
       const int64_t zstride = (n / Lps[b]) * Bs[b];
+      const int64_t first = (int64_t)items.size();
+      std::vector<int64_t> grp(G + 1, 0);  // items of reference g in this bucket: [grp[g], grp[g+1]) from first
+      std::vector<int> pmax(G, 1);
       int64_t row0 = 0;
       for (int g = 0; g < G; ++g) {
         const rf_kernels* k = ks[g];
-        for (const int j : k->os_buckets[b].idx)
+        for (const int j : k->os_buckets[b].idx) {
           items.push_back(OsItem{k->os_spec.as<float2>() + k->os_off[j], zs_all + (int64_t)g * zstride,
                                  k->os_parts[j], k->lag0[j], (long long)(row0 + j)});
+          pmax[g] = std::max(pmax[g], k->os_parts[j]);
+        }
         row0 += k->k;
+        grp[g + 1] = (int64_t)items.size() - first;
       }
       c->batch_lay_off[b + 1] = (int64_t)items.size();
+      const int64_t cnt = grp[G];
+      const int B = Bs[b], Lp = Lps[b];
+      const int64_t NB = (n + (B - Lp) - 1) / (B - Lp);
+      // output blocks per unit: 8, fewer when the units would not fill the GPU a few times
+      int SC = 8;
+      const int64_t fill = (B == kB2 ? 4LL : 8LL) * c->nsm;
+      while (SC > 1 && cnt * ((NB + SC - 1) / SC) < fill) SC /= 2;
+      c->batch_sc[b] = SC;
+      const int64_t nchunk = (NB + SC - 1) / SC;
+      // tiles: a time tile of Ts chunks reads (Ts SC (Q - 1) + P) segment spectra of B values;
+      // keep that near 24 MB, and give a tile about as many units as blocks run at once
+      const int64_t seg_bytes = (int64_t)B * (int64_t)sizeof(float2);
+      const int64_t inflight = B > 16384 ? c->nsm / 2 : (int64_t)c->nsm * (16384 / B);
+      for (int g = 0; g < G; ++g) {
+        const int64_t lo = first + grp[g], hi = first + grp[g + 1];
+        if (lo == hi) continue;
+        const int64_t segs = std::max<int64_t>(1, ((int64_t)24 << 20) / seg_bytes - pmax[g]);
+        const int64_t Ts = std::max<int64_t>(1, std::min<int64_t>(nchunk, segs / ((int64_t)SC * (B / Lp - 1))));
+        const int64_t Tj = std::max<int64_t>(1, std::min<int64_t>(hi - lo, (inflight + Ts - 1) / Ts));
+        for (int64_t c0 = 0; c0 < nchunk; c0 += Ts)
+          for (int64_t j0 = lo; j0 < hi; j0 += Tj)
+            for (int64_t it = j0; it < std::min(hi, j0 + Tj); ++it)
+              for (int64_t ch = c0; ch < std::min(nchunk, c0 + Ts); ++ch)
+                order.push_back((long long)((it - first) * nchunk + ch));
+      }
+      c->batch_unit_off[b + 1] = (int64_t)order.size();
     }
     std::vector<const float2*> zp(G);
     for (int g = 0; g < G; ++g) zp[g] = static_cast<const float2*>(z_refs[g]);
@@ -985,6 +1025,9 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     c->batch_keys.ensure(sizeof(unsigned long long) * ((size_t)rows * nw + nb));
     if (!items.empty())
       RF_CUDA(cudaMemcpy(c->batch_items.p, items.data(), sizeof(OsItem) * items.size(), cudaMemcpyHostToDevice));
+    c->batch_order.ensure(std::max<size_t>(16, sizeof(long long) * order.size()));
+    if (!order.empty())
+      RF_CUDA(cudaMemcpy(c->batch_order.p, order.data(), sizeof(long long) * order.size(), cudaMemcpyHostToDevice));
     RF_CUDA(cudaMemcpy(c->batch_zptr.p, zp.data(), sizeof(const float2*) * G, cudaMemcpyHostToDevice));
     c->batch_key = key;
     c->batch_rows = rows;
@@ -1000,11 +1043,10 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     const int B = Bs[b], Lp = Lps[b];
     const int NQ = (int)(n / Lp);
     const int NB = (int)((n + (B - Lp) - 1) / (B - Lp));
+    const int SC = c->batch_sc[b];
+    const int nchunk = (NB + SC - 1) / SC;
     if (B == kB2) {
       // CTA pairs: one cluster per (chunk of output blocks, work item), no work counter
-      int SC = 8;
-      while (SC > 1 && cnt * ((NB + SC - 1) / SC) < 4LL * c->nsm) SC /= 2;
-      const int nchunk = (NB + SC - 1) / SC;
       launch_os2_segments(c, nullptr, c->batch_zptr.as<const float2*>(), G, Lp, c->batch_zs.as<float2>(), s);
       const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
       const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
@@ -1022,10 +1064,8 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
       else run(k_os2_batched<4>);
       continue;
     }
-    int SC = 8;
-    while (SC > 1 && cnt * ((NB + SC - 1) / SC) < 8LL * c->nsm) SC /= 2;
-    const int nchunk = (NB + SC - 1) / SC;
-    const int64_t units = cnt * nchunk;
+    const int64_t units = c->batch_unit_off[b + 1] - c->batch_unit_off[b];
+    RF_REQUIRE(units == cnt * nchunk, "batched plan: unit count");
     unsigned long long* counter = keys + rows * nw + b;
     dispatch_bq(B, B / Lp, [&](auto bc, auto qc) {
       constexpr int BB = decltype(bc)::value, QQ = decltype(qc)::value;
@@ -1041,8 +1081,9 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
       int per_sm = 0;
       RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BB / 16, os_smem<BB>()));
       const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * c->nsm, units));
-      fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>() + first, units, nchunk, tw, n,
-                                                        NQ, NB, SC, keys, W, nw, fastwin, counter);
+      fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>() + first,
+                                                        c->batch_order.as<long long>() + c->batch_unit_off[b], units,
+                                                        nchunk, tw, n, NQ, NB, SC, keys, W, nw, fastwin, counter);
       RF_LAUNCHED();
     });
   }

@@ -138,6 +138,12 @@ struct rf_ctx {
   std::vector<int64_t> batch_lay_off;  // work items of layout bucket b: [off[b], off[b+1])
   int64_t batch_rows = 0, batch_nw = 0;
   rf::DevBuf batch_items, batch_zptr, batch_zs, batch_keys;
+  // work units (item * nchunk + chunk) in launch order, bucket after bucket: per reference, tiles
+  // of output chunks x neighbours small enough that their segment and partition spectra stay
+  // in L2 while the units of a tile run
+  rf::DevBuf batch_order;
+  std::vector<int64_t> batch_unit_off;  // units of layout bucket b: [off[b], off[b+1])
+  std::vector<int> batch_sc;            // output blocks per unit, per bucket
   // Streaming (rf_stream_winmax): two device strain buffers, the references' series, the window
   // peaks, and one pinned host block for the strain staging and the peaks; kept between calls.
   rf::DevBuf st_x[2], st_z, st_pm, st_pa;
