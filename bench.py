@@ -1,22 +1,24 @@
 #!/usr/bin/env python3
 """Throughput of the ratio-filter hot path on one GB300 (template*samples/s).
 
-One step = the whole online path for one data segment of the paper-shaped FP32
-workload (fs 2048 Hz, f_low 20 Hz, 512 s, n = 2^20, one reference and 256
-TaylorF2 3.5PN neighbours):
-    mf_filtered (data FFT, reference matched filter)   ->  z_ref
-    winmax of z_ref                                     ->  reference peaks
-    reconstruct_winmax (all neighbours, fused peaks)    ->  neighbour peaks
-Units per step: (1 + K) * n template-samples.  Kernel building is offline
+One step = the whole online path for one data segment.  The default workload is the
+long-duration batched configuration (fs 2048 Hz, f_low 5 Hz, 4096 s, n = 2^23, 128
+references x 128 TaylorF2 3.5PN neighbours, kernels up to 3e5 taps on per-neighbour
+build grids, autotuned overlap-save buckets, one persistent launch per bucket, the
+whole step replayed from one CUDA graph); `--config 1..4` select the others:
+    mf_filtered (data FFT, reference matched filters)   ->  z_ref of every reference
+    winmax of z_ref                                      ->  reference peaks
+    reconstruct (batched, all neighbours, fused peaks)   ->  neighbour peaks
+Units per step: (G + sum K_g) * n template-samples.  Kernel building is offline
 (its time is reported as `build_s`, outside the metric), and so is the stored
 reference filter conj(h~_ref) / S_n / N_ref of each reference, which depends on
 the template and the PSD only (`--mf onthefly` regenerates it in every step).
 
-Also measured in the same run: per-template full-length cuFFT matched
-filtering of every template (the plain method) and the SNR error of our
-peaks against it; the roofline of the dominant kernel; the e2e number through
-the public API with host buffers; the FP64 oracle on the host cores
-(`cpu_baseline`).  `--impl reference` times only the oracle.
+Also measured in the same run: the plain method (per-template full-length matched
+filtering) on the same GPU in three arms, and the SNR error of our peaks against it;
+the roofline of the dominant kernel; the e2e number through the public API with host
+buffers; the FP64 oracle on the host cores (`cpu_baseline`).  `--impl reference`
+times only the oracle.
 """
 from __future__ import annotations
 
@@ -49,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=5)
     ap.add_argument("--algo", default="auto", choices=["auto", "direct", "os", "gemm"])
     ap.add_argument("--prec", default=None, choices=["native", "bf16", "bf16x3", "bf16x6", "bf16x9", "3xtf32"],
                     help="arithmetic of the reconstruction (default: native; bf16x6 for --algo gemm)")
@@ -200,52 +202,70 @@ def cufft_matched_filter_peaks(x, ip, templates_fd, cfg, torch, chunk=16):
 
 # --------------------------------------------------------------------------- oracle on the host
 
-def cpu_baseline(cfg, n_nbrs=4, slice_len=1 << 12, budget_s=20.0):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload:
-    the reference matched filter over the whole segment, then the direct
-    reconstruction of `n_nbrs` neighbours over `slice_len` output samples."""
-    from oracle import data as odata, mf as omf, ratio as oratio, reconstruct as orec
-    ref, nb = cfg.groups[0]
-    ip = workload.inv_psd(cfg)
-    x = odata.strain(cfg)
-    t0 = time.perf_counter()
-    z_ref, _ = omf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2, cfg.pn_order)
-    t_mf = time.perf_counter() - t0
-    units = cfg.n
-    # kernels of a few neighbours (offline in the method; not timed), chosen at quantiles of
-    # the duration offset, which sets the kernel length (Sec. II.B)
-    tau_ref = workload.newtonian_duration(ref, cfg.f_low)
-    off = np.array([abs(workload.newtonian_duration(t, cfg.f_low) - tau_ref) for t in nb])
-    order = np.argsort(off)
-    sel = [int(order[min(len(nb) - 1, int((q + 0.5) * len(nb) / n_nbrs))]) for q in range(n_nbrs)]
-    pk = oratio.build_ratio_kernels(ref, [nb[j] for j in sel], cfg.n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order,
-                                    ip, cfg.threshold)
-    idx = np.arange(slice_len, dtype=np.int64) * (cfg.n // slice_len)
-    t1 = time.perf_counter()
-    done = 0
-    for j in range(len(sel)):
-        orec.reconstruct_at(z_ref, *pk.kernel(j), idx)
-        done += 1
-        if time.perf_counter() - t1 > budget_s:
-            break
-    t_rec = time.perf_counter() - t1
-    units_rec = done * slice_len
-    # normalise: reference MF costs t_mf per n samples; reconstruction t_rec per units_rec
-    per_unit_mf = t_mf / units
-    per_unit_rec = t_rec / max(units_rec, 1)
-    K = len(nb)
-    total_units = (1 + K) * cfg.n
-    total_time = per_unit_mf * cfg.n + per_unit_rec * K * cfg.n
-    mean_len = float(np.mean(pk.length))
-    return {
-        "value": total_units / total_time,
-        "unit": "template*samples/s",
-        "cores": 1,
-        "kind": "oracle",
-        "sample": (f"reference MF over n={cfg.n} ({t_mf:.2f}s) + direct reconstruction of {done} neighbours "
-                   f"(mean L={mean_len:.0f}) at {slice_len} output samples ({t_rec:.2f}s); scaled to "
-                   f"(1+{K}) x n; numpy single-threaded on {os.cpu_count()} host cores"),
-    }
+class OracleSample:
+    """The FP64 oracle as it stands, on a bounded sample of the workload.
+
+    Set-up (untimed, like the method's offline phase): the strain and the kernels of
+    `n_nbrs` neighbours of the first reference, chosen at quantiles of their duration offset
+    (which sets the kernel length, Sec. II.B), on the same build grid as the GPU arm.
+    Timed once: the reference matched filter over the whole segment (data FFT, template,
+    inverse FFT; Eqs. 2-3).  Timed per step: the direct reconstruction (Eq. 8) of those
+    neighbours at `slice_len` output samples.  `value()` scales both to the step's units:
+    G reference filters and sum_j L_j n multiply-adds of the neighbours, the latter by the
+    workload's total taps over the sample's."""
+
+    def __init__(self, cfg, n_nbrs: int, slice_len: int, n_build: int, thr: float, total_taps: float = None):
+        from oracle import data as odata, mf as omf, ratio as oratio
+        self.cfg = cfg
+        ref, nb = cfg.groups[0]
+        ip = workload.inv_psd(cfg)
+        x = odata.strain(cfg)
+        t0 = time.perf_counter()
+        self.z_ref, _ = omf.matched_filter(x, ip, cfg.n, cfg.fs, cfg.f_low, cfg.f_high, ref.m1, ref.m2,
+                                           cfg.pn_order)
+        self.t_mf = time.perf_counter() - t0
+        tau_ref = workload.newtonian_duration(ref, cfg.f_low)
+        off = np.array([abs(workload.newtonian_duration(t, cfg.f_low) - tau_ref) for t in nb])
+        order = np.argsort(off)
+        sel = sorted({int(order[min(len(nb) - 1, int((q + 0.5) * len(nb) / n_nbrs))]) for q in range(n_nbrs)})
+        self.pk = oratio.build_ratio_kernels(ref, [nb[j] for j in sel], cfg.n, cfg.fs, cfg.f_low, cfg.f_high,
+                                             cfg.pn_order, ip, thr, n_build=n_build)
+        self.idx = np.arange(slice_len, dtype=np.int64) * (cfg.n // slice_len)
+        self.sample_taps = float(np.sum(self.pk.length))
+        rows = sum(len(g[1]) for g in cfg.groups)
+        # the workload's taps: the GPU arm's kernels when given, else the sample's mean length
+        self.total_taps = float(total_taps) if total_taps else self.sample_taps / len(sel) * rows
+        self.n_sel = len(sel)
+        self.rows = rows
+
+    def step(self) -> float:
+        from oracle import reconstruct as orec
+        t1 = time.perf_counter()
+        for j in range(self.n_sel):
+            orec.reconstruct_at(self.z_ref, *self.pk.kernel(j), self.idx)
+        return time.perf_counter() - t1
+
+    def value(self, t_rec: float) -> float:
+        cfg = self.cfg
+        G = len(cfg.groups)
+        units = (G + self.rows) * cfg.n
+        # reconstruction time per tap-output from the sample, times the workload's tap-outputs
+        per_tap_out = t_rec / (self.sample_taps * len(self.idx))
+        total = G * self.t_mf + per_tap_out * self.total_taps * cfg.n
+        return units / total
+
+    def describe(self, t_rec: float) -> str:
+        return (f"reference MF over n={self.cfg.n} ({self.t_mf:.2f}s, timed once) + direct reconstruction of "
+                f"{self.n_sel} neighbours (mean L={self.sample_taps / self.n_sel:.0f}) at {len(self.idx)} output "
+                f"samples ({t_rec:.2f}s per step); scaled to {len(self.cfg.groups)} reference MFs and "
+                f"{self.total_taps:.4g} taps x n; numpy single-threaded on {os.cpu_count()} host cores")
+
+
+def cpu_baseline(cfg, n_build: int, thr: float, total_taps: float):
+    """The oracle leg of the GPU arm's line (one timed step of OracleSample)."""
+    o = OracleSample(cfg, n_nbrs=4, slice_len=1 << 11, n_build=n_build, thr=thr, total_taps=total_taps)
+    t = o.step()
+    return {"value": o.value(t), "unit": "template*samples/s", "cores": 1, "kind": "oracle", "sample": o.describe(t)}
 
 
 def scipy_baseline(cfg, x, filt_row, kern, n_nbrs=8, budget_s=20.0):
@@ -335,6 +355,17 @@ def stream_rate(rf, cfg, x, filt, kerns, W: int, hops: int) -> dict:
                                           "batched reconstruction -> host window peaks of the stream"}
 
 
+def tune_groups(kerns, max_groups: int = 8):
+    """Indices of at most `max_groups` reference groups spread over the batch's total kernel
+    length per group (the quantiles of that distribution), for the autotuner."""
+    G = len(kerns)
+    if G <= max_groups:
+        return list(range(G))
+    tot = [int(np.sum(k.length)) for k in kerns]
+    order = sorted(range(G), key=lambda g: (tot[g], g))
+    return sorted({order[min(G - 1, int((q + 0.5) * G / max_groups))] for q in range(max_groups)})
+
+
 def load_workload(args):
     """The configuration to run: one of the five workloads, or (--bank N) the batched
     workload's grid with the sets of a structured synthetic bank as its reference groups."""
@@ -363,20 +394,21 @@ def run_reference(args):
     if rank != 0:
         return
     cfg = workload.config(args.config)
-    vals = []
-    cb = None
+    thr = args.threshold if args.threshold is not None else GATE_THRESHOLD
+    n_build = args.n_build if args.n_build is not None else (-1 if cfg.n > (1 << 20) else 0)
+    o = OracleSample(cfg, n_nbrs=2, slice_len=1 << 10, n_build=n_build, thr=thr)
+    vals, t = [], 0.0
     for s in range(args.warmup + args.steps):
-        cb = cpu_baseline(cfg, n_nbrs=2, slice_len=1 << 10, budget_s=5.0)
+        t = o.step()
         if s >= args.warmup:
-            vals.append(cb["value"])
-    v = statistics.median(vals) if vals else cb["value"]
+            vals.append(o.value(t))
+    v = statistics.median(vals) if vals else o.value(t)
+    cb = {"value": v, "unit": "template*samples/s", "cores": 1, "kind": "oracle", "sample": o.describe(t)}
     line = {"impl": "reference", "metric": "template*samples/s", "value": v, "unit": "template*samples/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_label(cfg, args.config,
-                                                  args.threshold if args.threshold is not None else GATE_THRESHOLD),
-                       "parallelism": "host"},
-            "cpu_baseline": {**cb, "value": v},
+            "config": {"workload": workload_label(cfg, args.config, thr), "parallelism": "host"},
+            "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "template*samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -397,20 +429,34 @@ def main():
     build.build()
 
     cfg = load_workload(args)
-    # multi-reference workloads are sharded by whole groups across ranks (no data-path
-    # collective; every rank builds the same strain from the same seed); a single-group
-    # workload runs as one replica per rank
+    # multi-reference workloads are sharded by whole groups across ranks, a single group by its
+    # neighbours (every rank filtering the one reference); every rank builds the same strain
+    # from the same seed, and the only exchange is the final gather of the window peaks
     from paper_2511_12894_gb300 import shard
+    from dataclasses import replace as _replace
     all_groups = cfg.groups
-    sharded = world > 1 and len(all_groups) > 1
-    if sharded:
+    sharded = world > 1
+    nb_sizes = [len(nb) for _, nb in all_groups]
+    if sharded and len(all_groups) > 1:
         def est_lengths(ref, nb):
             t0 = workload.newtonian_duration(ref, cfg.f_low)
             return [max(512.0, abs(workload.newtonian_duration(t, cfg.f_low) - t0) * cfg.fs) for t in nb]
         costs = [shard.group_cost(cfg.n, est_lengths(r, nb)) for r, nb in all_groups]
-        mine = shard.my_groups(costs, world, rank)
-        from dataclasses import replace as _replace
+        assign = shard.assign(costs, world)
+        mine = assign[rank]
         cfg = _replace(cfg, groups=tuple(all_groups[g] for g in mine))
+        ref_rows = [list(a) for a in assign]
+        nb_rows = [shard.global_rows(nb_sizes, a) for a in assign]
+        shard_mode = f"groups sharded over {world} ranks"
+    elif sharded:
+        ref0, nb0 = all_groups[0]
+        runs = [shard.split_neighbours(len(nb0), world, r) for r in range(world)]
+        cfg = _replace(cfg, groups=((ref0, tuple(nb0[j] for j in runs[rank])),))
+        ref_rows = [[0]] + [[] for _ in range(world - 1)]   # rank 0 reports the reference
+        nb_rows = [list(r) for r in runs]
+        shard_mode = f"neighbours split over {world} ranks"
+    else:
+        shard_mode = "one GPU"
     units_total = sum(1 + len(nb) for _, nb in all_groups) * cfg.n
     full_cfg = load_workload(args)   # the whole workload, for its label
     # relative truncation threshold: the largest of 1e-3, 1e-4, 3e-5 whose window peaks stay
@@ -429,21 +475,36 @@ def main():
     kerns = [rf.build_ratio_kernels(r, nb, ip, thr, relative=not args.absolute, n_build=n_build,
                                     analytic=args.analytic, real=args.real) for r, nb in cfg.groups]
     filt, sig = rf.reference_filters(ip, refs)
-    tune, tune_s = None, 0.0
+    tune, tune_s, tune_info, tuned_call = None, 0.0, None, None
     if args.buckets:
         spec = [tuple(int(v) for v in b.split(":")) for b in args.buckets.split(",")]
         for k in kerns:
             k.prepare_buckets([c for c, _, _ in spec], [b for _, b, _ in spec], [p for _, _, p in spec])
         algo_used = "os"
     elif args.algo == "auto" and not args.no_autotune and args.block == 0 and args.part == 0:
-        # the autotuner times candidate forms on a z_ref of this segment (offline, like the kernels)
+        # the autotuner times candidate forms on a z_ref of this segment (offline, like the
+        # kernels), on at most 8 groups spread over the batch's per-group kernel lengths; the
+        # winning form and layout then apply to every group
         t1 = time.perf_counter()
-        zt = rf.mf_filtered(x, filt)
-        tune = rf.autotune([zt[g] for g in range(G)], kerns, W, allow_split=cfg.dtype == "f32")
+        pick = tune_groups(kerns)
+        zt = rf.mf_filtered(x, filt[pick] if len(pick) < G else filt)
+        tune = rf.autotune([zt[q] for q in range(len(pick))], [kerns[g] for g in pick], W,
+                           allow_split=cfg.dtype == "f32")
         del zt
+        w = tune[0]
+        if len(pick) < G:
+            if w["algo"] == "os":
+                cuts = [0, w["cut"]] if w["cut"] else [0]
+                blocks = [w["block"], w["block2"]] if w["cut"] else [w["block"]]
+                parts = [w["part"], w["part2"]] if w["cut"] else [w["part"]]
+                for k in kerns:
+                    k.prepare_buckets(cuts, blocks, parts)
+            # groups outside the tuned subset resolve AUTO by default; name the form instead
+            tuned_call = (w["algo"], w["prec"])
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t1
-        algo_used = tune[0]["algo"]
+        algo_used = w["algo"]
+        tune_info = {"groups_timed": len(pick), "of": G}
     else:
         algo_used = args.algo if args.algo != "auto" else ("os" if cfg.dtype == "f32" else "direct")
         if algo_used == "os":
@@ -467,13 +528,16 @@ def main():
         rf.reserve(rows)
 
     call_prec = args.prec or ("bf16x6" if args.algo == "gemm" else "native")
+    call_algo = args.algo
+    if tuned_call is not None:
+        call_algo, call_prec = tuned_call
     prec = tune[0]["prec"] if tune else call_prec   # the precision the reconstruction runs at
 
     def recon():
         if G == 1:
-            rf.reconstruct_winmax(z[0], kerns[0], W, args.algo, max_out=Pn, arg_out=An, prec=call_prec)
+            rf.reconstruct_winmax(z[0], kerns[0], W, call_algo, max_out=Pn, arg_out=An, prec=call_prec)
         else:
-            rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, args.algo, max_out=Pn, arg_out=An,
+            rf.reconstruct_batched([z[g] for g in range(G)], kerns, W, call_algo, max_out=Pn, arg_out=An,
                                       prec=call_prec)
 
     def mf_step(xs):
@@ -531,7 +595,20 @@ def main():
         total_ms = t.item()
     ms_per_step = total_ms / args.steps
     units_step = (G + rows) * n
-    value = (units_total if sharded else world * units_step) * args.steps / (total_ms / 1e3)
+    value = units_total * args.steps / (total_ms / 1e3)
+    gathered = None
+    if world > 1:
+        # the one exchange: every rank's window peaks to rank 0, in the single-process row order
+        import torch.distributed as dist
+        nr = len(ref_rows[rank])
+        total_nb = sum(nb_sizes)
+        outs = [shard.gather_rows(t, rows_, tot, rank, world, dist)
+                for t, rows_, tot in ((Pr[:nr], ref_rows, len(all_groups)), (Ar[:nr], ref_rows, len(all_groups)),
+                                      (Pn, nb_rows, total_nb), (An, nb_rows, total_nb))]
+        if rank == 0:
+            gathered = {"reference_rows": int(outs[0].shape[0]), "neighbour_rows": int(outs[2].shape[0]),
+                        "windows": int(outs[0].shape[1]), "how": "torch.distributed.gather to rank 0, "
+                                                                 "after the timed region"}
 
     # ---------------- the dominant kernel alone (events on its stream), for the roofline: the
     # reconstruction's launches replayed from a graph of their own, so that the host work of an
@@ -584,7 +661,7 @@ def main():
         if s >= args.warmup:
             e_ms.append(e0.elapsed_time(e1))
     e2e_ms = statistics.mean(e_ms)
-    e2e = {"value": (units_total if sharded else world * units_step) / (e2e_ms / 1e3), "unit": "template*samples/s",
+    e2e = {"value": units_total / (e2e_ms / 1e3), "unit": "template*samples/s",
            "h2d_bytes_per_step": int(x_host.numel() * x_host.element_size()),
            "d2h_bytes_per_step": int(P_host.numel() * 4 + A_host.numel() * 4), "ms_per_step": e2e_ms,
            "path": f"pinned host x -> mf_{args.mf} -> winmax -> reconstruct (eager calls) -> pinned host peaks"}
@@ -628,6 +705,9 @@ def main():
                                  (" x 1.1/2.25 nominal TF32:BF16" if prec == "3xtf32" else "") +
                                  "; achieved counts the MMA flops issued (split terms included)",
                     "algorithmic_tflops": flops / (rec_avg_ms / 1e3) / 1e12,
+                    # the method's own work (8 L flops per template-sample) against what the pipe can
+                    # deliver for it: the peak divided by the split products each flop needs
+                    "algorithmic_frac": (flops / (rec_avg_ms / 1e3) / 1e12) / (peak_tflops / nprod),
                     "kernel_ms": rec_avg_ms, "share_of_step": rec_avg_ms / ms_per_step}
     else:
         peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -652,25 +732,68 @@ def main():
         row0 = sum(len(nb) for _, nb in cfg.groups[:gs])
         sub = [(gs, refs[gs], -1)] + [(gs, t, j) for j, t in enumerate(cfg.groups[gs][1])]
         sub = sub[:257]
-        hs = torch.stack([rf.template_fd(t) for _, t, _ in sub]).to(torch.complex64)
-        for _ in range(2):
-            cufft_matched_filter_peaks(x, ip, hs, cfg, torch)
-        torch.cuda.synchronize()
-        b_ms = []
-        for _ in range(3):
-            flush.zero_()
+        tmpl = [t for _, t, _ in sub]
+        hs = torch.stack([rf.template_fd(t) for t in tmpl]).to(torch.complex64)
+
+        def timed(fn, reps=3):
+            fn()
+            fn()
             torch.cuda.synchronize()
-            b0 = torch.cuda.Event(enable_timing=True)
-            b1 = torch.cuda.Event(enable_timing=True)
-            b0.record(stream)
-            Pf, Af = cufft_matched_filter_peaks(x, ip, hs, cfg, torch)
-            b1.record(stream)
-            b1.synchronize()
-            b_ms.append(b0.elapsed_time(b1))
-        bm = statistics.median(b_ms) * (G + rows) / len(sub)
-        baseline = {"value": units_step / (bm / 1e3), "unit": "template*samples/s", "ms_per_step": bm,
-                    "what": "per-template cuFFT C2C inverse (n) of stored-template products + window max, batched 16",
-                    "templates_timed": len(sub)}
+            ms, out = [], None
+            for _ in range(reps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                b0 = torch.cuda.Event(enable_timing=True)
+                b1 = torch.cuda.Event(enable_timing=True)
+                b0.record(stream)
+                out = fn()
+                b1.record(stream)
+                b1.synchronize()
+                ms.append(b0.elapsed_time(b1))
+            return statistics.median(ms), out
+
+        # the minimum a stored-filter matched filter moves per template: its filter (n/2 + 1
+        # complex64 values) in, its window peaks (8 B per window) out
+        alg_bytes = 8.0 * (n // 2 + 1) + 8.0 * nw
+
+        def arm(ms_sub, what):
+            per_t = ms_sub / len(sub)
+            return {"value": units_step / (per_t * (G + rows) / 1e3), "unit": "template*samples/s",
+                    "ms_per_step": per_t * (G + rows), "us_per_template": per_t * 1e3,
+                    "achieved_gbs": alg_bytes / (per_t / 1e3) / 1e9, "what": what}
+
+        arms = {}
+        t_cu, (Pf, Af) = timed(lambda: cufft_matched_filter_peaks(x, ip, hs, cfg, torch))
+        arms["torch_cufft"] = arm(t_cu, "torch: product kernel, cuFFT C2C inverse (n), |z|^2 and window max as "
+                                        "separate kernels, batched 16; stored template spectra")
+        # the library's own fused path: stored per-template filters (the product formed inside the
+        # first inverse-FFT pass), then the window peaks of the series
+        filt_s, _ = rf.reference_filters(ip, tmpl)
+        zs_s = torch.empty((len(sub), n), dtype=rf.cdtype, device=dev)
+        Ps = torch.empty((len(sub), nw), dtype=torch.float32, device=dev)
+        As = torch.empty((len(sub), nw), dtype=torch.int32, device=dev)
+        t_lib, _ = timed(lambda: (rf.mf_filtered(x, filt_s, z_out=zs_s), rf.winmax(zs_s, W, max_out=Ps, arg_out=As)))
+        arms["library_stored_filter"] = arm(t_lib, "rf_mf_filtered (data FFT, product in the first inverse pass) "
+                                                   "+ rf_winmax; stored per-template filters")
+        del filt_s
+        # templates generated in every step (the paper's standard: generation + correlation)
+        sig_s = torch.empty(len(sub), dtype=torch.float64, device=dev)
+        t_otf, _ = timed(lambda: (rf.mf_reference(x, ip, tmpl, z_out=zs_s, sigma_out=sig_s),
+                                  rf.winmax(zs_s, W, max_out=Ps, arg_out=As)))
+        arms["library_on_the_fly"] = arm(t_otf, "rf_mf_reference (TaylorF2 template generated per step, FP64 "
+                                                "phase) + rf_winmax: waveform generation + correlation")
+        del zs_s
+        fastest = max(arms, key=lambda a: arms[a]["value"])
+        fits = 8.0 * (n // 2 + 1) * (G + rows) <= 0.8 * torch.cuda.get_device_properties(dev).total_memory
+        # the stored-spectrum arms need every template's n/2 + 1 values in HBM; where they do not
+        # fit, only the on-the-fly arm can run the whole bank from one GPU
+        runnable = [a for a in arms if fits or a == "library_on_the_fly"]
+        fastest_run = max(runnable, key=lambda a: arms[a]["value"])
+        baseline = {**arms[fastest], "arm": fastest, "arms": arms, "templates_timed": len(sub),
+                    "stored_filters_fit_in_hbm": bool(fits),
+                    "speedup_vs_fastest": value / arms[fastest]["value"],
+                    "fastest_whole_bank_arm": fastest_run,
+                    "speedup_vs_fastest_whole_bank": value / arms[fastest_run]["value"]}
         ours_P = torch.cat([Pr[gs:gs + 1], Pn[row0:row0 + len(sub) - 1]]).double().sqrt()
         full_P = Pf.double().sqrt()
         err = {"peak_snr_max_abs_over_max": ((ours_P - full_P).abs().max() / full_P.max()).item()}
@@ -683,7 +806,7 @@ def main():
     cb = None
     sb = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_baseline(cfg)
+        cb = cpu_baseline(cfg, n_build, thr, float(L.sum()))
         if G == 1:
             try:
                 sb = scipy_baseline(cfg, x.double().cpu().numpy(), filt[0].cpu().numpy(), kerns[0])
@@ -698,7 +821,7 @@ def main():
         line = {
             "metric": "template*samples/s", "value": value, "unit": "template*samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+            "scaling": "strong", "vs_baseline": None,
             "dtype": "f32" if cfg.dtype == "f32" else "f64",
             "data": "synthetic",
             "config": {"workload": workload_label(full_cfg, full_cfg.index, thr,
@@ -708,14 +831,15 @@ def main():
                        "kernel_len": {"min": int(L.min()), "median": float(np.median(L)), "max": int(L.max()),
                                       "sum": int(L.sum())},
                        "l2": "flushed between steps (256 MB write outside the events)", "algo": algo_used, "mf": args.mf, "n_build": n_build,
-                       "autotune": ({"seconds": tune_s, "timed": tune} if tune else None),
+                       "autotune": ({"seconds": tune_s, "timed": tune, **(tune_info or {})} if tune else None),
                        "prec": prec,
                        "graph": graph is not None,
-                       "parallelism": (f"groups sharded over {world} ranks" if sharded else f"replicas x{world}")},
+                       "parallelism": shard_mode},
             "build_s": build_s, "gpu_launches": int(launches_per_step * args.steps),
-            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "plain_mf_cufft": baseline, "err_vs_full_mf": err,
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "plain_mf": baseline, "err_vs_full_mf": err,
             "scipy_oaconvolve": sb,
             "stream": st,
+            "gathered": gathered,
             # what a search keeps per template between analyses (Sec. IV): the plain method a
             # template spectrum of n/2 + 1 complex values per neighbour, the ratio filter the
             # neighbour's truncated kernel (sum of the kernel lengths); the references' own
