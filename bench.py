@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--kernels", type=int, default=None, help="neighbours per group (default: the config's)")
+    ap.add_argument("--groups", type=int, default=0,
+                    help="keep only the first N reference groups (small cases for profiling; 0: all)")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of one CUDA graph")
     return ap.parse_args()
 
@@ -370,7 +372,11 @@ def load_workload(args):
     """The configuration to run: one of the five workloads, or (--bank N) the batched
     workload's grid with the sets of a structured synthetic bank as its reference groups."""
     if not args.bank:
-        return workload.config(args.config, k_override=args.kernels)
+        cfg = workload.config(args.config, k_override=args.kernels)
+        groups = getattr(args, "groups", 0)
+        if groups and groups < len(cfg.groups):
+            cfg = workload.with_groups(cfg, cfg.groups[:groups], cfg.name)
+        return cfg
     from paper_2511_12894_gb300 import bank_structure
     base = workload.config(4)
     b = workload.synthetic_bank(args.bank, seed=2025)

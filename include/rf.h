@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define RF_ABI_VERSION 4
+#define RF_ABI_VERSION 5
 
 typedef struct rf_ctx rf_ctx;
 typedef struct rf_kernels rf_kernels;
@@ -185,9 +185,13 @@ rf_status rf_mf_filtered(rf_ctx* ctx, const void* x, int32_t nref, const void* f
  * App. A bounds are asymptotic, so A should leave the reach well past the taper widths (the
  * paper's absolute 1e-3 / s, or a relative threshold of 1e-4 or less).
  * RF_KERNEL_REAL: the paper's real-kernel form (Eq. 8 with r(t) = 2 Re of the App. A integrand):
- * rho is replaced by 2 Re rho (imaginary parts zero) before truncation, which then acts on
- * |2 Re rho| (analytic: |r| = fs |2 Re rho| / (N_ref/N_j)).  z_ref has no negative-frequency
- * content, so untruncated the result equals the complex kernel's; truncated, the two differ.
+ * rho is replaced by 2 Re rho before truncation, which then acts on |2 Re rho| (analytic:
+ * |r| = fs |2 Re rho| / (N_ref/N_j)).  z_ref has no negative-frequency content, so untruncated
+ * the result equals the complex kernel's; truncated, the two differ.  The set then stores its
+ * taps as REAL values of the grid dtype (half the bytes; rf_kernels_is_real reports it), the
+ * direct form multiplies complex z_ref by real taps (half the multiply-adds), and the
+ * overlap-save preparation keeps the Hermitian half of each partition spectrum (bins 0..B/2).
+ * The tensor-core form builds its complex operands from the real taps (same cost).
  * Taps c[l] = rho[m0+l] are stored packed (grid dtype) with int32 signed m0 and length L per
  * neighbour.
  * Normalisation: the templates are the stationary-phase family A f^-7/6 e^{-i Psi} on one band,
@@ -219,8 +223,18 @@ rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_t
 rf_status rf_kernels_import(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len,
                             const void* taps, rf_kernels** out);
 
+/* As rf_kernels_import for real-form kernels (RF_KERNEL_REAL): taps are HOST real values of
+ * the grid dtype (double or float), sum(len) of them. */
+rf_status rf_kernels_import_real(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len,
+                                 const void* taps, rf_kernels** out);
+
+/* *real = 1 when the set holds real-form taps (built with RF_KERNEL_REAL or imported with
+ * rf_kernels_import_real), else 0.  RF_EINVAL if either pointer is NULL. */
+rf_status rf_kernels_is_real(const rf_kernels* kern, int32_t* real);
+
 /* Borrowed views of a kernel set: host arrays len[k], lag0[k], offset[k+1] (int64) and
- * df_low[k] (Hz; NaN for imported kernels), and the device tap buffer (grid dtype).
+ * df_low[k] (Hz; NaN for imported kernels), and the device tap buffer (grid dtype complex, or
+ * grid dtype real for a real-form set).
  * Any output pointer may be NULL. */
 rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** len,
                           const int32_t** lag0, const int64_t** offset, const double** df_low,
@@ -233,7 +247,8 @@ rf_status rf_kernels_info(const rf_kernels* kern, int32_t* k, const int32_t** le
  * modelled cost for this set's kernel lengths (a per-block cost table measured on GB300,
  * plus a penalty for launches too small to fill the GPU).  Computes the partition spectra
  * FFT_B(taps)/B in FP64 and stores them as complex64 inside the kernel set
- * (sum_j ceil(L_j / Lp) x B complex64).  Each output block transform then keeps B - Lp
+ * (sum_j ceil(L_j / Lp) x B complex64; for a real-form set the Hermitian half, bins 0..B/2 in
+ * rows of B/2 + 8, and block sizes up to 16384).  Each output block transform then keeps B - Lp
  * outputs.  The first overlap-save reconstruction prepares with the modelled choice if this
  * was not called.  Allocates; SYNCHRONISES `stream`.  RF_EINVAL for other sizes. */
 rf_status rf_kernels_prepare(rf_ctx* ctx, rf_kernels* kern, int32_t block, int32_t part, rf_stream stream);
@@ -251,14 +266,37 @@ rf_status rf_kernels_os_layout(const rf_kernels* kern, int32_t* block, int32_t* 
 rf_status rf_kernels_prepare_buckets(rf_ctx* ctx, rf_kernels* kern, int32_t nb, const int32_t* cuts,
                                      const int32_t* blocks, const int32_t* parts, rf_stream stream);
 
+/* Preparation with a form per kernel-length bucket (bucket b: cuts[b] <= L < cuts[b+1], cuts as in
+ * rf_kernels_prepare_buckets): algos[b] = RF_ALGO_OS runs overlap-save with block size blocks[b]
+ * and partition length parts[b]; RF_ALGO_GEMM runs the tensor-core form at the split precision
+ * precs[b] with the tile layout (blocks[b] neighbours per group, parts[b] output tiles stacked
+ * per MMA): (16, widest stack) or (widest group, 1), or (0, 0) for the library's rule; kernels of
+ * at most 65536 taps; RF_ALGO_DIRECT runs the CUDA-core direct sum.  The overlap-save buckets
+ * share one segment transform per layout and launch as rf_kernels_prepare_buckets; each other
+ * bucket runs on a kernel set holding just its neighbours (taps copied, tensor-core operands
+ * prepared here) into a temporary whose rows are then scattered to the neighbours' rows, so a
+ * reconstruction of the set (RF_ALGO_AUTO or RF_ALGO_OS; rf_reconstruct, _winmax, _batched) mixes
+ * forms within one call.  The temporary (rows x windows, or rows x n for the series form) is
+ * sized on the first call: make one before capturing a CUDA graph.  RF_F32 grids, n >= 512.
+ * Allocates; SYNCHRONISES `stream`.  RF_EINVAL for invalid forms, layouts or lengths. */
+rf_status rf_kernels_prepare_forms(rf_ctx* ctx, rf_kernels* kern, int32_t nb, const int32_t* cuts,
+                                   const int32_t* algos, const int32_t* precs, const int32_t* blocks,
+                                   const int32_t* parts, rf_stream stream);
+
+/* The form (rf_algo) and precision of each bucket of a prepared kernel set, up to max_nb, and
+ * their number into *nb (0 when not prepared); any output pointer may be NULL. */
+rf_status rf_kernels_bucket_forms(const rf_kernels* kern, int32_t max_nb, int32_t* algos, int32_t* precs,
+                                  int32_t* nb);
+
 /* The bucket layout of a prepared kernel set: up to max_nb buckets into the host arrays cuts,
  * blocks, parts and their number, at most max_nb, into *nb (0 when not prepared); any of the
- * four may be NULL.  RF_EINVAL if kern is NULL or max_nb < 0. */
+ * four may be NULL (a tensor-core bucket reports its tile layout in blocks and parts).
+ * RF_EINVAL if kern is NULL or max_nb < 0. */
 rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t* cuts, int32_t* blocks,
                                 int32_t* parts, int32_t* nb);
 
-/* Copy the packed taps (sum(len) complex entries, grid dtype) into caller device memory
- * `dst`.  Async on stream. */
+/* Copy the packed taps (sum(len) entries, grid dtype: complex, or real for a real-form set)
+ * into caller device memory `dst`.  Async on stream. */
 rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream);
 
 /* Tensor-core layout a kernel set was last prepared for (by its last RF_ALGO_GEMM call): out[0]
@@ -365,11 +403,15 @@ typedef struct {
  * Candidates: on RF_F32 grids the max_os overlap-save layouts of least modelled cost (the batch
  * runs them as in rf_reconstruct_batched) and two-bucket variants (kernels shorter than 2048,
  * 4096 or 8192 taps with one of the two layouts of least modelled cost for them, the others with
- * the fastest single layout), the tensor-core form at RF_PREC_BF16X6 when flags has
- * RF_TUNE_ALLOW_SPLIT and the mean kernel length is at most 4096 taps, and the direct sum when the
- * grid is RF_F64 or no kernel is longer than 1024 taps.  out (host, may be NULL): up to max_out entries, the winner first; *n_out (host, may
- * be NULL) the number written.  Overlap-save kernel sets end up prepared for the winning layout
- * (or the last one timed when another form wins).  Allocates; SYNCHRONISES `stream`. */
+ * the fastest single layout), the tensor-core form at RF_PREC_BF16X6 in both tile layouts when
+ * flags has RF_TUNE_ALLOW_SPLIT and the mean kernel length is at most 4096 taps, with that flag
+ * also the mixed form (the tensor-core form for the shortest eighth of the kernels, up to a
+ * power-of-two cut of at most 4096 taps, the fastest single layout for the rest;
+ * rf_kernels_prepare_forms), and the direct sum when the grid is RF_F64 or no kernel is longer
+ * than 1024 taps.  out (host, may be NULL): up to max_out entries, the winner first; *n_out (host,
+ * may be NULL) the number written.  Kernel sets end up prepared for the winner (a bucketed
+ * winner, overlap-save or mixed, is then what RF_ALGO_AUTO runs; for another form, the last
+ * layout timed).  Allocates; SYNCHRONISES `stream`. */
 rf_status rf_autotune(rf_ctx* ctx, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
                       int32_t flags, int32_t max_os, rf_tune_entry* out, int32_t max_out, int32_t* n_out,
                       rf_stream stream);

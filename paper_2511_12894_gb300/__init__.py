@@ -32,8 +32,10 @@ PRECS = {"native": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4, "3xtf32"
 
 EXPORTED = (
     "rf_version", "rf_launch_count", "rf_last_error", "rf_create", "rf_destroy", "rf_reserve", "rf_template_fd",
-    "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_info", "rf_kernels_prepare",
-    "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_os_buckets", "rf_kernels_grids",
+    "rf_mf_reference", "rf_build_ratio_kernels", "rf_kernels_import", "rf_kernels_import_real",
+    "rf_kernels_is_real", "rf_kernels_info", "rf_kernels_prepare",
+    "rf_kernels_os_layout", "rf_kernels_prepare_buckets", "rf_kernels_prepare_forms", "rf_kernels_bucket_forms",
+    "rf_kernels_os_buckets", "rf_kernels_grids",
     "rf_kernels_gemm_layout", "rf_bank_structure", "rf_stream_winmax",
     "rf_kernels_copy_taps", "rf_kernels_free", "rf_reconstruct", "rf_reconstruct_winmax", "rf_reconstruct_batched", "rf_winmax",
     "rf_mf_reference_noalloc", "rf_device_status", "rf_reference_filters", "rf_mf_filtered",
@@ -90,6 +92,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_build_ratio_kernels": (i32, [vp, P(rf_template), P(rf_template), i32, vp, dbl, i32, i64, P(vp), vp]),
         "rf_kernels_grids": (i32, [vp, P(P(i64))]),
         "rf_kernels_import": (i32, [vp, i32, P(i32), P(i32), vp, P(vp)]),
+        "rf_kernels_import_real": (i32, [vp, i32, P(i32), P(i32), vp, P(vp)]),
+        "rf_kernels_is_real": (i32, [vp, P(i32)]),
         "rf_kernels_info": (i32, [vp, P(i32), P(P(i32)), P(P(i32)), P(P(i64)), P(P(dbl)), P(vp)]),
         "rf_kernels_copy_taps": (i32, [vp, vp, vp]),
         "rf_kernels_prepare": (i32, [vp, vp, i32, i32, vp]),
@@ -99,6 +103,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "rf_stream_winmax": (i32, [vp, vp, i64, i32, vp, vp, i64, i64, vp, vp, vp, vp, vp]),
         "rf_kernels_prepare_buckets": (i32, [vp, vp, i32, P(i32), P(i32), P(i32), vp]),
         "rf_kernels_os_buckets": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
+        "rf_kernels_prepare_forms": (i32, [vp, vp, i32, P(i32), P(i32), P(i32), P(i32), P(i32), vp]),
+        "rf_kernels_bucket_forms": (i32, [vp, i32, P(i32), P(i32), P(i32)]),
         "rf_kernels_free": (None, [vp]),
         "rf_reconstruct": (i32, [vp, vp, vp, i32, i32, vp, vp]),
         "rf_reconstruct_winmax": (i32, [vp, vp, vp, i32, i32, i64, vp, vp, vp]),
@@ -214,11 +220,14 @@ class Kernels:
     offset: np.ndarray
     df_low: np.ndarray
     grid: np.ndarray = None   # build grid of each kernel
+    real: bool = False        # real-form taps (stored as real values)
 
     def taps(self):
-        """Packed taps as a new CUDA tensor (complex, sum(length) entries)."""
+        """Packed taps as a new CUDA tensor (sum(length) entries: complex, or real for a
+        real-form set)."""
         import torch
-        t = torch.empty(int(self.offset[-1]), dtype=self.ctx.cdtype, device="cuda")
+        dt = self.ctx.rdtype if self.real else self.ctx.cdtype
+        t = torch.empty(int(self.offset[-1]), dtype=dt, device="cuda")
         if t.numel():
             _check(_lib.rf_kernels_copy_taps(self.handle, ctypes.c_void_p(t.data_ptr()), _stream()))
         return t
@@ -234,6 +243,25 @@ class Kernels:
         arr = lambda v: (ctypes.c_int32 * nb)(*[int(x) for x in v])
         _check(_lib.rf_kernels_prepare_buckets(self.ctx.handle, self.handle, nb, arr(cuts), arr(blocks), arr(parts),
                                                _stream(stream)))
+
+    def prepare_forms(self, cuts: Sequence[int], algos: Sequence[str], precs: Sequence[str],
+                      blocks: Sequence[int], parts: Sequence[int], stream=None) -> None:
+        """A form per kernel-length bucket: 'os' (blocks/parts = block size, partition length),
+        'gemm' (precs = split precision, blocks/parts = tile layout or 0, 0) or 'direct'."""
+        nb = len(cuts)
+        arr = lambda v: (ctypes.c_int32 * nb)(*[int(x) for x in v])
+        _check(_lib.rf_kernels_prepare_forms(self.ctx.handle, self.handle, nb, arr(cuts),
+                                             arr([ALGOS[a] for a in algos]), arr([PRECS[p] for p in precs]),
+                                             arr(blocks), arr(parts), _stream(stream)))
+
+    def bucket_forms(self):
+        """[(algo, prec), ...] of the bucketed preparation ([] if none)."""
+        a, p = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)()
+        nb = ctypes.c_int32(0)
+        _check(_lib.rf_kernels_bucket_forms(self.handle, 8, a, p, ctypes.byref(nb)))
+        an = {v: k for k, v in ALGOS.items()}
+        pn = {v: k for k, v in PRECS.items()}
+        return [(an[a[i]], pn[p[i]]) for i in range(nb.value)]
 
     def os_buckets(self):
         """[(cut, block, part), ...] of the overlap-save preparation ([] if none)."""
@@ -376,8 +404,10 @@ class RatioFilter:
         arr = lambda p, m, dt: np.ctypeslib.as_array(p, shape=(m,)).astype(dt).copy() if m else np.zeros(m, dt)
         gp = ctypes.POINTER(ctypes.c_int64)()
         _check(_lib.rf_kernels_grids(h, ctypes.byref(gp)))
+        real = ctypes.c_int32(0)
+        _check(_lib.rf_kernels_is_real(h, ctypes.byref(real)))
         return Kernels(h, self, kk, arr(ln, kk, np.int64), arr(lg, kk, np.int64), arr(of, kk + 1, np.int64),
-                       arr(dl, kk, np.float64), arr(gp, kk, np.int64))
+                       arr(dl, kk, np.float64), arr(gp, kk, np.int64), bool(real.value))
 
     def build_ratio_kernels(self, ref, nbrs: Sequence, inv_psd, threshold: float = 1e-3, relative: bool = True,
                             stream=None, n_build: int = 0, analytic: bool = False, real: bool = False) -> Kernels:
@@ -397,15 +427,23 @@ class RatioFilter:
                                            int(n_build), ctypes.byref(h), _stream(stream)))
         return self._wrap_kernels(h)
 
-    def kernels_import(self, lag0: Iterable[int], length: Iterable[int], taps: np.ndarray) -> Kernels:
-        """Kernels from host arrays (signed first lags, lengths, packed complex taps)."""
+    def kernels_import(self, lag0: Iterable[int], length: Iterable[int], taps: np.ndarray,
+                       real: bool = False) -> Kernels:
+        """Kernels from host arrays (signed first lags, lengths, packed taps: complex, or real
+        values for a real-form set)."""
         lag0 = np.ascontiguousarray(lag0, dtype=np.int32)
         length = np.ascontiguousarray(length, dtype=np.int32)
-        taps = np.ascontiguousarray(taps, dtype=np.complex128 if self.dtype == "f64" else np.complex64)
+        if real:
+            taps = np.ascontiguousarray(taps, dtype=np.float64 if self.dtype == "f64" else np.float32)
+        else:
+            taps = np.ascontiguousarray(taps, dtype=np.complex128 if self.dtype == "f64" else np.complex64)
+        if taps.size < int(length.sum()):
+            raise ValueError(f"taps holds {taps.size} values; the lengths need {int(length.sum())}")
         h = ctypes.c_void_p()
         P32 = ctypes.POINTER(ctypes.c_int32)
-        _check(_lib.rf_kernels_import(self.handle, len(length), lag0.ctypes.data_as(P32), length.ctypes.data_as(P32),
-                                      ctypes.c_void_p(taps.ctypes.data), ctypes.byref(h)))
+        fn = _lib.rf_kernels_import_real if real else _lib.rf_kernels_import
+        _check(fn(self.handle, len(length), lag0.ctypes.data_as(P32), length.ctypes.data_as(P32),
+                  ctypes.c_void_p(taps.ctypes.data), ctypes.byref(h)))
         return self._wrap_kernels(h)
 
     def reconstruct(self, z_ref, kern: Kernels, algo: str = "auto", out=None, stream=None, prec: str = "native"):

@@ -251,9 +251,9 @@ rf_status rf_build_ratio_kernels(rf_ctx* ctx, const rf_template* ref, const rf_t
   });
 }
 
-rf_status rf_kernels_import(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len, const void* taps,
-                            rf_kernels** out) {
-  return guard([&] {
+static void import_checked(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len, const void* taps,
+                           bool real, rf_kernels** out) {
+  {  // argument checks, then the copy (thrown failures become the caller's status)
     RF_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
     check_ctx(ctx);
@@ -269,7 +269,24 @@ rf_status rf_kernels_import(rf_ctx* ctx, int32_t k, const int32_t* lag0, const i
       }
     }
     if (total) check_host(taps, "taps");
-    *out = import_impl(ctx, k, lag0, len, taps);
+    *out = import_impl(ctx, k, lag0, len, taps, real);
+  }
+}
+
+rf_status rf_kernels_import(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len, const void* taps,
+                            rf_kernels** out) {
+  return guard([&] { import_checked(ctx, k, lag0, len, taps, false, out); });
+}
+
+rf_status rf_kernels_import_real(rf_ctx* ctx, int32_t k, const int32_t* lag0, const int32_t* len, const void* taps,
+                                 rf_kernels** out) {
+  return guard([&] { import_checked(ctx, k, lag0, len, taps, true, out); });
+}
+
+rf_status rf_kernels_is_real(const rf_kernels* kern, int32_t* real) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr && real != nullptr, "kern and real must be non-NULL");
+    *real = kern->real ? 1 : 0;
   });
 }
 
@@ -318,6 +335,43 @@ rf_status rf_kernels_prepare_buckets(rf_ctx* ctx, rf_kernels* kern, int32_t nb, 
   });
 }
 
+rf_status rf_kernels_prepare_forms(rf_ctx* ctx, rf_kernels* kern, int32_t nb, const int32_t* cuts,
+                                   const int32_t* algos, const int32_t* precs, const int32_t* blocks,
+                                   const int32_t* parts, rf_stream stream) {
+  return guard([&] {
+    check_ctx(ctx);
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    RF_REQUIRE(kern->n == ctx->n && kern->dtype == ctx->g.dtype, "kernels were made for another grid");
+    if (ctx->g.dtype != RF_F32 || ctx->n < 512) {
+      set_error("bucketed preparation needs an RF_F32 grid with n >= 512");
+      throw Fail{RF_EUNSUPPORTED};
+    }
+    RF_REQUIRE(nb >= 1 && nb <= 8, "nb must be in [1, 8]");
+    check_host(cuts, "cuts");
+    check_host(algos, "algos");
+    check_host(precs, "precs");
+    check_host(blocks, "blocks");
+    check_host(parts, "parts");
+    std::vector<BucketSpec> spec(nb);
+    for (int b = 0; b < nb; ++b) spec[b] = BucketSpec{cuts[b], algos[b], precs[b], blocks[b], parts[b]};
+    os_prepare_forms(ctx, kern, nb, spec.data(), (cudaStream_t)stream);
+  });
+}
+
+rf_status rf_kernels_bucket_forms(const rf_kernels* kern, int32_t max_nb, int32_t* algos, int32_t* precs,
+                                  int32_t* nb) {
+  return guard([&] {
+    RF_REQUIRE(kern != nullptr, "kern is NULL");
+    RF_REQUIRE(max_nb >= 0, "max_nb must be >= 0");
+    const int cnt = kern->os_ready ? (int)kern->os_buckets.size() : 0;
+    for (int b = 0; b < std::min(cnt, (int)max_nb); ++b) {
+      if (algos) algos[b] = kern->os_buckets[b].algo;
+      if (precs) precs[b] = kern->os_buckets[b].prec;
+    }
+    if (nb) *nb = std::min(cnt, (int)max_nb);
+  });
+}
+
 rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t* cuts, int32_t* blocks,
                                 int32_t* parts, int32_t* nb) {
   return guard([&] {
@@ -325,9 +379,10 @@ rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t*
     RF_REQUIRE(max_nb >= 0, "max_nb must be >= 0");
     const int cnt = kern->os_ready ? (int)kern->os_buckets.size() : 0;
     for (int b = 0; b < std::min(cnt, (int)max_nb); ++b) {
-      if (cuts) cuts[b] = kern->os_buckets[b].cut_lo;
-      if (blocks) blocks[b] = kern->os_buckets[b].B;
-      if (parts) parts[b] = kern->os_buckets[b].Lp;
+      const OsBucket& o = kern->os_buckets[b];
+      if (cuts) cuts[b] = o.cut_lo;
+      if (blocks) blocks[b] = o.algo == RF_ALGO_OS ? o.B : o.gemm_nj;
+      if (parts) parts[b] = o.algo == RF_ALGO_OS ? o.Lp : o.gemm_s;
     }
     if (nb) *nb = std::min(cnt, (int)max_nb);
   });
@@ -413,8 +468,7 @@ rf_status rf_kernels_gemm_layout(const rf_kernels* kern, int32_t* out) {
 rf_status rf_kernels_copy_taps(const rf_kernels* kern, void* dst, rf_stream stream) {
   return guard([&] {
     RF_REQUIRE(kern != nullptr, "kern is NULL");
-    const size_t esz = kern->dtype == RF_F64 ? sizeof(double2) : sizeof(float2);
-    const size_t bytes = (size_t)kern->offset[kern->k] * esz;
+    const size_t bytes = (size_t)kern->offset[kern->k] * tap_bytes(kern);
     if (!bytes) return;
     check_dev(dst, "dst");
     RF_CUDA(cudaMemcpyAsync(dst, kern->taps.p, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
@@ -552,6 +606,7 @@ rf_status rf_autotune(rf_ctx* ctx, int32_t G, const void* const* z_refs, rf_kern
     RF_REQUIRE((flags & ~RF_TUNE_ALLOW_SPLIT) == 0, "unknown flags %d", flags);
     for (int g = 0; g < G; ++g) {
       RF_REQUIRE(ks[g] != nullptr, "ks[%d] is NULL", g);
+      RF_REQUIRE(ks[g]->real == ks[0]->real, "the kernel sets of a batch are all complex or all real-form");
       RF_REQUIRE(ks[g]->n == ctx->n && ks[g]->dtype == ctx->g.dtype, "kernels were made for another grid");
       check_dev(z_refs[g], "z_refs[g]");
     }

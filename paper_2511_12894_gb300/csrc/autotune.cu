@@ -3,8 +3,9 @@
 // Lp; the cost model of reconstruct_os.cu ranks them and the best few are timed), two-bucket
 // overlap-save (short kernels with their own layout, the rest with the fastest single one), the
 // tensor-core form at the cheapest split precision that meets the FP32-equivalent accuracy
-// (bf16x6) when the kernels are short enough for it to compete, and the direct sum for short
-// kernels.  Each candidate runs the fused window-peak
+// (bf16x6) in both of its tile layouts when the kernels are short enough for it to compete,
+// mixed forms (the tensor-core form for the shortest kernels, the fastest overlap-save layout for
+// the rest, within one call), and the direct sum for short kernels.  Each candidate runs the fused window-peak
 // form once to warm up and then three times between CUDA events; the fastest wins and is
 // recorded in every kernel set, so that RF_ALGO_AUTO follows it.
 #include <algorithm>
@@ -23,10 +24,10 @@ struct Cand {
 };
 
 // layouts of least modelled cost for kernels of the given lengths
-std::vector<Cand> os_candidates_for(const rf_ctx* c, const std::vector<int>& all, int max_os) {
+std::vector<Cand> os_candidates_for(const rf_ctx* c, const std::vector<int>& all, int max_os, bool real) {
   std::vector<Cand> out;
   for (int B = 512; B <= 32768; B *= 2) {  // 32768: the CTA-pair layout (partitions B/2 or B/4)
-    if (B > c->n) continue;
+    if (B > c->n || (real && B == 32768)) continue;  // real-form sets: single-CTA blocks only
     for (int Q = 2; Q <= (B == 32768 ? 4 : 8); Q *= 2)
       out.push_back(Cand{RF_ALGO_OS, B, B / Q, RF_PREC_NATIVE, os_layout_cost(c, all, B, B / Q)});
   }
@@ -39,7 +40,7 @@ std::vector<Cand> os_candidates_for(const rf_ctx* c, const std::vector<int>& all
 std::vector<Cand> os_candidates(const rf_ctx* c, int G, rf_kernels* const* ks, int max_os) {
   std::vector<int> all;
   for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
-  return os_candidates_for(c, all, max_os);
+  return os_candidates_for(c, all, max_os, ks[0]->real);
 }
 
 }  // namespace
@@ -60,8 +61,11 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   if (f32 && c->n >= 512) cands = os_candidates(c, G, ks, std::max(1, max_os));
   // the tensor-core form costs 8 L flops per output times the split products, so it is timed
   // only for short kernels (mean length <= 4096 taps)
-  if ((flags & RF_TUNE_ALLOW_SPLIT) && max_len <= gemm_max_len() && c->n % 128 == 0 && mean_len <= 4096.0)
-    cands.push_back(Cand{RF_ALGO_GEMM, 0, 0, RF_PREC_BF16X6, 0.0});
+  // both tile layouts: 16-neighbour groups with stacked output tiles, and the widest groups
+  if ((flags & RF_TUNE_ALLOW_SPLIT) && max_len <= gemm_max_len() && c->n % 128 == 0 && mean_len <= 4096.0) {
+    cands.push_back(Cand{RF_ALGO_GEMM, 16, gemm_stacked_shifts(RF_PREC_BF16X6), RF_PREC_BF16X6, 0.0});
+    cands.push_back(Cand{RF_ALGO_GEMM, gemm_wide_nj(RF_PREC_BF16X6), 1, RF_PREC_BF16X6, 0.0});
+  }
   if (!f32 || max_len <= 1024) cands.push_back(Cand{RF_ALGO_DIRECT, 0, 0, RF_PREC_NATIVE, 0.0});
   RF_REQUIRE(!cands.empty(), "no reconstruction form to tune");
   const int64_t nw = (c->n + W - 1) / W;
@@ -72,7 +76,7 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   RF_CUDA(cudaEventCreate(&e0));
   RF_CUDA(cudaEventCreate(&e1));
   auto run = [&](const Cand& cd) {
-    if (cd.algo == RF_ALGO_OS && G > 1) {
+    if ((cd.algo == RF_ALGO_OS || cd.cut) && G > 1) {  // overlap-save or mixed buckets: batched
       reconstruct_batched(c, G, z_refs, ks, W, pk.as<float>(), ak.as<int32_t>(), s);
       return;
     }
@@ -82,7 +86,7 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
       if (k->k) {
         float* mo = pk.as<float>() + row * nw;
         int32_t* ao = ak.as<int32_t>() + row * nw;
-        if (cd.algo == RF_ALGO_OS) reconstruct_os(c, z_refs[g], k, nullptr, W, mo, ao, s);
+        if (cd.algo == RF_ALGO_OS || cd.cut) reconstruct_os(c, z_refs[g], k, nullptr, W, mo, ao, s);
         else if (cd.algo == RF_ALGO_GEMM) reconstruct_gemm(c, z_refs[g], k, cd.prec, nullptr, W, mo, ao, s);
         else reconstruct_direct(c, z_refs[g], k, nullptr, W, mo, ao, s);
       }
@@ -90,12 +94,17 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
     }
   };
   auto prepare = [&](const Cand& cd) {
-    if (cd.algo != RF_ALGO_OS) return;
-    if (!cd.cut) {
+    if (cd.cut) {  // two buckets: (algo, prec, block, part) below the cut, overlap-save above
+      const BucketSpec spec[2] = {BucketSpec{0, cd.algo, cd.prec, cd.block, cd.part},
+                                  BucketSpec{cd.cut, RF_ALGO_OS, RF_PREC_NATIVE, cd.block2, cd.part2}};
+      for (int g = 0; g < G; ++g) os_prepare_forms(c, ks[g], 2, spec, s);
+    } else if (cd.algo == RF_ALGO_OS) {
       for (int g = 0; g < G; ++g) os_prepare(c, ks[g], cd.block, cd.part, s);
-    } else {
-      const int32_t cuts[2] = {0, cd.cut}, Bs[2] = {cd.block, cd.block2}, Lps[2] = {cd.part, cd.part2};
-      for (int g = 0; g < G; ++g) os_prepare_buckets(c, ks[g], 2, cuts, Bs, Lps, s);
+    } else if (cd.algo == RF_ALGO_GEMM) {
+      for (int g = 0; g < G; ++g) {
+        ks[g]->gemm_pref_nj = cd.block;
+        ks[g]->gemm_pref_s = cd.part;
+      }
     }
   };
   auto time_cand = [&](const Cand& cd) {
@@ -133,13 +142,32 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
             else any_long = true;
           }
         if (shortL.empty() || !any_long) continue;
-        std::vector<Cand> sc = os_candidates_for(c, shortL, 2);
+        std::vector<Cand> sc = os_candidates_for(c, shortL, 2, ks[0]->real);
         for (Cand cd : sc) {
           if (cd.block == lead.block && cd.part == lead.part) continue;
           cd.cut = cut;
           cd.block2 = lead.block;
           cd.part2 = lead.part;
           extra.push_back(cd);
+        }
+      }
+      // mixed forms: the tensor-core form (bf16x6, the library's tile rule) for the shortest
+      // kernels (about an eighth of them, at most 4096 taps), the fastest layout above
+      if ((flags & RF_TUNE_ALLOW_SPLIT) && c->n % 128 == 0) {
+        std::vector<int> all;
+        for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
+        std::sort(all.begin(), all.end());
+        if (all.size() >= 8) {
+          int cut = 256;
+          while (cut < 4096 && cut <= all[all.size() / 8]) cut *= 2;
+          const bool some_short = all.front() < cut, some_long = all.back() >= cut;
+          if (some_short && some_long) {
+            Cand cd{RF_ALGO_GEMM, 0, 0, RF_PREC_BF16X6, 0.0};
+            cd.cut = cut;
+            cd.block2 = lead.block;
+            cd.part2 = lead.part;
+            extra.push_back(cd);
+          }
         }
       }
       for (const Cand& cd : extra) {
@@ -156,8 +184,9 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   const Cand& w = cands[win];
   prepare(w);
   for (int g = 0; g < G; ++g) {
-    ks[g]->tuned_algo = w.algo;
-    ks[g]->tuned_prec = w.prec;
+    // bucketed preparations (overlap-save or mixed) run through the overlap-save entry
+    ks[g]->tuned_algo = w.cut ? RF_ALGO_OS : w.algo;
+    ks[g]->tuned_prec = w.cut ? RF_PREC_NATIVE : w.prec;
   }
   RF_CUDA(cudaStreamSynchronize(s));
   // the winner first, then the others in the order they were timed

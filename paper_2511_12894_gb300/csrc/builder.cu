@@ -226,19 +226,33 @@ __global__ void __launch_bounds__(256) k_pack(const double2* __restrict__ rho, i
   }
 }
 
+// Real-kernel form: the real parts only (the imaginary parts are zero after k_real_form).
+template <typename R>
+__global__ void __launch_bounds__(256) k_pack_real(const double2* __restrict__ rho, int64_t n,
+                                                   const int* __restrict__ m0, const int* __restrict__ len,
+                                                   const int64_t* __restrict__ off, R* __restrict__ taps) {
+  const int j = blockIdx.y;
+  const int L = len[j];
+  const int64_t mask = n - 1;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (int64_t)gridDim.x * blockDim.x)
+    taps[off[j] + l] = (R)rho[(int64_t)j * n + ((m0[j] + l) & mask)].x;
+}
+
 }  // namespace
 
 rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbrs, int32_t k, const double* inv_psd,
                        double thr, int relative, int64_t n_build, cudaStream_t s) {
   const int64_t n = c->n;
   const bool f64 = c->g.dtype == RF_F64;
-  const size_t esz = f64 ? sizeof(double2) : sizeof(float2);
+  const bool real_form = (relative & RF_KERNEL_REAL) != 0;
 
   std::unique_ptr<rf_kernels> owner(new rf_kernels());
   rf_kernels* kern = owner.get();
   kern->k = k;
   kern->n = n;
+  kern->real = real_form;
   kern->dtype = c->g.dtype;
+  const size_t esz = tap_bytes(kern);
   kern->len.assign(k, 0);
   kern->lag0.assign(k, 0);
   kern->offset.assign((size_t)k + 1, 0);
@@ -383,7 +397,11 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
     offd.ensure(sizeof(int64_t) * (cnt + 1));
     RF_CUDA(cudaMemcpyAsync(offd.p, off.data(), sizeof(int64_t) * (cnt + 1), cudaMemcpyHostToDevice, s));
     dim3 g2(64, (unsigned)cnt);
-    if (f64)
+    if (real_form && f64)
+      k_pack_real<double><<<g2, 256, 0, s>>>(bufR, nb, d_m0, d_len, offd.as<int64_t>(), part->as<double>());
+    else if (real_form)
+      k_pack_real<float><<<g2, 256, 0, s>>>(bufR, nb, d_m0, d_len, offd.as<int64_t>(), part->as<float>());
+    else if (f64)
       k_pack<double2><<<g2, 256, 0, s>>>(bufR, nb, d_m0, d_len, offd.as<int64_t>(), part->as<double2>());
     else
       k_pack<float2><<<g2, 256, 0, s>>>(bufR, nb, d_m0, d_len, offd.as<int64_t>(), part->as<float2>());
@@ -427,14 +445,14 @@ rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbr
   return owner.release();
 }
 
-rf_kernels* import_impl(rf_ctx* c, int32_t k, const int32_t* lag0, const int32_t* len, const void* taps) {
-  const bool f64 = c->g.dtype == RF_F64;
-  const size_t esz = f64 ? sizeof(double2) : sizeof(float2);
+rf_kernels* import_impl(rf_ctx* c, int32_t k, const int32_t* lag0, const int32_t* len, const void* taps, bool real) {
   std::unique_ptr<rf_kernels> owner(new rf_kernels());
   rf_kernels* kern = owner.get();
   kern->k = k;
   kern->n = c->n;
   kern->dtype = c->g.dtype;
+  kern->real = real;
+  const size_t esz = tap_bytes(kern);
   kern->grid.assign(k, c->n);
   kern->len.assign(len, len + k);
   kern->lag0.assign(lag0, lag0 + k);

@@ -8,8 +8,10 @@
 // E entries so that the per-thread stride of E is bank-conflict free).  Each
 // thread owns E consecutive outputs and keeps the E strip values it needs in
 // registers, sliding them by one sample per tap: one shared load and one
-// broadcast tap load per E complex multiply-adds.
+// broadcast tap load per E complex multiply-adds.  Real-form kernels (real taps T = R) take
+// complex x real products: two multiply-adds per tap and output instead of four.
 #include <cfloat>
+#include <type_traits>
 
 #include "cplx.cuh"
 #include "rf_internal.h"
@@ -56,26 +58,27 @@ __device__ Best<R> block_best(R v, long long i) {
   return b;
 }
 
-template <typename V, int E, int NT, int LC, bool WINMAX>
-__global__ void __launch_bounds__(NT) k_direct(const V* __restrict__ z_ref, int64_t n, const V* __restrict__ taps,
+template <typename V, typename T, int E, int NT, int LC, bool WINMAX>
+__global__ void __launch_bounds__(NT) k_direct(const V* __restrict__ z_ref, int64_t n, const T* __restrict__ taps,
                                                const int64_t* __restrict__ off, const int* __restrict__ len,
                                                const int* __restrict__ lag0, int64_t range, V* __restrict__ z_out,
                                                int64_t W, int64_t nw, float* __restrict__ max_out,
                                                int* __restrict__ arg_out) {
   using R = typename real_of<V>::type;
+  constexpr bool REAL = std::is_same<T, R>::value;
   constexpr int TILE = NT * E;
   constexpr int SPAN = TILE + LC;               // strip entries (last one unused)
   constexpr int PAD = SPAN + SPAN / E + 1;       // padded strip size
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* strip = reinterpret_cast<V*>(smem_raw);
-  V* tp = strip + PAD;
+  T* tp = reinterpret_cast<T*>(strip + PAD);
   R* mag = reinterpret_cast<R*>(tp + LC);
   Best<R>* run = reinterpret_cast<Best<R>*>(mag + TILE);  // running best per window of the range
 
   const int j = blockIdx.y;
   const int L = len[j];
   const int64_t m0 = lag0[j];
-  const V* c = taps + off[j];
+  const T* c = taps + off[j];
   const int64_t mask = n - 1;
   const int64_t r0 = (int64_t)blockIdx.x * range;
   const int64_t r1 = min(n, r0 + range);
@@ -96,7 +99,10 @@ __global__ void __launch_bounds__(NT) k_direct(const V* __restrict__ z_ref, int6
       // strip[p] = z_ref[(c0 - m0 - l0 - LC + 1 + p) mod n]
       const int64_t base = c0 - m0 - l0 - LC + 1;
       for (int p = tid; p < SPAN - 1; p += NT) strip[p + p / E] = z_ref[(base + p) & mask];
-      for (int r = tid; r < LC; r += NT) tp[r] = (r < lc) ? c[l0 + r] : cmake<V>((R)0, (R)0);
+      for (int r = tid; r < LC; r += NT) {
+        if constexpr (REAL) tp[r] = (r < lc) ? c[l0 + r] : (R)0;
+        else tp[r] = (r < lc) ? c[l0 + r] : cmake<V>((R)0, (R)0);
+      }
       __syncthreads();
       const int p0 = tid * E + LC - 1;
       V win[E], part[E];
@@ -107,13 +113,18 @@ __global__ void __launch_bounds__(NT) k_direct(const V* __restrict__ z_ref, int6
       }
 #pragma unroll 2
       for (int r = 0; r < LC; ++r) {
-        const V cr = tp[r];
+        const T cr = tp[r];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          part[e].x = fma(cr.x, win[e].x, part[e].x);
-          part[e].x = fma(-cr.y, win[e].y, part[e].x);
-          part[e].y = fma(cr.x, win[e].y, part[e].y);
-          part[e].y = fma(cr.y, win[e].x, part[e].y);
+          if constexpr (REAL) {
+            part[e].x = fma(cr, win[e].x, part[e].x);
+            part[e].y = fma(cr, win[e].y, part[e].y);
+          } else {
+            part[e].x = fma(cr.x, win[e].x, part[e].x);
+            part[e].x = fma(-cr.y, win[e].y, part[e].x);
+            part[e].y = fma(cr.x, win[e].y, part[e].y);
+            part[e].y = fma(cr.y, win[e].x, part[e].y);
+          }
         }
 #pragma unroll
         for (int e = E - 1; e > 0; --e) win[e] = win[e - 1];
@@ -168,7 +179,7 @@ __global__ void __launch_bounds__(NT) k_direct(const V* __restrict__ z_ref, int6
   }
 }
 
-template <typename V, int E, int NT, int LC, bool WINMAX>
+template <typename V, typename T, int E, int NT, int LC, bool WINMAX>
 void launch_direct(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, int64_t W, float* max_out,
                    int32_t* arg_out, cudaStream_t s) {
   using R = typename real_of<V>::type;
@@ -185,11 +196,11 @@ void launch_direct(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, 
     range = TILE;
   }
   const int64_t nblk = (n + range - 1) / range;
-  const size_t smem = sizeof(V) * (PAD + LC) + sizeof(R) * TILE + sizeof(Best<R>) * (size_t)(wpc + 2) + 16;
+  const size_t smem = sizeof(V) * PAD + sizeof(T) * LC + sizeof(R) * TILE + sizeof(Best<R>) * (size_t)(wpc + 2) + 16;
   constexpr size_t smem_cap = 200 * 1024;
   RF_REQUIRE(smem <= smem_cap, "direct reconstruct: window of %lld samples needs too much shared memory",
              (long long)W);
-  auto kfn = k_direct<V, E, NT, LC, WINMAX>;
+  auto kfn = k_direct<V, T, E, NT, LC, WINMAX>;
   // a process-wide attribute of the function: set to the cap that bounds every launch, so that a
   // context on another host thread never lowers it under this launch
   RF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
@@ -197,7 +208,7 @@ void launch_direct(rf_ctx* c, const rf_kernels* kern, const V* z_ref, V* z_out, 
   while (done < kern->k) {
     const int cnt = (int)std::min<int64_t>(65535, kern->k - done);
     dim3 grid((unsigned)nblk, (unsigned)cnt);
-    kfn<<<grid, NT, smem, s>>>(z_ref, n, static_cast<const V*>(kern->taps.p), kern->off_d.as<int64_t>() + done,
+    kfn<<<grid, NT, smem, s>>>(z_ref, n, static_cast<const T*>(kern->taps.p), kern->off_d.as<int64_t>() + done,
                                kern->len_d.as<int>() + done, kern->lag0_d.as<int>() + done, range,
                                z_out ? z_out + done * n : nullptr, W, nw, max_out ? max_out + done * nw : nullptr,
                                arg_out ? arg_out + done * nw : nullptr);
@@ -238,16 +249,23 @@ void reconstruct_direct(rf_ctx* c, const void* z_ref, const rf_kernels* kern, vo
                         float* max_out, int32_t* argmax_out, cudaStream_t s) {
   if (kern->k == 0) return;
   const bool win = max_out != nullptr;
+  auto run = [&](auto vtag, auto ttag, auto etag) {
+    using V = decltype(vtag);
+    using T = decltype(ttag);
+    constexpr int E = decltype(etag)::value;
+    auto zr = static_cast<const V*>(z_ref);
+    auto zo = static_cast<V*>(z_out);
+    if (win) launch_direct<V, T, E, 256, 256, true>(c, kern, zr, nullptr, W, max_out, argmax_out, s);
+    else launch_direct<V, T, E, 256, 256, false>(c, kern, zr, zo, W, nullptr, nullptr, s);
+  };
+  using E4 = std::integral_constant<int, 4>;
+  using E8 = std::integral_constant<int, 8>;
   if (c->g.dtype == RF_F64) {
-    auto zr = static_cast<const double2*>(z_ref);
-    auto zo = static_cast<double2*>(z_out);
-    if (win) launch_direct<double2, 4, 256, 256, true>(c, kern, zr, nullptr, W, max_out, argmax_out, s);
-    else launch_direct<double2, 4, 256, 256, false>(c, kern, zr, zo, W, nullptr, nullptr, s);
+    if (kern->real) run(double2{}, double{}, E4{});
+    else run(double2{}, double2{}, E4{});
   } else {
-    auto zr = static_cast<const float2*>(z_ref);
-    auto zo = static_cast<float2*>(z_out);
-    if (win) launch_direct<float2, 8, 256, 256, true>(c, kern, zr, nullptr, W, max_out, argmax_out, s);
-    else launch_direct<float2, 8, 256, 256, false>(c, kern, zr, zo, W, nullptr, nullptr, s);
+    if (kern->real) run(float2{}, float{}, E8{});
+    else run(float2{}, float2{}, E8{});
   }
 }
 

@@ -110,9 +110,9 @@ __host__ __device__ constexpr int prec_terms(int prec) {
 // shift s, holding tap l = LP - 1 - t + 128 s (zero outside the kernel); plane r holds
 // (cr, ci), plane i holds (-ci, cr).
 template <typename V>
-__global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restrict__ off, const int* __restrict__ len,
-                              int k, int NJ, int S, int KC, int NCK, int LP, int terms, bool tf32,
-                              void* __restrict__ out_v) {
+__global__ void k_gemm_prep_b(const void* __restrict__ taps_v, bool real_taps, const int64_t* __restrict__ off,
+                              const int* __restrict__ len, int k, int NJ, int S, int KC, int NCK, int LP, int terms,
+                              bool tf32, void* __restrict__ out_v) {
   using R = typename real_of<V>::type;
   const int g = blockIdx.y;
   const int NC = S * 2 * NJ;
@@ -128,9 +128,13 @@ __global__ void k_gemm_prep_b(const V* __restrict__ taps, const int64_t* __restr
     if (j < k) {
       const int l = LP - 1 - t + kGemmM * sh;
       if (l >= 0 && l < len[j]) {
-        const V v = taps[off[j] + l];
-        cr = v.x;
-        ci = v.y;
+        if (real_taps) {  // real-form set: real taps, imaginary parts zero
+          cr = static_cast<const R*>(taps_v)[off[j] + l];
+        } else {
+          const V v = static_cast<const V*>(taps_v)[off[j] + l];
+          cr = v.x;
+          ci = v.y;
+        }
       }
     }
     const R vr = (col & 1) ? ci : cr;
@@ -724,6 +728,33 @@ size_t gemm_zplanes_bytes(int64_t n, int64_t LP, int prec) {
 
 int gemm_max_len() { return 1 << 16; }
 
+// The two tile layouts of a precision: (16 neighbours, the widest output-shift stack) and (the
+// widest group, no shifts); (0, 0) leaves the choice to the rule of gemm_prepare.
+bool gemm_layout_ok(int prec, int nj, int s) {
+  if (nj == 0 && s == 0) return true;
+  int smax = 1;
+  switch (prec) {
+    case RF_PREC_BF16: smax = gemm_shifts_max(RF_PREC_BF16, 16); break;
+    case RF_PREC_BF16X3: smax = gemm_shifts_max(RF_PREC_BF16X3, 16); break;
+    case RF_PREC_BF16X6: smax = gemm_shifts_max(RF_PREC_BF16X6, 16); break;
+    case RF_PREC_3XTF32: smax = gemm_shifts_max(RF_PREC_3XTF32, 16); break;
+    default: smax = gemm_shifts_max(RF_PREC_BF16X9, 16); break;
+  }
+  return (nj == 16 && s == smax && smax > 1) || (nj == gemm_nj_max(prec) && s == 1);
+}
+
+int gemm_stacked_shifts(int prec) {
+  switch (prec) {
+    case RF_PREC_BF16: return gemm_shifts_max(RF_PREC_BF16, 16);
+    case RF_PREC_BF16X3: return gemm_shifts_max(RF_PREC_BF16X3, 16);
+    case RF_PREC_BF16X6: return gemm_shifts_max(RF_PREC_BF16X6, 16);
+    case RF_PREC_3XTF32: return gemm_shifts_max(RF_PREC_3XTF32, 16);
+    default: return gemm_shifts_max(RF_PREC_BF16X9, 16);
+  }
+}
+
+int gemm_wide_nj(int prec) { return gemm_nj_max(prec); }
+
 void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
   const int terms = prec_terms(prec);
   const bool tf32 = prec_tf32(prec);
@@ -736,7 +767,9 @@ void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
   const int L16 = std::max(16, (kern->max_len + 15) / 16 * 16);
   int KC = 16;
   while (KC < 128 && KC < L16) KC *= 2;
-  const bool stack = kern->k <= 16 && L16 > kGemmM;
+  // a requested layout (the autotuner times both) replaces the rule
+  const bool stack = kern->gemm_pref_nj ? kern->gemm_pref_nj == 16 && kern->gemm_pref_s > 1
+                                        : kern->k <= 16 && L16 > kGemmM;
   const int NJ = stack ? 16 : gemm_nj_max(prec);
   int S = 1;
   if (stack) {
@@ -765,11 +798,11 @@ void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s) {
   kern->gemm_B.ensure((size_t)prec_ebytes(prec) * std::max<size_t>(elems, 8));
   dim3 grid((unsigned)std::max<int64_t>(1, ((int64_t)NC * KC * NCK + 255) / 256), (unsigned)groups);
   if (kern->dtype == RF_F64)
-    k_gemm_prep_b<double2><<<grid, 256, 0, s>>>(kern->taps.as<double2>(), kern->off_d.as<int64_t>(),
+    k_gemm_prep_b<double2><<<grid, 256, 0, s>>>(kern->taps.p, kern->real, kern->off_d.as<int64_t>(),
                                                 kern->len_d.as<int>(), kern->k, NJ, S, KC, NCK, LP, terms, tf32,
                                                 kern->gemm_B.as<unsigned char>());
   else
-    k_gemm_prep_b<float2><<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(),
+    k_gemm_prep_b<float2><<<grid, 256, 0, s>>>(kern->taps.p, kern->real, kern->off_d.as<int64_t>(),
                                                kern->len_d.as<int>(), kern->k, NJ, S, KC, NCK, LP, terms, tf32,
                                                kern->gemm_B.as<unsigned char>());
   RF_LAUNCHED();

@@ -12,7 +12,9 @@
 // which is w_j[i'] = sum_l c_j[l] z_ref[(i' - l) mod n] (the circular product of a B-point
 // segment with a partition of Lp taps is free of wrap-around from t = Lp - 1 on), and
 // z_j[i] = w_j[(i - m0_j) mod n]: the first lag is applied by relabelling outputs, so every
-// neighbour shares Zs.  Q = 2 is the classic half-overlap form; larger Q keeps more outputs
+// neighbour shares Zs.  Real-form kernels have Hermitian partition spectra (C[B - k] =
+// conj C[k]); their sets keep bins 0..B/2 only, in rows of B/2 + 8, and the product reads a
+// bin above B/2 as the conjugate of its mirror (`herm`).  Q = 2 is the classic half-overlap form; larger Q keeps more outputs
 // per block transform at the price of more (cheap) partition products.
 // The window peaks are reduced per warp and merged across blocks with 64-bit
 // atomicMax on (float bits of |z|^2) << 32 | (2^32 - 1 - i), which orders by value
@@ -30,6 +32,17 @@ namespace {
 
 __device__ __forceinline__ unsigned long long pack_key(float v, unsigned int i) {
   return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - i);
+}
+
+// Largest packed key of the warp: the largest high word (value bits), then the largest low
+// word among the lanes holding it (the smallest index), two 32-bit warp reductions in place of
+// a 64-bit shuffle tree.  Key 0 (no output) never wins against a real key, whose low word is
+// at least 2^31.
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k) {
+  const unsigned hi = (unsigned)(k >> 32);
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? (unsigned)k : 0u);
+  return ((unsigned long long)mh << 32) | ml;
 }
 
 template <int B>
@@ -138,11 +151,8 @@ __device__ __forceinline__ void window_keys(const float (&mv)[CH], int cnt, int 
       }
     }
   } else {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      kA = max(kA, __shfl_xor_sync(0xffffffffu, kA, o));
-      kB = max(kB, __shfl_xor_sync(0xffffffffu, kB, o));
-    }
+    kA = warp_max_key(kA);
+    kB = warp_max_key(kB);
     if (lane == 0) {
       if (kA) atomicMax(kj + wA, kA);
       if (kB) atomicMax(kj + wB, kB);
@@ -152,11 +162,14 @@ __device__ __forceinline__ void window_keys(const float (&mv)[CH], int cnt, int 
 
 // One neighbour's output blocks [s0, s1): spectral products, inverse block FFT, then either
 // the series (zrow != nullptr) or the window peaks (keys row kj).
+// Row stride of a partition spectrum: B bins, or the Hermitian half (bins 0..B/2, padded).
+__host__ __device__ constexpr int os_row(int B, bool herm) { return herm ? B / 2 + 8 : B; }
+
 template <int B, int Q, bool WINMAX>
 __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const float2* __restrict__ C, int P,
                                           int64_t m0, const float2* __restrict__ tw, int64_t n, int NQ, int s0,
                                           int s1, float2* __restrict__ zrow, unsigned long long* __restrict__ kj,
-                                          int64_t W, int64_t nw, int fastwin, float2* sm) {
+                                          int64_t W, int64_t nw, int fastwin, int herm, float2* sm) {
   using S = BlockFFTShape<B>;
   constexpr int NT = S::NT;
   constexpr int LP = B / Q;   // partition length: outputs start at block position LP
@@ -166,6 +179,12 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
   static_assert(Q == 2 || Q == 4 || Q == 8, "partition ratio");
   const int tid = threadIdx.x;
   const int64_t mask = n - 1;
+  // partition spectrum loads: bins tid + t B/16; with the Hermitian half, the upper eight
+  // (t >= 8, above B/2) come from the mirrors B/2 - tid - (t - 8) B/16, conjugated
+  const int crow = os_row(B, herm != 0);
+  const int hi_base = herm ? B / 2 - tid : B / 2 + tid;
+  const int hi_step = herm ? -(B / 16) : B / 16;
+  const float csgn = herm ? -1.f : 1.f;
   for (int s = s0; s < s1; ++s) {
     float2 v[16];
 #pragma unroll
@@ -177,14 +196,18 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
     for (int p = 0; p < P; ++p, --sp) {
       const int q = sp + ((sp < 0) ? NQ : 0);  // sp >= -NQ because P <= NQ
       const float2* zp = Zs + (int64_t)q * B + tid;
-      const float2* cp = C + (int64_t)p * B + tid;
+      const float2* cb = C + (int64_t)p * crow;
 #pragma unroll
       for (int h = 0; h < 16; h += 8) {
         float2 z[8], c[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           z[t] = __ldcg(zp + (h + t) * (B / 16));
-          c[t] = __ldcg(cp + (h + t) * (B / 16));
+          c[t] = h == 0 ? __ldcg(cb + tid + t * (B / 16)) : __ldcg(cb + hi_base + t * hi_step);
+        }
+        if (h != 0) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) c[t].y *= csgn;
         }
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -248,14 +271,14 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restri
                                               const float2* __restrict__ tw, int64_t n,
                                               int NQ, int NB, int SC, float2* __restrict__ z_out,
                                               unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
-                                              int fastwin) {
+                                              int fastwin, int herm) {
   extern __shared__ float2 sm[];
   const int j = idx[y0 + blockIdx.y];
   const int s0 = blockIdx.x * SC;
   const int s1 = min(NB, s0 + SC);
   os_blocks<B, Q, WINMAX>(Zs, Cs + spec_off[j], parts[j], lag0[j], tw, n, NQ, s0, s1,
                        WINMAX ? nullptr : z_out + (int64_t)j * n, WINMAX ? keys + (int64_t)j * nw : nullptr, W, nw,
-                       fastwin, sm);
+                       fastwin, herm, sm);
 }
 
 // Batched form: neighbours of several references in one persistent launch.  Each item
@@ -280,7 +303,7 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* 
                                                                  int nchunk, const float2* __restrict__ tw, int64_t n,
                                                                  int NQ, int NB, int SC,
                                                                  unsigned long long* __restrict__ keys,
-                                                                 int64_t W, int64_t nw, int fastwin,
+                                                                 int64_t W, int64_t nw, int fastwin, int herm,
                                                                  unsigned long long* __restrict__ counter) {
   extern __shared__ float2 sm[];
   __shared__ long long s_unit;
@@ -295,7 +318,7 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* 
     const int s0 = (int)(code % nchunk) * SC;
     const int s1 = min(NB, s0 + SC);
     os_blocks<B, Q, true>(it.Zs, it.C, it.P, it.lag0, tw, n, NQ, s0, s1, nullptr, keys + it.row * nw, W, nw, fastwin,
-                          sm);
+                          herm, sm);
   }
 }
 
@@ -309,7 +332,8 @@ __global__ void k_unpack_keys(const unsigned long long* __restrict__ keys, int64
 }
 
 // rows[g][u] = taps of partition (j, p) = g, promoted to FP64, zero from u = Lp or l = L_j on
-__global__ void k_os_fill(const float2* __restrict__ taps, const int64_t* __restrict__ off,
+// (taps: float2, or float for a real-form set)
+__global__ void k_os_fill(const void* __restrict__ taps, int real, const int64_t* __restrict__ off,
                           const int* __restrict__ len, const int* __restrict__ gj, const int* __restrict__ gp,
                           int B, int Lp, double2* __restrict__ rows) {
   const int g = blockIdx.y;
@@ -318,8 +342,12 @@ __global__ void k_os_fill(const float2* __restrict__ taps, const int64_t* __rest
     double2 v = make_double2(0.0, 0.0);
     const int64_t l = (int64_t)p * Lp + u;
     if (u < Lp && l < len[j]) {
-      const float2 c = taps[off[j] + l];
-      v = make_double2((double)c.x, (double)c.y);
+      if (real) {
+        v = make_double2((double)static_cast<const float*>(taps)[off[j] + l], 0.0);
+      } else {
+        const float2 c = static_cast<const float2*>(taps)[off[j] + l];
+        v = make_double2((double)c.x, (double)c.y);
+      }
     }
     rows[(int64_t)g * B + u] = v;
   }
@@ -328,6 +356,24 @@ __global__ void k_os_fill(const float2* __restrict__ taps, const int64_t* __rest
 __global__ void k_os_round(const double2* __restrict__ spec, int64_t count, double scale, float2* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) out[i] = make_float2((float)(spec[i].x * scale), (float)(spec[i].y * scale));
+}
+
+// Hermitian half of `rows` B-point spectra of real partitions: bins 0..B/2 into rows of
+// B/2 + 8 (the pad zero); bins 0 and B/2 are real, so their imaginary rounding noise is dropped.
+__global__ void k_os_round_half(const double2* __restrict__ spec, int rows, int B, double scale,
+                                float2* __restrict__ out) {
+  const int rs = B / 2 + 8;
+  const int64_t count = (int64_t)rows * rs;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t g = i / rs;
+  const int k = (int)(i - g * rs);
+  float2 v = make_float2(0.f, 0.f);
+  if (k <= B / 2) {
+    const double2 c = spec[g * B + k];
+    v = make_float2((float)(c.x * scale), (k == 0 || k == B / 2) ? 0.f : (float)(c.y * scale));
+  }
+  out[i] = v;
 }
 
 // ------------------------------------------------------- 32768-point blocks on CTA pairs
@@ -581,7 +627,7 @@ void launch_os(rf_ctx* c, const rf_kernels* kern, const OsBucket& bk, const floa
     dim3 grid((unsigned)nchunk, (unsigned)cnt);
     fn<<<grid, B / 16, os_smem<B>(), s>>>(Zs, kern->os_spec.as<float2>(), kern->os_off_d.as<int64_t>(),
                                           kern->os_parts_d.as<int>(), kern->lag0_d.as<int>(), bk.idx_d.as<int>(), done,
-                                          tw, c->n, NQ, NB, SC, z_out, keys, W, nw, fastwin);
+                                          tw, c->n, NQ, NB, SC, z_out, keys, W, nw, fastwin, kern->real ? 1 : 0);
     RF_LAUNCHED();
   }
 }
@@ -730,11 +776,12 @@ double os_layout_cost(const rf_ctx* c, const std::vector<int>& lengths, int B, i
   return blocks < slots ? cost * slots / blocks : cost;
 }
 
-void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, int* B_out, int* Lp_out) {
+void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, bool real, int* B_out,
+                      int* Lp_out) {
   double best = 0.0;
   int bB = 0, bL = 0;
   for (int B = 512; B <= kB2; B *= 2) {
-    if (B > c->n || (block && B != block)) continue;
+    if (B > c->n || (block && B != block) || (real && B == kB2)) continue;
     for (int Q = 2; Q <= (B == kB2 ? 4 : 8); Q *= 2) {
       const double cost = os_layout_cost(c, lengths, B, B / Q);
       if (!bB || cost < best) {
@@ -749,54 +796,182 @@ void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int bloc
   *Lp_out = bL;
 }
 
-static void check_layout(const rf_ctx* c, int B, int Lp) {
+static void check_layout(const rf_ctx* c, int B, int Lp, bool real) {
   RF_REQUIRE(B >= 512 && B <= kB2 && (B & (B - 1)) == 0 && B <= c->n, "overlap-save block %d invalid for n=%lld", B,
              (long long)c->n);
+  RF_REQUIRE(!real || B < kB2, "real-form kernels take overlap-save blocks of at most %d points", kB2 / 2);
   RF_REQUIRE(Lp == B / 2 || Lp == B / 4 || (Lp == B / 8 && B < kB2),
              "overlap-save partition length %d must be B/2, B/4 or (below 32768) B/8", Lp);
 }
 
+// ---------------------------------------------------------------- buckets of other forms
+
+// Kernel set of the neighbours idx of `kern` (taps copied), for a bucket that runs the direct
+// or tensor-core form.
+std::shared_ptr<rf_kernels> make_subset(const rf_kernels* kern, const std::vector<int32_t>& idx, cudaStream_t s) {
+  std::shared_ptr<rf_kernels> sub(new rf_kernels());
+  const int k = (int)idx.size();
+  sub->k = k;
+  sub->n = kern->n;
+  sub->dtype = kern->dtype;
+  sub->real = kern->real;
+  sub->offset.assign((size_t)k + 1, 0);
+  for (int q = 0; q < k; ++q) {
+    const int j = idx[q];
+    sub->len.push_back(kern->len[j]);
+    sub->lag0.push_back(kern->lag0[j]);
+    sub->df_low.push_back(kern->df_low[j]);
+    sub->grid.push_back(kern->grid[j]);
+    sub->offset[q + 1] = sub->offset[q] + kern->len[j];
+  }
+  sub->max_len = k ? *std::max_element(sub->len.begin(), sub->len.end()) : 0;
+  const size_t esz = tap_bytes(kern);
+  sub->taps.ensure(std::max<size_t>(16, (size_t)sub->offset[k] * esz));
+  for (int q = 0; q < k; ++q)
+    if (sub->len[q])
+      RF_CUDA(cudaMemcpyAsync(static_cast<char*>(sub->taps.p) + sub->offset[q] * esz,
+                              static_cast<const char*>(kern->taps.p) + kern->offset[idx[q]] * esz,
+                              (size_t)sub->len[q] * esz, cudaMemcpyDeviceToDevice, s));
+  sub->len_d.ensure(std::max<size_t>(16, sizeof(int32_t) * k));
+  sub->lag0_d.ensure(std::max<size_t>(16, sizeof(int32_t) * k));
+  sub->off_d.ensure(sizeof(int64_t) * (k + 1));
+  if (k) {
+    RF_CUDA(cudaMemcpyAsync(sub->len_d.p, sub->len.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+    RF_CUDA(cudaMemcpyAsync(sub->lag0_d.p, sub->lag0.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+  }
+  RF_CUDA(cudaMemcpyAsync(sub->off_d.p, sub->offset.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, s));
+  RF_CUDA(cudaStreamSynchronize(s));  // the host vectors are read by the copies above
+  return sub;
+}
+
+__global__ void k_scatter_peaks(const float* __restrict__ P, const int* __restrict__ A, int rows, int64_t nw,
+                                const int* __restrict__ idx, int64_t row0, float* __restrict__ max_out,
+                                int* __restrict__ arg_out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)rows * nw) return;
+  const int64_t r = i / nw, w = i - r * nw;
+  const int64_t d = (row0 + idx[r]) * nw + w;
+  max_out[d] = P[i];
+  arg_out[d] = A[i];
+}
+
+template <typename V>
+__global__ void k_scatter_series(const V* __restrict__ src, int rows, int64_t n, const int* __restrict__ idx,
+                                 V* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)rows * n) return;
+  const int64_t r = i / n, t = i - r * n;
+  dst[(int64_t)idx[r] * n + t] = src[i];
+}
+
+// Rows of a direct or tensor-core bucket: its subset runs into a temporary, whose rows go to
+// rows row0 + idx of the window peaks (or of the series z_out).
+void run_bucket_form(rf_ctx* c, const void* z_ref, const OsBucket& bk, int64_t W, float* max_out,
+                     int32_t* argmax_out, void* z_out, int64_t row0, cudaStream_t s) {
+  rf_kernels* sub = bk.sub.get();
+  const int rows = sub ? sub->k : 0;
+  if (!rows) return;
+  const int64_t n = c->n;
+  if (max_out) {
+    const int64_t nw = (n + W - 1) / W;
+    c->mix_tmp.ensure((sizeof(float) + sizeof(int32_t)) * (size_t)rows * nw + 256);
+    float* P = c->mix_tmp.as<float>();
+    int32_t* A = reinterpret_cast<int32_t*>(P + (int64_t)rows * nw);
+    if (bk.algo == RF_ALGO_GEMM) reconstruct_gemm(c, z_ref, sub, bk.prec, nullptr, W, P, A, s);
+    else reconstruct_direct(c, z_ref, sub, nullptr, W, P, A, s);
+    const int64_t count = (int64_t)rows * nw;
+    k_scatter_peaks<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(P, A, rows, nw, bk.idx_d.as<int>(), row0,
+                                                                     max_out, argmax_out);
+    RF_LAUNCHED();
+  } else {
+    c->mix_tmp.ensure(sizeof(float2) * (size_t)rows * n + 256);
+    float2* zt = c->mix_tmp.as<float2>();
+    if (bk.algo == RF_ALGO_GEMM) reconstruct_gemm(c, z_ref, sub, bk.prec, zt, 0, nullptr, nullptr, s);
+    else reconstruct_direct(c, z_ref, sub, zt, 0, nullptr, nullptr, s);
+    const int64_t count = (int64_t)rows * n;
+    k_scatter_series<float2><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(
+        zt, rows, n, bk.idx_d.as<int>(), static_cast<float2*>(z_out) + row0 * n);
+    RF_LAUNCHED();
+  }
+}
+
 void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts, const int32_t* Bs,
                         const int32_t* Lps, cudaStream_t s) {
+  RF_REQUIRE(nb >= 1 && nb <= 8, "between 1 and 8 layout buckets");
+  std::vector<BucketSpec> spec(nb);
+  for (int b = 0; b < nb; ++b) spec[b] = BucketSpec{cuts[b], RF_ALGO_OS, RF_PREC_NATIVE, Bs[b], Lps[b]};
+  os_prepare_forms(c, kern, nb, spec.data(), s);
+}
+
+void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spec, cudaStream_t s) {
   RF_REQUIRE(kern->dtype == RF_F32, "overlap-save needs the FP32 grid");
   RF_REQUIRE(nb >= 1 && nb <= 8, "between 1 and 8 layout buckets");
-  RF_REQUIRE(cuts[0] == 0, "the first bucket starts at length 0");
+  RF_REQUIRE(spec[0].cut == 0, "the first bucket starts at length 0");
   for (int b = 0; b < nb; ++b) {
-    check_layout(c, Bs[b], Lps[b]);
-    RF_REQUIRE(b == 0 || cuts[b] > cuts[b - 1], "bucket cuts must increase");
+    const BucketSpec& o = spec[b];
+    RF_REQUIRE(b == 0 || o.cut > spec[b - 1].cut, "bucket cuts must increase");
+    if (o.algo == RF_ALGO_OS) {
+      check_layout(c, o.block, o.part, kern->real);
+    } else if (o.algo == RF_ALGO_GEMM) {
+      RF_REQUIRE(o.prec >= RF_PREC_BF16 && o.prec <= RF_PREC_3XTF32, "a tensor-core bucket needs a split precision");
+      RF_REQUIRE(c->n % 128 == 0, "the tensor-core form needs n to be a multiple of 128");
+      RF_REQUIRE(gemm_layout_ok(o.prec, o.block, o.part),
+                 "tensor-core layout (%d neighbours, %d tiles) is not one of (16, %d), (%d, 1), (0, 0)", o.block,
+                 o.part, gemm_stacked_shifts(o.prec), gemm_wide_nj(o.prec));
+    } else {
+      RF_REQUIRE(o.algo == RF_ALGO_DIRECT, "bucket %d: unknown form %d", b, o.algo);
+    }
   }
   if (kern->os_ready && (int)kern->os_buckets.size() == nb) {
     bool same = true;
     for (int b = 0; b < nb; ++b) {
       const OsBucket& o = kern->os_buckets[b];
-      same = same && o.cut_lo == cuts[b] && o.B == Bs[b] && o.Lp == Lps[b];
+      const BucketSpec& q = spec[b];
+      same = same && o.cut_lo == q.cut && o.algo == q.algo &&
+             (q.algo == RF_ALGO_OS ? (o.B == q.block && o.Lp == q.part)
+                                   : (q.algo != RF_ALGO_GEMM ||
+                                      (o.prec == q.prec && o.gemm_nj == q.block && o.gemm_s == q.part)));
     }
     if (same) return;
   }
   const int k = kern->k;
   std::vector<OsBucket> bk(nb);
   for (int b = 0; b < nb; ++b) {
-    bk[b].cut_lo = cuts[b];
-    bk[b].B = Bs[b];
-    bk[b].Lp = Lps[b];
+    bk[b].cut_lo = spec[b].cut;
+    bk[b].algo = spec[b].algo;
+    if (spec[b].algo == RF_ALGO_OS) {
+      bk[b].B = spec[b].block;
+      bk[b].Lp = spec[b].part;
+    } else if (spec[b].algo == RF_ALGO_GEMM) {
+      bk[b].prec = spec[b].prec;
+      bk[b].gemm_nj = spec[b].block;
+      bk[b].gemm_s = spec[b].part;
+    }
   }
   std::vector<int> bucket_of(k);
   for (int j = 0; j < k; ++j) {
     int b = nb - 1;
-    while (b > 0 && kern->len[j] < cuts[b]) --b;
+    while (b > 0 && kern->len[j] < spec[b].cut) --b;
     bucket_of[j] = b;
     bk[b].idx.push_back(j);
   }
-  // spectra bucket after bucket, kernels in index order inside a bucket
-  std::vector<int> parts(k);
+  for (int b = 0; b < nb; ++b)
+    if (bk[b].algo == RF_ALGO_GEMM)
+      for (const int j : bk[b].idx)
+        RF_REQUIRE(kern->len[j] <= gemm_max_len(), "a tensor-core bucket takes kernels of at most %d taps",
+                   gemm_max_len());
+  // spectra bucket after bucket (overlap-save buckets only), kernels in index order inside a bucket
+  std::vector<int> parts(k, 0);
   std::vector<int64_t> off(k, 0);
   int64_t total = 0;
-  for (int b = 0; b < nb; ++b)
+  for (int b = 0; b < nb; ++b) {
+    if (bk[b].algo != RF_ALGO_OS) continue;
     for (const int j : bk[b].idx) {
       parts[j] = std::max(1, (kern->len[j] + bk[b].Lp - 1) / bk[b].Lp);
       off[j] = total;
-      total += (int64_t)parts[j] * bk[b].B;
+      total += (int64_t)parts[j] * os_row(bk[b].B, kern->real);
     }
+  }
   kern->os_ready = false;
   kern->os_spec.ensure(std::max<size_t>(16, sizeof(float2) * (size_t)total));
   kern->os_off_d.ensure(std::max<size_t>(16, sizeof(int64_t) * k));
@@ -810,6 +985,17 @@ void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts
     o.idx_d.ensure(std::max<size_t>(16, sizeof(int32_t) * o.idx.size()));
     if (!o.idx.empty())
       RF_CUDA(cudaMemcpyAsync(o.idx_d.p, o.idx.data(), sizeof(int32_t) * o.idx.size(), cudaMemcpyHostToDevice, s));
+    if (o.algo != RF_ALGO_OS) {
+      // the direct or tensor-core form on the bucket's own kernel set, prepared now so that a
+      // reconstruction call launches without synchronising
+      o.sub = make_subset(kern, o.idx, s);
+      if (o.algo == RF_ALGO_GEMM && o.sub->k) {
+        o.sub->gemm_pref_nj = o.gemm_nj;
+        o.sub->gemm_pref_s = o.gemm_s;
+        gemm_prepare(c, o.sub.get(), o.prec, s);
+      }
+      continue;
+    }
     // partition rows (kernel, partition) of this bucket, contiguous in os_spec
     std::vector<int> gj, gp;
     for (const int j : o.idx)
@@ -835,12 +1021,16 @@ void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts
     for (int g0 = 0; g0 < G; g0 += chunk) {
       const int cnt = std::min(chunk, G - g0);
       dim3 grid((unsigned)((B + 255) / 256), (unsigned)cnt);
-      k_os_fill<<<grid, 256, 0, s>>>(kern->taps.as<float2>(), kern->off_d.as<int64_t>(), kern->len_d.as<int>(),
-                                     gjd.as<int>() + g0, gpd.as<int>() + g0, B, Lp, in);
+      k_os_fill<<<grid, 256, 0, s>>>(kern->taps.p, kern->real ? 1 : 0, kern->off_d.as<int64_t>(),
+                                     kern->len_d.as<int>(), gjd.as<int>() + g0, gpd.as<int>() + g0, B, Lp, in);
       RF_LAUNCHED();
       fft_c2c_f64(in, out, tmp, B, cnt, -1, c->tw64.as<double2>(), c->n, s);
       const int64_t count = (int64_t)cnt * B;
-      if (B == kB2)
+      if (kern->real) {
+        const int64_t hc = (int64_t)cnt * os_row(B, true);
+        k_os_round_half<<<(unsigned)((hc + 255) / 256), 256, 0, s>>>(out, cnt, B, 1.0 / (double)B,
+                                                                       dst + (int64_t)g0 * os_row(B, true));
+      } else if (B == kB2)
         k_os2_round<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, count, 1.0 / (double)B,
                                                                      dst + (int64_t)g0 * B);
       else
@@ -854,8 +1044,8 @@ void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts
   kern->os_parts = parts;
   kern->os_off = off;
   kern->os_buckets = std::move(bk);
-  kern->os_B = Bs[0];
-  kern->os_Lp = Lps[0];
+  kern->os_B = kern->os_buckets[0].B;
+  kern->os_Lp = kern->os_buckets[0].Lp;
   kern->os_ready = true;
   static unsigned long long version = 0;
   kern->os_version = ++version;
@@ -867,7 +1057,7 @@ void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s) {
              "overlap-save block %d invalid for n=%lld", B, (long long)c->n);
   if (!B || !Lp) {
     RF_REQUIRE(Lp == 0, "a partition length needs a block size");
-    os_choose_layout(c, kern->len, B, &B, &Lp);
+    os_choose_layout(c, kern->len, B, kern->real, &B, &Lp);
   }
   const int32_t cut = 0;
   os_prepare_buckets(c, kern, 1, &cut, &B, &Lp, s);
@@ -884,7 +1074,8 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
   if (kern->k == 0) return;
   if (!kern->os_ready) os_prepare(c, kern, 0, 0, s);
   int Qmax = 2;
-  for (const OsBucket& bk : kern->os_buckets) Qmax = std::max(Qmax, bk.B / bk.Lp);
+  for (const OsBucket& bk : kern->os_buckets)
+    if (bk.algo == RF_ALGO_OS) Qmax = std::max(Qmax, bk.B / bk.Lp);
   const bool win = max_out != nullptr;
   const size_t need = os_workspace_bytes(c, kern->k, win ? W : 0, Qmax);
   c->scratch.ensure(need);
@@ -894,7 +1085,7 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
   if (win) RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)kern->k * nw, s));
   // one segment transform and one launch per layout bucket (stream order keeps Zs consistent)
   for (const OsBucket& bk : kern->os_buckets) {
-    if (bk.idx.empty()) continue;
+    if (bk.idx.empty() || bk.algo != RF_ALGO_OS) continue;
     if (bk.B == kB2) {
       launch_os2_segments(c, static_cast<const float2*>(z_ref), nullptr, 1, bk.Lp, Zs, s);
       const bool q2 = bk.B / bk.Lp == 2;
@@ -921,6 +1112,9 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
     k_unpack_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
     RF_LAUNCHED();
   }
+  // buckets of the direct or tensor-core form overwrite their rows (after the unpack)
+  for (const OsBucket& bk : kern->os_buckets)
+    if (bk.algo != RF_ALGO_OS && !bk.idx.empty()) run_bucket_form(c, z_ref, bk, W, max_out, argmax_out, z_out, 0, s);
 }
 
 void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
@@ -931,23 +1125,30 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   for (int g = 0; g < G && !lead; ++g)
     if (ks[g]->os_ready) lead = ks[g];
   std::vector<int32_t> cuts, Bs, Lps;
+  std::vector<BucketSpec> spec;
   if (lead) {
     for (const OsBucket& b : lead->os_buckets) {
       cuts.push_back(b.cut_lo);
       Bs.push_back(b.B);
       Lps.push_back(b.Lp);
+      spec.push_back(BucketSpec{b.cut_lo, b.algo, b.prec, b.algo == RF_ALGO_OS ? b.B : b.gemm_nj,
+                                b.algo == RF_ALGO_OS ? b.Lp : b.gemm_s});
     }
   } else {
     std::vector<int> all;
     for (int g = 0; g < G; ++g) all.insert(all.end(), ks[g]->len.begin(), ks[g]->len.end());
     int B = 0, Lp = 0;
-    os_choose_layout(c, all, 0, &B, &Lp);
+    os_choose_layout(c, all, 0, ks[0]->real, &B, &Lp);
     cuts.push_back(0);
     Bs.push_back(B);
     Lps.push_back(Lp);
+    spec.push_back(BucketSpec{0, RF_ALGO_OS, RF_PREC_NATIVE, B, Lp});
   }
   const int nb = (int)cuts.size();
-  for (int g = 0; g < G; ++g) os_prepare_buckets(c, ks[g], nb, cuts.data(), Bs.data(), Lps.data(), s);
+  for (int g = 1; g < G; ++g)
+    RF_REQUIRE(ks[g]->real == ks[0]->real, "the kernel sets of a batch are all complex or all real-form");
+  const int herm = ks[0]->real ? 1 : 0;
+  for (int g = 0; g < G; ++g) os_prepare_forms(c, ks[g], nb, spec.data(), s);
   const int64_t n = c->n;
   const int64_t nw = (n + W - 1) / W;
   // plan key: window, references and kernel sets with their spectra versions (which change
@@ -962,7 +1163,9 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   int64_t rows = 0;
   for (int g = 0; g < G; ++g) rows += ks[g]->k;
   size_t zs_need = 16;
-  for (int b = 0; b < nb; ++b) zs_need = std::max(zs_need, sizeof(float2) * (size_t)G * (size_t)(n / Lps[b]) * Bs[b]);
+  for (int b = 0; b < nb; ++b)
+    if (spec[b].algo == RF_ALGO_OS)
+      zs_need = std::max(zs_need, sizeof(float2) * (size_t)G * (size_t)(n / Lps[b]) * Bs[b]);
   if (key != c->batch_key) {
     // work items bucket after bucket (the reference's segment spectra of that bucket's layout)
     std::vector<OsItem> items;
@@ -974,6 +1177,11 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     c->batch_sc.assign(nb, 1);
     std::vector<long long> order;
     for (int b = 0; b < nb; ++b) {
+      if (spec[b].algo != RF_ALGO_OS) {  // direct or tensor-core bucket: no work items
+        c->batch_lay_off[b + 1] = (int64_t)items.size();
+        c->batch_unit_off[b + 1] = (int64_t)order.size();
+        continue;
+      }
       const int64_t zstride = (n / Lps[b]) * Bs[b];
       const int64_t first = (int64_t)items.size();
       std::vector<int64_t> grp(G + 1, 0);  // items of reference g in this bucket: [grp[g], grp[g+1]) from first
@@ -1083,13 +1291,24 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
       const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * c->nsm, units));
       fn<<<(unsigned)grid, BB / 16, os_smem<BB>(), s>>>(c->batch_items.as<OsItem>() + first,
                                                         c->batch_order.as<long long>() + c->batch_unit_off[b], units,
-                                                        nchunk, tw, n, NQ, NB, SC, keys, W, nw, fastwin, counter);
+                                                        nchunk, tw, n, NQ, NB, SC, keys, W, nw, fastwin, herm,
+                                                        counter);
       RF_LAUNCHED();
     });
   }
   const int64_t count = rows * nw;
   k_unpack_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(keys, count, max_out, argmax_out);
   RF_LAUNCHED();
+  // buckets of the direct or tensor-core form, group by group, into their rows
+  for (int b = 0; b < nb; ++b) {
+    if (spec[b].algo == RF_ALGO_OS) continue;
+    int64_t row0 = 0;
+    for (int g = 0; g < G; ++g) {
+      const OsBucket& bk = ks[g]->os_buckets[b];
+      if (!bk.idx.empty()) run_bucket_form(c, z_refs[g], bk, W, max_out, argmax_out, nullptr, row0, s);
+      row0 += ks[g]->k;
+    }
+  }
 }
 
 }  // namespace rf

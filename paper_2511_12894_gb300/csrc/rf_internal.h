@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -142,6 +143,7 @@ struct rf_ctx {
   // of output chunks x neighbours small enough that their segment and partition spectra stay
   // in L2 while the units of a tile run
   rf::DevBuf batch_order;
+  rf::DevBuf mix_tmp;  // rows of buckets that run the direct or tensor-core form, before scattering
   std::vector<int64_t> batch_unit_off;  // units of layout bucket b: [off[b], off[b+1])
   std::vector<int> batch_sc;            // output blocks per unit, per bucket
   // Streaming (rf_stream_winmax): two device strain buffers, the references' series, the window
@@ -150,13 +152,19 @@ struct rf_ctx {
   rf::PinBuf st_pin;
 };
 
-// One overlap-save layout bucket of a kernel set: the neighbours whose lengths fall in
-// [cut_lo, next bucket's cut_lo) run with block size B and partitions of Lp taps.
+// One layout bucket of a kernel set: the neighbours whose lengths fall in [cut_lo, next
+// bucket's cut_lo) run overlap-save with block size B and partitions of Lp taps, or (algo
+// RF_ALGO_GEMM / RF_ALGO_DIRECT) the tensor-core or CUDA-core direct sum on `sub`, a kernel
+// set holding just those neighbours, whose rows are then scattered to their places.
 struct OsBucket {
   int32_t cut_lo = 0;
   int B = 0, Lp = 0;
+  int algo = 2;              // RF_ALGO_OS
+  int prec = 0;              // split precision of a tensor-core bucket
+  int gemm_nj = 0, gemm_s = 0;  // its tile layout (0, 0: the library's rule)
   std::vector<int32_t> idx;  // neighbour indices, increasing
   rf::DevBuf idx_d;          // int32 copy of idx
+  std::shared_ptr<rf_kernels> sub;
 };
 
 struct rf_kernels {
@@ -168,7 +176,11 @@ struct rf_kernels {
   std::vector<double> df_low;
   std::vector<int64_t> grid;   // build grid of each kernel (its lags are signed on it)
   int32_t max_len = 0;
-  rf::DevBuf taps;             // packed taps (grid dtype complex)
+  // Real-kernel form (the paper's r = 2 Re of the App. A integrand): taps stored as real values
+  // of the grid dtype (half the bytes), complex x real products in the direct form, Hermitian
+  // half spectra (bins 0..B/2) in the overlap-save preparation.
+  bool real = false;
+  rf::DevBuf taps;             // packed taps (grid dtype complex, or grid dtype real when `real`)
   rf::DevBuf len_d, lag0_d;    // int32[k]
   rf::DevBuf off_d;            // int64[k+1]
   // Overlap-save preparation (FP32 only): one or more layout buckets by kernel length; kernel j
@@ -192,10 +204,17 @@ struct rf_kernels {
   bool gemm_ready = false;
   int gemm_prec = 0, gemm_terms = 0, gemm_KC = 0, gemm_NCK = 0, gemm_NJ = 0, gemm_S = 1, gemm_LP = 0;
   bool gemm_tf32 = false;
+  int gemm_pref_nj = 0, gemm_pref_s = 0;  // requested tile layout (0, 0: the rule)
   rf::DevBuf gemm_B;
 };
 
 namespace rf {
+
+// Bytes of one packed tap of a kernel set: a complex or (real form) a real value of the grid dtype.
+inline size_t tap_bytes(const rf_kernels* k) {
+  const size_t r = k->dtype == RF_F64 ? sizeof(double) : sizeof(float);
+  return k->real ? r : 2 * r;
+}
 
 // ---------------------------------------------------------------- FFT (fft.cu)
 // Batched out-of-place Stockham FFT of length n (power of two) over `batch`
@@ -233,7 +252,7 @@ void sigma2_impl(rf_ctx* c, const double* inv_psd, int count, double* out, cudaS
 rf_kernels* build_impl(rf_ctx* c, const rf_template& ref, const rf_template* nbrs, int32_t k,
                        const double* inv_psd, double thr, int relative, int64_t n_build, cudaStream_t s);
 rf_kernels* import_impl(rf_ctx* c, int32_t k, const int32_t* lag0, const int32_t* len,
-                        const void* taps);
+                        const void* taps, bool real);
 
 // ---------------------------------------------------------------- reconstruct
 void reconstruct_direct(rf_ctx* c, const void* z_ref, const rf_kernels* kern, void* z_out,
@@ -243,7 +262,7 @@ void winmax_series(rf_ctx* c, const void* z, int32_t count, int64_t W, float* ma
 // overlap-save (reconstruct_os.cu); FP32 grids, block sizes 512..16384
 // Overlap-save layout (block size, partition length) of least modelled cost for kernels of
 // the given lengths; block != 0 fixes the block size.
-void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, int* B, int* Lp);
+void os_choose_layout(const rf_ctx* c, const std::vector<int>& lengths, int block, bool real, int* B, int* Lp);
 // modelled cost (ns, whole GPU) of one layout for kernels of the given lengths
 double os_layout_cost(const rf_ctx* c, const std::vector<int>& lengths, int B, int Lp);
 // autotune.cu
@@ -256,6 +275,13 @@ void os_prepare(rf_ctx* c, rf_kernels* kern, int B, int Lp, cudaStream_t s);
 // (cuts[0] = 0, increasing) and runs with (Bs[b], Lps[b]).
 void os_prepare_buckets(rf_ctx* c, rf_kernels* kern, int nb, const int32_t* cuts, const int32_t* Bs,
                         const int32_t* Lps, cudaStream_t s);
+// One bucket of a mixed preparation: kernels with cut <= L < next cut run overlap-save (algo
+// RF_ALGO_OS; block, part), the tensor-core form (RF_ALGO_GEMM; prec, tile layout block =
+// neighbours per group and part = stacked tiles, 0 and 0 for the rule) or the direct sum.
+struct BucketSpec {
+  int32_t cut, algo, prec, block, part;
+};
+void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spec, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
 // launches the bounded-wait health check (reconstruct_gemm.cu)
 void wait_selftest(rf_ctx* c, cudaStream_t s);
@@ -267,6 +293,10 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
                          float* max_out, int32_t* argmax_out, cudaStream_t s);
 // tensor-core direct form (reconstruct_gemm.cu); kernels of at most gemm_max_len() taps
 int gemm_max_len();
+// tile layouts: (16, gemm_stacked_shifts(prec)) or (gemm_wide_nj(prec), 1); (0, 0) = the rule
+bool gemm_layout_ok(int prec, int nj, int s);
+int gemm_stacked_shifts(int prec);
+int gemm_wide_nj(int prec);
 void gemm_prepare(rf_ctx* c, rf_kernels* kern, int prec, cudaStream_t s);
 void reconstruct_gemm(rf_ctx* c, const void* z_ref, rf_kernels* kern, int prec, void* z_out, int64_t W,
                       float* max_out, int32_t* argmax_out, cudaStream_t s);

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_error_string(lib):
-    assert lib.rf_version() == 4
+    assert lib.rf_version() == 5
     assert isinstance(lib.rf_last_error(), bytes)
 
 

@@ -220,7 +220,8 @@ def test_build_ratio_kernels_analytic(torch, n_build, rel, thr):
 @pytest.mark.parametrize("analytic,rel,thr", [(False, True, 1e-3), (True, False, 1e-2)])
 def test_build_ratio_kernels_real_form(torch, analytic, rel, thr):
     """The paper's real-kernel form (taps 2 Re rho) against the oracle's same definition,
-    numeric and analytic truncation: spans exact, taps to FP64 rounding, imaginary parts 0."""
+    numeric and analytic truncation: spans exact, taps (stored as real values) to FP64
+    rounding, the oracle's imaginary parts 0."""
     n = 1 << 16
     cfg = workload.config(1, n_override=n, k_override=6)
     ref, nb = cfg.groups[0]
@@ -231,8 +232,11 @@ def test_build_ratio_kernels_real_form(torch, analytic, rel, thr):
     pk = ratio.build_ratio_kernels(ref, nb, n, cfg.fs, cfg.f_low, cfg.f_high, cfg.pn_order, ip, thr, rel,
                                    analytic=analytic, real=True)
     assert np.array_equal(kern.lag0, pk.lag0) and np.array_equal(kern.length, pk.length)
+    # stored as real values: half the bytes of complex taps
+    assert kern.real and np.all(pk.taps.imag == 0)
     taps = kern.taps().cpu().numpy()
-    assert _relerr(taps, pk.taps) < TOL["f64"] and np.all(taps.imag == 0)
+    assert taps.dtype == np.float64 and taps.shape == pk.taps.shape
+    assert _relerr(taps, pk.taps.real) < TOL["f64"]
 
 
 def test_build_rejects_unknown_truncation_flags(torch):
