@@ -77,8 +77,8 @@ def parse():
     ap.add_argument("--mf", default="filtered", choices=["filtered", "onthefly"],
                     help="reference matched filter from stored filters, or template regenerated every step")
     ap.add_argument("--buckets", default="",
-                    help="overlap-save layout per kernel-length bucket, 'cut:block:part,...' (first cut 0); "
-                         "skips the autotuner")
+                    help="layout per kernel-length bucket, 'cut:block:part[:form],...' (first cut 0; form os "
+                         "(default) or os_bins, the two-phase overlap-save); skips the autotuner")
     ap.add_argument("--part", type=int, default=0,
                     help="overlap-save partition length: block/2, /4 or /8 (0: library default)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT plain-method arm")
@@ -483,9 +483,10 @@ def main():
     filt, sig = rf.reference_filters(ip, refs)
     tune, tune_s, tune_info, tuned_call = None, 0.0, None, None
     if args.buckets:
-        spec = [tuple(int(v) for v in b.split(":")) for b in args.buckets.split(",")]
+        spec = [b.split(":") for b in args.buckets.split(",")]
         for k in kerns:
-            k.prepare_buckets([c for c, _, _ in spec], [b for _, b, _ in spec], [p for _, _, p in spec])
+            k.prepare_forms([int(b[0]) for b in spec], [b[3] if len(b) > 3 else "os" for b in spec],
+                            ["native"] * len(spec), [int(b[1]) for b in spec], [int(b[2]) for b in spec])
         algo_used = "os"
     elif args.algo == "auto" and not args.no_autotune and args.block == 0 and args.part == 0:
         # the autotuner times candidate forms on a z_ref of this segment (offline, like the
@@ -498,18 +499,25 @@ def main():
                            allow_split=cfg.dtype == "f32")
         del zt
         w = tune[0]
+        bucketed = bool(w["cut"]) or w["algo"] in ("os", "os_bins")
         if len(pick) < G:
-            if w["algo"] == "os":
-                cuts = [0, w["cut"]] if w["cut"] else [0]
-                blocks = [w["block"], w["block2"]] if w["cut"] else [w["block"]]
-                parts = [w["part"], w["part2"]] if w["cut"] else [w["part"]]
+            if bucketed:
+                if w["cut3"]:
+                    forms = ([0, w["cut"], w["cut3"]], [w["algo"], w["algo2"], w["algo3"]],
+                             [w["prec"], "native", "native"], [w["block"], w["block2"], w["block3"]],
+                             [w["part"], w["part2"], w["part3"]])
+                elif w["cut"]:
+                    forms = ([0, w["cut"]], [w["algo"], w["algo2"]], [w["prec"], "native"], [w["block"], w["block2"]],
+                             [w["part"], w["part2"]])
+                else:
+                    forms = ([0], [w["algo"]], [w["prec"]], [w["block"]], [w["part"]])
                 for k in kerns:
-                    k.prepare_buckets(cuts, blocks, parts)
+                    k.prepare_forms(*forms)
             # groups outside the tuned subset resolve AUTO by default; name the form instead
-            tuned_call = (w["algo"], w["prec"])
+            tuned_call = ("os", "native") if bucketed else (w["algo"], w["prec"])
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t1
-        algo_used = w["algo"]
+        algo_used = "os" if bucketed else w["algo"]
         tune_info = {"groups_timed": len(pick), "of": G}
     else:
         algo_used = args.algo if args.algo != "auto" else ("os" if cfg.dtype == "f32" else "direct")
@@ -521,7 +529,9 @@ def main():
     L = np.concatenate([k.length for k in kerns]).astype(np.float64)
     rows = int(L.size)
     buckets = kerns[0].os_buckets() if algo_used == "os" else []   # [(cut, B, Lp), ...]
-    layout = ",".join(f"B={b},Lp={p}" + (f"@{c}" if c else "") for c, b, p in buckets)
+    forms = kerns[0].bucket_forms() if algo_used == "os" else []    # [(algo, prec), ...]
+    layout = ",".join((f"{a}:" if a != "os" else "") + f"B={b},Lp={p}" + (f"@{c}" if c else "")
+                      for (c, b, p), (a, _) in zip(buckets, forms))
 
     nw = -(-n // W)
     z = torch.empty((G, n), dtype=rf.cdtype, device=dev)
@@ -720,8 +730,12 @@ def main():
         achieved = flops / (rec_avg_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops,
-                    "traffic": ncu_traffic("k_os", layout) if (algo_used == "os" and G == 1
-                                                                            and args.config == 2) else None,
+                    # DRAM bytes of one reconstruction call from the committed capture of this
+                    # workload and layout (null when the sources or the layout changed since)
+                    "traffic": (ncu_traffic(f"reconstruct_cfg{args.config}", layout)
+                                if (algo_used == "os" and not args.groups and not args.kernels and not args.bank
+                                    and not args.real and not args.analytic and not args.absolute
+                                    and args.threshold is None) else None),
                     "kernel": f"reconstruct ({algo_used}{', ' + layout if algo_used == 'os' else ''}, "
                               f"{'FP64' if cfg.dtype == 'f64' and algo_used == 'direct' else 'FP32'} CUDA cores, "
                               f"{'batched persistent' if G > 1 else 'one reference'})",

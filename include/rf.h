@@ -74,8 +74,11 @@ typedef enum {
   RF_ALGO_AUTO = 0,
   RF_ALGO_DIRECT = 1,    /* direct time-domain sum on CUDA cores (Eq. 8) */
   RF_ALGO_OS = 2,        /* overlap-save block FFT (frequency form, Eq. 7), FP32 */
-  RF_ALGO_GEMM = 3       /* direct sum as a Hankel x taps complex GEMM on the tcgen05 tensor
+  RF_ALGO_GEMM = 3,      /* direct sum as a Hankel x taps complex GEMM on the tcgen05 tensor
                             cores (n a multiple of 128) */
+  RF_ALGO_OS_BINS = 4    /* bucket form only (rf_kernels_prepare_forms): two-phase overlap-save,
+                            the partition sums per bin over runs of output blocks, then the
+                            block transforms; for kernels of many partitions */
 } rf_algo;
 
 /* Arithmetic of the reconstruction.  RF_PREC_NATIVE: the grid dtype on CUDA cores (direct,
@@ -388,12 +391,16 @@ rf_status rf_reconstruct_batched(rf_ctx* ctx, int32_t G, const void* const* z_re
 enum { RF_TUNE_ALLOW_SPLIT = 1 }; /* the tensor-core form (bf16x6, error about 3e-7 of max|z|) may
                                      be chosen; without it only exact-arithmetic forms compete */
 
-/* One timed candidate of rf_autotune: form (rf_algo), precision (rf_prec), overlap-save block
- * size and partition length (0 for the other forms) of the kernels shorter than `cut` taps, and
- * block2 / part2 for the others (cut = block2 = part2 = 0: one layout for all), and the best of
- * three timings (ms) of the fused window-peak reconstruction of the whole batch. */
+/* One timed candidate of rf_autotune: form (rf_algo), precision (rf_prec) and shape of the
+ * kernels shorter than `cut` taps (overlap-save, single-pass or two-phase: block size and
+ * partition length; tensor-core form: neighbours per group and stacked output tiles, 0 and 0 for
+ * the library's rule; direct sum: 0 and 0), and the form algo2 (RF_ALGO_OS or RF_ALGO_OS_BINS)
+ * with block size block2 and partition length part2 of the others (cut = block2 = part2 = algo2
+ * = 0: one form and shape for all), and the best of three timings (ms) of the fused window-peak
+ * reconstruction of the whole batch. */
 typedef struct {
-  int32_t algo, block, part, prec, cut, block2, part2;
+  int32_t algo, block, part, prec, cut, block2, part2, algo2;
+  int32_t cut3, block3, part3, algo3; /* a third bucket from cut3 taps on (all 0: none) */
   float ms;
 } rf_tune_entry;
 
@@ -407,7 +414,9 @@ typedef struct {
  * flags has RF_TUNE_ALLOW_SPLIT and the mean kernel length is at most 4096 taps, with that flag
  * also the mixed form (the tensor-core form for the shortest eighth of the kernels, up to a
  * power-of-two cut of at most 4096 taps, the fastest single layout for the rest;
- * rf_kernels_prepare_forms), and the direct sum when the grid is RF_F64 or no kernel is longer
+ * rf_kernels_prepare_forms), the two-phase form (RF_ALGO_OS_BINS) at the fastest single layout,
+ * as the upper bucket of every two-bucket candidate whose layout it takes, and as a third bucket
+ * for the kernels of at least 8 or 16 partitions above such a candidate's two, and the direct sum when the grid is RF_F64 or no kernel is longer
  * than 1024 taps.  out (host, may be NULL): up to max_out entries, the winner first; *n_out (host,
  * may be NULL) the number written.  Kernel sets end up prepared for the winner (a bucketed
  * winner, overlap-save or mixed, is then what RF_ALGO_AUTO runs; for another form, the last

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(HERE, "librf.so")
 
 RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ETIMEOUT, RF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 RF_F64, RF_F32 = 0, 1
-ALGOS = {"auto": 0, "direct": 1, "os": 2, "gemm": 3}
+ALGOS = {"auto": 0, "direct": 1, "os": 2, "gemm": 3, "os_bins": 4}   # os_bins: a bucket form only
 RF_TRUNC_RELATIVE = 1
 RF_TRUNC_ANALYTIC = 2
 RF_KERNEL_REAL = 4
@@ -46,7 +46,9 @@ EXPORTED = (
 class rf_tune_entry(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("block", ctypes.c_int32), ("part", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("cut", ctypes.c_int32), ("block2", ctypes.c_int32),
-                ("part2", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("part2", ctypes.c_int32), ("algo2", ctypes.c_int32), ("cut3", ctypes.c_int32),
+                ("block3", ctypes.c_int32), ("part3", ctypes.c_int32), ("algo3", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
 
 class RFError(RuntimeError):
@@ -477,7 +479,9 @@ class RatioFilter:
         names = {v: k for k, v in ALGOS.items()}
         pnames = {v: k for k, v in PRECS.items()}
         return [{"algo": names[e.algo], "block": e.block, "part": e.part, "prec": pnames[e.prec], "cut": e.cut,
-                 "block2": e.block2, "part2": e.part2, "ms": e.ms} for e in out[:n.value]]
+                 "block2": e.block2, "part2": e.part2, "algo2": names[e.algo2] if e.cut else None,
+                 "cut3": e.cut3, "block3": e.block3, "part3": e.part3, "algo3": names[e.algo3] if e.cut3 else None,
+                 "ms": e.ms} for e in out[:n.value]]
 
     def selftest_bounded_wait(self, stream=None) -> None:
         """Exercise the timeout path: the next device_status() raises RF_ETIMEOUT."""

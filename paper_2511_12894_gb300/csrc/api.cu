@@ -380,9 +380,10 @@ rf_status rf_kernels_os_buckets(const rf_kernels* kern, int32_t max_nb, int32_t*
     const int cnt = kern->os_ready ? (int)kern->os_buckets.size() : 0;
     for (int b = 0; b < std::min(cnt, (int)max_nb); ++b) {
       const OsBucket& o = kern->os_buckets[b];
+      const bool os_like = o.algo == RF_ALGO_OS || o.algo == RF_ALGO_OS_BINS;
       if (cuts) cuts[b] = o.cut_lo;
-      if (blocks) blocks[b] = o.algo == RF_ALGO_OS ? o.B : o.gemm_nj;
-      if (parts) parts[b] = o.algo == RF_ALGO_OS ? o.Lp : o.gemm_s;
+      if (blocks) blocks[b] = os_like ? o.B : o.gemm_nj;
+      if (parts) parts[b] = os_like ? o.Lp : o.gemm_s;
     }
     if (nb) *nb = std::min(cnt, (int)max_nb);
   });

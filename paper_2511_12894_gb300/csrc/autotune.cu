@@ -20,7 +20,9 @@ namespace {
 struct Cand {
   int algo, block, part, prec;
   double model;
-  int cut = 0, block2 = 0, part2 = 0;  // two-bucket overlap-save: (block, part) below cut
+  int cut = 0, block2 = 0, part2 = 0;  // two buckets: (algo, block, part) below cut, (algo2, block2, part2) above
+  int algo2 = RF_ALGO_OS;
+  int cut3 = 0, block3 = 0, part3 = 0, algo3 = RF_ALGO_OS;  // a third bucket from cut3 on
 };
 
 // layouts of least modelled cost for kernels of the given lengths
@@ -76,7 +78,7 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   RF_CUDA(cudaEventCreate(&e0));
   RF_CUDA(cudaEventCreate(&e1));
   auto run = [&](const Cand& cd) {
-    if ((cd.algo == RF_ALGO_OS || cd.cut) && G > 1) {  // overlap-save or mixed buckets: batched
+    if ((cd.algo == RF_ALGO_OS || cd.algo == RF_ALGO_OS_BINS || cd.cut) && G > 1) {  // bucketed: batched
       reconstruct_batched(c, G, z_refs, ks, W, pk.as<float>(), ak.as<int32_t>(), s);
       return;
     }
@@ -86,7 +88,8 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
       if (k->k) {
         float* mo = pk.as<float>() + row * nw;
         int32_t* ao = ak.as<int32_t>() + row * nw;
-        if (cd.algo == RF_ALGO_OS || cd.cut) reconstruct_os(c, z_refs[g], k, nullptr, W, mo, ao, s);
+        if (cd.algo == RF_ALGO_OS || cd.algo == RF_ALGO_OS_BINS || cd.cut)
+          reconstruct_os(c, z_refs[g], k, nullptr, W, mo, ao, s);
         else if (cd.algo == RF_ALGO_GEMM) reconstruct_gemm(c, z_refs[g], k, cd.prec, nullptr, W, mo, ao, s);
         else reconstruct_direct(c, z_refs[g], k, nullptr, W, mo, ao, s);
       }
@@ -94,10 +97,14 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
     }
   };
   auto prepare = [&](const Cand& cd) {
-    if (cd.cut) {  // two buckets: (algo, prec, block, part) below the cut, overlap-save above
-      const BucketSpec spec[2] = {BucketSpec{0, cd.algo, cd.prec, cd.block, cd.part},
-                                  BucketSpec{cd.cut, RF_ALGO_OS, RF_PREC_NATIVE, cd.block2, cd.part2}};
-      for (int g = 0; g < G; ++g) os_prepare_forms(c, ks[g], 2, spec, s);
+    if (cd.cut) {  // two or three buckets: (algo, prec, block, part) below the cut, then the others
+      const BucketSpec spec[3] = {BucketSpec{0, cd.algo, cd.prec, cd.block, cd.part},
+                                  BucketSpec{cd.cut, cd.algo2, RF_PREC_NATIVE, cd.block2, cd.part2},
+                                  BucketSpec{cd.cut3, cd.algo3, RF_PREC_NATIVE, cd.block3, cd.part3}};
+      for (int g = 0; g < G; ++g) os_prepare_forms(c, ks[g], cd.cut3 ? 3 : 2, spec, s);
+    } else if (cd.algo == RF_ALGO_OS_BINS) {
+      const BucketSpec spec = BucketSpec{0, RF_ALGO_OS_BINS, RF_PREC_NATIVE, cd.block, cd.part};
+      for (int g = 0; g < G; ++g) os_prepare_forms(c, ks[g], 1, &spec, s);
     } else if (cd.algo == RF_ALGO_OS) {
       for (int g = 0; g < G; ++g) os_prepare(c, ks[g], cd.block, cd.part, s);
     } else if (cd.algo == RF_ALGO_GEMM) {
@@ -170,6 +177,34 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
           }
         }
       }
+      // two-phase overlap-save (partition sums per bin) for the long kernels: the fastest single
+      // layout in that form, and every two-bucket candidate so far with its upper bucket so
+      if (bins_layout_ok(lead.block, lead.part)) {
+        Cand one{RF_ALGO_OS_BINS, lead.block, lead.part, RF_PREC_NATIVE, 0.0};
+        extra.push_back(one);
+      }
+      // ... and three buckets: the two-phase form only for the kernels of many partitions (at
+      // least 8 or 16), where its per-bin sums pay for the buffer round trip
+      std::vector<Cand> twos;
+      int32_t lmax = 0;
+      for (int g = 0; g < G; ++g) lmax = std::max(lmax, ks[g]->max_len);
+      for (const Cand& cd : extra)
+        if (cd.cut && cd.algo == RF_ALGO_OS && cd.algo2 == RF_ALGO_OS && bins_layout_ok(cd.block2, cd.part2)) {
+          Cand t = cd;
+          t.algo2 = RF_ALGO_OS_BINS;
+          twos.push_back(t);
+          for (const int np : {8, 16}) {
+            const int cut3 = np * cd.part2;
+            if (cut3 <= cd.cut || cut3 > lmax) continue;
+            Cand three = cd;
+            three.cut3 = cut3;
+            three.block3 = cd.block2;
+            three.part3 = cd.part2;
+            three.algo3 = RF_ALGO_OS_BINS;
+            twos.push_back(three);
+          }
+        }
+      extra.insert(extra.end(), twos.begin(), twos.end());
       for (const Cand& cd : extra) {
         cands.push_back(cd);
         ms.push_back(time_cand(cd));
@@ -184,9 +219,10 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   const Cand& w = cands[win];
   prepare(w);
   for (int g = 0; g < G; ++g) {
-    // bucketed preparations (overlap-save or mixed) run through the overlap-save entry
-    ks[g]->tuned_algo = w.cut ? RF_ALGO_OS : w.algo;
-    ks[g]->tuned_prec = w.cut ? RF_PREC_NATIVE : w.prec;
+    // bucketed preparations (overlap-save, two-phase or mixed) run through the overlap-save entry
+    const bool bucketed = w.cut || w.algo == RF_ALGO_OS_BINS;
+    ks[g]->tuned_algo = bucketed ? RF_ALGO_OS : w.algo;
+    ks[g]->tuned_prec = bucketed ? RF_PREC_NATIVE : w.prec;
   }
   RF_CUDA(cudaStreamSynchronize(s));
   // the winner first, then the others in the order they were timed
@@ -194,7 +230,9 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
   auto put = [&](size_t i) {
     const Cand& cd = cands[i];
     if (n < max_out && out)
-      out[n] = rf_tune_entry{cd.algo, cd.block, cd.part, cd.prec, cd.cut, cd.block2, cd.part2, ms[i]};
+      out[n] = rf_tune_entry{cd.algo,  cd.block,  cd.part,  cd.prec,  cd.cut,  cd.block2,
+                             cd.part2, cd.cut ? cd.algo2 : 0,     cd.cut3, cd.block3, cd.part3,
+                             cd.cut3 ? cd.algo3 : 0,               ms[i]};
     ++n;
   };
   put(win);

@@ -23,27 +23,12 @@
 #include <cmath>
 #include <memory>
 
-#include "blockfft.cuh"
+#include "os_tail.cuh"
 #include "rf_internal.h"
 
 namespace rf {
 
 namespace {
-
-__device__ __forceinline__ unsigned long long pack_key(float v, unsigned int i) {
-  return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - i);
-}
-
-// Largest packed key of the warp: the largest high word (value bits), then the largest low
-// word among the lanes holding it (the smallest index), two 32-bit warp reductions in place of
-// a 64-bit shuffle tree.  Key 0 (no output) never wins against a real key, whose low word is
-// at least 2^31.
-__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k) {
-  const unsigned hi = (unsigned)(k >> 32);
-  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
-  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? (unsigned)k : 0u);
-  return ((unsigned long long)mh << 32) | ml;
-}
 
 template <int B>
 __global__ void __launch_bounds__(B / 16) k_os_segments(const float2* __restrict__ z_ref, int64_t n, int Lp,
@@ -88,97 +73,15 @@ __global__ void __launch_bounds__(B / 16) k_os_segments_batched(const float2* co
     for (int t = 0; t < S::RL; ++t) out[tid + q * S::NT + t * (B / S::RL)] = v[q * S::RL + t];
 }
 
-// Window peaks of this thread's CH consecutive outputs mv[0..cnt) whose first sample index is
-// i0 (later ones step by one and wrap to 0 at n), merged into the packed keys kj[window].
-// Warp-wide: every lane of the warp calls it (lanes without outputs pass cnt = 0).
-template <int CH>
-__device__ __forceinline__ void window_keys(const float (&mv)[CH], int cnt, int i0, int64_t n, int64_t W,
-                                            int64_t nw, int fastwin, unsigned long long* __restrict__ kj) {
-  const int lane = threadIdx.x & 31;
-  // sample index and window of this thread's first output; its outputs i0 + e (wrapping to
-  // 0 at n) lie in window w0 below e_b = min(W - r0, n - i0) and in the next window w1 (w0 + 1,
-  // or 0 after the wrap) from e_b on: at most two windows when W >= CH, which fastwin implies
-  const int w0 = i0 / (int)W;
-  const int r0 = i0 - w0 * (int)W;
-  const int to_wrap = (int)n - i0;
-  const int e_b = min((int)W - r0, to_wrap);
-  const int w1 = to_wrap <= (int)W - r0 ? 0 : w0 + 1;
-  const int wA = __shfl_sync(0xffffffffu, w0, 0);
-  const int wB = (wA + 1 == (int)nw) ? 0 : wA + 1;
-  // per window the largest |z|^2 and its first position (strict > keeps the first of equals)
-  float b0 = -1.f, b1 = -1.f;
-  int e0 = 0, e1 = 0;
-#pragma unroll
-  for (int e = 0; e < CH; ++e) {
-    const float m = mv[e];
-    if (e < cnt) {
-      if (e < e_b) {
-        if (m > b0) {
-          b0 = m;
-          e0 = e;
-        }
-      } else if (m > b1) {
-        b1 = m;
-        e1 = e;
-      }
-    }
-  }
-  unsigned long long kA = 0, kB = 0;
-  bool slow = !fastwin;
-  auto put = [&](int w, unsigned long long k) {
-    if (w == wA) kA = max(kA, k);
-    else if (w == wB) kB = max(kB, k);
-    else slow = true;
-  };
-  if (b0 >= 0.f) put(w0, pack_key(b0, (unsigned int)(i0 + e0)));
-  if (b1 >= 0.f) put(w1, pack_key(b1, (unsigned int)(i0 + e1 >= (int)n ? i0 + e1 - (int)n : i0 + e1)));
-  const bool any_slow = __any_sync(0xffffffffu, slow);
-  if (any_slow) {
-    // per output, stepping the index and window by one (wrapping at n)
-    int i = i0, w = w0, r = r0;
-#pragma unroll
-    for (int e = 0; e < CH; ++e) {
-      if (e < cnt) atomicMax(kj + w, pack_key(mv[e], (unsigned int)i));
-      ++i;
-      ++r;
-      if (i == (int)n) {
-        i = 0;
-        w = 0;
-        r = 0;
-      } else if (r == (int)W) {
-        ++w;
-        r = 0;
-      }
-    }
-  } else {
-    kA = warp_max_key(kA);
-    kB = warp_max_key(kB);
-    if (lane == 0) {
-      if (kA) atomicMax(kj + wA, kA);
-      if (kB) atomicMax(kj + wB, kB);
-    }
-  }
-}
-
-// One neighbour's output blocks [s0, s1): spectral products, inverse block FFT, then either
-// the series (zrow != nullptr) or the window peaks (keys row kj).
-// Row stride of a partition spectrum: B bins, or the Hermitian half (bins 0..B/2, padded).
-__host__ __device__ constexpr int os_row(int B, bool herm) { return herm ? B / 2 + 8 : B; }
-
+// One neighbour's output blocks [s0, s1): spectral products, then the block tail (inverse block
+// FFT and either the series (zrow != nullptr) or the window peaks (keys row kj)).
 template <int B, int Q, bool WINMAX>
 __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const float2* __restrict__ C, int P,
                                           int64_t m0, const float2* __restrict__ tw, int64_t n, int NQ, int s0,
                                           int s1, float2* __restrict__ zrow, unsigned long long* __restrict__ kj,
                                           int64_t W, int64_t nw, int fastwin, int herm, float2* sm) {
-  using S = BlockFFTShape<B>;
-  constexpr int NT = S::NT;
-  constexpr int LP = B / Q;   // partition length: outputs start at block position LP
-  constexpr int H = B - LP;   // outputs per block
-  constexpr int RL = S::RL;
-  constexpr int CH = H / NT;  // outputs per thread in the peak reduction (8, 12 or 14)
   static_assert(Q == 2 || Q == 4 || Q == 8, "partition ratio");
   const int tid = threadIdx.x;
-  const int64_t mask = n - 1;
   // partition spectrum loads: bins tid + t B/16; with the Hermitian half, the upper eight
   // (t >= 8, above B/2) come from the mirrors B/2 - tid - (t - 8) B/16, conjugated
   const int crow = os_row(B, herm != 0);
@@ -216,50 +119,7 @@ __device__ __forceinline__ void os_blocks(const float2* __restrict__ Zs, const f
         }
       }
     }
-    block_fft<B, +1>(v, sm, tw);
-    const int64_t o0 = (int64_t)s * H;                // pre-relabel index of block position LP
-    const int64_t base = (o0 + m0) & mask;            // its output index
-    const int64_t lim = n - o0;                       // block positions LP + t with t < lim exist
-    if (!WINMAX) {
-#pragma unroll
-      for (int q = 0; q < 16 / RL; ++q)
-#pragma unroll
-        for (int t = 0; t < RL; ++t) {
-          const int idx = tid + q * NT + t * (B / RL);
-          if (idx >= LP && idx - LP < lim) zrow[(base + idx - LP) & mask] = v[q * RL + t];
-        }
-      __syncthreads();  // the next block's FFT overwrites the shared memory read above
-    } else {
-      __syncthreads();  // the last FFT stage has finished reading shared memory
-      float* mag = reinterpret_cast<float*>(sm);
-#pragma unroll
-      for (int q = 0; q < 16 / RL; ++q)
-#pragma unroll
-        for (int t = 0; t < RL; ++t) {
-          const int idx = tid + q * NT + t * (B / RL);
-          if (idx >= LP) {
-            const float2 y = v[q * RL + t];
-            mag[idx - LP] = y.x * y.x + y.y * y.y;
-          }
-        }
-      __syncthreads();
-      const int qbase = tid * CH;
-      float mv[CH];
-      if constexpr (CH % 4 == 0) {
-#pragma unroll
-        for (int e = 0; e < CH; e += 4)
-          *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + qbase + e);
-      } else {
-#pragma unroll
-        for (int e = 0; e < CH; e += 2)
-          *reinterpret_cast<float2*>(mv + e) = *reinterpret_cast<const float2*>(mag + qbase + e);
-      }
-      // outputs of this thread that exist (all but possibly in the last block)
-      const int64_t avail = lim - qbase;
-      const int cnt = avail <= 0 ? 0 : (avail >= CH ? CH : (int)avail);
-      window_keys<CH>(mv, cnt, (int)((base + qbase) & mask), n, W, nw, fastwin, kj);
-      __syncthreads();  // mag (shared memory) is reused by the next block's FFT
-    }
+    os_block_tail<B, Q, WINMAX>(v, s, m0, n, zrow, kj, W, nw, fastwin, tw, sm);
   }
 }
 
@@ -289,13 +149,6 @@ __global__ void __launch_bounds__(B / 16, 16384 / B) k_os(const float2* __restri
 // neighbours, so the segment spectra a tile reads and its neighbours' partition spectra stay
 // in L2 while the tile's units run (a 2^23-sample reference has 134-268 MB of segment
 // spectra, more than L2 holds).
-struct OsItem {
-  const float2* C;
-  const float2* Zs;
-  int P;
-  int lag0;
-  long long row;
-};
 
 template <int B, int Q>
 __global__ void __launch_bounds__(B / 16, 16384 / B) k_os_batched(const OsItem* __restrict__ items,
@@ -912,6 +765,11 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
     RF_REQUIRE(b == 0 || o.cut > spec[b - 1].cut, "bucket cuts must increase");
     if (o.algo == RF_ALGO_OS) {
       check_layout(c, o.block, o.part, kern->real);
+    } else if (o.algo == RF_ALGO_OS_BINS) {
+      check_layout(c, o.block, o.part, kern->real);
+      RF_REQUIRE(bins_layout_ok(o.block, o.part),
+                 "two-phase overlap-save takes B in {4096, 8192, 16384} and Lp = B/2 or B/4 (got %d, %d)", o.block,
+                 o.part);
     } else if (o.algo == RF_ALGO_GEMM) {
       RF_REQUIRE(o.prec >= RF_PREC_BF16 && o.prec <= RF_PREC_3XTF32, "a tensor-core bucket needs a split precision");
       RF_REQUIRE(c->n % 128 == 0, "the tensor-core form needs n to be a multiple of 128");
@@ -928,7 +786,7 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
       const OsBucket& o = kern->os_buckets[b];
       const BucketSpec& q = spec[b];
       same = same && o.cut_lo == q.cut && o.algo == q.algo &&
-             (q.algo == RF_ALGO_OS ? (o.B == q.block && o.Lp == q.part)
+             ((q.algo == RF_ALGO_OS || q.algo == RF_ALGO_OS_BINS) ? (o.B == q.block && o.Lp == q.part)
                                    : (q.algo != RF_ALGO_GEMM ||
                                       (o.prec == q.prec && o.gemm_nj == q.block && o.gemm_s == q.part)));
     }
@@ -939,7 +797,7 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
   for (int b = 0; b < nb; ++b) {
     bk[b].cut_lo = spec[b].cut;
     bk[b].algo = spec[b].algo;
-    if (spec[b].algo == RF_ALGO_OS) {
+    if (spec[b].algo == RF_ALGO_OS || spec[b].algo == RF_ALGO_OS_BINS) {
       bk[b].B = spec[b].block;
       bk[b].Lp = spec[b].part;
     } else if (spec[b].algo == RF_ALGO_GEMM) {
@@ -965,7 +823,7 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
   std::vector<int64_t> off(k, 0);
   int64_t total = 0;
   for (int b = 0; b < nb; ++b) {
-    if (bk[b].algo != RF_ALGO_OS) continue;
+    if (bk[b].algo != RF_ALGO_OS && bk[b].algo != RF_ALGO_OS_BINS) continue;
     for (const int j : bk[b].idx) {
       parts[j] = std::max(1, (kern->len[j] + bk[b].Lp - 1) / bk[b].Lp);
       off[j] = total;
@@ -985,7 +843,7 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
     o.idx_d.ensure(std::max<size_t>(16, sizeof(int32_t) * o.idx.size()));
     if (!o.idx.empty())
       RF_CUDA(cudaMemcpyAsync(o.idx_d.p, o.idx.data(), sizeof(int32_t) * o.idx.size(), cudaMemcpyHostToDevice, s));
-    if (o.algo != RF_ALGO_OS) {
+    if (o.algo != RF_ALGO_OS && o.algo != RF_ALGO_OS_BINS) {
       // the direct or tensor-core form on the bucket's own kernel set, prepared now so that a
       // reconstruction call launches without synchronising
       o.sub = make_subset(kern, o.idx, s);
@@ -1040,6 +898,20 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
     }
     RF_CUDA(cudaStreamSynchronize(s));  // the row buffers are released at the end of the iteration
   }
+  // two-phase buckets: their plan for single-reference calls (the segment spectra come with
+  // the call) and its items on the device
+  for (int b = 0; b < nb; ++b) {
+    OsBucket& o = bk[b];
+    if (o.algo != RF_ALGO_OS_BINS || o.idx.empty()) continue;
+    std::vector<OsItem> items;
+    for (const int j : o.idx)
+      items.push_back(OsItem{kern->os_spec.as<float2>() + off[j], nullptr, parts[j], kern->lag0[j], (long long)j});
+    o.bins = std::make_shared<BinsPlan>(bins_plan(items, o.B, o.Lp, kern->real, c->n));
+    o.bins_items_d.ensure(sizeof(OsItem) * o.bins->items.size());
+    RF_CUDA(cudaMemcpy(o.bins_items_d.p, o.bins->items.data(), sizeof(OsItem) * o.bins->items.size(),
+                       cudaMemcpyHostToDevice));
+    c->bins_y.ensure(o.bins->y_bytes);
+  }
   RF_CUDA(cudaStreamSynchronize(s));
   kern->os_parts = parts;
   kern->os_off = off;
@@ -1075,7 +947,7 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
   if (!kern->os_ready) os_prepare(c, kern, 0, 0, s);
   int Qmax = 2;
   for (const OsBucket& bk : kern->os_buckets)
-    if (bk.algo == RF_ALGO_OS) Qmax = std::max(Qmax, bk.B / bk.Lp);
+    if (bk.algo == RF_ALGO_OS || bk.algo == RF_ALGO_OS_BINS) Qmax = std::max(Qmax, bk.B / bk.Lp);
   const bool win = max_out != nullptr;
   const size_t need = os_workspace_bytes(c, kern->k, win ? W : 0, Qmax);
   c->scratch.ensure(need);
@@ -1085,7 +957,19 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
   if (win) RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)kern->k * nw, s));
   // one segment transform and one launch per layout bucket (stream order keeps Zs consistent)
   for (const OsBucket& bk : kern->os_buckets) {
-    if (bk.idx.empty() || bk.algo != RF_ALGO_OS) continue;
+    if (bk.idx.empty()) continue;
+    if (bk.algo == RF_ALGO_OS_BINS) {
+      // the bucket's segment spectra, then the two-phase launches of its plan
+      dispatch_bq(bk.B, bk.B / bk.Lp, [&](auto bc, auto qc) {
+        constexpr int BB = decltype(bc)::value;
+        launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), bk.Lp, Zs, s);
+      });
+      c->bins_y.ensure(bk.bins->y_bytes);
+      bins_run(c, *bk.bins, bk.bins_items_d.as<OsItem>(), Zs, c->bins_y.as<float2>(),
+               win ? nullptr : static_cast<float2*>(z_out), win ? keys : nullptr, W, s);
+      continue;
+    }
+    if (bk.algo != RF_ALGO_OS) continue;
     if (bk.B == kB2) {
       launch_os2_segments(c, static_cast<const float2*>(z_ref), nullptr, 1, bk.Lp, Zs, s);
       const bool q2 = bk.B / bk.Lp == 2;
@@ -1114,7 +998,8 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
   }
   // buckets of the direct or tensor-core form overwrite their rows (after the unpack)
   for (const OsBucket& bk : kern->os_buckets)
-    if (bk.algo != RF_ALGO_OS && !bk.idx.empty()) run_bucket_form(c, z_ref, bk, W, max_out, argmax_out, z_out, 0, s);
+    if (bk.algo != RF_ALGO_OS && bk.algo != RF_ALGO_OS_BINS && !bk.idx.empty())
+      run_bucket_form(c, z_ref, bk, W, max_out, argmax_out, z_out, 0, s);
 }
 
 void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* const* ks, int64_t W,
@@ -1131,8 +1016,8 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
       cuts.push_back(b.cut_lo);
       Bs.push_back(b.B);
       Lps.push_back(b.Lp);
-      spec.push_back(BucketSpec{b.cut_lo, b.algo, b.prec, b.algo == RF_ALGO_OS ? b.B : b.gemm_nj,
-                                b.algo == RF_ALGO_OS ? b.Lp : b.gemm_s});
+      const bool os_like = b.algo == RF_ALGO_OS || b.algo == RF_ALGO_OS_BINS;
+      spec.push_back(BucketSpec{b.cut_lo, b.algo, b.prec, os_like ? b.B : b.gemm_nj, os_like ? b.Lp : b.gemm_s});
     }
   } else {
     std::vector<int> all;
@@ -1164,7 +1049,7 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   for (int g = 0; g < G; ++g) rows += ks[g]->k;
   size_t zs_need = 16;
   for (int b = 0; b < nb; ++b)
-    if (spec[b].algo == RF_ALGO_OS)
+    if (spec[b].algo == RF_ALGO_OS || spec[b].algo == RF_ALGO_OS_BINS)
       zs_need = std::max(zs_need, sizeof(float2) * (size_t)G * (size_t)(n / Lps[b]) * Bs[b]);
   if (key != c->batch_key) {
     // work items bucket after bucket (the reference's segment spectra of that bucket's layout)
@@ -1176,8 +1061,28 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     c->batch_unit_off.assign(nb + 1, 0);
     c->batch_sc.assign(nb, 1);
     std::vector<long long> order;
+    c->batch_bins.assign(nb, nullptr);
+    c->batch_bins_off.assign(nb + 1, 0);
+    std::vector<OsItem> bins_all;
     for (int b = 0; b < nb; ++b) {
-      if (spec[b].algo != RF_ALGO_OS) {  // direct or tensor-core bucket: no work items
+      if (spec[b].algo == RF_ALGO_OS_BINS) {
+        // two-phase bucket: its items (every reference's neighbours in the bucket) and plan
+        const int64_t zstride = (n / Lps[b]) * Bs[b];
+        std::vector<OsItem> bi;
+        int64_t row0 = 0;
+        for (int g = 0; g < G; ++g) {
+          const rf_kernels* k = ks[g];
+          for (const int j : k->os_buckets[b].idx)
+            bi.push_back(OsItem{k->os_spec.as<float2>() + k->os_off[j], zs_all + (int64_t)g * zstride,
+                                k->os_parts[j], k->lag0[j], (long long)(row0 + j)});
+          row0 += k->k;
+        }
+        c->batch_bins[b] = std::make_shared<BinsPlan>(bins_plan(bi, Bs[b], Lps[b], ks[0]->real, n));
+        c->batch_bins_off[b] = (int64_t)bins_all.size();
+        bins_all.insert(bins_all.end(), c->batch_bins[b]->items.begin(), c->batch_bins[b]->items.end());
+        c->bins_y.ensure(c->batch_bins[b]->y_bytes);
+      }
+      if (spec[b].algo != RF_ALGO_OS) {  // direct, tensor-core or two-phase bucket: no work units
         c->batch_lay_off[b + 1] = (int64_t)items.size();
         c->batch_unit_off[b + 1] = (int64_t)order.size();
         continue;
@@ -1233,6 +1138,10 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     c->batch_keys.ensure(sizeof(unsigned long long) * ((size_t)rows * nw + nb));
     if (!items.empty())
       RF_CUDA(cudaMemcpy(c->batch_items.p, items.data(), sizeof(OsItem) * items.size(), cudaMemcpyHostToDevice));
+    c->batch_bins_items.ensure(std::max<size_t>(16, sizeof(OsItem) * bins_all.size()));
+    if (!bins_all.empty())
+      RF_CUDA(cudaMemcpy(c->batch_bins_items.p, bins_all.data(), sizeof(OsItem) * bins_all.size(),
+                         cudaMemcpyHostToDevice));
     c->batch_order.ensure(std::max<size_t>(16, sizeof(long long) * order.size()));
     if (!order.empty())
       RF_CUDA(cudaMemcpy(c->batch_order.p, order.data(), sizeof(long long) * order.size(), cudaMemcpyHostToDevice));
@@ -1246,6 +1155,22 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   RF_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * ((size_t)rows * nw + nb), s));
   RF_REQUIRE(G <= 65535, "at most 65535 references per batch");
   for (int b = 0; b < nb; ++b) {
+    if (spec[b].algo == RF_ALGO_OS_BINS) {
+      const BinsPlan& pl = *c->batch_bins[b];
+      if (pl.items.empty()) continue;
+      dispatch_bq(Bs[b], Bs[b] / Lps[b], [&](auto bc, auto qc) {
+        constexpr int BB = decltype(bc)::value;
+        const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<BB>::LOGB];
+        auto seg = k_os_segments_batched<BB>;
+        RF_CUDA(cudaFuncSetAttribute(seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
+        seg<<<dim3((unsigned)(n / Lps[b]), (unsigned)G), BB / 16, os_smem<BB>(), s>>>(
+            c->batch_zptr.as<const float2*>(), n, Lps[b], tw, c->batch_zs.as<float2>());
+        RF_LAUNCHED();
+      });
+      bins_run(c, pl, c->batch_bins_items.as<OsItem>() + c->batch_bins_off[b], nullptr, c->bins_y.as<float2>(),
+               nullptr, keys, W, s);
+      continue;
+    }
     const int64_t first = c->batch_lay_off[b], cnt = c->batch_lay_off[b + 1] - first;
     if (!cnt) continue;
     const int B = Bs[b], Lp = Lps[b];
@@ -1301,7 +1226,7 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
   RF_LAUNCHED();
   // buckets of the direct or tensor-core form, group by group, into their rows
   for (int b = 0; b < nb; ++b) {
-    if (spec[b].algo == RF_ALGO_OS) continue;
+    if (spec[b].algo == RF_ALGO_OS || spec[b].algo == RF_ALGO_OS_BINS) continue;
     int64_t row0 = 0;
     for (int g = 0; g < G; ++g) {
       const OsBucket& bk = ks[g]->os_buckets[b];

@@ -86,6 +86,30 @@ struct PinBuf {
   }
 };
 
+// Work item of the batched and two-phase overlap-save launches: one neighbour's partition
+// spectra C (P of them), the segment spectra Zs of its reference, its first lag and its row.
+struct OsItem {
+  const float2* C;
+  const float2* Zs;
+  int P;
+  int lag0;
+  long long row;
+};
+// Two-phase overlap-save (reconstruct_bins.cu): items sorted by partition count, cut into waves
+// of (item tile, time tile); phase 1 per-bin partition sums into a buffer, phase 2 block tails.
+struct BinsWave {
+  int item0, nitems;  // items [item0, item0 + nitems) of the plan
+  int s0, ns;         // output blocks [s0, s0 + ns)
+  int pmax;           // most partitions among the tile's items
+};
+struct BinsPlan {
+  int B = 0, Lp = 0, NQ = 0, NB = 0;
+  bool herm = false;
+  std::vector<OsItem> items;  // in plan order
+  std::vector<BinsWave> waves;
+  size_t y_bytes = 0;         // buffer of one wave's partition sums
+};
+
 // ---------------------------------------------------------------- template model
 // TaylorF2 coefficients of one template (App. A, Eq. A1), prepared on the host
 // from the published post-Newtonian series and evaluated on the device in FP64.
@@ -144,6 +168,10 @@ struct rf_ctx {
   // in L2 while the units of a tile run
   rf::DevBuf batch_order;
   rf::DevBuf mix_tmp;  // rows of buckets that run the direct or tensor-core form, before scattering
+  rf::DevBuf bins_y;   // two-phase overlap-save: one wave's partition sums
+  std::vector<std::shared_ptr<rf::BinsPlan>> batch_bins;  // per bucket (null unless two-phase)
+  rf::DevBuf batch_bins_items;                            // their items, bucket after bucket
+  std::vector<int64_t> batch_bins_off;
   std::vector<int64_t> batch_unit_off;  // units of layout bucket b: [off[b], off[b+1])
   std::vector<int> batch_sc;            // output blocks per unit, per bucket
   // Streaming (rf_stream_winmax): two device strain buffers, the references' series, the window
@@ -152,10 +180,12 @@ struct rf_ctx {
   rf::PinBuf st_pin;
 };
 
+
 // One layout bucket of a kernel set: the neighbours whose lengths fall in [cut_lo, next
-// bucket's cut_lo) run overlap-save with block size B and partitions of Lp taps, or (algo
-// RF_ALGO_GEMM / RF_ALGO_DIRECT) the tensor-core or CUDA-core direct sum on `sub`, a kernel
-// set holding just those neighbours, whose rows are then scattered to their places.
+// bucket's cut_lo) run overlap-save with block size B and partitions of Lp taps (single-pass,
+// or RF_ALGO_OS_BINS: two-phase, partition sums per bin), or (algo RF_ALGO_GEMM /
+// RF_ALGO_DIRECT) the tensor-core or CUDA-core direct sum on `sub`, a kernel set holding just
+// those neighbours, whose rows are then scattered to their places.
 struct OsBucket {
   int32_t cut_lo = 0;
   int B = 0, Lp = 0;
@@ -165,6 +195,8 @@ struct OsBucket {
   std::vector<int32_t> idx;  // neighbour indices, increasing
   rf::DevBuf idx_d;          // int32 copy of idx
   std::shared_ptr<rf_kernels> sub;
+  std::shared_ptr<rf::BinsPlan> bins;  // two-phase plan of this bucket alone (single-reference calls)
+  rf::DevBuf bins_items_d;             // its items on the device
 };
 
 struct rf_kernels {
@@ -282,6 +314,13 @@ struct BucketSpec {
   int32_t cut, algo, prec, block, part;
 };
 void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spec, cudaStream_t s);
+// two-phase overlap-save (reconstruct_bins.cu): layouts it takes, its plan over a list of items,
+// and the launches of a plan (zs_one: the segment spectra of every item, or null for the items'
+// own; keys null for the series form into z_out rows)
+bool bins_layout_ok(int B, int Lp);
+BinsPlan bins_plan(std::vector<OsItem> items, int B, int Lp, bool herm, int64_t n);
+void bins_run(rf_ctx* c, const BinsPlan& pl, const OsItem* items_dev, const float2* zs_one, float2* Y,
+              float2* z_out, unsigned long long* keys, int64_t W, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
 // launches the bounded-wait health check (reconstruct_gemm.cu)
 void wait_selftest(rf_ctx* c, cudaStream_t s);

@@ -999,9 +999,10 @@ def test_bounded_wait_timeout_is_reported_and_context_survives(torch):
 
 
 def test_autotune_records_the_fastest_form_and_auto_follows_it(torch):
-    """The autotuner times overlap-save layouts, the tensor-core form and the direct sum on a
-    batch, records the fastest, and AUTO then gives the same rows as that form called
-    explicitly; on an FP64 grid without split precisions only the exact direct sum competes."""
+    """The autotuner times overlap-save layouts and buckets (single-pass and two-phase), the
+    tensor-core form, mixed forms and the direct sum on a batch, records the fastest, and AUTO
+    then gives the same rows as that form called explicitly; on an FP64 grid without split
+    precisions only the exact direct sum competes."""
     cfg = _batch_cfg()
     ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
     x = torch.tensor(data.strain(cfg), dtype=torch.float32, device="cuda")
@@ -1015,14 +1016,24 @@ def test_autotune_records_the_fastest_form_and_auto_follows_it(torch):
     assert len(table) >= 3 and all(e["ms"] > 0 for e in table)
     assert sum(e["algo"] == "os" and e["cut"] == 0 for e in table) == 3       # single layouts
     assert all(e["block2"] and e["part2"] for e in table if e["cut"])          # two-bucket variants
-    assert {e["algo"] for e in table} <= {"os", "gemm", "direct"}
+    assert {e["algo"] for e in table} <= {"os", "os_bins", "gemm", "direct"}
     win = table[0]
     assert win["ms"] == min(e["ms"] for e in table)
-    if win["algo"] == "os":
-        want = [(0, win["block"], win["part"])] + ([(win["cut"], win["block2"], win["part2"])] if win["cut"] else [])
-        assert all(k.os_buckets() == want for k in kerns)
+    # a bucketed winner (overlap-save, two-phase or mixed) is prepared bucket by bucket
+    bucketed = bool(win["cut"]) or win["algo"] in ("os", "os_bins")
+    if bucketed:
+        want = [(0, win["block"], win["part"])]
+        forms = [(win["algo"], win["prec"])]
+        if win["cut"]:
+            want.append((win["cut"], win["block2"], win["part2"]))
+            forms.append((win["algo2"], "native"))
+        if win["cut3"]:
+            want.append((win["cut3"], win["block3"], win["part3"]))
+            forms.append((win["algo3"], "native"))
+        assert all(k.os_buckets() == want and k.bucket_forms() == forms for k in kerns)
     P, A = rf.reconstruct_batched(zs, kerns, W)                       # AUTO -> the tuned form
-    P2, A2 = rf.reconstruct_batched(zs, kerns, W, win["algo"], prec=win["prec"])
+    P2, A2 = rf.reconstruct_batched(zs, kerns, W, "os" if bucketed else win["algo"],
+                                    prec="native" if bucketed else win["prec"])
     assert torch.equal(P, P2) and torch.equal(A, A2)
     # FP64 grid, exact forms only
     c1 = workload.config(1, n_override=1 << 13, k_override=3)

@@ -1,0 +1,144 @@
+"""Two-phase overlap-save (bucket form RF_ALGO_OS_BINS): the partition sums of Eq. 7's block
+form per bin over runs of output blocks, then the block transforms; against the FP64 oracle's
+direct sum (Eq. 8) on full series, at sampled outputs and on window peaks, for single-reference
+and batched calls, complex and real-form kernels, partition ratios 2 and 4, and kernels of more
+than 40 partitions (several passes over the register window)."""
+import numpy as np
+import pytest
+
+import workload
+from oracle import reconstruct
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-6
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_12894_gb300 import build
+    build.build()
+    return t
+
+
+def _rf(n):
+    from paper_2511_12894_gb300 import RatioFilter
+    return RatioFilter.from_config(workload.config(2, n_override=n, k_override=1))
+
+
+def _random_set(rng, n, lengths, real=False):
+    lags = [int(v) for v in rng.integers(-n // 2 + 1, n // 2, len(lengths))]
+    if real:
+        taps = [(rng.standard_normal(L) / np.sqrt(max(L, 1))).astype(np.float32) for L in lengths]
+    else:
+        taps = [((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / np.sqrt(max(L, 1))).astype(np.complex64)
+                for L in lengths]
+    return lags, taps
+
+
+def _check_peaks(P, A, zs, W):
+    for j, zh in enumerate(zs):
+        zmax = np.abs(zh).max()
+        Po, Ao = reconstruct.window_peaks(zh, W)
+        assert np.abs(np.sqrt(P[j]) - np.sqrt(Po)).max() <= TOL32 * zmax, j
+        m2 = zh.real ** 2 + zh.imag ** 2
+        for w in range(Po.shape[0]):
+            seg = np.sort(m2[w * W:(w + 1) * W])
+            bound = 4.0 * TOL32 * zmax * np.sqrt(seg[-1])
+            if seg[-1] - seg[-2] > bound:
+                assert A[j, w] == Ao[w], (j, w)
+            else:
+                assert m2[A[j, w]] >= seg[-1] - bound
+
+
+@pytest.mark.parametrize("B,Lp,real", [(4096, 2048, False), (4096, 1024, False), (8192, 4096, True),
+                                       (16384, 4096, False)])
+def test_two_phase_single_reference(torch, B, Lp, real):
+    n, W = 1 << 15, 2000
+    rng = np.random.default_rng(B + Lp + real)
+    lengths = [1, 700, 2048, 5000, 9000, 13000, 3, 4096]
+    lags, taps = _random_set(rng, n, lengths, real)
+    rf = _rf(n)
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps), real=real)
+    kern.prepare_forms([0], ["os_bins"], ["native"], [B], [Lp])
+    assert kern.bucket_forms() == [("os_bins", "native")]
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    zt = torch.tensor(z, device="cuda")
+    zs = [reconstruct.reconstruct_direct(z.astype(np.complex128), lags[j], taps[j].astype(np.complex128))
+          for j in range(len(lengths))]
+    out = rf.reconstruct(zt, kern, "auto").cpu().numpy()
+    for j, zh in enumerate(zs):
+        assert np.abs(out[j] - zh).max() <= TOL32 * np.abs(zh).max(), (j, np.abs(out[j] - zh).max() / np.abs(zh).max())
+    P, A = rf.reconstruct_winmax(zt, kern, W, "auto")
+    _check_peaks(P.cpu().numpy(), A.cpu().numpy(), zs, W)
+
+
+def test_two_phase_many_partitions(torch):
+    """Kernels of up to 60 partitions (two passes over the 40-partition register window, the
+    second adding to the buffer), sampled outputs by the oracle's defining sum."""
+    n, W = 1 << 16, 2048
+    rng = np.random.default_rng(60)
+    lengths = [60000, 49 * 1024, 48 * 1024, 30000, 47 * 1024 + 1, 40 * 1024, 40 * 1024 + 1, 32 * 1024 + 1]
+    lags, taps = _random_set(rng, n, lengths)
+    rf = _rf(n)
+    kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
+    kern.prepare_forms([0], ["os_bins"], ["native"], [4096], [1024])
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    zt = torch.tensor(z, device="cuda")
+    out = rf.reconstruct(zt, kern, "auto").cpu().numpy()
+    P, A = rf.reconstruct_winmax(zt, kern, W, "auto")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    zd = z.astype(np.complex128)
+    for j in range(len(lengths)):
+        c = taps[j].astype(np.complex128)
+        idx = rng.choice(n, 192, replace=False)
+        ref = reconstruct.reconstruct_at(zd, lags[j], c, idx)
+        zmax = np.abs(out[j]).max()
+        assert np.abs(out[j][idx] - ref).max() <= TOL32 * zmax, j
+        # the reported peaks against the defining sum at their indices, and against the series
+        wins = rng.choice(P.shape[1], 6, replace=False)
+        vals = np.abs(reconstruct.reconstruct_at(zd, lags[j], c, A[j, wins].astype(np.int64)))
+        assert np.abs(np.sqrt(P[j, wins]) - vals).max() <= TOL32 * zmax
+        m2 = np.abs(out[j]) ** 2
+        Pg, _ = reconstruct.window_peaks(out[j].astype(np.complex128), W)
+        assert np.abs(np.sqrt(P[j]) - np.sqrt(Pg)).max() <= TOL32 * zmax
+
+
+def test_two_phase_batched_next_to_single_pass(torch):
+    """Three references: single-pass overlap-save below 3000 taps, two-phase above, one batched
+    call (the two-phase launches cover every reference's long kernels together)."""
+    n, W = 1 << 15, 1024
+    rng = np.random.default_rng(33)
+    rf = _rf(n)
+    kerns, zts, zss = [], [], []
+    for lengths in ([300, 7000, 12000], [3000], [10, 2999, 9000, 4000, 1]):
+        lags, taps = _random_set(rng, n, lengths)
+        k = rf.kernels_import(lags, lengths, np.concatenate(taps))
+        k.prepare_forms([0, 3000], ["os", "os_bins"], ["native", "native"], [4096, 8192], [1024, 2048])
+        z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+        kerns.append(k)
+        zts.append(torch.tensor(z, device="cuda"))
+        zss.append([reconstruct.reconstruct_direct(z.astype(np.complex128), lags[j], taps[j].astype(np.complex128))
+                    for j in range(len(lengths))])
+    P, A = rf.reconstruct_batched(zts, kerns, W, "auto")
+    P, A = P.cpu().numpy(), A.cpu().numpy()
+    row = 0
+    for k, zs in zip(kerns, zss):
+        _check_peaks(P[row:row + k.k], A[row:row + k.k], zs, W)
+        row += k.k
+
+
+def test_two_phase_layouts_refused(torch):
+    from paper_2511_12894_gb300 import RFError
+    n = 1 << 15
+    rng = np.random.default_rng(34)
+    lags, taps = _random_set(rng, n, [100, 5000])
+    rf = _rf(n)
+    kern = rf.kernels_import(lags, [100, 5000], np.concatenate(taps))
+    with pytest.raises(RFError):   # block sizes 4096, 8192, 16384 only
+        kern.prepare_forms([0], ["os_bins"], ["native"], [2048], [1024])
+    with pytest.raises(RFError):   # partitions of B/2 or B/4
+        kern.prepare_forms([0], ["os_bins"], ["native"], [8192], [1024])
