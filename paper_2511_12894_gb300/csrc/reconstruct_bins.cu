@@ -84,20 +84,24 @@ __global__ void __launch_bounds__(kBinsThreads, 1)
   // The window as a ring of registers inside a group of U steps: at step u, logical entry p sits
   // in register (p - (Q - 1) u) mod PM, so moving to the next block renames registers (the Q - 1
   // newest values take the oldest ones' registers) instead of moving values; after the group one
-  // rotation by (Q - 1) U restores entry p to register p.  U = 4 keeps the unrolled code small
+  // rotation by (Q - 1) U restores entry p to register p.  U = 8 keeps the unrolled code small
   // enough for the instruction cache and the rotation at 2 PM / U moves per step.  The values
-  // entering at block s + 1 are loaded one step ahead and those of s + 2 issued during step s.
+  // entering at block s + 1 and s + 2 are held, and those of s + 3 issued during step s, so that
+  // a load has three steps of multiply-adds to arrive.
   auto seg_load = [&](int sb, int p) {
     return __ldcg(Zs + (int64_t)((sb * (Q - 1) - 1 - p0 - p) & qmask) * B + k);
   };
-  float2 nxt[Q - 1];
+  float2 nxt[Q - 1], nx2[Q - 1];
 #pragma unroll
-  for (int p = 0; p < Q - 1; ++p) nxt[p] = seg_load(s0 + 1, p);
+  for (int p = 0; p < Q - 1; ++p) {
+    nxt[p] = seg_load(s0 + 1, p);
+    nx2[p] = seg_load(s0 + 2, p);
+  }
   auto step = [&](int si, auto uc) {
     constexpr int u = decltype(uc)::value;
     float2 nn[Q - 1];
 #pragma unroll
-    for (int p = 0; p < Q - 1; ++p) nn[p] = seg_load(s0 + si + 2, p);
+    for (int p = 0; p < Q - 1; ++p) nn[p] = seg_load(s0 + si + 3, p);
     float2 a[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) a[r] = make_float2(0.f, 0.f);
@@ -119,7 +123,8 @@ __global__ void __launch_bounds__(kBinsThreads, 1)
 #pragma unroll
     for (int p = 0; p < Q - 1; ++p) {
       w[((p - (Q - 1) * (u + 1)) % PM + PM) % PM] = nxt[p];
-      nxt[p] = nn[p];
+      nxt[p] = nx2[p];
+      nx2[p] = nn[p];
     }
   };
   // entry p back in register p after a group of G steps
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(kBinsThreads, 1)
 #pragma unroll
     for (int p = 0; p < PM; ++p) w[p] = t[p];
   };
-  constexpr int U = 4;
+  constexpr int U = 8;
   int si = 0;
   for (; si + U <= ns; si += U) {
     unroll_steps<U>([&](auto uc) { step(si + decltype(uc)::value, uc); });
