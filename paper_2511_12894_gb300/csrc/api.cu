@@ -138,6 +138,16 @@ rf_status rf_create(const rf_grid* grid, rf_ctx** out) {
     for (int64_t m = 0; m < n; ++m) tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
     c->tw32.ensure(sizeof(float2) * n);
     RF_CUDA(cudaMemcpy(c->tw32.p, tw32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    if (g.dtype == RF_F32 && fft4_supported(n)) {
+      // four-step FFT twiddles: the low table, then every 2^lo-th entry
+      const int lo = fft4_lo_bits(n);
+      std::vector<float2> t4((size_t)((int64_t(1) << lo) + (n >> lo)));
+      for (int64_t m = 0; m < (int64_t(1) << lo); ++m) t4[m] = tw32[m];
+      for (int64_t m = 0; m < (n >> lo); ++m) t4[(int64_t(1) << lo) + m] = tw32[m << lo];
+      c->tw4.ensure(sizeof(float2) * t4.size());
+      RF_CUDA(cudaMemcpy(c->tw4.p, t4.data(), sizeof(float2) * t4.size(), cudaMemcpyHostToDevice));
+      c->tw4_lo_bits = lo;
+    }
     // stage twiddle tables of the overlap-save block FFTs
     const std::vector<float2> twb = block_fft_tables(c->twb_off);
     c->twb32.ensure(sizeof(float2) * twb.size());

@@ -80,15 +80,17 @@ __host__ __device__ constexpr int block_table_size() {
   return s + B;
 }
 
-// tw: the stage tables of B.  SIGN: -1 forward, +1 inverse (unnormalised).
+// tw: the stage tables of B.  SIGN: -1 forward, +1 inverse (unnormalised).  tid: the
+// thread's index within the transform (0 .. B/16 - 1); several transforms can share a thread
+// block, each with its own shared-memory region, as long as every thread of the block calls
+// block_fft (it synchronises the whole block).
 // Every access of a stage is base + t * stride in the padded index (the strides are
 // multiples of 16, so pad(base + t stride) = pad(base) + t (stride + stride / 16)), which
 // lets the compiler use one base register and immediate offsets.
 template <int B, int SIGN>
-__device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const float2* __restrict__ tw) {
+__device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const float2* __restrict__ tw, int tid) {
   using S = BlockFFTShape<B>;
   constexpr int NT = S::NT;
-  const int tid = threadIdx.x;
   // first stage: Ns = 1, no twiddles, out[b*16 + t] at padded index 17 b + t
   dft<16, SIGN>(v);
   {
@@ -149,6 +151,12 @@ __device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const flo
 #pragma unroll
     for (int t = 0; t < RL; ++t) v[q * RL + t] = a[t];
   }
+}
+
+// One transform per thread block (tid = threadIdx.x).
+template <int B, int SIGN>
+__device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const float2* __restrict__ tw) {
+  block_fft<B, SIGN>(v, sm, tw, (int)threadIdx.x);
 }
 
 }  // namespace rf

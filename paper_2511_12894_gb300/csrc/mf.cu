@@ -49,6 +49,8 @@ namespace {
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 512;
+// complex values of the four-step inverse transforms launched together (their intermediate)
+constexpr int64_t kF4Chunk = int64_t(1) << 23;
 
 // Partial sums of 4 df B(f_k)^2 inv_psd[k] over the band, one partial per block.
 __global__ void __launch_bounds__(kRedThreads) k_sigma2_partial(const double* __restrict__ ip, int64_t nbins,
@@ -201,15 +203,24 @@ void mf_reference_impl(rf_ctx* c, const void* x, const double* inv_psd, int32_t 
                   +1, c->tw64.as<double2>(), n, s);
     }
   } else {
-    real_to_complex_f32(static_cast<const float*>(x), c->fa.as<float2>(), n, s);
-    fft_c2c_f32(c->fa.as<float2>(), c->xf.as<float2>(), c->fb.as<float2>(), n, 1, -1, c->tw32.as<float2>(), n, s);
+    const bool four = fft4_supported(n);  // two-pass four-step transforms, else radix passes
+    if (four) {
+      fft4_forward_real(c, static_cast<const float*>(x), c->xf.as<float2>(), c->fb.as<float2>(), s);
+    } else {
+      real_to_complex_f32(static_cast<const float*>(x), c->fa.as<float2>(), n, s);
+      fft_c2c_f32(c->fa.as<float2>(), c->xf.as<float2>(), c->fb.as<float2>(), n, 1, -1, c->tw32.as<float2>(), n,
+                  s);
+    }
     for (int r = 0; r < nref; ++r) {
       const Tf2 p = make_tf2(refs[r], c->g.pn_order);
       k_mf_pointwise<float2><<<grid, 256, 0, s>>>(c->xf.as<float2>(), inv_psd, sig2, p, n, df, c->g.f_low,
                                                   c->g.f_high, c->fa.as<float2>(), sigma_out ? sigma_out + r : nullptr);
       RF_LAUNCHED();
-      fft_c2c_f32(c->fa.as<float2>(), static_cast<float2*>(z_out) + (int64_t)r * n, c->fb.as<float2>(), n, 1, +1,
-                  c->tw32.as<float2>(), n, s);
+      float2* zr = static_cast<float2*>(z_out) + (int64_t)r * n;
+      if (four)
+        fft4_inverse(c, c->fa.as<float2>(), zr, c->fb.as<float2>(), 1, s);
+      else
+        fft_c2c_f32(c->fa.as<float2>(), zr, c->fb.as<float2>(), n, 1, +1, c->tw32.as<float2>(), n, s);
     }
   }
 }
@@ -254,6 +265,17 @@ void mf_filtered_impl(rf_ctx* c, const void* x, int32_t nref, const void* filt, 
       ifft_product_f64(c->xf.as<double2>(), static_cast<const double2*>(filt) + (int64_t)r0 * nb, nb,
                        static_cast<double2*>(z_out) + (int64_t)r0 * n, c->mf_tmp.as<double2>(), n, cnt,
                        c->tw64.as<double2>(), n, s);
+    }
+  } else if (fft4_supported(n)) {
+    // two-pass four-step transforms; the inverses of kF4Chunk references share one launch pair,
+    // whose intermediate (kF4Chunk n complex values) is meant to stay in L2
+    const int c4 = (int)std::min<int64_t>(nref, std::max<int64_t>(1, kF4Chunk / n));
+    c->mf_tmp.ensure(sizeof(float2) * (size_t)c4 * n);
+    fft4_forward_real(c, static_cast<const float*>(x), c->xf.as<float2>(), c->mf_tmp.as<float2>(), s);
+    for (int r0 = 0; r0 < nref; r0 += c4) {
+      const int cnt = std::min(c4, nref - r0);
+      fft4_inverse_product(c, c->xf.as<float2>(), static_cast<const float2*>(filt) + (int64_t)r0 * nb, nb,
+                           static_cast<float2*>(z_out) + (int64_t)r0 * n, c->mf_tmp.as<float2>(), cnt, s);
     }
   } else {
     c->mf_tmp.ensure(sizeof(float2) * (size_t)chunk * n);

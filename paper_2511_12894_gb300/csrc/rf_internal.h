@@ -146,6 +146,10 @@ struct rf_ctx {
   // block size 2^b start at entry twb_off[b].
   rf::DevBuf twb32;
   int64_t twb_off[16] = {0};
+  // Four-step FFT twiddles (float2): w[m] = exp(-2 pi i m / n) for m < 2^tw4_lo_bits, then
+  // w[2^tw4_lo_bits m] for m < n / 2^tw4_lo_bits; empty where the four-step FFT does not apply.
+  rf::DevBuf tw4;
+  int tw4_lo_bits = 0;
   // Workspaces (grid dtype complex unless stated).
   rf::DevBuf xf;       // data spectrum, complex[n]
   rf::DevBuf fa, fb;   // FFT ping-pong, complex[n]
@@ -262,6 +266,16 @@ void ifft_product_f32(const float2* X, const float2* F, int64_t fstride, float2*
                       int batch, const float2* tw, int64_t table_n, cudaStream_t s);
 void fft_c2c_f32(const float2* in, float2* out, float2* tmp, int64_t n, int batch, int sign,
                  const float2* tw_table, int64_t table_n, cudaStream_t s);
+// Four-step FP32 transforms of the context's n (fft4.cu), for n = 2^18 .. 2^24: two passes
+// through HBM.  Forward of real data (natural order out), the unnormalised inverse of batch
+// complex rows, and the inverse of the one-sided product X[k] F_r[k] (k <= n/2, zero above;
+// row r of F at r fstride).  tmp holds batch n complex values.
+bool fft4_supported(int64_t n);
+int fft4_lo_bits(int64_t n);
+void fft4_forward_real(const rf_ctx* c, const float* x, float2* out, float2* tmp, cudaStream_t s);
+void fft4_inverse(const rf_ctx* c, const float2* in, float2* out, float2* tmp, int batch, cudaStream_t s);
+void fft4_inverse_product(const rf_ctx* c, const float2* X, const float2* F, int64_t fstride, float2* out,
+                          float2* tmp, int batch, cudaStream_t s);
 void real_to_complex_f64(const double* x, double2* out, int64_t n, cudaStream_t s);
 void real_to_complex_f32(const float* x, float2* out, int64_t n, cudaStream_t s);
 // Host-side FP64 twiddle table exp(-2 pi i m / n), m < n (octant symmetric, accurate).
