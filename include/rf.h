@@ -416,7 +416,7 @@ typedef struct {
  * power-of-two cut of at most 4096 taps, the fastest single layout for the rest;
  * rf_kernels_prepare_forms), the two-phase form (RF_ALGO_OS_BINS) at the fastest single layout,
  * as the upper bucket of every two-bucket candidate whose layout it takes, and as a third bucket
- * for the kernels of at least 8 or 16 partitions above such a candidate's two, and the direct sum when the grid is RF_F64 or no kernel is longer
+ * for the kernels of at least 4, 8 or 16 partitions above such a candidate's two, and the direct sum when the grid is RF_F64 or no kernel is longer
  * than 1024 taps.  out (host, may be NULL): up to max_out entries, the winner first; *n_out (host,
  * may be NULL) the number written.  Kernel sets end up prepared for the winner (a bucketed
  * winner, overlap-save or mixed, is then what RF_ALGO_AUTO runs; for another form, the last

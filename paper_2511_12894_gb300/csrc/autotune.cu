@@ -184,7 +184,7 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
         extra.push_back(one);
       }
       // ... and three buckets: the two-phase form only for the kernels of many partitions (at
-      // least 8 or 16), where its per-bin sums pay for the buffer round trip
+      // least 4, 8 or 16), where its per-bin sums pay for the buffer round trip
       std::vector<Cand> twos;
       int32_t lmax = 0;
       for (int g = 0; g < G; ++g) lmax = std::max(lmax, ks[g]->max_len);
@@ -193,7 +193,7 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
           Cand t = cd;
           t.algo2 = RF_ALGO_OS_BINS;
           twos.push_back(t);
-          for (const int np : {8, 16}) {
+          for (const int np : {4, 8, 16}) {
             const int cut3 = np * cd.part2;
             if (cut3 <= cd.cut || cut3 > lmax) continue;
             Cand three = cd;

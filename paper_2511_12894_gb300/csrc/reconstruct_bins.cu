@@ -30,7 +30,14 @@ namespace rf {
 
 namespace {
 
-constexpr int kBinsThreads = 256;
+constexpr int kBinsThreads = 128;
+// Blocks per SM that phase 1 asks the register allocator for: the window of PM partitions takes
+// four registers per partition in the ring and the partition values, so fewer partitions leave
+// room for more warps.
+template <int PM>
+__host__ __device__ constexpr int bins_min_blocks() {
+  return PM <= 16 ? 4 : (PM <= 24 ? 3 : 2);
+}
 constexpr int kBinsPMax = 40;
 
 // f(std::integral_constant<int, u>) for u = 0 .. N - 1, unrolled at compile time.
@@ -43,11 +50,11 @@ __device__ __forceinline__ void unroll_steps(F&& f) {
   unroll_steps_impl<N>(f, std::make_integer_sequence<int, N>{});
 }
 
-// Phase 1.  Block (bin slice, item): thread k = slice * 256 + tid.  Partitions p0 .. p0 + PM - 1
+// Phase 1.  Block (bin slice, item): thread k = slice * 128 + tid.  Partitions p0 .. p0 + PM - 1
 // of each item (those below its P); `accumulate` adds to the buffer (passes after the first).
 // Zs: per-item segment spectra, or zs_one for every item when not null.  Y: [item][ns][B].
 template <int PM, int Q>
-__global__ void __launch_bounds__(kBinsThreads, 1)
+__global__ void __launch_bounds__(kBinsThreads, bins_min_blocks<PM>())
     k_bins_products(const OsItem* __restrict__ items, const float2* __restrict__ zs_one, int B, int NQ, int crow,
                     int herm, int s0, int ns, int p0, int accumulate, float2* __restrict__ Y) {
   const int ii = blockIdx.y;
@@ -85,23 +92,29 @@ __global__ void __launch_bounds__(kBinsThreads, 1)
   // in register (p - (Q - 1) u) mod PM, so moving to the next block renames registers (the Q - 1
   // newest values take the oldest ones' registers) instead of moving values; after the group one
   // rotation by (Q - 1) U restores entry p to register p.  U = 8 keeps the unrolled code small
-  // enough for the instruction cache and the rotation at 2 PM / U moves per step.  The values
-  // entering at block s + 1 and s + 2 are held, and those of s + 3 issued during step s, so that
-  // a load has three steps of multiply-adds to arrive.
+  // enough for the instruction cache and the rotation at 2 PM / U moves per step.
+  //
+  // The entering values come through a second ring of DP register slots (DP divides U): at the
+  // start of a group, slot d holds the values entering at block s0 + si + 1 + d; step u takes
+  // slot u mod DP and refills it with the values of DP blocks later, so that every load has DP
+  // steps of multiply-adds to arrive.  A last partial group loads its values directly.
+  constexpr int U = 8;
+  constexpr int DP = Q == 2 ? 8 : 2;
+  static_assert(U % DP == 0, "prefetch ring");
   auto seg_load = [&](int sb, int p) {
     return __ldcg(Zs + (int64_t)((sb * (Q - 1) - 1 - p0 - p) & qmask) * B + k);
   };
-  float2 nxt[Q - 1], nx2[Q - 1];
+  float2 pf[DP][Q - 1];
 #pragma unroll
-  for (int p = 0; p < Q - 1; ++p) {
-    nxt[p] = seg_load(s0 + 1, p);
-    nx2[p] = seg_load(s0 + 2, p);
-  }
-  auto step = [&](int si, auto uc) {
+  for (int d = 0; d < DP; ++d)
+#pragma unroll
+    for (int p = 0; p < Q - 1; ++p) pf[d][p] = seg_load(s0 + 1 + d, p);
+  auto step = [&](int si, auto uc, auto rc) {
     constexpr int u = decltype(uc)::value;
+    constexpr bool ring = decltype(rc)::value;
     float2 nn[Q - 1];
 #pragma unroll
-    for (int p = 0; p < Q - 1; ++p) nn[p] = seg_load(s0 + si + 3, p);
+    for (int p = 0; p < Q - 1; ++p) nn[p] = seg_load(ring ? s0 + si + 1 + DP : s0 + si + 1, p);
     float2 a[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) a[r] = make_float2(0.f, 0.f);
@@ -122,9 +135,13 @@ __global__ void __launch_bounds__(kBinsThreads, 1)
     *yp = sum;
 #pragma unroll
     for (int p = 0; p < Q - 1; ++p) {
-      w[((p - (Q - 1) * (u + 1)) % PM + PM) % PM] = nxt[p];
-      nxt[p] = nx2[p];
-      nx2[p] = nn[p];
+      float2& r = w[((p - (Q - 1) * (u + 1)) % PM + PM) % PM];
+      if constexpr (ring) {
+        r = pf[u % DP][p];
+        pf[u % DP][p] = nn[p];
+      } else {
+        r = nn[p];
+      }
     }
   };
   // entry p back in register p after a group of G steps
@@ -136,14 +153,13 @@ __global__ void __launch_bounds__(kBinsThreads, 1)
 #pragma unroll
     for (int p = 0; p < PM; ++p) w[p] = t[p];
   };
-  constexpr int U = 8;
   int si = 0;
   for (; si + U <= ns; si += U) {
-    unroll_steps<U>([&](auto uc) { step(si + decltype(uc)::value, uc); });
+    unroll_steps<U>([&](auto uc) { step(si + decltype(uc)::value, uc, std::true_type{}); });
     rotate(std::integral_constant<int, U>{});
   }
   for (; si < ns; ++si) {
-    step(si, std::integral_constant<int, 0>{});
+    step(si, std::integral_constant<int, 0>{}, std::false_type{});
     rotate(std::integral_constant<int, 1>{});
   }
 }
@@ -174,14 +190,32 @@ void launch_products(const OsItem* items, const float2* zs_one, int B, int NQ, i
   RF_LAUNCHED();
 }
 
+// The smallest register window that holds pm partitions: steps of 4 at Q = 2 (the long-kernel
+// layouts), of 8 at Q = 4.
 template <int Q>
 void products_pm(int pm, const OsItem* items, const float2* zs_one, int B, int NQ, int crow, int herm, int s0,
                  int ns, int p0, int accumulate, float2* Y, int nitems, cudaStream_t s) {
-  if (pm <= 8) launch_products<8, Q>(items, zs_one, B, NQ, crow, herm, s0, ns, p0, accumulate, Y, nitems, s);
-  else if (pm <= 16) launch_products<16, Q>(items, zs_one, B, NQ, crow, herm, s0, ns, p0, accumulate, Y, nitems, s);
-  else if (pm <= 24) launch_products<24, Q>(items, zs_one, B, NQ, crow, herm, s0, ns, p0, accumulate, Y, nitems, s);
-  else if (pm <= 32) launch_products<32, Q>(items, zs_one, B, NQ, crow, herm, s0, ns, p0, accumulate, Y, nitems, s);
-  else launch_products<kBinsPMax, Q>(items, zs_one, B, NQ, crow, herm, s0, ns, p0, accumulate, Y, nitems, s);
+#define RF_BINS_PM(PMV)                                                                                          \
+  if (pm <= PMV) return launch_products<PMV, Q>(items, zs_one, B, NQ, crow, herm, s0, ns, p0, accumulate, Y, \
+                                                nitems, s);
+  RF_BINS_PM(8)
+  if constexpr (Q == 2) {
+    RF_BINS_PM(12)
+  }
+  RF_BINS_PM(16)
+  if constexpr (Q == 2) {
+    RF_BINS_PM(20)
+  }
+  RF_BINS_PM(24)
+  if constexpr (Q == 2) {
+    RF_BINS_PM(28)
+  }
+  RF_BINS_PM(32)
+  if constexpr (Q == 2) {
+    RF_BINS_PM(36)
+  }
+#undef RF_BINS_PM
+  launch_products<kBinsPMax, Q>(items, zs_one, B, NQ, crow, herm, s0, ns, p0, accumulate, Y, nitems, s);
 }
 
 template <int B, int Q, bool WINMAX>

@@ -2,7 +2,7 @@
 form per bin over runs of output blocks, then the block transforms; against the FP64 oracle's
 direct sum (Eq. 8) on full series, at sampled outputs and on window peaks, for single-reference
 and batched calls, complex and real-form kernels, partition ratios 2 and 4, and kernels of more
-than 40 partitions (several passes over the register window)."""
+partitions than one pass over the register window holds (40)."""
 import numpy as np
 import pytest
 
@@ -76,16 +76,21 @@ def test_two_phase_single_reference(torch, B, Lp, real):
     _check_peaks(P.cpu().numpy(), A.cpu().numpy(), zs, W)
 
 
-def test_two_phase_many_partitions(torch):
-    """Kernels of up to 60 partitions (two passes over the 40-partition register window, the
-    second adding to the buffer), sampled outputs by the oracle's defining sum."""
-    n, W = 1 << 16, 2048
+@pytest.mark.parametrize("n,Lp,lengths", [
+    # Q = 4: up to 59 partitions, two passes (the second adding to the buffer)
+    (1 << 16, 1024, [60000, 49 * 1024, 48 * 1024, 30000, 47 * 1024 + 1, 40 * 1024, 40 * 1024 + 1, 32 * 1024 + 1]),
+    # Q = 2: up to 44 partitions, two passes
+    (1 << 17, 2048, [90000, 80 * 1024, 80 * 1024 + 1, 10000, 82 * 1024 + 1]),
+])
+def test_two_phase_many_partitions(torch, n, Lp, lengths):
+    """Kernels of more partitions than one phase-1 pass holds (several passes over the register
+    window, the later ones adding to the buffer), sampled outputs by the oracle's defining sum."""
+    W = 2048
     rng = np.random.default_rng(60)
-    lengths = [60000, 49 * 1024, 48 * 1024, 30000, 47 * 1024 + 1, 40 * 1024, 40 * 1024 + 1, 32 * 1024 + 1]
     lags, taps = _random_set(rng, n, lengths)
     rf = _rf(n)
     kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
-    kern.prepare_forms([0], ["os_bins"], ["native"], [4096], [1024])
+    kern.prepare_forms([0], ["os_bins"], ["native"], [4096], [Lp])
     z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
     zt = torch.tensor(z, device="cuda")
     out = rf.reconstruct(zt, kern, "auto").cpu().numpy()
