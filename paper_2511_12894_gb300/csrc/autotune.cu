@@ -185,9 +185,12 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
       }
       // ... and three buckets: the two-phase form only for the kernels of many partitions (at
       // least 4, 8 or 16), where its per-bin sums pay for the buffer round trip
+      // The two-phase form also runs 32768-point blocks on CTA pairs (Lp = 16384: half the
+      // partitions of Lp = 8192, so half the per-bin multiply-adds, for a block tail on two SMs).
       std::vector<Cand> twos;
       int32_t lmax = 0;
       for (int g = 0; g < G; ++g) lmax = std::max(lmax, ks[g]->max_len);
+      const bool pair_ok = !ks[0]->real && c->n >= 32768;
       for (const Cand& cd : extra)
         if (cd.cut && cd.algo == RF_ALGO_OS && cd.algo2 == RF_ALGO_OS && bins_layout_ok(cd.block2, cd.part2)) {
           Cand t = cd;
@@ -202,6 +205,11 @@ void autotune_impl(rf_ctx* c, int32_t G, const void* const* z_refs, rf_kernels* 
             three.part3 = cd.part2;
             three.algo3 = RF_ALGO_OS_BINS;
             twos.push_back(three);
+            if (pair_ok && cd.block2 == 16384) {
+              three.block3 = 32768;
+              three.part3 = 16384;
+              twos.push_back(three);
+            }
           }
         }
       extra.insert(extra.end(), twos.begin(), twos.end());

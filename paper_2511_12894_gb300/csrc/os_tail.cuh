@@ -1,10 +1,13 @@
 // Overlap-save block epilogue shared by the single-pass and two-phase forms: the window-peak
 // key packing and warp reduction, the per-thread window scan, and the tail of an output block
-// (inverse block transform, then the series or the fused window peaks).
+// (inverse block transform, then the series or the fused window peaks), on one CTA or, for
+// 32768-point blocks, on a CTA pair.
 //
 // A window peak is kept as a 64-bit key (float bits of |z|^2) << 32 | (2^32 - 1 - i), so that
 // atomicMax orders by value and then by the smallest index.
 #pragma once
+
+#include <cstdint>
 
 #include "blockfft.cuh"
 
@@ -163,5 +166,110 @@ __device__ __forceinline__ void os_block_tail(float2 (&v)[16], int s, int64_t m0
     __syncthreads();  // mag (shared memory) is reused by the next block's FFT
   }
 }
+
+// ------------------------------------------------------- 32768-point blocks on CTA pairs
+// A block of B2 = 32768 points is split by the parity of its bins between the two CTAs of a
+// cluster: CTA r holds Y[2k' + r], k' < BH = 16384, and transforms it with the 16384-point
+// block FFT; the halves combine as
+//   y[t] = E0[t] + w^t E1[t],  y[t + BH] = E0[t] - w^t E1[t],  t < BH,  w = exp(+2 pi i / B2),
+// each CTA computing half of the t and reading the other CTA's half from distributed shared
+// memory.  Spectra of this layout are stored parity-split: bin 2k' + r at r BH + k'.
+constexpr int kBH = 16384;
+constexpr int kB2 = 2 * kBH;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of both CTAs arrives; memory written before is visible after (release/acquire).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_peer_addr(const void* p, unsigned rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ float2 ld_peer_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+// Tail of output block s of one neighbour on a CTA pair: v holds this CTA's parity half of the
+// block's partition sums (bins r BH + tid + t BH/16 of the parity-split row).  Both CTAs call
+// it for the same blocks and so pass the same cluster barriers: transform, store the half in
+// shared memory, barrier, combine (reading the peer's half), barrier (the peer is done with
+// this CTA's half, so the next transform may rewrite it), then the outputs at block positions
+// LP .. B2 - 1 go to the series row zrow or, as window peaks, into the keys row kj.
+// Shared memory: the block FFT's, then BH floats of magnitudes.  r: this CTA's rank in the
+// pair; peer: the peer CTA's sm (cluster_peer_addr(sm, r ^ 1)).
+template <int Q, bool WINMAX>
+__device__ __forceinline__ void os2_block_tail(float2 (&v)[16], int s, int64_t m0, int64_t n,
+                                               float2* __restrict__ zrow, unsigned long long* __restrict__ kj,
+                                               int64_t W, int64_t nw, int fastwin, const float2* __restrict__ tw,
+                                               const float2* __restrict__ twc, float2* sm, unsigned r, uint32_t peer) {
+  using S = BlockFFTShape<kBH>;
+  constexpr int NT = S::NT;
+  constexpr int RL = S::RL;
+  constexpr int LP = kB2 / Q;  // outputs start at block position LP (<= BH)
+  constexpr int H = kB2 - LP;
+  static_assert(Q == 2 || Q == 4, "partition ratio");
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  const int tb = (int)r * (kBH / 2) + tid * 8;  // this thread's first position in the scan
+  float* mag_lo = reinterpret_cast<float*>(sm + S::SMEM);  // |y|^2 of t, per CTA range
+  float* mag_hi = mag_lo + kBH / 2;                         // |y|^2 of t + BH
+  block_fft<kBH, +1>(v, sm, tw);
+  __syncthreads();  // the last stage has read shared memory
+#pragma unroll
+  for (int qq = 0; qq < 16 / RL; ++qq)
+#pragma unroll
+    for (int t = 0; t < RL; ++t) sm[tid + qq * NT + t * (kBH / RL)] = v[qq * RL + t];
+  cluster_sync_all();  // both halves in shared memory
+  // combine: this CTA takes t = r BH/2 + e NT + tid, e < 8 (consecutive lanes, consecutive t)
+  const int64_t o0 = (int64_t)s * H;  // pre-relabel index of block position LP
+  const int64_t lim = n - o0;         // positions LP + u with u < lim exist
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int t = (int)r * (kBH / 2) + e * NT + tid;
+    const float2 eo = sm[t];
+    const float2 ep = ld_peer_f2(peer + (uint32_t)t * 8u);
+    const float2 e0 = r ? ep : eo;
+    const float2 e1 = r ? eo : ep;
+    const float2 x = cmulc(e1, __ldg(twc + t));  // w^t E1, twc = exp(-2 pi i t / B2)
+    const float2 ylo = cadd(e0, x), yhi = csub(e0, x);
+    if (!WINMAX) {
+      if (t >= LP && t - LP < lim) zrow[(o0 + m0 + t - LP) & mask] = ylo;
+      if (t + kBH - LP < lim) zrow[(o0 + m0 + t + kBH - LP) & mask] = yhi;
+    } else {
+      mag_lo[e * NT + tid] = ylo.x * ylo.x + ylo.y * ylo.y;
+      mag_hi[e * NT + tid] = yhi.x * yhi.x + yhi.y * yhi.y;
+    }
+  }
+  cluster_sync_all();  // the peer has read this CTA's half; the magnitudes are in place
+  if (WINMAX) {
+    // runs of 8 consecutive positions per thread: t = tb + e (kept when tb >= LP; LP and tb
+    // are multiples of 8) and t = tb + BH + e (always kept since LP <= BH)
+    float ml[8], mh[8];
+    *reinterpret_cast<float4*>(ml) = *reinterpret_cast<const float4*>(mag_lo + tid * 8);
+    *reinterpret_cast<float4*>(ml + 4) = *reinterpret_cast<const float4*>(mag_lo + tid * 8 + 4);
+    *reinterpret_cast<float4*>(mh) = *reinterpret_cast<const float4*>(mag_hi + tid * 8);
+    *reinterpret_cast<float4*>(mh + 4) = *reinterpret_cast<const float4*>(mag_hi + tid * 8 + 4);
+    auto count = [&](int64_t u0) { return u0 >= lim ? 0 : (lim - u0 >= 8 ? 8 : (int)(lim - u0)); };
+    const int cl = tb >= LP ? count(tb - LP) : 0;
+    const int ch = count(tb + kBH - LP);
+    window_keys<8>(ml, cl, (int)((o0 + m0 + tb - LP) & mask), n, W, nw, fastwin, kj);
+    window_keys<8>(mh, ch, (int)((o0 + m0 + tb + kBH - LP) & mask), n, W, nw, fastwin, kj);
+  }
+}
+
+// Shared memory of a CTA of the pair layout: the block FFT's and the magnitudes.
+constexpr size_t os2_tail_smem() { return sizeof(float2) * BlockFFTShape<kBH>::SMEM + sizeof(float) * kBH; }
 
 }  // namespace rf

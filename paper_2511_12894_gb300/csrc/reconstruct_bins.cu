@@ -182,6 +182,26 @@ __global__ void __launch_bounds__(B / 16, 16384 / B)
                               WINMAX ? keys + it.row * nw : nullptr, W, nw, fastwin, tw, sm);
 }
 
+// Phase 2 of the pair layout (B = 32768, Q = 2): cluster (s - s0, item); CTA r loads its
+// parity half of the block's partition sums and runs the pair's block tail.
+template <bool WINMAX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBH / 16, 1)
+    k_bins_tail2(const OsItem* __restrict__ items, const float2* __restrict__ Y, int s0, int ns,
+                 const float2* __restrict__ tw, const float2* __restrict__ twc, int64_t n, float2* __restrict__ z_out,
+                 unsigned long long* __restrict__ keys, int64_t W, int64_t nw, int fastwin) {
+  extern __shared__ float2 sm[];
+  const int si = (int)(blockIdx.x >> 1), ii = blockIdx.y;
+  const unsigned r = cluster_rank();
+  const OsItem it = items[ii];
+  const float2* y = Y + ((int64_t)ii * ns + si) * kB2 + (int64_t)r * kBH + threadIdx.x;
+  float2 v[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) v[t] = __ldcg(y + t * (kBH / 16));
+  os2_block_tail<2, WINMAX>(v, s0 + si, it.lag0, n, WINMAX ? nullptr : z_out + it.row * n,
+                            WINMAX ? keys + it.row * nw : nullptr, W, nw, fastwin, tw, twc, sm, r,
+                            cluster_peer_addr(sm, r ^ 1u));
+}
+
 template <int PM, int Q>
 void launch_products(const OsItem* items, const float2* zs_one, int B, int NQ, int crow, int herm, int s0, int ns,
                      int p0, int accumulate, float2* Y, int nitems, cudaStream_t s) {
@@ -230,6 +250,19 @@ void launch_tail(const OsItem* items, const float2* Y, int s0, int ns, int nitem
 }
 
 template <bool WINMAX>
+void launch_tail2(const OsItem* items, const float2* Y, int s0, int ns, int nitems, const float2* tw,
+                  const float2* twc, int64_t n, float2* z_out, unsigned long long* keys, int64_t W, int64_t nw,
+                  cudaStream_t s) {
+  auto fn = k_bins_tail2<WINMAX>;
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os2_tail_smem()));
+  // a warp's scan covers 256 consecutive positions: at most two windows when W >= 256
+  const int fastwin = (WINMAX && W >= 256) ? 1 : 0;
+  fn<<<dim3((unsigned)(2 * ns), (unsigned)nitems), kBH / 16, os2_tail_smem(), s>>>(items, Y, s0, ns, tw, twc, n, z_out,
+                                                                                  keys, W, nw, fastwin);
+  RF_LAUNCHED();
+}
+
+template <bool WINMAX>
 void tail_bq(int B, int Q, const OsItem* items, const float2* Y, int s0, int ns, int nitems, const float2* tw,
              int64_t n, float2* z_out, unsigned long long* keys, int64_t W, int64_t nw, int fastwin, cudaStream_t s) {
 #define RF_BINS_TAIL(BB, QQ) \
@@ -247,11 +280,13 @@ void tail_bq(int B, int Q, const OsItem* items, const float2* Y, int s0, int ns,
 }  // namespace
 
 bool bins_layout_ok(int B, int Lp) {
-  return (B == 4096 || B == 8192 || B == 16384) && (Lp == B / 2 || Lp == B / 4);
+  return ((B == 4096 || B == 8192 || B == 16384) && (Lp == B / 2 || Lp == B / 4)) || (B == kB2 && Lp == kBH);
 }
 
 BinsPlan bins_plan(std::vector<OsItem> items, int B, int Lp, bool herm, int64_t n) {
-  RF_REQUIRE(bins_layout_ok(B, Lp), "two-phase overlap-save takes B in {4096, 8192, 16384} and Lp = B/2 or B/4");
+  RF_REQUIRE(bins_layout_ok(B, Lp), "two-phase overlap-save takes B in {4096, 8192, 16384} with Lp = B/2 or B/4, "
+                                    "or B = 32768 with Lp = 16384");
+  RF_REQUIRE(!(herm && B == kB2), "real-form kernels take two-phase blocks of at most 16384 points");
   BinsPlan pl;
   pl.B = B;
   pl.Lp = Lp;
@@ -297,10 +332,18 @@ void bins_run(rf_ctx* c, const BinsPlan& pl, const OsItem* items_dev, const floa
       else
         products_pm<4>(pm, it, zs_one, B, pl.NQ, crow, pl.herm, wv.s0, wv.ns, p0, p0 > 0, Y, wv.nitems, s);
     }
-    if (win)
+    if (B == kB2) {
+      const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
+      const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
+      if (win)
+        launch_tail2<true>(it, Y, wv.s0, wv.ns, wv.nitems, tw, twc, n, nullptr, keys, W, nw, s);
+      else
+        launch_tail2<false>(it, Y, wv.s0, wv.ns, wv.nitems, tw, twc, n, z_out, nullptr, W, 0, s);
+    } else if (win) {
       tail_bq<true>(B, Q, it, Y, wv.s0, wv.ns, wv.nitems, twb, n, nullptr, keys, W, nw, fastwin, s);
-    else
+    } else {
       tail_bq<false>(B, Q, it, Y, wv.s0, wv.ns, wv.nitems, twb, n, z_out, nullptr, W, 0, 0, s);
+    }
   }
 }
 

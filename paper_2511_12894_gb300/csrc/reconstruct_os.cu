@@ -229,39 +229,8 @@ __global__ void k_os_round_half(const double2* __restrict__ spec, int rows, int 
   out[i] = v;
 }
 
-// ------------------------------------------------------- 32768-point blocks on CTA pairs
-// A block of B2 = 32768 points is split by the parity of its bins between the two CTAs of a
-// cluster: CTA r holds Y[2k' + r], k' < BH = 16384, and transforms it with the 16384-point
-// block FFT; the halves combine as
-//   y[t] = E0[t] + w^t E1[t],  y[t + BH] = E0[t] - w^t E1[t],  t < BH,  w = exp(+2 pi i / B2),
-// each CTA computing half of the t and reading the other CTA's half from distributed shared
-// memory.  Spectra of this layout are stored parity-split: bin 2k' + r at r BH + k'.
-constexpr int kBH = 16384;
-constexpr int kB2 = 2 * kBH;
-
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// Every thread of both CTAs arrives; memory written before is visible after (release/acquire).
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_peer_addr(const void* p, unsigned rank) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
-
-__device__ __forceinline__ float2 ld_peer_f2(uint32_t addr) {
-  float2 v;
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
-  return v;
-}
+// 32768-point blocks on CTA pairs: the layout, the cluster helpers and the block tail are in
+// os_tail.cuh.
 
 // Segment spectra of the B2 layout (no cluster needed): block (q, r, g) transforms
 //   u_0[m] = x[m] + x[m + BH],  u_1[m] = (x[m] - x[m + BH]) exp(-2 pi i m / B2),
@@ -324,10 +293,8 @@ __device__ __forceinline__ void os2_products(float2 (&v)[16], const float2* __re
   }
 }
 
-// Output blocks [s0, s1) of one neighbour on a CTA pair.  Both CTAs run the same blocks and
-// so pass the same cluster barriers: per block, transform, store the half in shared memory,
-// barrier, combine (reading the peer's half), barrier (the peer is done with this CTA's half,
-// so the next transform may rewrite it), window scan.
+// Output blocks [s0, s1) of one neighbour on a CTA pair: per block, this CTA's parity half of
+// the spectral products, then the pair's block tail (os_tail.cuh).
 // Zs: the reference's segment spectra [NQ][B2]; C: the neighbour's partition spectra [P][B2],
 // both parity-split.
 template <int Q, bool WINMAX>
@@ -336,64 +303,14 @@ __device__ __forceinline__ void os2_blocks(const float2* __restrict__ Zs, const 
                                            int64_t n, int NQ, int s0, int s1, float2* __restrict__ zrow,
                                            unsigned long long* __restrict__ kj, int64_t W, int64_t nw, int fastwin,
                                            float2* sm) {
-  using S = BlockFFTShape<kBH>;
-  constexpr int NT = S::NT;
-  constexpr int RL = S::RL;
-  constexpr int LP = kB2 / Q;  // outputs start at block position LP (<= BH)
-  constexpr int H = kB2 - LP;
   static_assert(Q == 2 || Q == 4, "partition ratio");
   const unsigned r = cluster_rank();
-  const int tid = threadIdx.x;
-  const int64_t mask = n - 1;
   const uint32_t peer = cluster_peer_addr(sm, r ^ 1u);
-  const int tb = (int)r * (kBH / 2) + tid * 8;  // this thread's first position in the scan
-  float* mag_lo = reinterpret_cast<float*>(sm + S::SMEM);  // |y|^2 of t, per CTA range
-  float* mag_hi = mag_lo + kBH / 2;                         // |y|^2 of t + BH
+  const int tid = threadIdx.x;
   for (int s = s0; s < s1; ++s) {
     float2 v[16];
     os2_products<Q>(v, Zs, C, P, NQ, s, r, tid);
-    block_fft<kBH, +1>(v, sm, tw);
-    __syncthreads();  // the last stage has read shared memory
-#pragma unroll
-    for (int qq = 0; qq < 16 / RL; ++qq)
-#pragma unroll
-      for (int t = 0; t < RL; ++t) sm[tid + qq * NT + t * (kBH / RL)] = v[qq * RL + t];
-    cluster_sync_all();  // both halves in shared memory
-    // combine: this CTA takes t = r BH/2 + e NT + tid, e < 8 (consecutive lanes, consecutive t)
-    const int64_t o0 = (int64_t)s * H;  // pre-relabel index of block position LP
-    const int64_t lim = n - o0;         // positions LP + u with u < lim exist
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int t = (int)r * (kBH / 2) + e * NT + tid;
-      const float2 eo = sm[t];
-      const float2 ep = ld_peer_f2(peer + (uint32_t)t * 8u);
-      const float2 e0 = r ? ep : eo;
-      const float2 e1 = r ? eo : ep;
-      const float2 x = cmulc(e1, __ldg(twc + t));  // w^t E1, twc = exp(-2 pi i t / B2)
-      const float2 ylo = cadd(e0, x), yhi = csub(e0, x);
-      if (!WINMAX) {
-        if (t >= LP && t - LP < lim) zrow[(o0 + m0 + t - LP) & mask] = ylo;
-        if (t + kBH - LP < lim) zrow[(o0 + m0 + t + kBH - LP) & mask] = yhi;
-      } else {
-        mag_lo[e * NT + tid] = ylo.x * ylo.x + ylo.y * ylo.y;
-        mag_hi[e * NT + tid] = yhi.x * yhi.x + yhi.y * yhi.y;
-      }
-    }
-    cluster_sync_all();  // the peer has read this CTA's half; the magnitudes are in place
-    if (WINMAX) {
-      // runs of 8 consecutive positions per thread: t = tb + e (kept when tb >= LP; LP and tb
-      // are multiples of 8) and t = tb + BH + e (always kept since LP <= BH)
-      float ml[8], mh[8];
-      *reinterpret_cast<float4*>(ml) = *reinterpret_cast<const float4*>(mag_lo + tid * 8);
-      *reinterpret_cast<float4*>(ml + 4) = *reinterpret_cast<const float4*>(mag_lo + tid * 8 + 4);
-      *reinterpret_cast<float4*>(mh) = *reinterpret_cast<const float4*>(mag_hi + tid * 8);
-      *reinterpret_cast<float4*>(mh + 4) = *reinterpret_cast<const float4*>(mag_hi + tid * 8 + 4);
-      auto count = [&](int64_t u0) { return u0 >= lim ? 0 : (lim - u0 >= 8 ? 8 : (int)(lim - u0)); };
-      const int cl = tb >= LP ? count(tb - LP) : 0;
-      const int ch = count(tb + kBH - LP);
-      window_keys<8>(ml, cl, (int)((o0 + m0 + tb - LP) & mask), n, W, nw, fastwin, kj);
-      window_keys<8>(mh, ch, (int)((o0 + m0 + tb + kBH - LP) & mask), n, W, nw, fastwin, kj);
-    }
+    os2_block_tail<Q, WINMAX>(v, s, m0, n, zrow, kj, W, nw, fastwin, tw, twc, sm, r, peer);
   }
 }
 
@@ -434,9 +351,6 @@ __global__ void k_os2_round(const double2* __restrict__ spec, int64_t count, dou
   out[(i - k) + (k & 1) * kBH + (k >> 1)] = make_float2((float)(spec[i].x * scale), (float)(spec[i].y * scale));
 }
 
-// dynamic shared memory of the pair kernels: the 16384-point transform plus two 8192-float
-// |y|^2 staging rows
-size_t os2_smem();
 
 template <int B>
 size_t os_smem() {
@@ -485,7 +399,9 @@ void launch_os(rf_ctx* c, const rf_kernels* kern, const OsBucket& bk, const floa
   }
 }
 
-size_t os2_smem() { return os_smem<kBH>() + sizeof(float) * kBH; }
+// dynamic shared memory of the pair kernels: the 16384-point transform plus two 8192-float
+// |y|^2 staging rows
+size_t os2_smem() { return os2_tail_smem(); }
 
 // Segment spectra of the pair layout for one reference (z_many == nullptr) or G of them.
 void launch_os2_segments(rf_ctx* c, const float2* z_one, const float2* const* z_many, int G, int Lp, float2* Zs,
@@ -768,8 +684,8 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
     } else if (o.algo == RF_ALGO_OS_BINS) {
       check_layout(c, o.block, o.part, kern->real);
       RF_REQUIRE(bins_layout_ok(o.block, o.part),
-                 "two-phase overlap-save takes B in {4096, 8192, 16384} and Lp = B/2 or B/4 (got %d, %d)", o.block,
-                 o.part);
+                 "two-phase overlap-save takes B in {4096, 8192, 16384} with Lp = B/2 or B/4, or B = 32768 with "
+                 "Lp = 16384 (got %d, %d)", o.block, o.part);
     } else if (o.algo == RF_ALGO_GEMM) {
       RF_REQUIRE(o.prec >= RF_PREC_BF16 && o.prec <= RF_PREC_3XTF32, "a tensor-core bucket needs a split precision");
       RF_REQUIRE(c->n % 128 == 0, "the tensor-core form needs n to be a multiple of 128");
@@ -960,10 +876,13 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
     if (bk.idx.empty()) continue;
     if (bk.algo == RF_ALGO_OS_BINS) {
       // the bucket's segment spectra, then the two-phase launches of its plan
-      dispatch_bq(bk.B, bk.B / bk.Lp, [&](auto bc, auto qc) {
-        constexpr int BB = decltype(bc)::value;
-        launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), bk.Lp, Zs, s);
-      });
+      if (bk.B == kB2)
+        launch_os2_segments(c, static_cast<const float2*>(z_ref), nullptr, 1, bk.Lp, Zs, s);
+      else
+        dispatch_bq(bk.B, bk.B / bk.Lp, [&](auto bc, auto qc) {
+          constexpr int BB = decltype(bc)::value;
+          launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), bk.Lp, Zs, s);
+        });
       c->bins_y.ensure(bk.bins->y_bytes);
       bins_run(c, *bk.bins, bk.bins_items_d.as<OsItem>(), Zs, c->bins_y.as<float2>(),
                win ? nullptr : static_cast<float2*>(z_out), win ? keys : nullptr, W, s);
@@ -1158,15 +1077,18 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
     if (spec[b].algo == RF_ALGO_OS_BINS) {
       const BinsPlan& pl = *c->batch_bins[b];
       if (pl.items.empty()) continue;
-      dispatch_bq(Bs[b], Bs[b] / Lps[b], [&](auto bc, auto qc) {
-        constexpr int BB = decltype(bc)::value;
-        const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<BB>::LOGB];
-        auto seg = k_os_segments_batched<BB>;
-        RF_CUDA(cudaFuncSetAttribute(seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
-        seg<<<dim3((unsigned)(n / Lps[b]), (unsigned)G), BB / 16, os_smem<BB>(), s>>>(
-            c->batch_zptr.as<const float2*>(), n, Lps[b], tw, c->batch_zs.as<float2>());
-        RF_LAUNCHED();
-      });
+      if (Bs[b] == kB2)
+        launch_os2_segments(c, nullptr, c->batch_zptr.as<const float2*>(), G, Lps[b], c->batch_zs.as<float2>(), s);
+      else
+        dispatch_bq(Bs[b], Bs[b] / Lps[b], [&](auto bc, auto qc) {
+          constexpr int BB = decltype(bc)::value;
+          const float2* tw = c->twb32.as<float2>() + c->twb_off[BlockFFTShape<BB>::LOGB];
+          auto seg = k_os_segments_batched<BB>;
+          RF_CUDA(cudaFuncSetAttribute(seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem<BB>()));
+          seg<<<dim3((unsigned)(n / Lps[b]), (unsigned)G), BB / 16, os_smem<BB>(), s>>>(
+              c->batch_zptr.as<const float2*>(), n, Lps[b], tw, c->batch_zs.as<float2>());
+          RF_LAUNCHED();
+        });
       bins_run(c, pl, c->batch_bins_items.as<OsItem>() + c->batch_bins_off[b], nullptr, c->bins_y.as<float2>(),
                nullptr, keys, W, s);
       continue;

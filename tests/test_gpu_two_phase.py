@@ -76,21 +76,25 @@ def test_two_phase_single_reference(torch, B, Lp, real):
     _check_peaks(P.cpu().numpy(), A.cpu().numpy(), zs, W)
 
 
-@pytest.mark.parametrize("n,Lp,lengths", [
+@pytest.mark.parametrize("n,B,Lp,lengths", [
     # Q = 4: up to 59 partitions, two passes (the second adding to the buffer)
-    (1 << 16, 1024, [60000, 49 * 1024, 48 * 1024, 30000, 47 * 1024 + 1, 40 * 1024, 40 * 1024 + 1, 32 * 1024 + 1]),
+    (1 << 16, 4096, 1024, [60000, 49 * 1024, 48 * 1024, 30000, 47 * 1024 + 1, 40 * 1024, 40 * 1024 + 1,
+                           32 * 1024 + 1]),
     # Q = 2: up to 44 partitions, two passes
-    (1 << 17, 2048, [90000, 80 * 1024, 80 * 1024 + 1, 10000, 82 * 1024 + 1]),
+    (1 << 17, 4096, 2048, [90000, 80 * 1024, 80 * 1024 + 1, 10000, 82 * 1024 + 1]),
+    # 32768-point blocks on CTA pairs (parity-split spectra, the pair's block tail)
+    (1 << 17, 32768, 16384, [90000, 5 * 16384, 5 * 16384 + 1, 10000, 16384, 1, 300]),
 ])
-def test_two_phase_many_partitions(torch, n, Lp, lengths):
+def test_two_phase_many_partitions(torch, n, B, Lp, lengths):
     """Kernels of more partitions than one phase-1 pass holds (several passes over the register
-    window, the later ones adding to the buffer), sampled outputs by the oracle's defining sum."""
+    window, the later ones adding to the buffer), and the pair layout, sampled outputs by the
+    oracle's defining sum."""
     W = 2048
     rng = np.random.default_rng(60)
     lags, taps = _random_set(rng, n, lengths)
     rf = _rf(n)
     kern = rf.kernels_import(lags, lengths, np.concatenate(taps))
-    kern.prepare_forms([0], ["os_bins"], ["native"], [4096], [Lp])
+    kern.prepare_forms([0], ["os_bins"], ["native"], [B], [Lp])
     z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
     zt = torch.tensor(z, device="cuda")
     out = rf.reconstruct(zt, kern, "auto").cpu().numpy()
@@ -112,17 +116,23 @@ def test_two_phase_many_partitions(torch, n, Lp, lengths):
         assert np.abs(np.sqrt(P[j]) - np.sqrt(Pg)).max() <= TOL32 * zmax
 
 
-def test_two_phase_batched_next_to_single_pass(torch):
+@pytest.mark.parametrize("n,B2,Lp2,long_lengths", [
+    (1 << 15, 8192, 2048, (7000, 12000, 9000, 4000)),
+    # the pair layout's two-phase bucket (32768-point blocks on CTA pairs)
+    (1 << 16, 32768, 16384, (7000, 20000, 17000, 4000)),
+])
+def test_two_phase_batched_next_to_single_pass(torch, n, B2, Lp2, long_lengths):
     """Three references: single-pass overlap-save below 3000 taps, two-phase above, one batched
     call (the two-phase launches cover every reference's long kernels together)."""
-    n, W = 1 << 15, 1024
+    W = 1024
     rng = np.random.default_rng(33)
     rf = _rf(n)
     kerns, zts, zss = [], [], []
-    for lengths in ([300, 7000, 12000], [3000], [10, 2999, 9000, 4000, 1]):
+    a, b, c, d = long_lengths
+    for lengths in ([300, a, b], [3000], [10, 2999, c, d, 1]):
         lags, taps = _random_set(rng, n, lengths)
         k = rf.kernels_import(lags, lengths, np.concatenate(taps))
-        k.prepare_forms([0, 3000], ["os", "os_bins"], ["native", "native"], [4096, 8192], [1024, 2048])
+        k.prepare_forms([0, 3000], ["os", "os_bins"], ["native", "native"], [4096, B2], [1024, Lp2])
         z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
         kerns.append(k)
         zts.append(torch.tensor(z, device="cuda"))
@@ -143,7 +153,9 @@ def test_two_phase_layouts_refused(torch):
     lags, taps = _random_set(rng, n, [100, 5000])
     rf = _rf(n)
     kern = rf.kernels_import(lags, [100, 5000], np.concatenate(taps))
-    with pytest.raises(RFError):   # block sizes 4096, 8192, 16384 only
+    with pytest.raises(RFError):   # block sizes 4096, 8192, 16384 (and 32768 on CTA pairs) only
         kern.prepare_forms([0], ["os_bins"], ["native"], [2048], [1024])
     with pytest.raises(RFError):   # partitions of B/2 or B/4
         kern.prepare_forms([0], ["os_bins"], ["native"], [8192], [1024])
+    with pytest.raises(RFError):   # the pair layout with partitions of B/2 only
+        kern.prepare_forms([0], ["os_bins"], ["native"], [32768], [8192])
