@@ -182,24 +182,79 @@ __global__ void __launch_bounds__(B / 16, 16384 / B)
                               WINMAX ? keys + it.row * nw : nullptr, W, nw, fastwin, tw, sm);
 }
 
-// Phase 2 of the pair layout (B = 32768, Q = 2): cluster (s - s0, item); CTA r loads its
-// parity half of the block's partition sums and runs the pair's block tail.
+// Phase 2 of the 32768-point layout (Q = 2: the kept outputs are block positions BH .. B2 - 1).
+// With the partition sums split by bin parity (Y[2k' + r] at r BH + k'), the inverse transforms
+// E_r of the two halves give y[t + BH] = E_0[t] - w^t E_1[t], w = exp(+2 pi i / B2), t < BH.
+// One CTA runs both 16384-point transforms in turn, parking E_0 in a per-CTA row of global
+// scratch (L2-resident: one row per resident CTA) and staging E_1 in shared memory, so the pair
+// needs no cluster exchange.  Shared memory: the transform's, then BH magnitudes.
+// Persistent: CTA b takes the units u = b, b + gridDim.x, .. of the wave's (item, block) units.
 template <bool WINMAX>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBH / 16, 1)
-    k_bins_tail2(const OsItem* __restrict__ items, const float2* __restrict__ Y, int s0, int ns,
-                 const float2* __restrict__ tw, const float2* __restrict__ twc, int64_t n, float2* __restrict__ z_out,
-                 unsigned long long* __restrict__ keys, int64_t W, int64_t nw, int fastwin) {
+__global__ void __launch_bounds__(kBH / 16, 1)
+    k_bins_tail_pair(const OsItem* __restrict__ items, const float2* __restrict__ Y, int s0, int ns, int units,
+                     const float2* __restrict__ tw, const float2* __restrict__ twc, int64_t n,
+                     float2* __restrict__ z_out, unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
+                     int fastwin, float2* __restrict__ e0_all) {
+  using S = BlockFFTShape<kBH>;
+  constexpr int NT = S::NT;
+  constexpr int RL = S::RL;
+  constexpr int CH = kBH / NT;  // kept outputs per thread in the window scan
   extern __shared__ float2 sm[];
-  const int si = (int)(blockIdx.x >> 1), ii = blockIdx.y;
-  const unsigned r = cluster_rank();
-  const OsItem it = items[ii];
-  const float2* y = Y + ((int64_t)ii * ns + si) * kB2 + (int64_t)r * kBH + threadIdx.x;
-  float2 v[16];
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  float2* e0 = e0_all + (int64_t)blockIdx.x * kBH;
+  float* mag = reinterpret_cast<float*>(sm + S::SMEM);
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int ii = u / ns, si = u - ii * ns;
+    const float2* y = Y + ((int64_t)u) * kB2 + tid;  // unit u = (item ii, block si) of the wave
+    // E_0 (even bins) to the scratch row in natural order, then E_1 (odd bins) staged in shared
+    // memory in natural order; one loop body, so that the code holds one transform
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      float2 v[16];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) v[t] = __ldcg(y + t * (kBH / 16));
-  os2_block_tail<2, WINMAX>(v, s0 + si, it.lag0, n, WINMAX ? nullptr : z_out + it.row * n,
-                            WINMAX ? keys + it.row * nw : nullptr, W, nw, fastwin, tw, twc, sm, r,
-                            cluster_peer_addr(sm, r ^ 1u));
+      for (int t = 0; t < 16; ++t) v[t] = __ldcg(y + h * kBH + t * NT);
+      block_fft<kBH, +1>(v, sm, tw);
+      __syncthreads();  // the last stage has read shared memory
+#pragma unroll
+      for (int q = 0; q < 16 / RL; ++q)
+#pragma unroll
+        for (int t = 0; t < RL; ++t) {
+          const int idx = tid + q * NT + t * (kBH / RL);
+          if (h == 0)
+            __stcg(e0 + idx, v[q * RL + t]);
+          else
+            sm[idx] = v[q * RL + t];
+        }
+    }
+    __syncthreads();  // E_1 staged; E_0 of every thread written to the scratch row
+    const int64_t lag0 = items[ii].lag0, row = items[ii].row;  // read after the transforms
+    const int64_t o0 = (int64_t)(s0 + si) * kBH;  // pre-relabel index of block position BH
+    const int64_t base = (o0 + lag0) & mask;
+    const int64_t lim = n - o0;                   // kept positions BH + t with t < lim exist
+    // y[t + BH] = E_0[t] - w^t E_1[t] at t = tid + j NT (consecutive lanes, consecutive t)
+#pragma unroll 4
+    for (int j = 0; j < 16; ++j) {
+      const int idx = tid + j * NT;
+      const float2 yh = csub(__ldcg(e0 + idx), cmulc(sm[idx], __ldg(twc + idx)));
+      if (!WINMAX) {
+        if (idx < lim) z_out[row * n + ((base + idx) & mask)] = yh;
+      } else {
+        mag[idx] = yh.x * yh.x + yh.y * yh.y;
+      }
+    }
+    if (WINMAX) {
+      __syncthreads();
+      float mv[CH];
+#pragma unroll
+      for (int e = 0; e < CH; e += 4)
+        *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + tid * CH + e);
+      const int64_t avail = lim - (int64_t)tid * CH;
+      const int cnt = avail <= 0 ? 0 : (avail >= CH ? CH : (int)avail);
+      window_keys<CH>(mv, cnt, (int)((base + (int64_t)tid * CH) & mask), n, W, nw, fastwin, keys + row * nw);
+    }
+    __syncthreads();  // shared memory and the scratch row are reused by the next unit
+  }
 }
 
 template <int PM, int Q>
@@ -250,15 +305,21 @@ void launch_tail(const OsItem* items, const float2* Y, int s0, int ns, int nitem
 }
 
 template <bool WINMAX>
-void launch_tail2(const OsItem* items, const float2* Y, int s0, int ns, int nitems, const float2* tw,
-                  const float2* twc, int64_t n, float2* z_out, unsigned long long* keys, int64_t W, int64_t nw,
-                  cudaStream_t s) {
-  auto fn = k_bins_tail2<WINMAX>;
-  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os2_tail_smem()));
-  // a warp's scan covers 256 consecutive positions: at most two windows when W >= 256
-  const int fastwin = (WINMAX && W >= 256) ? 1 : 0;
-  fn<<<dim3((unsigned)(2 * ns), (unsigned)nitems), kBH / 16, os2_tail_smem(), s>>>(items, Y, s0, ns, tw, twc, n, z_out,
-                                                                                  keys, W, nw, fastwin);
+void launch_tail_pair(rf_ctx* c, const OsItem* items, const float2* Y, int s0, int ns, int nitems, int64_t n,
+                      float2* z_out, unsigned long long* keys, int64_t W, int64_t nw, cudaStream_t s) {
+  auto fn = k_bins_tail_pair<WINMAX>;
+  const size_t smem = os2_tail_smem();  // the transform's shared memory, then BH magnitudes
+  RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int units = ns * nitems;
+  const int grid = std::min(units, c->nsm);
+  RF_REQUIRE(c->bins_e0.bytes >= sizeof(float2) * (size_t)kBH * (size_t)grid,
+             "two-phase 32768-point tail: scratch not prepared");
+  // a warp's scan covers 32 x 16 consecutive positions: at most two windows when W >= 512
+  const int fastwin = (WINMAX && W >= 32 * 16) ? 1 : 0;
+  const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
+  const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
+  fn<<<grid, kBH / 16, smem, s>>>(items, Y, s0, ns, units, tw, twc, n, z_out, keys, W, nw, fastwin,
+                                  c->bins_e0.as<float2>());
   RF_LAUNCHED();
 }
 
@@ -278,6 +339,10 @@ void tail_bq(int B, int Q, const OsItem* items, const float2* Y, int s0, int ns,
 }
 
 }  // namespace
+
+void bins_prepare_scratch(rf_ctx* c, int B) {
+  if (B == kB2) c->bins_e0.ensure(sizeof(float2) * (size_t)kBH * (size_t)c->nsm);
+}
 
 bool bins_layout_ok(int B, int Lp) {
   return ((B == 4096 || B == 8192 || B == 16384) && (Lp == B / 2 || Lp == B / 4)) || (B == kB2 && Lp == kBH);
@@ -333,12 +398,10 @@ void bins_run(rf_ctx* c, const BinsPlan& pl, const OsItem* items_dev, const floa
         products_pm<4>(pm, it, zs_one, B, pl.NQ, crow, pl.herm, wv.s0, wv.ns, p0, p0 > 0, Y, wv.nitems, s);
     }
     if (B == kB2) {
-      const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
-      const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
       if (win)
-        launch_tail2<true>(it, Y, wv.s0, wv.ns, wv.nitems, tw, twc, n, nullptr, keys, W, nw, s);
+        launch_tail_pair<true>(c, it, Y, wv.s0, wv.ns, wv.nitems, n, nullptr, keys, W, nw, s);
       else
-        launch_tail2<false>(it, Y, wv.s0, wv.ns, wv.nitems, tw, twc, n, z_out, nullptr, W, 0, s);
+        launch_tail_pair<false>(c, it, Y, wv.s0, wv.ns, wv.nitems, n, z_out, nullptr, W, 0, s);
     } else if (win) {
       tail_bq<true>(B, Q, it, Y, wv.s0, wv.ns, wv.nitems, twb, n, nullptr, keys, W, nw, fastwin, s);
     } else {

@@ -827,6 +827,7 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
     RF_CUDA(cudaMemcpy(o.bins_items_d.p, o.bins->items.data(), sizeof(OsItem) * o.bins->items.size(),
                        cudaMemcpyHostToDevice));
     c->bins_y.ensure(o.bins->y_bytes);
+    bins_prepare_scratch(c, o.B);
   }
   RF_CUDA(cudaStreamSynchronize(s));
   kern->os_parts = parts;
@@ -884,6 +885,7 @@ void reconstruct_os(rf_ctx* c, const void* z_ref, rf_kernels* kern, void* z_out,
           launch_os_segments<BB>(c, static_cast<const float2*>(z_ref), bk.Lp, Zs, s);
         });
       c->bins_y.ensure(bk.bins->y_bytes);
+      bins_prepare_scratch(c, bk.B);
       bins_run(c, *bk.bins, bk.bins_items_d.as<OsItem>(), Zs, c->bins_y.as<float2>(),
                win ? nullptr : static_cast<float2*>(z_out), win ? keys : nullptr, W, s);
       continue;
@@ -1000,6 +1002,7 @@ void reconstruct_batched(rf_ctx* c, int32_t G, const void* const* z_refs, rf_ker
         c->batch_bins_off[b] = (int64_t)bins_all.size();
         bins_all.insert(bins_all.end(), c->batch_bins[b]->items.begin(), c->batch_bins[b]->items.end());
         c->bins_y.ensure(c->batch_bins[b]->y_bytes);
+        bins_prepare_scratch(c, Bs[b]);
       }
       if (spec[b].algo != RF_ALGO_OS) {  // direct, tensor-core or two-phase bucket: no work units
         c->batch_lay_off[b + 1] = (int64_t)items.size();

@@ -173,6 +173,7 @@ struct rf_ctx {
   rf::DevBuf batch_order;
   rf::DevBuf mix_tmp;  // rows of buckets that run the direct or tensor-core form, before scattering
   rf::DevBuf bins_y;   // two-phase overlap-save: one wave's partition sums
+  rf::DevBuf bins_e0;  // two-phase 32768-point tail: one 16384-point half transform per SM
   std::vector<std::shared_ptr<rf::BinsPlan>> batch_bins;  // per bucket (null unless two-phase)
   rf::DevBuf batch_bins_items;                            // their items, bucket after bucket
   std::vector<int64_t> batch_bins_off;
@@ -333,6 +334,8 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
 // own; keys null for the series form into z_out rows)
 bool bins_layout_ok(int B, int Lp);
 BinsPlan bins_plan(std::vector<OsItem> items, int B, int Lp, bool herm, int64_t n);
+// scratch the phase-2 launches of block size B need (allocated outside any stream capture)
+void bins_prepare_scratch(rf_ctx* c, int B);
 void bins_run(rf_ctx* c, const BinsPlan& pl, const OsItem* items_dev, const float2* zs_one, float2* Y,
               float2* z_out, unsigned long long* keys, int64_t W, cudaStream_t s);
 size_t os_workspace_bytes(const rf_ctx* c, int32_t k, int64_t W, int Q);
