@@ -272,4 +272,85 @@ __device__ __forceinline__ void os2_block_tail(float2 (&v)[16], int s, int64_t m
 // Shared memory of a CTA of the pair layout: the block FFT's and the magnitudes.
 constexpr size_t os2_tail_smem() { return sizeof(float2) * BlockFFTShape<kBH>::SMEM + sizeof(float) * kBH; }
 
+// ------------------------------------------------------- 32768-point blocks on one CTA (Q = 2)
+// With the block's spectrum split by bin parity (Y[2k' + r] at r BH + k'), the inverse
+// transforms E_r of the halves give y[t + BH] = E_0[t] - w^t E_1[t], w = exp(+2 pi i / B2),
+// t < BH: at Q = 2 exactly the kept outputs (block positions LP = BH .. B2 - 1).  One CTA runs the
+// two 16384-point transforms in turn: E_0 is parked in natural order in a scratch row of its own
+// (global memory that stays in L2: one row per resident CTA), E_1 is staged in shared memory,
+// and no cluster exchange is needed.  Shared memory: os2_tail_smem().
+
+// The two half transforms: load(h, v) fills v with half h (bins tid + t BH/16 of the half).
+template <typename Load>
+__device__ __forceinline__ void pair1_halves(Load&& load, float2* __restrict__ e0, const float2* __restrict__ tw,
+                                             float2* sm) {
+  using S = BlockFFTShape<kBH>;
+  constexpr int NT = S::NT;
+  constexpr int RL = S::RL;
+  const int tid = threadIdx.x;
+  // one loop body, so that the code holds one transform
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    float2 v[16];
+    load(h, v);
+    block_fft<kBH, +1>(v, sm, tw);
+    __syncthreads();  // the last stage has read shared memory
+#pragma unroll
+    for (int q = 0; q < 16 / RL; ++q)
+#pragma unroll
+      for (int t = 0; t < RL; ++t) {
+        const int idx = tid + q * NT + t * (kBH / RL);
+        if (h == 0)
+          __stcg(e0 + idx, v[q * RL + t]);
+        else
+          sm[idx] = v[q * RL + t];
+      }
+  }
+  __syncthreads();  // E_1 staged; E_0 of every thread written to the scratch row
+}
+
+// The kept outputs of block s (pre-relabel index s BH of block position BH), relabelled by the
+// first lag m0, to the series row zrow or, as window peaks, into the keys row kj.  Every thread of
+// the CTA calls it; it ends with a barrier (shared memory and the scratch row are free again).
+template <bool WINMAX>
+__device__ __forceinline__ void pair1_tail(const float2* __restrict__ e0, const float2* __restrict__ twc, int s,
+                                           int64_t m0, int64_t n, float2* __restrict__ zrow,
+                                           unsigned long long* __restrict__ kj, int64_t W, int64_t nw, int fastwin,
+                                           float2* sm) {
+  using S = BlockFFTShape<kBH>;
+  constexpr int NT = S::NT;
+  constexpr int CH = kBH / NT;  // kept outputs per thread in the window scan
+  const int tid = threadIdx.x;
+  const int64_t mask = n - 1;
+  float* mag = reinterpret_cast<float*>(sm + S::SMEM);
+  const int64_t o0 = (int64_t)s * kBH;
+  const int64_t base = (o0 + m0) & mask;
+  const int64_t lim = n - o0;  // kept positions BH + t with t < lim exist
+  // y[t + BH] at t = tid + j NT (consecutive lanes, consecutive t)
+#pragma unroll 4
+  for (int j = 0; j < 16; ++j) {
+    const int idx = tid + j * NT;
+    const float2 yh = csub(__ldcg(e0 + idx), cmulc(sm[idx], __ldg(twc + idx)));
+    if (!WINMAX) {
+      if (idx < lim) zrow[(base + idx) & mask] = yh;
+    } else {
+      mag[idx] = yh.x * yh.x + yh.y * yh.y;
+    }
+  }
+  if (WINMAX) {
+    __syncthreads();
+    float mv[CH];
+#pragma unroll
+    for (int e = 0; e < CH; e += 4)
+      *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + tid * CH + e);
+    const int64_t avail = lim - (int64_t)tid * CH;
+    const int cnt = avail <= 0 ? 0 : (avail >= CH ? CH : (int)avail);
+    window_keys<CH>(mv, cnt, (int)((base + (int64_t)tid * CH) & mask), n, W, nw, fastwin, kj);
+  }
+  __syncthreads();
+}
+
+// a warp's scan in pair1_tail covers 32 x 16 consecutive positions: at most two windows when W >= 512
+constexpr int pair1_warp_span() { return 32 * 16; }
+
 }  // namespace rf

@@ -182,78 +182,31 @@ __global__ void __launch_bounds__(B / 16, 16384 / B)
                               WINMAX ? keys + it.row * nw : nullptr, W, nw, fastwin, tw, sm);
 }
 
-// Phase 2 of the 32768-point layout (Q = 2: the kept outputs are block positions BH .. B2 - 1).
-// With the partition sums split by bin parity (Y[2k' + r] at r BH + k'), the inverse transforms
-// E_r of the two halves give y[t + BH] = E_0[t] - w^t E_1[t], w = exp(+2 pi i / B2), t < BH.
-// One CTA runs both 16384-point transforms in turn, parking E_0 in a per-CTA row of global
-// scratch (L2-resident: one row per resident CTA) and staging E_1 in shared memory, so the pair
-// needs no cluster exchange.  Shared memory: the transform's, then BH magnitudes.
-// Persistent: CTA b takes the units u = b, b + gridDim.x, .. of the wave's (item, block) units.
+// Phase 2 of the 32768-point layout (Q = 2) on one CTA per block (os_tail.cuh: both half
+// transforms in turn, no cluster exchange).  Persistent: CTA b takes the units
+// u = b, b + gridDim.x, .. of the wave's (item, block) units, with scratch row b.
 template <bool WINMAX>
 __global__ void __launch_bounds__(kBH / 16, 1)
     k_bins_tail_pair(const OsItem* __restrict__ items, const float2* __restrict__ Y, int s0, int ns, int units,
                      const float2* __restrict__ tw, const float2* __restrict__ twc, int64_t n,
                      float2* __restrict__ z_out, unsigned long long* __restrict__ keys, int64_t W, int64_t nw,
                      int fastwin, float2* __restrict__ e0_all) {
-  using S = BlockFFTShape<kBH>;
-  constexpr int NT = S::NT;
-  constexpr int RL = S::RL;
-  constexpr int CH = kBH / NT;  // kept outputs per thread in the window scan
   extern __shared__ float2 sm[];
+  constexpr int NT = kBH / 16;
   const int tid = threadIdx.x;
-  const int64_t mask = n - 1;
   float2* e0 = e0_all + (int64_t)blockIdx.x * kBH;
-  float* mag = reinterpret_cast<float*>(sm + S::SMEM);
   for (int u = blockIdx.x; u < units; u += gridDim.x) {
     const int ii = u / ns, si = u - ii * ns;
     const float2* y = Y + ((int64_t)u) * kB2 + tid;  // unit u = (item ii, block si) of the wave
-    // E_0 (even bins) to the scratch row in natural order, then E_1 (odd bins) staged in shared
-    // memory in natural order; one loop body, so that the code holds one transform
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      float2 v[16];
+    pair1_halves(
+        [&](int h, float2(&v)[16]) {
 #pragma unroll
-      for (int t = 0; t < 16; ++t) v[t] = __ldcg(y + h * kBH + t * NT);
-      block_fft<kBH, +1>(v, sm, tw);
-      __syncthreads();  // the last stage has read shared memory
-#pragma unroll
-      for (int q = 0; q < 16 / RL; ++q)
-#pragma unroll
-        for (int t = 0; t < RL; ++t) {
-          const int idx = tid + q * NT + t * (kBH / RL);
-          if (h == 0)
-            __stcg(e0 + idx, v[q * RL + t]);
-          else
-            sm[idx] = v[q * RL + t];
-        }
-    }
-    __syncthreads();  // E_1 staged; E_0 of every thread written to the scratch row
+          for (int t = 0; t < 16; ++t) v[t] = __ldcg(y + h * kBH + t * NT);
+        },
+        e0, tw, sm);
     const int64_t lag0 = items[ii].lag0, row = items[ii].row;  // read after the transforms
-    const int64_t o0 = (int64_t)(s0 + si) * kBH;  // pre-relabel index of block position BH
-    const int64_t base = (o0 + lag0) & mask;
-    const int64_t lim = n - o0;                   // kept positions BH + t with t < lim exist
-    // y[t + BH] = E_0[t] - w^t E_1[t] at t = tid + j NT (consecutive lanes, consecutive t)
-#pragma unroll 4
-    for (int j = 0; j < 16; ++j) {
-      const int idx = tid + j * NT;
-      const float2 yh = csub(__ldcg(e0 + idx), cmulc(sm[idx], __ldg(twc + idx)));
-      if (!WINMAX) {
-        if (idx < lim) z_out[row * n + ((base + idx) & mask)] = yh;
-      } else {
-        mag[idx] = yh.x * yh.x + yh.y * yh.y;
-      }
-    }
-    if (WINMAX) {
-      __syncthreads();
-      float mv[CH];
-#pragma unroll
-      for (int e = 0; e < CH; e += 4)
-        *reinterpret_cast<float4*>(mv + e) = *reinterpret_cast<const float4*>(mag + tid * CH + e);
-      const int64_t avail = lim - (int64_t)tid * CH;
-      const int cnt = avail <= 0 ? 0 : (avail >= CH ? CH : (int)avail);
-      window_keys<CH>(mv, cnt, (int)((base + (int64_t)tid * CH) & mask), n, W, nw, fastwin, keys + row * nw);
-    }
-    __syncthreads();  // shared memory and the scratch row are reused by the next unit
+    pair1_tail<WINMAX>(e0, twc, s0 + si, lag0, n, WINMAX ? nullptr : z_out + row * n,
+                       WINMAX ? keys + row * nw : nullptr, W, nw, fastwin, sm);
   }
 }
 
@@ -314,8 +267,7 @@ void launch_tail_pair(rf_ctx* c, const OsItem* items, const float2* Y, int s0, i
   const int grid = std::min(units, c->nsm);
   RF_REQUIRE(c->bins_e0.bytes >= sizeof(float2) * (size_t)kBH * (size_t)grid,
              "two-phase 32768-point tail: scratch not prepared");
-  // a warp's scan covers 32 x 16 consecutive positions: at most two windows when W >= 512
-  const int fastwin = (WINMAX && W >= 32 * 16) ? 1 : 0;
+  const int fastwin = (WINMAX && W >= pair1_warp_span()) ? 1 : 0;
   const float2* tw = c->twb32.as<float2>() + c->twb_off[14];
   const float2* twc = c->twb32.as<float2>() + c->twb_off[15];
   fn<<<grid, kBH / 16, smem, s>>>(items, Y, s0, ns, units, tw, twc, n, z_out, keys, W, nw, fastwin,

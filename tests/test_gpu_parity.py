@@ -476,9 +476,11 @@ def test_reconstruct_os_length_buckets(torch, os_case, cuts, blocks, parts):
         kern.prepare_buckets([0, 100], [4096, 4096], [1024, 3000])      # partition not B/2, B/4, B/8
 
 
-def test_batched_length_buckets_match_per_group(torch):
+@pytest.mark.parametrize("long_part", [8192, 16384])
+def test_batched_length_buckets_match_per_group(torch, long_part):
     """The persistent batched launch runs one pass per layout bucket and writes the same rows
-    as the per-group bucketed reconstruction."""
+    as the per-group bucketed reconstruction (the long bucket on 32768-point blocks: on CTA
+    pairs at Q = 4, on one CTA per block at Q = 2)."""
     cfg = _batch_cfg()
     ip = torch.tensor(workload.inv_psd(cfg), device="cuda")
     x = torch.tensor(data.strain(cfg), dtype=torch.float32, device="cuda")
@@ -489,7 +491,7 @@ def test_batched_length_buckets_match_per_group(torch):
     allL = np.concatenate([k.length for k in kerns])
     cut = int(np.median(allL)) + 1
     for k in kerns:
-        k.prepare_buckets([0, cut], [4096, 32768], [1024, 8192])   # the long bucket on CTA pairs
+        k.prepare_buckets([0, cut], [4096, 32768], [1024, long_part])
     W = cfg.window
     P, A = rf.reconstruct_batched([z[g] for g in range(len(refs))], kerns, W)
     row = 0
