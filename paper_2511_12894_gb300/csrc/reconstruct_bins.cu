@@ -294,6 +294,10 @@ void tail_bq(int B, int Q, const OsItem* items, const float2* Y, int s0, int ns,
 
 void bins_prepare_scratch(rf_ctx* c, int B) {
   if (B == kB2) c->bins_e0.ensure(sizeof(float2) * (size_t)kBH * (size_t)c->nsm);
+  if (!c->bins_side) {
+    RF_CUDA(cudaStreamCreateWithFlags(&c->bins_side, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->bins_ev) RF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
 }
 
 bool bins_layout_ok(int B, int Lp) {
@@ -324,7 +328,8 @@ BinsPlan bins_plan(std::vector<OsItem> items, int B, int Lp, bool herm, int64_t 
     for (int s0 = 0; s0 < pl.NB; s0 += ns)
       pl.waves.push_back(BinsWave{i0, m, s0, (int)std::min<int64_t>(ns, pl.NB - s0), pmax});
   }
-  pl.y_bytes = sizeof(float2) * (size_t)T * (size_t)ns * (size_t)B + 256;
+  pl.y_stride = (size_t)T * (size_t)ns * (size_t)B;
+  pl.y_bytes = 2 * sizeof(float2) * pl.y_stride + 256;
   return pl;
 }
 
@@ -340,26 +345,52 @@ void bins_run(rf_ctx* c, const BinsPlan& pl, const OsItem* items_dev, const floa
   const int crow = os_row(B, pl.herm);
   // a warp's outputs in the epilogue span at most two windows when W covers 32 threads' runs
   const int fastwin = (win && W >= 32 * ((B - pl.Lp) / (B / 16))) ? 1 : 0;
-  for (const BinsWave& wv : pl.waves) {
+  // Phase 1 of every wave on s, phase 2 on the side stream; wave w uses buffer w mod 2, so
+  // phase 1 of wave w + 1 may run beside phase 2 of wave w.  Edges: phase 2 of w after phase 1
+  // of w; phase 1 of w + 2 (same buffer) after phase 2 of w; the caller's stream after the last
+  // phase 2.  Under stream capture the events become the graph's edges (fork and join).
+  RF_REQUIRE(c->bins_side != nullptr, "two-phase overlap-save: side stream not prepared");
+  RF_REQUIRE(c->bins_y.bytes >= pl.y_bytes, "two-phase overlap-save: buffer not prepared");
+  cudaStream_t side = c->bins_side;
+  cudaEvent_t* ev = c->bins_ev;  // [0] fork, [1] join, [2 + b] phase 1 done, [4 + b] phase 2 done
+  RF_CUDA(cudaEventRecord(ev[0], s));
+  RF_CUDA(cudaStreamWaitEvent(side, ev[0], 0));
+  for (size_t w = 0; w < pl.waves.size(); ++w) {
+    const BinsWave& wv = pl.waves[w];
+    const int b = (int)(w & 1);
+    float2* Yw = Y + (size_t)b * pl.y_stride;
     const OsItem* it = items_dev + wv.item0;
+    if (w >= 2) RF_CUDA(cudaStreamWaitEvent(s, ev[4 + b], 0));
     for (int p0 = 0; p0 < wv.pmax; p0 += kBinsPMax) {
       const int pm = std::min(kBinsPMax, wv.pmax - p0);
       if (Q == 2)
-        products_pm<2>(pm, it, zs_one, B, pl.NQ, crow, pl.herm, wv.s0, wv.ns, p0, p0 > 0, Y, wv.nitems, s);
+        products_pm<2>(pm, it, zs_one, B, pl.NQ, crow, pl.herm, wv.s0, wv.ns, p0, p0 > 0, Yw, wv.nitems, s);
       else
-        products_pm<4>(pm, it, zs_one, B, pl.NQ, crow, pl.herm, wv.s0, wv.ns, p0, p0 > 0, Y, wv.nitems, s);
+        products_pm<4>(pm, it, zs_one, B, pl.NQ, crow, pl.herm, wv.s0, wv.ns, p0, p0 > 0, Yw, wv.nitems, s);
     }
+    RF_CUDA(cudaEventRecord(ev[2 + b], s));
+    RF_CUDA(cudaStreamWaitEvent(side, ev[2 + b], 0));
     if (B == kB2) {
       if (win)
-        launch_tail_pair<true>(c, it, Y, wv.s0, wv.ns, wv.nitems, n, nullptr, keys, W, nw, s);
+        launch_tail_pair<true>(c, it, Yw, wv.s0, wv.ns, wv.nitems, n, nullptr, keys, W, nw, side);
       else
-        launch_tail_pair<false>(c, it, Y, wv.s0, wv.ns, wv.nitems, n, z_out, nullptr, W, 0, s);
+        launch_tail_pair<false>(c, it, Yw, wv.s0, wv.ns, wv.nitems, n, z_out, nullptr, W, 0, side);
     } else if (win) {
-      tail_bq<true>(B, Q, it, Y, wv.s0, wv.ns, wv.nitems, twb, n, nullptr, keys, W, nw, fastwin, s);
+      tail_bq<true>(B, Q, it, Yw, wv.s0, wv.ns, wv.nitems, twb, n, nullptr, keys, W, nw, fastwin, side);
     } else {
-      tail_bq<false>(B, Q, it, Y, wv.s0, wv.ns, wv.nitems, twb, n, z_out, nullptr, W, 0, 0, s);
+      tail_bq<false>(B, Q, it, Yw, wv.s0, wv.ns, wv.nitems, twb, n, z_out, nullptr, W, 0, 0, side);
     }
+    RF_CUDA(cudaEventRecord(ev[4 + b], side));
   }
+  RF_CUDA(cudaEventRecord(ev[1], side));
+  RF_CUDA(cudaStreamWaitEvent(s, ev[1], 0));
 }
 
 }  // namespace rf
+
+// the two-phase side stream and events (created by rf::bins_prepare_scratch)
+rf_ctx::~rf_ctx() {
+  for (cudaEvent_t e : bins_ev)
+    if (e) cudaEventDestroy(e);
+  if (bins_side) cudaStreamDestroy(bins_side);
+}

@@ -107,7 +107,8 @@ struct BinsPlan {
   bool herm = false;
   std::vector<OsItem> items;  // in plan order
   std::vector<BinsWave> waves;
-  size_t y_bytes = 0;         // buffer of one wave's partition sums
+  size_t y_bytes = 0;         // buffers of two waves' partition sums (waves alternate)
+  size_t y_stride = 0;        // float2 elements from the first wave buffer to the second
 };
 
 // ---------------------------------------------------------------- template model
@@ -174,6 +175,15 @@ struct rf_ctx {
   rf::DevBuf mix_tmp;  // rows of buckets that run the direct or tensor-core form, before scattering
   rf::DevBuf bins_y;   // two-phase overlap-save: one wave's partition sums
   rf::DevBuf bins_e0;  // two-phase 32768-point tail: one 16384-point half transform per SM
+  // Two-phase waves run phase 2 on this side stream, so that phase 1 of the next wave (on the
+  // caller's stream, into the other buffer) can fill SMs that phase 2 leaves idle.  Events:
+  // fork, join, phase 1 done (two buffers), phase 2 done (two buffers).
+  cudaStream_t bins_side = nullptr;
+  cudaEvent_t bins_ev[6] = {};
+  rf_ctx() = default;
+  rf_ctx(const rf_ctx&) = delete;
+  rf_ctx& operator=(const rf_ctx&) = delete;
+  ~rf_ctx();
   std::vector<std::shared_ptr<rf::BinsPlan>> batch_bins;  // per bucket (null unless two-phase)
   rf::DevBuf batch_bins_items;                            // their items, bucket after bucket
   std::vector<int64_t> batch_bins_off;
@@ -334,7 +344,8 @@ void os_prepare_forms(rf_ctx* c, rf_kernels* kern, int nb, const BucketSpec* spe
 // own; keys null for the series form into z_out rows)
 bool bins_layout_ok(int B, int Lp);
 BinsPlan bins_plan(std::vector<OsItem> items, int B, int Lp, bool herm, int64_t n);
-// scratch the phase-2 launches of block size B need (allocated outside any stream capture)
+// scratch, side stream and events the two-phase launches of block size B need (created outside
+// any stream capture)
 void bins_prepare_scratch(rf_ctx* c, int B);
 void bins_run(rf_ctx* c, const BinsPlan& pl, const OsItem* items_dev, const float2* zs_one, float2* Y,
               float2* z_out, unsigned long long* keys, int64_t W, cudaStream_t s);
