@@ -159,3 +159,43 @@ def test_two_phase_layouts_refused(torch):
         kern.prepare_forms([0], ["os_bins"], ["native"], [8192], [1024])
     with pytest.raises(RFError):   # the pair layout with partitions of B/2 only
         kern.prepare_forms([0], ["os_bins"], ["native"], [32768], [8192])
+
+
+@pytest.mark.parametrize("B2,Lp2", [(8192, 4096), (32768, 16384)])
+def test_two_phase_waves_batched_and_graph(torch, B2, Lp2):
+    """Three references x 12 long kernels: three waves of two-phase launches (two buffers, phase 2
+    on the library's second stream beside the next wave's phase 1).  The batched call equals the
+    per-reference calls row for row, and replays from a CUDA graph with the same result."""
+    n, W = 1 << 15, 1024
+    rng = np.random.default_rng(35)
+    rf = _rf(n)
+    kerns, zts = [], []
+    for _ in range(3):
+        lengths = [int(v) for v in rng.integers(3000, 20000, 12)]
+        lags, taps = _random_set(rng, n, lengths)
+        k = rf.kernels_import(lags, lengths, np.concatenate(taps))
+        k.prepare_forms([0, 2000], ["os", "os_bins"], ["native", "native"], [4096, B2], [1024, Lp2])
+        kerns.append(k)
+        z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+        zts.append(torch.tensor(z, device="cuda"))
+    P, A = rf.reconstruct_batched(zts, kerns, W, "auto")
+    row = 0
+    for g, k in enumerate(kerns):
+        Pg, Ag = rf.reconstruct_winmax(zts[g], k, W, "auto")
+        assert torch.equal(P[row:row + k.k], Pg) and torch.equal(A[row:row + k.k], Ag), g
+        row += k.k
+    P2, A2 = torch.zeros_like(P), torch.zeros_like(A)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rf.reconstruct_batched(zts, kerns, W, "auto", max_out=P2, arg_out=A2)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    P2.zero_()
+    A2.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rf.reconstruct_batched(zts, kerns, W, "auto", max_out=P2, arg_out=A2)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(P2, P) and torch.equal(A2, A)
