@@ -274,7 +274,11 @@ rf_status rf_kernels_prepare_buckets(rf_ctx* ctx, rf_kernels* kern, int32_t nb, 
  * and partition length parts[b]; RF_ALGO_GEMM runs the tensor-core form at the split precision
  * precs[b] with the tile layout (blocks[b] neighbours per group, parts[b] output tiles stacked
  * per MMA): (16, widest stack) or (widest group, 1), or (0, 0) for the library's rule; kernels of
- * at most 65536 taps; RF_ALGO_DIRECT runs the CUDA-core direct sum.  The overlap-save buckets
+ * at most 65536 taps; RF_ALGO_OS_BINS runs two-phase overlap-save (the partition sums per bin,
+ * then the block transforms; blocks[b] of 4096, 8192 or 16384 with parts[b] = blocks[b]/2 or /4,
+ * or 32768 with 16384; its waves run phase 2 on a stream of the context's own, joined back to
+ * `stream` by events, so a captured call still forms one graph); RF_ALGO_DIRECT runs the
+ * CUDA-core direct sum.  The overlap-save buckets
  * share one segment transform per layout and launch as rf_kernels_prepare_buckets; each other
  * bucket runs on a kernel set holding just its neighbours (taps copied, tensor-core operands
  * prepared here) into a temporary whose rows are then scattered to the neighbours' rows, so a

@@ -11,13 +11,17 @@
 // next segment value, 8 P flops, one 8-byte store of Y_s[k] into a buffer.  Moving to block
 // s + 1 shifts the window by Q - 1 segments.  Phase 2: one thread block per (neighbour, s)
 // reads Y_s and runs the block tail of the single-pass form (inverse transform, series or fused
-// window peaks).  Same arithmetic per output (the products in the same FP32 operations, summed
-// in another order), so the error bound is that of the single-pass form.
+// window peaks); for 32768-point blocks, a persistent CTA runs the two 16384-point half
+// transforms of a block in turn (os_tail.cuh).  Same arithmetic per output (the products in the
+// same FP32 operations, summed in another order), so the error bound is that of the single-pass
+// form.
 //
 // Waves: the neighbours of a bucket, sorted by partition count, are cut into tiles of T items;
 // each tile runs every output block in time tiles of ns blocks, phase 1 then phase 2 per
-// (item tile, time tile), stream-ordered (no launch waits on another).  Kernels with more than
-// PMAX = 40 partitions take several phase-1 passes, each adding its partitions to the buffer.
+// (item tile, time tile).  Waves alternate two buffers, phase 1 on the caller's stream and
+// phase 2 on a second stream (events order them; no kernel waits on another).  Kernels with
+// more than kBinsPMax = 40 partitions take several phase-1 passes, each adding its partitions to
+// the buffer.
 #include <algorithm>
 #include <type_traits>
 #include <utility>
