@@ -326,11 +326,15 @@ __device__ __forceinline__ void pair1_tail(const float2* __restrict__ e0, const 
   const int64_t o0 = (int64_t)s * kBH;
   const int64_t base = (o0 + m0) & mask;
   const int64_t lim = n - o0;  // kept positions BH + t with t < lim exist
-  // y[t + BH] at t = tid + j NT (consecutive lanes, consecutive t)
+  // y[t + BH] at t = tid + j NT (consecutive lanes, consecutive t).  The table entry of t is
+  // formed as twc[tid] twc[NT j] (about 1 ulp more): one entry per thread and one per j that the
+  // whole block shares, instead of 128 KB of table per block.
+  const float2 wt = __ldg(twc + tid);
 #pragma unroll 4
   for (int j = 0; j < 16; ++j) {
     const int idx = tid + j * NT;
-    const float2 yh = csub(__ldcg(e0 + idx), cmulc(sm[idx], __ldg(twc + idx)));
+    const float2 w = j == 0 ? wt : cmul(wt, __ldg(twc + j * NT));
+    const float2 yh = csub(__ldcg(e0 + idx), cmulc(sm[idx], w));
     if (!WINMAX) {
       if (idx < lim) zrow[(base + idx) & mask] = yh;
     } else {
