@@ -27,22 +27,23 @@ namespace rf {
 __device__ __forceinline__ int bf_pad(int p) { return p + (p >> 4); }
 
 // Multiplies a[t], 0 < t < R (R = 8 or 16), by w^t (conjugated for SIGN = +1) where w^t is
-// table entry t * stride: the entries t = 1, 2, 4 and 8 are loaded and the others formed by
-// at most two complex products of loaded entries (about 3 ulp), which takes 11 of the 15
-// table loads of a radix-16 stage off the load/store pipe.
+// table entry t * stride: the entries t = 1 and 4 are loaded and the others formed by complex
+// products (w^2 = w w, w^8 = w^4 w^4, at most three products deep: a few ulp), which keeps 13 of
+// the 15 table loads of a radix-16 stage off the load/store pipe, the scarcer one in the block
+// transforms (loading all 15 made the 2^23-sample step 12% slower, loading 4 was 2% slower).
 template <int R, int SIGN>
 __device__ __forceinline__ void apply_stage_twiddles(float2* a, const float2* __restrict__ tw, int stride) {
   static_assert(R == 8 || R == 16, "radix");
   float2 w[R];
   w[1] = __ldg(tw + stride);
-  w[2] = __ldg(tw + 2 * stride);
   w[4] = __ldg(tw + 4 * stride);
+  w[2] = cmul(w[1], w[1]);
   w[3] = cmul(w[2], w[1]);
   w[5] = cmul(w[4], w[1]);
   w[6] = cmul(w[4], w[2]);
   w[7] = cmul(w[4], w[3]);
   if constexpr (R == 16) {
-    w[8] = __ldg(tw + 8 * stride);
+    w[8] = cmul(w[4], w[4]);
 #pragma unroll
     for (int t = 9; t < 16; ++t) w[t] = cmul(w[8], w[t - 8]);
   }
@@ -127,17 +128,20 @@ __device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const flo
   // last stage: radix RL, Ns = B / RL, every butterfly index b < Ns so k = b
   constexpr int RL = S::RL;
   constexpr int LSTR = B / RL + B / (16 * RL);
-#pragma unroll
-  for (int q = 0; q < 16 / RL; ++q) {
+  // for RL <= 4, w^1 of butterfly b = tid + q NT is that of tid times exp(-2 pi i q / 16)
+  // (NT / B = 1/16): one table load for the thread, exact-constant rotations for the others
+  [[maybe_unused]] const float2 w1t = RL <= 4 ? __ldg(tw + (B / RL) + tid) : make_float2(1.f, 0.f);
+  static_for<0, 16 / RL>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
     const int b = tid + q * NT;
     float2 a[RL];
     const float2* in = sm + bf_pad(b);
 #pragma unroll
     for (int t = 0; t < RL; ++t) a[t] = in[t * LSTR];
     if constexpr (RL <= 4) {
-      // w^t for t < RL from the table's t = 1 row: the row of B/RL entries stays in L1,
-      // and the square (and cube) cost a complex product each (about 1 ulp more error)
-      const float2 w1 = __ldg(tw + (B / RL) + b);
+      // w^t for t < RL from w^1 (the table's t = 1 row): the square (and cube) cost a complex
+      // product each (about 1 ulp more error)
+      const float2 w1 = rot16<q, -1>(w1t);
       a[1] = tw_apply<SIGN>(a[1], w1);
       if constexpr (RL == 4) {
         const float2 w2 = cmul(w1, w1);
@@ -150,7 +154,7 @@ __device__ __forceinline__ void block_fft(float2 (&v)[16], float2* sm, const flo
     dft<RL, SIGN>(a);
 #pragma unroll
     for (int t = 0; t < RL; ++t) v[q * RL + t] = a[t];
-  }
+  });
 }
 
 // One transform per thread block (tid = threadIdx.x).
